@@ -1,0 +1,206 @@
+/*
+ * pbs.h - C ABI of the GB300 photonic band-structure library (libpbs.so).
+ *
+ * Computes the smallest non-zero eigenvalues of the 2-D curl-curl Maxwell
+ * operator with Bloch boundary conditions, discretised with lowest-order
+ * Nedelec edge elements on a regular n x m mesh of the periodic cell
+ * [0,a] x [0,b] (Boerm, Koehl, Talebi, "Computing Maxwell eigenmodes with Bloch
+ * boundary conditions", arXiv:2304.00337):
+ *
+ *   curl (1/eps) curl u = lambda u        (Section 1, eq. maxwell)
+ *   u1(x1,b) = exp(i k2 b) u1(x1,0),  u2(a,x2) = exp(i k1 a) u2(0,x2)
+ *                                         (Section 1, eq. bloch_boundary)
+ *   A e = lambda M e                      (Section 1, eq. matrix; Section 3)
+ *
+ * All arithmetic runs in the library's CUDA kernels on one GPU; there is no
+ * CPU fallback. Functions return 0 (PBS_OK) or a negative status; nothing is
+ * thrown across the ABI. The library never frees caller memory. Host buffers
+ * passed in are read or written only during the call. Device pointers are
+ * plain CUDA device addresses on the context's device.
+ *
+ * Vector conventions (shared by every entry point):
+ *  - complex numbers are interleaved (re, im) doubles (pbs_c64);
+ *  - level l of the multigrid hierarchy has n_l = n >> l, m_l = m >> l,
+ *    N_l = n_l * m_l cells (= nodes) and D_l = 2 N_l edges;
+ *  - edge vectors: x-edges first, then y-edges; x-edge (i,j) is the segment
+ *    [i h1,(i+1) h1] x {j h2} at index j*n_l + i, y-edge (i,j) is
+ *    {i h1} x [j h2,(j+1) h2] at index N_l + j*n_l + i;  h1 = a/n_l, h2 = b/m_l;
+ *    an edge coefficient is the line integral of the tangential component
+ *    (Section 3, basis b_{x,i}, b_{y,i});
+ *  - node (i,j) at (i h1, j h2) and cell (i,j) both have index j*n_l + i;
+ *  - a block of `ncols` vectors is column-major: column c starts at c*len;
+ *  - permittivity: one sample per finest-level cell, eps[j*n + i] > 0, taken
+ *    at the cell centre (the reading of the paper's "standard quadrature" for
+ *    a cellwise-constant 1/eps, Section 5).
+ */
+#ifndef PBS_H
+#define PBS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define PBS_API __attribute__((visibility("default")))
+#else
+#define PBS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define PBS_OK 0
+#define PBS_EINVAL (-1)   /* invalid argument or unsupported size           */
+#define PBS_ENOMEM (-2)   /* device allocation failed or over the budget    */
+#define PBS_ENOCONV (-3)  /* max_iter reached; outputs filled with the last iterate */
+#define PBS_ENUMERIC (-4) /* non-finite values or a breakdown of the small dense solves */
+#define PBS_ETIMEOUT (-5) /* a bounded device wait gave up                 */
+#define PBS_ECUDA (-6)    /* a CUDA runtime call failed                     */
+
+/* ---- precision policies (Section 4/5 preconditioner precision) -------- */
+#define PBS_FP64 0  /* every kernel in FP64 ("plain")                         */
+#define PBS_MIXED 1 /* FP32 multigrid V-cycles and nodal cycles; FP64 residual,
+                       Gram matrices, Rayleigh-Ritz, projection right-hand side
+                       and update                                              */
+
+/* ---- operators for pbs_apply ----------------------------------------- */
+#define PBS_OP_A 0             /* edge -> edge: y = A x  (Section 3)            */
+#define PBS_OP_M 1             /* edge -> edge: y = M x                         */
+#define PBS_OP_A_MU_M 2        /* edge -> edge: y = (A + mu M) x (Section 5)    */
+#define PBS_OP_C 3             /* edge -> cell: y = C x, (Cx)_c = int_c scurl x */
+#define PBS_OP_CH 4            /* cell -> edge: y = C^* x                       */
+#define PBS_OP_L 5             /* node -> edge: y = L x, gradient lifting (eq. potential_discrete) */
+#define PBS_OP_LH 6            /* edge -> node: y = L^* x                       */
+#define PBS_OP_P_NODAL 7       /* node -> node: y = L^* M L x (Section 5)       */
+#define PBS_OP_PROLONG 8       /* edge level l+1 -> level l: natural embedding (Section 5) */
+#define PBS_OP_RESTRICT 9      /* edge level l -> level l+1: adjoint of the embedding */
+#define PBS_OP_PROLONG_NODAL 10   /* node level l+1 -> level l                  */
+#define PBS_OP_RESTRICT_NODAL 11  /* node level l -> level l+1                  */
+#define PBS_OP_VCYCLE_EDGE 12  /* edge -> edge: y = B x, one V(nu_pre,nu_post) cycle for A + mu M */
+#define PBS_OP_VCYCLE_NODAL 13 /* node -> node: y = B_P x, one V-cycle for L^* M L */
+#define PBS_OP_PROJECT 14      /* edge -> edge: y = x - L phi, phi from nodal_cycles V-cycles on
+                                  L^* M L phi = L^* M x (Section 4); at k = 0 the two constant
+                                  edge fields are also M-projected out          */
+
+typedef struct pbs_ctx pbs_ctx; /* opaque; owns every device allocation of the library */
+
+typedef struct {
+  double re, im;
+} pbs_c64;
+
+/* Periodic cell and mesh (Section 1 periods a, b; Section 3 mesh n x m). */
+typedef struct {
+  double a, b;       /* cell sizes, > 0                                     */
+  int n, m;          /* cells per direction, even, >= 4                     */
+  const double *eps; /* host, n*m samples (index j*n+i), > 0; copied at call */
+} pbs_geom;
+
+/* Solver options; pbs_default_opts fills documented defaults. */
+typedef struct {
+  int nev;          /* wanted bands (smallest non-zero eigenvalues), >= 1          */
+  int block;        /* block width p (wanted + throw-away vectors, Section 7), nev <= block <= 32 */
+  int max_iter;     /* iteration limit per Bloch vector (default 400)              */
+  int precision;    /* PBS_FP64 or PBS_MIXED (default PBS_MIXED)                   */
+  int span;         /* trial space of the Rayleigh-Ritz step (Section 4): 1 = PINVIT,
+                       span(E - W) (Algorithm 1); 2 = gradient method, span(E, W);
+                       3 = LOBPCG, span(E, W, P) (Algorithm 2; default 3); W is the
+                       preconditioned residual, P the previous search direction    */
+  double tol;       /* convergence: ||A e - lambda M e||_2 / (lambda ||M e||_2) <= tol on
+                       the nev wanted bands (default 1e-8)                         */
+  double mu;        /* regularisation A + mu M of the preconditioner (Section 5); <= 0 selects 1/(a b) */
+  int nu_pre;       /* pre-smoothing sweeps (default 1)                            */
+  int nu_post;      /* post-smoothing sweeps (default 1)                           */
+  int coarsest;     /* coarsen while both sides are even and >= 2*coarsest (default 4, >= 2) */
+  int nodal_cycles; /* nodal V-cycles per projection (default 2)                   */
+  int extrap_depth; /* previous bases used for the initial guess along a path, 0..3 (default 3) */
+  uint64_t seed;    /* seed of the random initial block when no guess is given     */
+} pbs_opts;
+
+/* Create a context on CUDA device `device`. `hbm_budget_bytes` caps the
+ * library's device allocations (0 = no cap beyond free memory). */
+PBS_API int pbs_create(pbs_ctx **ctx, int device, size_t hbm_budget_bytes);
+
+/* Free every device allocation of the context and the context itself. NULL is a no-op. */
+PBS_API int pbs_destroy(pbs_ctx *ctx);
+
+/* Fill `o` with the defaults listed in pbs_opts. */
+PBS_API void pbs_default_opts(pbs_opts *o);
+
+/* Number of multigrid levels the hierarchy rule gives for (n, m, coarsest), or PBS_EINVAL. */
+PBS_API int pbs_num_levels(int n, int m, int coarsest);
+
+/*
+ * Smallest non-zero eigenpairs at one Bloch vector k (Section 4, Algorithm 2
+ * with the multigrid preconditioner of Section 5 and null-space elimination of
+ * Section 4).  At k = 0 (both phases equal to one) the two constant edge fields
+ * are deflated as well, so the reported values are the smallest non-zero ones.
+ *   k       host, 2 doubles (k1, k2)
+ *   init    host, D*block complex values (column-major) or NULL for a seeded
+ *           random start
+ *   eigvals host out, nev ascending Rayleigh quotients
+ *   resid   host out, nev relative residuals (see pbs_opts.tol)
+ *   iters   host out, iterations performed
+ *   evecs   host out, D*nev complex (column-major, M-orthonormal) or NULL
+ * Returns PBS_ENOCONV (outputs filled) when max_iter is reached.
+ */
+PBS_API int pbs_solve_k(pbs_ctx *ctx, const pbs_geom *geom, const pbs_opts *opts, const double k[2],
+                const pbs_c64 *init, double *eigvals, double *resid, int *iters, pbs_c64 *evecs);
+
+/*
+ * A sequence of Bloch vectors solved in order; each one after the first starts
+ * from the Rayleigh-quotient-minimising extrapolation of up to extrap_depth
+ * previous bases (Section 6).  ks: host nk*2; eigvals, resid: host nk*nev;
+ * iters: host nk.  Returns the first non-OK status met (later k still solved).
+ */
+PBS_API int pbs_solve_path(pbs_ctx *ctx, const pbs_geom *geom, const pbs_opts *opts, int nk, const double *ks,
+                   double *eigvals, double *resid, int *iters);
+
+/*
+ * Same as pbs_solve_path with every array on the device: d_eps (n*m doubles),
+ * d_ks (nk*2), d_eigvals (nk*nev), d_resid (nk*nev), d_iters (nk ints); the
+ * work is issued on `cuda_stream` (a cudaStream_t, NULL = legacy default) and
+ * the call returns after it finished.  The hierarchy of a geometry stays
+ * resident in the context between calls.
+ */
+PBS_API int pbs_solve_path_device(pbs_ctx *ctx, double a, double b, int n, int m, const double *d_eps,
+                          const pbs_opts *opts, int nk, const double *d_ks, double *d_eigvals,
+                          double *d_resid, int *d_iters, void *cuda_stream);
+
+/*
+ * Apply one operator of the discretisation or the multigrid (PBS_OP_*) to
+ * `ncols` columns.  x, y: device, interleaved complex FP64, lengths given by
+ * the operator and `level`; x and y must not overlap. mu, nu_pre, nu_post,
+ * coarsest, nodal_cycles and precision are taken from `opts`.
+ */
+PBS_API int pbs_apply(pbs_ctx *ctx, const pbs_geom *geom, const pbs_opts *opts, int op, int level, const double k[2],
+              int ncols, const pbs_c64 *x, pbs_c64 *y, void *cuda_stream);
+
+/*
+ * Block Gram matrices of the pencil at k (Section 4, used by Rayleigh-Ritz):
+ * GM = S^* M S and GA = (C S)^* W (C S) = S^* A S, W = diag(1/(eps_c h1 h2)).
+ * S: device D x q; GM, GA: device q x q column-major.
+ */
+PBS_API int pbs_gram(pbs_ctx *ctx, const pbs_geom *geom, const double k[2], int q, const pbs_c64 *S, pbs_c64 *GM,
+             pbs_c64 *GA, void *cuda_stream);
+
+/*
+ * Rayleigh-Ritz of the pencil on span(S) (Section 4, eq. ritz_eigenvalue):
+ * the p smallest Ritz values (host `theta`) and M-orthonormal Ritz vectors
+ * (device X, D x p).  With project != 0 the columns of S are first projected
+ * off the gradients (and at k = 0 the constant fields) with opts->nodal_cycles
+ * nodal V-cycles, which is the extrapolation step of Section 6. S is not modified.
+ */
+PBS_API int pbs_rayleigh_ritz(pbs_ctx *ctx, const pbs_geom *geom, const pbs_opts *opts, const double k[2], int q,
+                      const pbs_c64 *S, int p, int project, double *theta, pbs_c64 *X, void *cuda_stream);
+
+/* Static description of a status code. */
+PBS_API const char *pbs_strerror(int status);
+
+/* Detail of the last failure on the calling thread ("" if none). */
+PBS_API const char *pbs_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PBS_H */

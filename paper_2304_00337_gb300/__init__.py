@@ -1,0 +1,276 @@
+"""Python binding of libpbs, the GB300 photonic band-structure library.
+
+Argument marshalling only: every computation runs in the CUDA kernels of
+``libpbs.so`` behind the C ABI declared in ``include/pbs.h``.  Names follow
+that header.  Device arrays are passed as raw pointers (for example
+``torch.Tensor.data_ptr()`` of a contiguous ``complex128`` CUDA tensor) and a
+CUDA stream handle (``torch.cuda.Stream.cuda_stream``); host arrays are NumPy.
+
+There is no fallback: importing works without a GPU (to inspect the ABI), but
+every call that needs the library raises when ``libpbs.so`` is missing or the
+device is unavailable.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libpbs.so")
+
+# status codes
+PBS_OK = 0
+PBS_EINVAL = -1
+PBS_ENOMEM = -2
+PBS_ENOCONV = -3
+PBS_ENUMERIC = -4
+PBS_ETIMEOUT = -5
+PBS_ECUDA = -6
+# precision
+PBS_FP64 = 0
+PBS_MIXED = 1
+# operators
+OPS = dict(A=0, M=1, A_MU_M=2, C=3, CH=4, L=5, LH=6, P_NODAL=7, PROLONG=8, RESTRICT=9, PROLONG_NODAL=10,
+           RESTRICT_NODAL=11, VCYCLE_EDGE=12, VCYCLE_NODAL=13, PROJECT=14)
+for _k, _v in OPS.items():
+    globals()["PBS_OP_" + _k] = _v
+
+
+class PbsError(RuntimeError):
+    """A non-OK status returned by the library."""
+
+    def __init__(self, status: int, where: str, detail: str = ""):
+        self.status = status
+        msg = f"{where}: {strerror(status)} ({status})"
+        if detail:
+            msg += f": {detail}"
+        super().__init__(msg)
+
+
+class pbs_c64(ct.Structure):
+    _fields_ = [("re", ct.c_double), ("im", ct.c_double)]
+
+
+class pbs_geom(ct.Structure):
+    _fields_ = [("a", ct.c_double), ("b", ct.c_double), ("n", ct.c_int), ("m", ct.c_int),
+                ("eps", ct.POINTER(ct.c_double))]
+
+
+class pbs_opts(ct.Structure):
+    _fields_ = [("nev", ct.c_int), ("block", ct.c_int), ("max_iter", ct.c_int), ("precision", ct.c_int),
+                ("span", ct.c_int), ("tol", ct.c_double), ("mu", ct.c_double), ("nu_pre", ct.c_int),
+                ("nu_post", ct.c_int), ("coarsest", ct.c_int), ("nodal_cycles", ct.c_int),
+                ("extrap_depth", ct.c_int), ("seed", ct.c_uint64)]
+
+
+_lib = None
+
+
+def lib() -> ct.CDLL:
+    """Load ``libpbs.so`` (built in-tree by ``_build.build()``); raise if it is absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libpbs.so not built ({LIB_PATH}); run __graft_entry__.build()")
+    L = ct.CDLL(LIB_PATH)
+    P = ct.c_void_p
+    dp = ct.POINTER(ct.c_double)
+    ip = ct.POINTER(ct.c_int)
+    sig = {
+        "pbs_create": (ct.c_int, [ct.POINTER(P), ct.c_int, ct.c_size_t]),
+        "pbs_destroy": (ct.c_int, [P]),
+        "pbs_default_opts": (None, [ct.POINTER(pbs_opts)]),
+        "pbs_num_levels": (ct.c_int, [ct.c_int, ct.c_int, ct.c_int]),
+        "pbs_solve_k": (ct.c_int, [P, ct.POINTER(pbs_geom), ct.POINTER(pbs_opts), dp, P, dp, dp, ip, P]),
+        "pbs_solve_path": (ct.c_int, [P, ct.POINTER(pbs_geom), ct.POINTER(pbs_opts), ct.c_int, dp, dp, dp, ip]),
+        "pbs_solve_path_device": (ct.c_int, [P, ct.c_double, ct.c_double, ct.c_int, ct.c_int, P,
+                                             ct.POINTER(pbs_opts), ct.c_int, P, P, P, P, P]),
+        "pbs_apply": (ct.c_int, [P, ct.POINTER(pbs_geom), ct.POINTER(pbs_opts), ct.c_int, ct.c_int, dp, ct.c_int,
+                                 P, P, P]),
+        "pbs_gram": (ct.c_int, [P, ct.POINTER(pbs_geom), dp, ct.c_int, P, P, P, P]),
+        "pbs_rayleigh_ritz": (ct.c_int, [P, ct.POINTER(pbs_geom), ct.POINTER(pbs_opts), dp, ct.c_int, P, ct.c_int,
+                                         ct.c_int, dp, P, P]),
+        "pbs_strerror": (ct.c_char_p, [ct.c_int]),
+        "pbs_last_error": (ct.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def strerror(status: int) -> str:
+    return lib().pbs_strerror(status).decode()
+
+
+def last_error() -> str:
+    return lib().pbs_last_error().decode()
+
+
+def _check(status: int, where: str, allow=(PBS_OK,)):
+    if status not in allow:
+        raise PbsError(status, where, last_error())
+    return status
+
+
+def default_opts(**overrides) -> pbs_opts:
+    """``pbs_default_opts`` plus keyword overrides (field names of ``pbs_opts``)."""
+    o = pbs_opts()
+    lib().pbs_default_opts(ct.byref(o))
+    for k, v in overrides.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+def num_levels(n: int, m: int, coarsest: int = 4) -> int:
+    return lib().pbs_num_levels(n, m, coarsest)
+
+
+def _dp(a):
+    return a.ctypes.data_as(ct.POINTER(ct.c_double))
+
+
+class Geometry:
+    """Cell ``a x b``, mesh ``n x m`` and cell-centre permittivity samples (shape ``(m, n)``)."""
+
+    def __init__(self, eps, a: float = 1.0, b: float = 1.0):
+        self.eps = np.ascontiguousarray(np.asarray(eps, dtype=np.float64))
+        if self.eps.ndim != 2:
+            raise ValueError("eps must have shape (m, n)")
+        self.m, self.n = self.eps.shape
+        self.a, self.b = float(a), float(b)
+        self._g = pbs_geom(self.a, self.b, self.n, self.m, _dp(self.eps))
+
+    @property
+    def N(self) -> int:
+        return self.n * self.m
+
+    @property
+    def D(self) -> int:
+        return 2 * self.n * self.m
+
+    def ref(self):
+        return ct.byref(self._g)
+
+
+def _opts(opts) -> pbs_opts:
+    if opts is None:
+        return default_opts()
+    if isinstance(opts, dict):
+        return default_opts(**opts)
+    return opts
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        return None
+    return int(getattr(stream, "cuda_stream", stream))
+
+
+class Context:
+    """Owns a ``pbs_ctx`` (device memory, resident hierarchy) on one CUDA device."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0):
+        self._ptr = ct.c_void_p()
+        _check(lib().pbs_create(ct.byref(self._ptr), device, hbm_budget_bytes), "pbs_create")
+
+    def close(self):
+        if self._ptr:
+            _check(lib().pbs_destroy(self._ptr), "pbs_destroy")
+            self._ptr = ct.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve_k(self, geom: Geometry, opts=None, k=(0.0, 0.0), init=None, want_vectors: bool = False,
+                allow_noconv: bool = False):
+        """``pbs_solve_k``; returns ``(eigvals, resid, iters, evecs or None)``.
+
+        ``init``: complex array of shape ``(block, D)`` (row c = column c) or None.
+        ``evecs``: complex array of shape ``(nev, D)``.
+        """
+        o = _opts(opts)
+        kk = np.asarray(k, dtype=np.float64)
+        ev = np.zeros(o.nev)
+        rs = np.zeros(o.nev)
+        it = ct.c_int(0)
+        init_p = None
+        if init is not None:
+            init_arr = np.ascontiguousarray(np.asarray(init, dtype=np.complex128))
+            if init_arr.shape != (o.block, geom.D):
+                raise ValueError("init must have shape (block, D)")
+            init_p = init_arr.ctypes.data
+        vec = np.zeros((o.nev, geom.D), np.complex128) if want_vectors else None
+        st = lib().pbs_solve_k(self._ptr, geom.ref(), ct.byref(o), _dp(kk), init_p, _dp(ev), _dp(rs), ct.byref(it),
+                               vec.ctypes.data if vec is not None else None)
+        _check(st, "pbs_solve_k", (PBS_OK, PBS_ENOCONV) if allow_noconv else (PBS_OK,))
+        return ev, rs, it.value, vec
+
+    def solve_path(self, geom: Geometry, opts, ks, allow_noconv: bool = False):
+        """``pbs_solve_path`` over ``ks`` (shape ``(nk, 2)``); returns ``(eigvals, resid, iters)``."""
+        o = _opts(opts)
+        kk = np.ascontiguousarray(np.asarray(ks, dtype=np.float64).reshape(-1, 2))
+        nk = kk.shape[0]
+        ev = np.zeros((nk, o.nev))
+        rs = np.zeros((nk, o.nev))
+        it = np.zeros(nk, dtype=np.int32)
+        st = lib().pbs_solve_path(self._ptr, geom.ref(), ct.byref(o), nk, _dp(kk), _dp(ev), _dp(rs),
+                                  it.ctypes.data_as(ct.POINTER(ct.c_int)))
+        _check(st, "pbs_solve_path", (PBS_OK, PBS_ENOCONV) if allow_noconv else (PBS_OK,))
+        return ev, rs, it
+
+    def solve_path_device(self, a, b, n, m, d_eps: int, opts, nk: int, d_ks: int, d_eigvals: int, d_resid: int,
+                          d_iters: int, stream=None, allow_noconv: bool = False):
+        """``pbs_solve_path_device`` with raw device pointers."""
+        o = _opts(opts)
+        st = lib().pbs_solve_path_device(self._ptr, a, b, n, m, d_eps, ct.byref(o), nk, d_ks, d_eigvals, d_resid,
+                                         d_iters, _stream_ptr(stream))
+        _check(st, "pbs_solve_path_device", (PBS_OK, PBS_ENOCONV) if allow_noconv else (PBS_OK,))
+        return st
+
+    def apply(self, geom: Geometry, op, x_ptr: int, y_ptr: int, ncols: int, k=(0.0, 0.0), level: int = 0,
+              opts=None, stream=None):
+        """``pbs_apply`` on device arrays (interleaved complex128)."""
+        o = _opts(opts)
+        opc = OPS[op] if isinstance(op, str) else int(op)
+        kk = np.asarray(k, dtype=np.float64)
+        _check(lib().pbs_apply(self._ptr, geom.ref(), ct.byref(o), opc, level, _dp(kk), ncols, x_ptr, y_ptr,
+                               _stream_ptr(stream)), f"pbs_apply({op})")
+
+    def gram(self, geom: Geometry, k, q: int, s_ptr: int, gm_ptr: int, ga_ptr: int, stream=None):
+        kk = np.asarray(k, dtype=np.float64)
+        _check(lib().pbs_gram(self._ptr, geom.ref(), _dp(kk), q, s_ptr, gm_ptr, ga_ptr, _stream_ptr(stream)),
+               "pbs_gram")
+
+    def rayleigh_ritz(self, geom: Geometry, opts, k, q: int, s_ptr: int, p: int, project: bool, x_ptr: int,
+                      stream=None):
+        o = _opts(opts)
+        kk = np.asarray(k, dtype=np.float64)
+        theta = np.zeros(p)
+        _check(lib().pbs_rayleigh_ritz(self._ptr, geom.ref(), ct.byref(o), _dp(kk), q, s_ptr, p, int(bool(project)),
+                                       _dp(theta), x_ptr, _stream_ptr(stream)), "pbs_rayleigh_ritz")
+        return theta
+
+
+def abi_symbols_from_header(path: str | None = None) -> list[str]:
+    """Names of the functions ``include/pbs.h`` declares (for export checks)."""
+    import re
+    path = path or os.path.join(os.path.dirname(_PKG), "include", "pbs.h")
+    txt = open(path).read()
+    return sorted(set(re.findall(r"PBS_API\s+[\w\s\*]*?\b(pbs_\w+)\s*\(", txt)))

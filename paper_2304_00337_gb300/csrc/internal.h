@@ -1,0 +1,175 @@
+// Host-side declarations shared by the pbs translation units (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "pbs.h"
+
+namespace pbs {
+
+constexpr int kMaxLevels = 16;
+constexpr int kMaxBlock = 32;        // block width p
+constexpr int kMaxTrial = 3 * kMaxBlock;  // trial width q
+constexpr int kMaxCoarseEdges = 1024;     // dense coarsest edge system (2 n_c m_c)
+
+// Failure that the ABI layer turns into a status code.
+struct Error {
+  int status;
+  std::string what;
+};
+[[noreturn]] void fail(int status, const std::string& what);
+void check_cuda(cudaError_t e, const char* what);
+#define PBS_CUDA(call) ::pbs::check_cuda((call), #call)
+
+// One level of the bisection hierarchy (Section 5).  Geometry only: the
+// Bloch phases enter the kernels separately, so a level serves every k.
+struct Level {
+  int n = 0, m = 0;
+  double h1 = 0, h2 = 0;
+  double* winv64 = nullptr;  // 1/eps per cell (2x2 mean of the finer level's 1/eps)
+  float* winv32 = nullptr;
+  double* k3_64 = nullptr;   // per node: 6 entries of the inverse 3x3 patch block, SoA [6][N]
+  float* k3_32 = nullptr;
+  long N() const { return (long)n * m; }
+  long D() const { return 2L * n * m; }
+  template <class T> Lvl<T> lvl() const { return Lvl<T>{n, m, T(h2 / h1), T(h1 / h2)}; }
+  template <class T> Wts<T> wts() const;
+};
+template <> inline Wts<double> Level::wts<double>() const { return Wts<double>{winv64, n, m, 1.0 / (h1 * h2)}; }
+template <> inline Wts<float> Level::wts<float>() const { return Wts<float>{winv32, n, m, float(1.0 / (h1 * h2))}; }
+
+// Multigrid hierarchy of one geometry and regularisation mu.
+struct Hierarchy {
+  double a = 0, b = 0, mu = 0;
+  int n = 0, m = 0, nlev = 0;
+  uint64_t key = 0;
+  Level lev[kMaxLevels];
+  std::vector<void*> allocs;
+};
+
+// Per-Bloch-vector data: phases and the factored coarsest systems.
+struct KData {
+  double k1 = 0, k2 = 0;
+  double ph[4] = {1, 0, 1, 0};  // alpha, beta (host copy)
+  bool gamma = false;
+  double* d_ph = nullptr;       // device copy (4 doubles)
+  int Dc = 0, Nc = 0;
+  double2* edge64 = nullptr;    // Cholesky factor (lower, column-major Dc x Dc) of A_c + mu M_c
+  float2* edge32 = nullptr;
+  double2* node64 = nullptr;    // Cholesky factor of P_c (+ constant-mode term at k = 0)
+  float2* node32 = nullptr;
+};
+
+// Device allocator with a byte budget.
+class DevMem {
+ public:
+  explicit DevMem(size_t budget) : budget_(budget) {}
+  void* alloc(size_t bytes);
+  void free(void* p);
+  size_t used() const { return used_; }
+
+ private:
+  size_t budget_, used_ = 0;
+  std::vector<std::pair<void*, size_t>> live_;
+};
+
+int num_levels(int n, int m, int coarsest);
+
+// ---- hierarchy set-up (mg.cu) ---------------------------------------------
+void build_hierarchy(DevMem& mem, Hierarchy& H, const double* d_eps, int coarsest, cudaStream_t s);
+void free_hierarchy(DevMem& mem, Hierarchy& H);
+void build_kdata(DevMem& mem, const Hierarchy& H, KData& K, double k1, double k2, cudaStream_t s);
+void free_kdata(DevMem& mem, KData& K);
+
+// ---- operators (ops.cu); X, Y device blocks of ncols columns with stride ld ----
+// Y = sB*B + sA*(A X) + (sM + sL*lam[c]) (M X)   (B, lam may be null)
+template <class T>
+void apply_edge(const Level& L, const double* d_ph, int cpg, const cx<T>* X, cx<T>* Y, const cx<T>* B, long ld,
+                int ncols, T sA, T sM, T sL, const T* lam, T sB, cudaStream_t s);
+template <class T>
+void apply_curl(const Level& L, const double* d_ph, int cpg, const cx<T>* X, long ldx, cx<T>* Y, long ldy, int ncols,
+                cudaStream_t s);
+template <class T>
+void apply_curl_adj(const Level& L, const double* d_ph, int cpg, const cx<T>* X, long ldx, cx<T>* Y, long ldy,
+                    int ncols, cudaStream_t s);
+template <class T>
+void apply_lift(const Level& L, const double* d_ph, int cpg, const cx<T>* X, long ldx, cx<T>* Y, long ldy, int ncols,
+                cudaStream_t s);
+template <class T>
+void apply_lift_adj(const Level& L, const double* d_ph, int cpg, const cx<T>* X, long ldx, cx<T>* Y, long ldy,
+                    int ncols, cudaStream_t s);
+// Y = sB*B + sP*(P X) on nodes
+template <class T>
+void apply_nodal(const Level& L, const double* d_ph, int cpg, const cx<T>* X, cx<T>* Y, const cx<T>* B, long ld,
+                 int ncols, T sP, T sB, cudaStream_t s);
+// edge transfer: fine level `f` (index l) <-> coarse level `c` (l+1)
+template <class T>
+void prolong_edge(const Level& f, const Level& c, const double* d_ph, int cpg, const cx<T>* Xc, long ldc, cx<T>* Yf,
+                  long ldf, int ncols, bool accumulate, cudaStream_t s);
+template <class T>
+void restrict_edge(const Level& f, const Level& c, const double* d_ph, int cpg, const cx<T>* Xf, long ldf, cx<T>* Yc,
+                   long ldc, int ncols, cudaStream_t s);
+template <class T>
+void prolong_node(const Level& f, const Level& c, const double* d_ph, int cpg, const cx<T>* Xc, long ldc, cx<T>* Yf,
+                  long ldf, int ncols, bool accumulate, cudaStream_t s);
+template <class T>
+void restrict_node(const Level& f, const Level& c, const double* d_ph, int cpg, const cx<T>* Xf, long ldf, cx<T>* Yc,
+                   long ldc, int ncols, cudaStream_t s);
+
+// ---- multigrid (mg.cu) ----------------------------------------------------
+// Workspace for V-cycles of up to `ncols` columns on levels 1..nlev-1 (+ level-0 residual).
+template <class T> struct MgWork {
+  cx<T>* x[kMaxLevels] = {};
+  cx<T>* b[kMaxLevels] = {};
+  cx<T>* r[kMaxLevels] = {};
+  int ncols = 0;
+};
+template <class T> void alloc_mg_work(DevMem& mem, const Hierarchy& H, int ncols, bool nodal, MgWork<T>& w);
+template <class T> void free_mg_work(DevMem& mem, MgWork<T>& w);
+// Y = B X: one edge V-cycle for A + mu M started from zero (x, y on level `l0`).
+template <class T>
+void edge_vcycle(const Hierarchy& H, const KData& K, MgWork<T>& w, int l0, const cx<T>* X, cx<T>* Y, long ld,
+                 int ncols, int nu_pre, int nu_post, cudaStream_t s);
+template <class T>
+void nodal_vcycle(const Hierarchy& H, const KData& K, MgWork<T>& w, int l0, const cx<T>* X, cx<T>* Y, long ld,
+                  int ncols, int nu_pre, int nu_post, cudaStream_t s);
+
+// ---- dense block kernels (dense.cu) ---------------------------------------
+void convert_d2f(const double2* X, float2* Y, long n, cudaStream_t s);
+void convert_f2d(const float2* X, double2* Y, long n, cudaStream_t s);
+// x <- x - L phi (FP64 x, phi in T), level 0
+template <class T>
+void sub_lift(const Level& L, const double* d_ph, int cpg, const cx<T>* Phi, long ldp, double2* X, long ldx, int ncols,
+              cudaStream_t s);
+// rhs = L^* M x  (FP64), stored in T
+template <class T>
+void lift_adj_mass(const Level& L, const double* d_ph, int cpg, const double2* X, long ldx, cx<T>* Rhs, long ldr,
+                   int ncols, cudaStream_t s);
+// subtract the x-edge mean and the y-edge mean of every column (k = 0 deflation)
+void deflate_constants(const Level& L, double2* X, long ld, int ncols, double* d_partials, cudaStream_t s);
+// per column: out[2c] = e^* M e, out[2c+1] = (C e)^* W (C e)
+void rayleigh_parts(const Level& L, const double* d_ph, int cpg, const double2* X, long ld, int ncols,
+                    double* d_partials, double* d_out, cudaStream_t s);
+// R = A E - lam M E; per column out[2c] = |R|^2, out[2c+1] = |M E|^2
+void residual(const Level& L, const double* d_ph, int cpg, const double2* E, double2* R, long ld, int ncols,
+              const double* d_lam, double* d_partials, double* d_out, cudaStream_t s);
+// GM = S^* M S, GA = (C S)^* W (C S)  (q x q, column-major); work: D*q + N*q double2
+void gram(const Level& L, const double* d_ph, int cpg, const double2* S, long ld, int q, double2* GM, double2* GA,
+          double2* work, double2* d_partials, int npart, cudaStream_t s);
+int gram_partials(long rows);
+// Rayleigh-Ritz in coefficient space: C (q x p) and theta (p); status in d_info[0]
+void small_rr(const double2* GM, const double2* GA, int q, int p, double2* C, double* theta, double2* scratch,
+              int* d_info, cudaStream_t s);
+size_t small_rr_scratch(int q);
+// Y[:, j] = sum_i X[:, i] C[i, j] (+ Z[:, j]); X: rows x q, C: q x p column-major (device)
+void block_update(const double2* X, long ldx, int q, const double2* C, int ldc, double2* Y, long ldy, int p,
+                  const double2* Z, long ldz, long rows, cudaStream_t s);
+void random_block(double2* X, long ld, long rows, int ncols, uint64_t seed, cudaStream_t s);
+void scale_columns(double2* X, long ld, long rows, int ncols, const double* d_scale, cudaStream_t s);
+
+}  // namespace pbs

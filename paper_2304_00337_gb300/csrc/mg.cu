@@ -1,0 +1,495 @@
+// Geometric multigrid of Section 5: bisection hierarchy with Galerkin coarse
+// operators, node-patch block Gauss-Seidel for A + mu M (edges), point
+// Gauss-Seidel for P = L^* M L (nodes), dense Cholesky on the coarsest level.
+//
+// Coarse operators.  With the natural embedding as prolongation the Galerkin
+// product P^* A_f P is the curl-curl matrix of the coarse mesh whose 1/eps is
+// the mean of the four children's 1/eps, and P^* M_f P is the coarse mass
+// matrix (the curl is constant per cell, so a coarse cell's energy is the sum
+// of its children's).  Hence every level uses the same stencil code with its
+// own 1/eps and mesh widths, and the Bloch phases are unchanged (the periods
+// a, b are the same on every level).
+//
+// Patch solve.  The patch of node (i,j) holds its left, right, bottom and top
+// edges (L, R, B, T).  In "ghost" coordinates (values read through the Bloch
+// extension) the 4x4 block of A + mu M is real and independent of k:
+//   K = sum_cells w_c v_c v_c^T + mu diag(m1, m1, m2, m2),  m1 = 2/3 h2/h1, m2 = 2/3 h1/h2,
+//   v_SW = (1,0,-1,0), v_NW = (-1,0,0,-1), v_SE = (0,1,1,0), v_NE = (0,-1,0,1).
+// The gradient g = (1,-1,1,-1) of the node's hat function satisfies K g =
+// mu M_loc g, which makes K ill-conditioned for small mu (Section 5).  Following
+// the paper's stable variant, T = [g, t_a, t_b, t_c] with the M_loc-orthogonal
+// complement t_a = (1,1,0,0), t_b = (0,0,1,1), t_c = (m2,-m2,-m1,m1) gives
+// T^T K T = diag(mu g^T M_loc g, K3), so K^{-1} r = g (g^T r)/(mu g^T M_loc g)
+// + T3 K3^{-1} T3^T r.  K3^{-1} (3x3, symmetric) is stored per node and level.
+//
+// Colouring.  Nodes are processed by colour (i mod 2, j mod 2) in the order
+// (0,0), (1,0), (0,1), (1,1) (pre-smoothing) and reversed (post-smoothing).
+// Same-colour patches share no edge and are not coupled by A or M, so each
+// colour is one parallel launch and equals the sequential block Gauss-Seidel
+// sweep; the resulting V-cycle is Hermitian.
+#include <cmath>
+#include <cstring>
+
+#include "internal.h"
+
+namespace pbs {
+
+namespace {
+
+constexpr int kBX = 32, kBY = 8;
+constexpr int kColours[4][2] = {{0, 0}, {1, 0}, {0, 1}, {1, 1}};
+
+__global__ void k_inv_eps(const double* __restrict__ eps, double* __restrict__ w64, float* __restrict__ w32, long N,
+                          int* __restrict__ bad) {
+  const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (t >= N) return;
+  const double e = eps[t];
+  if (!(e > 0.0) || !isfinite(e)) {
+    atomicExch(bad, 1);
+    w64[t] = 1.0;
+    w32[t] = 1.0f;
+    return;
+  }
+  w64[t] = 1.0 / e;
+  w32[t] = float(1.0 / e);
+}
+
+__global__ void k_coarsen_w(const double* __restrict__ wf, int nf, double* __restrict__ wc, float* __restrict__ wc32,
+                            int nc, int mc) {
+  const int I = blockIdx.x * kBX + threadIdx.x, J = blockIdx.y * kBY + threadIdx.y;
+  if (I >= nc || J >= mc) return;
+  const long a = (long)(2 * J) * nf + 2 * I, b = a + nf;
+  const double v = 0.25 * (wf[a] + wf[a + 1] + wf[b] + wf[b + 1]);
+  wc[(long)J * nc + I] = v;
+  wc32[(long)J * nc + I] = float(v);
+}
+
+// K3 = sum_c w_c u_c u_c^T + mu diag(2 m1, 2 m2, 2 m1 m2 s), u_c = T3^T v_c, s = m1 + m2
+__global__ void k_patch_factors(const double* __restrict__ winv, int n, int m, double scale, double m1, double m2,
+                                double mu, double* __restrict__ k64, float* __restrict__ k32) {
+  const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y;
+  if (i >= n || j >= m) return;
+  const int im = (i + n - 1) % n, jm = (j + m - 1) % m;
+  const double wSW = scale * winv[(long)jm * n + im], wNW = scale * winv[(long)j * n + im];
+  const double wSE = scale * winv[(long)jm * n + i], wNE = scale * winv[(long)j * n + i];
+  const double s = m1 + m2;
+  const double u[4][3] = {{1, -1, s}, {-1, -1, -s}, {1, 1, -s}, {-1, 1, s}};
+  const double w[4] = {wSW, wNW, wSE, wNE};
+  double K[3][3] = {{mu * 2 * m1, 0, 0}, {0, mu * 2 * m2, 0}, {0, 0, mu * 2 * m1 * m2 * s}};
+  for (int c = 0; c < 4; ++c)
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) K[a][b] += w[c] * u[c][a] * u[c][b];
+  // inverse via the adjugate (K3 is symmetric positive definite and well conditioned)
+  const double c00 = K[1][1] * K[2][2] - K[1][2] * K[2][1];
+  const double c01 = K[0][2] * K[2][1] - K[0][1] * K[2][2];
+  const double c02 = K[0][1] * K[1][2] - K[0][2] * K[1][1];
+  const double c11 = K[0][0] * K[2][2] - K[0][2] * K[2][0];
+  const double c12 = K[0][2] * K[1][0] - K[0][0] * K[1][2];
+  const double c22 = K[0][0] * K[1][1] - K[0][1] * K[1][0];
+  const double det = K[0][0] * c00 + K[0][1] * (K[1][2] * K[2][0] - K[1][0] * K[2][2]) + K[0][2] * (K[1][0] * K[2][1] - K[1][1] * K[2][0]);
+  const double id = 1.0 / det;
+  const double inv[6] = {c00 * id, c01 * id, c02 * id, c11 * id, c12 * id, c22 * id};
+  const long N = (long)n * m, e = (long)j * n + i;
+  for (int q = 0; q < 6; ++q) {
+    k64[q * N + e] = inv[q];
+    k32[q * N + e] = float(inv[q]);
+  }
+}
+
+// Dense coarsest-level matrices, column-major: column `col` = operator applied to unit vector `col`.
+__global__ void k_assemble_edge(Lvl<double> L, Wts<double> w, double mu, const double* ph, double2* K) {
+  const int Nc = L.n * L.m, Dc = 2 * Nc;
+  const int row = blockIdx.x * blockDim.x + threadIdx.x, col = blockIdx.y;
+  if (row >= Dc || col >= Dc) return;
+  const UnitERd<double> r{L.n, L.m, col / Nc, col % Nc, load_ph<double>(ph, 0)};
+  const int kind = row / Nc, e = row % Nc, i = e % L.n, j = e / L.n;
+  double2 v = kind == 0 ? A_x<double>(r, w, i, j) + mu * M_x<double>(r, L, i, j)
+                        : A_y<double>(r, w, i, j) + mu * M_y<double>(r, L, i, j);
+  K[(long)col * Dc + row] = v;
+}
+
+__global__ void k_assemble_node(Lvl<double> L, const double* ph, double shift, double2* K) {
+  const int Nc = L.n * L.m;
+  const int row = blockIdx.x * blockDim.x + threadIdx.x, col = blockIdx.y;
+  if (row >= Nc || col >= Nc) return;
+  const UnitNRd<double> r{L.n, L.m, col, load_ph<double>(ph, 0)};
+  double2 v = P_at<double>(r, L, row % L.n, row / L.n);
+  v.x += shift / Nc;  // k = 0: the constant mode gets eigenvalue `shift` (zero-mean solutions)
+  K[(long)col * Nc + row] = v;
+}
+
+// In-place Cholesky (lower, column-major) of a Hermitian positive definite matrix; one block.
+__global__ void k_cholesky(double2* A, int n, float2* A32, int* info) {
+  __shared__ double piv;
+  for (int k = 0; k < n; ++k) {
+    if (threadIdx.x == 0) {
+      const double d = A[(long)k * n + k].x;
+      piv = (d > 0.0 && isfinite(d)) ? sqrt(d) : -1.0;
+      if (piv < 0 && *info == 0) *info = k + 1;
+      A[(long)k * n + k] = make_double2(piv > 0 ? piv : 1.0, 0.0);
+    }
+    __syncthreads();
+    const double p = piv > 0 ? piv : 1.0;
+    for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) {
+      double2 v = A[(long)k * n + i];
+      A[(long)k * n + i] = make_double2(v.x / p, v.y / p);
+    }
+    __syncthreads();
+    const int rem = n - k - 1;
+    for (long t = threadIdx.x; t < (long)rem * rem; t += blockDim.x) {
+      const int jj = k + 1 + int(t / rem), ii = k + 1 + int(t % rem);
+      if (ii < jj) continue;
+      const double2 lik = A[(long)k * n + ii], ljk = A[(long)k * n + jj];
+      double2 v = A[(long)jj * n + ii];
+      // A[ii][jj] -= L[ii][k] * conj(L[jj][k])
+      v.x -= lik.x * ljk.x + lik.y * ljk.y;
+      v.y -= lik.y * ljk.x - lik.x * ljk.y;
+      A[(long)jj * n + ii] = v;
+    }
+    __syncthreads();
+  }
+  for (long t = threadIdx.x; t < (long)n * n; t += blockDim.x) {
+    const int jj = int(t / n), ii = int(t % n);
+    const double2 v = ii >= jj ? A[t] : make_double2(0.0, 0.0);
+    A[t] = v;
+    A32[t] = make_float2(float(v.x), float(v.y));
+  }
+}
+
+// Solve L L^* x = b for each column (one warp per column).
+template <class T>
+__global__ void k_chol_solve(const cx<T>* __restrict__ Lf, int n, const cx<T>* __restrict__ B, long ldb,
+                             cx<T>* __restrict__ X, long ldx, int ncols) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= ncols) return;
+  const cx<T>* b = B + warp * ldb;
+  cx<T>* x = X + warp * ldx;
+  // forward: L y = b  (y stored in x)
+  for (int i = 0; i < n; ++i) {
+    cx<T> acc = czero<T>();
+    for (int k = lane; k < i; k += 32) acc = acc + cmul(Lf[(long)k * n + i], x[k]);
+    for (int o = 16; o > 0; o >>= 1) {
+      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+    }
+    if (lane == 0) {
+      const T d = Lf[(long)i * n + i].x;
+      const cx<T> v = b[i] - acc;
+      x[i] = mk<T>(v.x / d, v.y / d);
+    }
+    __syncwarp();
+  }
+  // backward: L^* x = y
+  for (int i = n - 1; i >= 0; --i) {
+    cx<T> acc = czero<T>();
+    for (int k = i + 1 + lane; k < n; k += 32) acc = acc + cmulc(Lf[(long)i * n + k], x[k]);
+    for (int o = 16; o > 0; o >>= 1) {
+      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+    }
+    if (lane == 0) {
+      const T d = Lf[(long)i * n + i].x;
+      const cx<T> v = x[i] - acc;
+      x[i] = mk<T>(v.x / d, v.y / d);
+    }
+    __syncwarp();
+  }
+}
+
+// One colour of the node-patch block Gauss-Seidel sweep for A + mu M.
+template <class T>
+__global__ void k_edge_smooth(Lvl<T> L, Wts<T> w, const T* __restrict__ k3, T mu, const double* ph, int cpg,
+                              cx<T>* X, const cx<T>* __restrict__ B, long ld, int ci, int cj) {
+  const int i = 2 * (blockIdx.x * kBX + threadIdx.x) + ci, j = 2 * (blockIdx.y * kBY + threadIdx.y) + cj;
+  const int c = blockIdx.z;
+  if (i >= L.n || j >= L.m) return;
+  const Ph<T> p = load_ph<T>(ph, c / cpg);
+  const ERd<T> r{X + c * ld, L.n, L.m, p};
+  const ERd<T> rb{B + c * ld, L.n, L.m, p};
+  // residual b - (A + mu M) x on the patch, in ghost coordinates
+  const cx<T> rL = rb.x(i - 1, j) - (A_x<T>(r, w, i - 1, j) + mu * M_x<T>(r, L, i - 1, j));
+  const cx<T> rR = rb.x(i, j) - (A_x<T>(r, w, i, j) + mu * M_x<T>(r, L, i, j));
+  const cx<T> rB = rb.y(i, j - 1) - (A_y<T>(r, w, i, j - 1) + mu * M_y<T>(r, L, i, j - 1));
+  const cx<T> rT = rb.y(i, j) - (A_y<T>(r, w, i, j) + mu * M_y<T>(r, L, i, j));
+  const T m1 = T(2.0 / 3.0) * L.mx, m2 = T(2.0 / 3.0) * L.my;
+  const cx<T> s0 = (T(1) / (mu * T(2) * (m1 + m2))) * (rL - rR + rB - rT);
+  const cx<T> ya = rL + rR, yb = rB + rT, yc = m2 * (rL - rR) + m1 * (rT - rB);
+  const long N = (long)L.n * L.m, e = (long)j * L.n + i;
+  const T K00 = k3[e], K01 = k3[N + e], K02 = k3[2 * N + e], K11 = k3[3 * N + e], K12 = k3[4 * N + e],
+          K22 = k3[5 * N + e];
+  const cx<T> za = K00 * ya + K01 * yb + K02 * yc;
+  const cx<T> zb = K01 * ya + K11 * yb + K12 * yc;
+  const cx<T> zc = K02 * ya + K12 * yb + K22 * yc;
+  const cx<T> dL = s0 + za + m2 * zc, dR = za - m2 * zc - s0;
+  const cx<T> dB = s0 + zb - m1 * zc, dT = zb + m1 * zc - s0;
+  cx<T>* Xx = X + c * ld;
+  cx<T>* Xy = Xx + N;
+  Xx[e] = Xx[e] + dR;
+  Xy[e] = Xy[e] + dT;
+  // a ghost-coordinate change d of an edge read as conj(alpha) x is alpha d in storage
+  if (i > 0) Xx[e - 1] = Xx[e - 1] + dL;
+  else Xx[(long)j * L.n + L.n - 1] = Xx[(long)j * L.n + L.n - 1] + cmul(p.al, dL);
+  if (j > 0) Xy[e - L.n] = Xy[e - L.n] + dB;
+  else Xy[(long)(L.m - 1) * L.n + i] = Xy[(long)(L.m - 1) * L.n + i] + cmul(p.be, dB);
+}
+
+// One colour of point Gauss-Seidel for P = L^* M L.
+template <class T>
+__global__ void k_node_smooth(Lvl<T> L, const double* ph, int cpg, cx<T>* X, const cx<T>* __restrict__ B, long ld,
+                              int ci, int cj) {
+  const int i = 2 * (blockIdx.x * kBX + threadIdx.x) + ci, j = 2 * (blockIdx.y * kBY + threadIdx.y) + cj;
+  const int c = blockIdx.z;
+  if (i >= L.n || j >= L.m) return;
+  const NRd<T> r{X + c * ld, L.n, L.m, load_ph<T>(ph, c / cpg)};
+  const long e = (long)j * L.n + i;
+  const cx<T> res = B[c * ld + e] - P_at<T>(r, L, i, j);
+  X[c * ld + e] = X[c * ld + e] + (T(1) / P_diag<T>(L)) * res;
+}
+
+template <class T> const cx<T>* edge_factor(const KData& K);
+template <> const double2* edge_factor<double>(const KData& K) { return K.edge64; }
+template <> const float2* edge_factor<float>(const KData& K) { return K.edge32; }
+template <class T> const cx<T>* node_factor(const KData& K);
+template <> const double2* node_factor<double>(const KData& K) { return K.node64; }
+template <> const float2* node_factor<float>(const KData& K) { return K.node32; }
+template <class T> const T* k3_of(const Level& L);
+template <> const double* k3_of<double>(const Level& L) { return L.k3_64; }
+template <> const float* k3_of<float>(const Level& L) { return L.k3_32; }
+
+inline dim3 half_grid(int n, int m, int ncols) {
+  return dim3(((n + 1) / 2 + kBX - 1) / kBX, ((m + 1) / 2 + kBY - 1) / kBY, ncols);
+}
+
+}  // namespace
+
+int num_levels(int n, int m, int coarsest) {
+  if (n < 2 || m < 2 || coarsest < 2) return PBS_EINVAL;
+  int L = 1;
+  while (n % 2 == 0 && m % 2 == 0 && n / 2 >= coarsest && m / 2 >= coarsest && L < kMaxLevels) {
+    n /= 2;
+    m /= 2;
+    ++L;
+  }
+  return L;
+}
+
+void build_hierarchy(DevMem& mem, Hierarchy& H, const double* d_eps, int coarsest, cudaStream_t s) {
+  H.nlev = num_levels(H.n, H.m, coarsest);
+  if (H.nlev < 1) fail(-1, "invalid mesh for the hierarchy");
+  int* d_bad = (int*)mem.alloc(sizeof(int));
+  H.allocs.push_back(d_bad);
+  PBS_CUDA(cudaMemsetAsync(d_bad, 0, sizeof(int), s));
+  int n = H.n, m = H.m;
+  for (int l = 0; l < H.nlev; ++l) {
+    Level& L = H.lev[l];
+    L.n = n;
+    L.m = m;
+    L.h1 = H.a / n;
+    L.h2 = H.b / m;
+    const long N = (long)n * m;
+    L.winv64 = (double*)mem.alloc(N * sizeof(double));
+    L.winv32 = (float*)mem.alloc(N * sizeof(float));
+    L.k3_64 = (double*)mem.alloc(6 * N * sizeof(double));
+    L.k3_32 = (float*)mem.alloc(6 * N * sizeof(float));
+    H.allocs.insert(H.allocs.end(), {L.winv64, L.winv32, L.k3_64, L.k3_32});
+    if (l == 0) {
+      k_inv_eps<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(d_eps, L.winv64, L.winv32, N, d_bad);
+    } else {
+      const Level& F = H.lev[l - 1];
+      k_coarsen_w<<<dim3((n + kBX - 1) / kBX, (m + kBY - 1) / kBY), dim3(kBX, kBY), 0, s>>>(F.winv64, F.n, L.winv64,
+                                                                                           L.winv32, n, m);
+    }
+    PBS_CUDA(cudaGetLastError());
+    const double m1 = 2.0 / 3.0 * L.h2 / L.h1, m2 = 2.0 / 3.0 * L.h1 / L.h2;
+    k_patch_factors<<<dim3((n + kBX - 1) / kBX, (m + kBY - 1) / kBY), dim3(kBX, kBY), 0, s>>>(
+        L.winv64, n, m, 1.0 / (L.h1 * L.h2), m1, m2, H.mu, L.k3_64, L.k3_32);
+    PBS_CUDA(cudaGetLastError());
+    n /= 2;
+    m /= 2;
+  }
+  int bad = 0;
+  PBS_CUDA(cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+  PBS_CUDA(cudaStreamSynchronize(s));
+  if (bad) fail(-1, "eps must be finite and positive");
+  const Level& C = H.lev[H.nlev - 1];
+  if (C.D() > kMaxCoarseEdges) fail(-1, "coarsest level too large for the dense solve (raise coarsest or use sides with more factors of 2)");
+}
+
+void free_hierarchy(DevMem& mem, Hierarchy& H) {
+  for (void* p : H.allocs) mem.free(p);
+  H.allocs.clear();
+  H.nlev = 0;
+}
+
+void build_kdata(DevMem& mem, const Hierarchy& H, KData& K, double k1, double k2, cudaStream_t s) {
+  K.k1 = k1;
+  K.k2 = k2;
+  K.ph[0] = std::cos(k1 * H.a);
+  K.ph[1] = std::sin(k1 * H.a);
+  K.ph[2] = std::cos(k2 * H.b);
+  K.ph[3] = std::sin(k2 * H.b);
+  K.gamma = std::hypot(K.ph[0] - 1.0, K.ph[1]) < 1e-14 && std::hypot(K.ph[2] - 1.0, K.ph[3]) < 1e-14;
+  if (K.gamma) {  // use the exact phases at the lattice points
+    K.ph[0] = 1.0; K.ph[1] = 0.0; K.ph[2] = 1.0; K.ph[3] = 0.0;
+  }
+  const Level& C = H.lev[H.nlev - 1];
+  const int Dc = (int)C.D(), Nc = (int)C.N();
+  if (!K.d_ph || K.Dc != Dc) {
+    free_kdata(mem, K);
+    K.d_ph = (double*)mem.alloc(4 * sizeof(double));
+    K.edge64 = (double2*)mem.alloc((size_t)Dc * Dc * sizeof(double2));
+    K.edge32 = (float2*)mem.alloc((size_t)Dc * Dc * sizeof(float2));
+    K.node64 = (double2*)mem.alloc((size_t)Nc * Nc * sizeof(double2));
+    K.node32 = (float2*)mem.alloc((size_t)Nc * Nc * sizeof(float2));
+    K.Dc = Dc;
+    K.Nc = Nc;
+  }
+  PBS_CUDA(cudaMemcpyAsync(K.d_ph, K.ph, 4 * sizeof(double), cudaMemcpyHostToDevice, s));
+  int* d_info = (int*)mem.alloc(2 * sizeof(int));
+  PBS_CUDA(cudaMemsetAsync(d_info, 0, 2 * sizeof(int), s));
+  k_assemble_edge<<<dim3((Dc + 127) / 128, Dc), 128, 0, s>>>(C.lvl<double>(), C.wts<double>(), H.mu, K.d_ph, K.edge64);
+  PBS_CUDA(cudaGetLastError());
+  k_cholesky<<<1, 256, 0, s>>>(K.edge64, Dc, K.edge32, d_info);
+  PBS_CUDA(cudaGetLastError());
+  const double shift = K.gamma ? P_diag<double>(C.lvl<double>()) : 0.0;
+  k_assemble_node<<<dim3((Nc + 127) / 128, Nc), 128, 0, s>>>(C.lvl<double>(), K.d_ph, shift, K.node64);
+  PBS_CUDA(cudaGetLastError());
+  k_cholesky<<<1, 256, 0, s>>>(K.node64, Nc, K.node32, d_info + 1);
+  PBS_CUDA(cudaGetLastError());
+  int info[2] = {0, 0};
+  PBS_CUDA(cudaMemcpyAsync(info, d_info, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+  PBS_CUDA(cudaStreamSynchronize(s));
+  mem.free(d_info);
+  if (info[0] || info[1]) fail(-4, "coarsest-level Cholesky factorisation failed");
+}
+
+void free_kdata(DevMem& mem, KData& K) {
+  for (void* p : {(void*)K.d_ph, (void*)K.edge64, (void*)K.edge32, (void*)K.node64, (void*)K.node32})
+    if (p) mem.free(p);
+  K.d_ph = nullptr;
+  K.edge64 = nullptr;
+  K.edge32 = nullptr;
+  K.node64 = nullptr;
+  K.node32 = nullptr;
+  K.Dc = K.Nc = 0;
+}
+
+template <class T> void alloc_mg_work(DevMem& mem, const Hierarchy& H, int ncols, bool nodal, MgWork<T>& w) {
+  free_mg_work<T>(mem, w);
+  w.ncols = ncols;
+  for (int l = 0; l < H.nlev; ++l) {
+    const long len = nodal ? H.lev[l].N() : H.lev[l].D();
+    const size_t bytes = (size_t)len * ncols * sizeof(cx<T>);
+    w.r[l] = (cx<T>*)mem.alloc(bytes);
+    if (l > 0) {
+      w.x[l] = (cx<T>*)mem.alloc(bytes);
+      w.b[l] = (cx<T>*)mem.alloc(bytes);
+    }
+  }
+}
+
+template <class T> void free_mg_work(DevMem& mem, MgWork<T>& w) {
+  for (int l = 0; l < kMaxLevels; ++l) {
+    for (cx<T>** p : {&w.x[l], &w.b[l], &w.r[l]}) {
+      if (*p) mem.free(*p);
+      *p = nullptr;
+    }
+  }
+  w.ncols = 0;
+}
+
+namespace {
+
+template <class T>
+void edge_cycle(const Hierarchy& H, const KData& K, MgWork<T>& w, int l, const cx<T>* b, cx<T>* x, long ld, int ncols,
+                int nu_pre, int nu_post, cudaStream_t s) {
+  const Level& L = H.lev[l];
+  if (l == H.nlev - 1) {
+    k_chol_solve<T><<<(ncols * 32 + 127) / 128, 128, 0, s>>>(edge_factor<T>(K), (int)L.D(), b, ld, x, ld, ncols);
+    PBS_CUDA(cudaGetLastError());
+    return;
+  }
+  for (int c = 0; c < ncols; ++c) PBS_CUDA(cudaMemsetAsync(x + c * ld, 0, L.D() * sizeof(cx<T>), s));
+  const Lvl<T> lv = L.lvl<T>();
+  const Wts<T> wt = L.wts<T>();
+  const T mu = T(H.mu);
+  for (int it = 0; it < nu_pre; ++it)
+    for (int q = 0; q < 4; ++q) {
+      k_edge_smooth<T><<<half_grid(L.n, L.m, ncols), dim3(kBX, kBY), 0, s>>>(lv, wt, k3_of<T>(L), mu, K.d_ph, ncols, x,
+                                                                             b, ld, kColours[q][0], kColours[q][1]);
+      PBS_CUDA(cudaGetLastError());
+    }
+  const Level& C = H.lev[l + 1];
+  const long ldc = C.D();
+  apply_edge<T>(L, K.d_ph, ncols, x, w.r[l], b, ld, ncols, T(-1), -mu, T(0), nullptr, T(1), s);
+  restrict_edge<T>(L, C, K.d_ph, ncols, w.r[l], ld, w.b[l + 1], ldc, ncols, s);
+  edge_cycle<T>(H, K, w, l + 1, w.b[l + 1], w.x[l + 1], ldc, ncols, nu_pre, nu_post, s);
+  prolong_edge<T>(L, C, K.d_ph, ncols, w.x[l + 1], ldc, x, ld, ncols, true, s);
+  for (int it = 0; it < nu_post; ++it)
+    for (int q = 3; q >= 0; --q) {
+      k_edge_smooth<T><<<half_grid(L.n, L.m, ncols), dim3(kBX, kBY), 0, s>>>(lv, wt, k3_of<T>(L), mu, K.d_ph, ncols, x,
+                                                                             b, ld, kColours[q][0], kColours[q][1]);
+      PBS_CUDA(cudaGetLastError());
+    }
+}
+
+template <class T>
+void node_cycle(const Hierarchy& H, const KData& K, MgWork<T>& w, int l, const cx<T>* b, cx<T>* x, long ld, int ncols,
+                int nu_pre, int nu_post, cudaStream_t s) {
+  const Level& L = H.lev[l];
+  if (l == H.nlev - 1) {
+    k_chol_solve<T><<<(ncols * 32 + 127) / 128, 128, 0, s>>>(node_factor<T>(K), (int)L.N(), b, ld, x, ld, ncols);
+    PBS_CUDA(cudaGetLastError());
+    return;
+  }
+  for (int c = 0; c < ncols; ++c) PBS_CUDA(cudaMemsetAsync(x + c * ld, 0, L.N() * sizeof(cx<T>), s));
+  const Lvl<T> lv = L.lvl<T>();
+  for (int it = 0; it < nu_pre; ++it)
+    for (int q = 0; q < 4; ++q) {
+      k_node_smooth<T><<<half_grid(L.n, L.m, ncols), dim3(kBX, kBY), 0, s>>>(lv, K.d_ph, ncols, x, b, ld,
+                                                                             kColours[q][0], kColours[q][1]);
+      PBS_CUDA(cudaGetLastError());
+    }
+  const Level& C = H.lev[l + 1];
+  const long ldc = C.N();
+  apply_nodal<T>(L, K.d_ph, ncols, x, w.r[l], b, ld, ncols, T(-1), T(1), s);
+  restrict_node<T>(L, C, K.d_ph, ncols, w.r[l], ld, w.b[l + 1], ldc, ncols, s);
+  node_cycle<T>(H, K, w, l + 1, w.b[l + 1], w.x[l + 1], ldc, ncols, nu_pre, nu_post, s);
+  prolong_node<T>(L, C, K.d_ph, ncols, w.x[l + 1], ldc, x, ld, ncols, true, s);
+  for (int it = 0; it < nu_post; ++it)
+    for (int q = 3; q >= 0; --q) {
+      k_node_smooth<T><<<half_grid(L.n, L.m, ncols), dim3(kBX, kBY), 0, s>>>(lv, K.d_ph, ncols, x, b, ld,
+                                                                             kColours[q][0], kColours[q][1]);
+      PBS_CUDA(cudaGetLastError());
+    }
+}
+
+}  // namespace
+
+template <class T>
+void edge_vcycle(const Hierarchy& H, const KData& K, MgWork<T>& w, int l0, const cx<T>* X, cx<T>* Y, long ld,
+                 int ncols, int nu_pre, int nu_post, cudaStream_t s) {
+  if (ncols <= 0) return;
+  if (ncols > w.ncols) fail(-1, "multigrid workspace too small");
+  edge_cycle<T>(H, K, w, l0, X, Y, ld, ncols, nu_pre, nu_post, s);
+}
+
+template <class T>
+void nodal_vcycle(const Hierarchy& H, const KData& K, MgWork<T>& w, int l0, const cx<T>* X, cx<T>* Y, long ld,
+                  int ncols, int nu_pre, int nu_post, cudaStream_t s) {
+  if (ncols <= 0) return;
+  if (ncols > w.ncols) fail(-1, "multigrid workspace too small");
+  node_cycle<T>(H, K, w, l0, X, Y, ld, ncols, nu_pre, nu_post, s);
+}
+
+#define PBS_INST_MG(T)                                                                                            \
+  template void alloc_mg_work<T>(DevMem&, const Hierarchy&, int, bool, MgWork<T>&);                               \
+  template void free_mg_work<T>(DevMem&, MgWork<T>&);                                                             \
+  template void edge_vcycle<T>(const Hierarchy&, const KData&, MgWork<T>&, int, const cx<T>*, cx<T>*, long, int, \
+                               int, int, cudaStream_t);                                                           \
+  template void nodal_vcycle<T>(const Hierarchy&, const KData&, MgWork<T>&, int, const cx<T>*, cx<T>*, long, int, \
+                                int, int, cudaStream_t);
+PBS_INST_MG(double)
+PBS_INST_MG(float)
+
+}  // namespace pbs

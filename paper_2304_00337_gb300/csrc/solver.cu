@@ -1,0 +1,983 @@
+// Host orchestration and C ABI of libpbs.
+//
+// Per Bloch vector k the iteration follows Algorithm 2 of the paper (Section 4):
+//   R = A E - M E Lambda                   (FP64, Lambda = Rayleigh quotients)
+//   W = B R                                (V-cycle for A + mu M, Section 5)
+//   [E, W] <- projected off the gradients  (nodal V-cycles on L^* M L, Section 4/5)
+//   Rayleigh-Ritz on span(E, W, P)         (Grams + small dense eigensolve, FP64)
+//   E <- lowest p Ritz vectors, P <- new search direction
+// until every wanted band has ||A e - lambda M e||_2 <= tol * lambda ||M e||_2.
+// Along a k-path the first block of every k after the first comes from
+// Rayleigh-Ritz of the new pencil on the span of up to three previous bases
+// (Section 6).  The span of (E, W, P) equals the paper's span of
+// (E_hat, E^(m), E^(m-1)) with E_hat = E - W; using W and the implicit
+// direction P keeps the trial basis well conditioned.
+#include <algorithm>
+#include <cstdlib>
+#include <cmath>
+#include <functional>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "pbs.h"
+
+namespace pbs {
+
+static thread_local std::string g_last_error;
+
+void fail(int status, const std::string& what) { throw Error{status, what}; }
+
+void check_cuda(cudaError_t e, const char* what) {
+  if (e != cudaSuccess) {
+    const int status = e == cudaErrorMemoryAllocation ? PBS_ENOMEM : PBS_ECUDA;
+    fail(status, std::string(what) + ": " + cudaGetErrorString(e));
+  }
+}
+
+void* DevMem::alloc(size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  bytes = (bytes + 255) & ~size_t(255);
+  if (budget_ && used_ + bytes > budget_) fail(PBS_ENOMEM, "device memory budget exceeded");
+  void* p = nullptr;
+  const cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    fail(PBS_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  live_.push_back({p, bytes});
+  used_ += bytes;
+  return p;
+}
+
+void DevMem::free(void* p) {
+  if (!p) return;
+  for (size_t i = 0; i < live_.size(); ++i) {
+    if (live_[i].first == p) {
+      used_ -= live_[i].second;
+      live_.erase(live_.begin() + i);
+      cudaFree(p);
+      return;
+    }
+  }
+}
+
+namespace {
+
+uint64_t fnv1a(const void* data, size_t bytes, uint64_t h = 1469598103934665603ull) {
+  const unsigned char* p = (const unsigned char*)data;
+  for (size_t i = 0; i < bytes; ++i) {
+    h ^= p[i];
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
+__global__ void k_hash_eps(const double* __restrict__ eps, long n, unsigned long long* out) {
+  unsigned long long h = 0;
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
+    unsigned long long v = (unsigned long long)__double_as_longlong(eps[t]);
+    v ^= (unsigned long long)t * 0x9e3779b97f4a7c15ull;
+    v *= 0xbf58476d1ce4e5b9ull;
+    v ^= v >> 31;
+    h += v;
+  }
+  atomicAdd(out, h);
+}
+
+__global__ void k_rq(const double* __restrict__ parts, double* __restrict__ lam, int n) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < n) lam[c] = parts[2 * c + 1] / parts[2 * c];
+}
+
+template <class T> __global__ void k_axpy(cx<T>* __restrict__ y, const cx<T>* __restrict__ x, long n) {
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x)
+    y[t] = y[t] + x[t];
+}
+
+__global__ void k_sub_from(const double2* __restrict__ e, double2* __restrict__ w, long n) {  // w = e - w
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x)
+    w[t] = e[t] - w[t];
+}
+
+// Per-iteration trace on stderr when the environment sets PBS_VERBOSE (diagnostics only).
+bool verbose() {
+  static const bool v = std::getenv("PBS_VERBOSE") != nullptr;
+  return v;
+}
+
+inline unsigned nblocks(long n) { return (unsigned)std::min<long>(std::max<long>((n + 255) / 256, 1), 4096); }
+
+}  // namespace
+
+// Solver workspace for one (hierarchy, block width) pair.
+struct Work {
+  int p = 0;
+  long D = 0, N = 0;
+  double2 *S = nullptr, *T2 = nullptr, *R = nullptr, *hist = nullptr, *gwork = nullptr;
+  double2 *GM = nullptr, *GA = nullptr, *C = nullptr, *rr_scr = nullptr, *gpart = nullptr;
+  double *theta = nullptr, *lam = nullptr, *parts = nullptr, *norms = nullptr, *rq = nullptr;
+  int* info = nullptr;
+  int gpart_n = 0;
+  // preconditioner / projection buffers (FP32 and FP64 variants)
+  float2 *r32 = nullptr, *w32 = nullptr, *nb32 = nullptr, *nx32 = nullptr, *nr32 = nullptr, *nd32 = nullptr;
+  double2 *nb64 = nullptr, *nx64 = nullptr, *nr64 = nullptr, *nd64 = nullptr;
+  MgWork<float> e32, n32;
+  MgWork<double> e64, n64;
+  std::vector<void*> allocs;
+};
+
+}  // namespace pbs
+
+using namespace pbs;
+
+struct pbs_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  DevMem mem;
+  Hierarchy H;
+  bool have_h = false;
+  int coarsest = 0;
+  KData K;
+  Work W;
+  bool have_w = false;
+  double last_theta_max = 1e300;  // largest Ritz value of the latest start block
+  explicit pbs_ctx(size_t budget) : mem(budget) {}
+};
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) PBS_CUDA(cudaSetDevice(dev));
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+void validate_opts(const pbs_opts& o) {
+  if (o.nev < 1 || o.block < o.nev || o.block > kMaxBlock) fail(PBS_EINVAL, "need 1 <= nev <= block <= 32");
+  if (o.max_iter < 0) fail(PBS_EINVAL, "max_iter must be >= 0");
+  if (o.precision != PBS_FP64 && o.precision != PBS_MIXED) fail(PBS_EINVAL, "unknown precision");
+  if (o.span < 1 || o.span > 3) fail(PBS_EINVAL, "span must be 1, 2 or 3");
+  if (!(o.tol > 0)) fail(PBS_EINVAL, "tol must be positive");
+  if (o.nu_pre < 0 || o.nu_post < 0 || o.nu_pre + o.nu_post < 1) fail(PBS_EINVAL, "need nu_pre + nu_post >= 1");
+  if (o.coarsest < 2) fail(PBS_EINVAL, "coarsest must be >= 2");
+  if (o.nodal_cycles < 1) fail(PBS_EINVAL, "nodal_cycles must be >= 1");
+  if (o.extrap_depth < 0 || o.extrap_depth > 3) fail(PBS_EINVAL, "extrap_depth must be 0..3");
+}
+
+void validate_mesh(double a, double b, int n, int m) {
+  if (!(a > 0) || !(b > 0) || !std::isfinite(a) || !std::isfinite(b)) fail(PBS_EINVAL, "a, b must be positive");
+  if (n < 4 || m < 4 || (n & 1) || (m & 1)) fail(PBS_EINVAL, "n, m must be even and >= 4");
+  if ((long)n * m > (1L << 28)) fail(PBS_EINVAL, "mesh too large");
+}
+
+double effective_mu(const pbs_opts& o, double a, double b) { return o.mu > 0 ? o.mu : 1.0 / (a * b); }
+
+// Make the context's hierarchy match (geometry, mu, coarsest); eps on the device.
+void ensure_hierarchy(pbs_ctx* ctx, double a, double b, int n, int m, const double* d_eps, uint64_t eps_hash, double mu,
+                      int coarsest) {
+  uint64_t key = eps_hash;
+  key = fnv1a(&a, sizeof a, key);
+  key = fnv1a(&b, sizeof b, key);
+  key = fnv1a(&n, sizeof n, key);
+  key = fnv1a(&m, sizeof m, key);
+  key = fnv1a(&mu, sizeof mu, key);
+  key = fnv1a(&coarsest, sizeof coarsest, key);
+  if (ctx->have_h && ctx->H.key == key) return;
+  if (ctx->have_w) {
+    // workspaces depend on the hierarchy sizes
+    for (void* p : ctx->W.allocs) ctx->mem.free(p);
+    free_mg_work(ctx->mem, ctx->W.e32);
+    free_mg_work(ctx->mem, ctx->W.n32);
+    free_mg_work(ctx->mem, ctx->W.e64);
+    free_mg_work(ctx->mem, ctx->W.n64);
+    ctx->W = Work();
+    ctx->have_w = false;
+  }
+  if (ctx->have_h) free_hierarchy(ctx->mem, ctx->H);
+  free_kdata(ctx->mem, ctx->K);
+  ctx->have_h = false;
+  ctx->H = Hierarchy();
+  ctx->H.a = a;
+  ctx->H.b = b;
+  ctx->H.n = n;
+  ctx->H.m = m;
+  ctx->H.mu = mu;
+  build_hierarchy(ctx->mem, ctx->H, d_eps, coarsest, ctx->stream);
+  ctx->H.key = key;
+  ctx->coarsest = coarsest;
+  ctx->have_h = true;
+}
+
+// Upload host eps (hashing it first) and make the hierarchy resident.
+void ensure_hierarchy_host(pbs_ctx* ctx, const pbs_geom* g, double mu, int coarsest) {
+  validate_mesh(g->a, g->b, g->n, g->m);
+  if (!g->eps) fail(PBS_EINVAL, "eps is NULL");
+  const long N = (long)g->n * g->m;
+  const uint64_t h = fnv1a(g->eps, N * sizeof(double));
+  uint64_t key = h;
+  key = fnv1a(&g->a, sizeof g->a, key);
+  key = fnv1a(&g->b, sizeof g->b, key);
+  key = fnv1a(&g->n, sizeof g->n, key);
+  key = fnv1a(&g->m, sizeof g->m, key);
+  key = fnv1a(&mu, sizeof mu, key);
+  key = fnv1a(&coarsest, sizeof coarsest, key);
+  if (ctx->have_h && ctx->H.key == key) return;
+  double* d_eps = (double*)ctx->mem.alloc(N * sizeof(double));
+  try {
+    PBS_CUDA(cudaMemcpyAsync(d_eps, g->eps, N * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    ensure_hierarchy(ctx, g->a, g->b, g->n, g->m, d_eps, h, mu, coarsest);
+  } catch (...) {
+    ctx->mem.free(d_eps);
+    throw;
+  }
+  PBS_CUDA(cudaStreamSynchronize(ctx->stream));
+  ctx->mem.free(d_eps);
+}
+
+uint64_t device_eps_hash(pbs_ctx* ctx, const double* d_eps, long N) {
+  unsigned long long* d_h = (unsigned long long*)ctx->mem.alloc(sizeof(unsigned long long));
+  unsigned long long h = 0;
+  PBS_CUDA(cudaMemsetAsync(d_h, 0, sizeof h, ctx->stream));
+  k_hash_eps<<<nblocks(N), 256, 0, ctx->stream>>>(d_eps, N, d_h);
+  PBS_CUDA(cudaGetLastError());
+  PBS_CUDA(cudaMemcpyAsync(&h, d_h, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
+  PBS_CUDA(cudaStreamSynchronize(ctx->stream));
+  ctx->mem.free(d_h);
+  return h;
+}
+
+void ensure_work(pbs_ctx* ctx, int p) {
+  Work& W = ctx->W;
+  if (ctx->have_w && W.p == p) return;
+  if (ctx->have_w) {
+    for (void* q : W.allocs) ctx->mem.free(q);
+    free_mg_work(ctx->mem, W.e32);
+    free_mg_work(ctx->mem, W.n32);
+    free_mg_work(ctx->mem, W.e64);
+    free_mg_work(ctx->mem, W.n64);
+    W = Work();
+    ctx->have_w = false;
+  }
+  const Hierarchy& H = ctx->H;
+  W.p = p;
+  W.D = H.lev[0].D();
+  W.N = H.lev[0].N();
+  const int q = 3 * p;
+  auto A = [&](size_t bytes) {
+    void* ptr = ctx->mem.alloc(bytes);
+    W.allocs.push_back(ptr);
+    return ptr;
+  };
+  const long D = W.D, N = W.N;
+  W.S = (double2*)A(sizeof(double2) * D * q);
+  W.T2 = (double2*)A(sizeof(double2) * D * 2 * p);
+  W.R = (double2*)A(sizeof(double2) * D * p);
+  W.hist = (double2*)A(sizeof(double2) * D * 3 * p);
+  W.gwork = (double2*)A(sizeof(double2) * (D + N) * q);
+  W.GM = (double2*)A(sizeof(double2) * q * q);
+  W.GA = (double2*)A(sizeof(double2) * q * q);
+  W.C = (double2*)A(sizeof(double2) * q * p);
+  W.rr_scr = (double2*)A(small_rr_scratch(q));
+  W.gpart_n = 2 * 152;
+  W.gpart = (double2*)A(sizeof(double2) * W.gpart_n * (q * (q + 1) / 2));
+  W.theta = (double*)A(sizeof(double) * q);
+  W.lam = (double*)A(sizeof(double) * q);
+  const long nblk = ((H.lev[0].n + 31) / 32) * ((H.lev[0].m + 7) / 8);
+  W.parts = (double*)A(sizeof(double) * std::max<long>(2 * nblk * q, 4 * 64 * q));
+  W.norms = (double*)A(sizeof(double) * 2 * q);
+  W.rq = (double*)A(sizeof(double) * 2 * q);
+  W.info = (int*)A(sizeof(int) * 4);
+  // preconditioner: p columns; projection: up to 3p columns (extrapolation spans)
+  W.r32 = (float2*)A(sizeof(float2) * D * p);
+  W.w32 = (float2*)A(sizeof(float2) * D * p);
+  W.nb32 = (float2*)A(sizeof(float2) * N * q);
+  W.nx32 = (float2*)A(sizeof(float2) * N * q);
+  W.nr32 = (float2*)A(sizeof(float2) * N * q);
+  W.nd32 = (float2*)A(sizeof(float2) * N * q);
+  W.nb64 = (double2*)A(sizeof(double2) * N * q);
+  W.nx64 = (double2*)A(sizeof(double2) * N * q);
+  W.nr64 = (double2*)A(sizeof(double2) * N * q);
+  W.nd64 = (double2*)A(sizeof(double2) * N * q);
+  alloc_mg_work<float>(ctx->mem, H, p, false, W.e32);
+  alloc_mg_work<float>(ctx->mem, H, q, true, W.n32);
+  alloc_mg_work<double>(ctx->mem, H, p, false, W.e64);
+  alloc_mg_work<double>(ctx->mem, H, q, true, W.n64);
+  ctx->have_w = true;
+}
+
+// --- steps of the iteration ---------------------------------------------------
+
+template <class T> struct Bufs;
+template <> struct Bufs<float> {
+  static float2* nb(Work& W) { return W.nb32; }
+  static float2* nx(Work& W) { return W.nx32; }
+  static float2* nr(Work& W) { return W.nr32; }
+  static float2* nd(Work& W) { return W.nd32; }
+  static MgWork<float>& emg(Work& W) { return W.e32; }
+  static MgWork<float>& nmg(Work& W) { return W.n32; }
+};
+template <> struct Bufs<double> {
+  static double2* nb(Work& W) { return W.nb64; }
+  static double2* nx(Work& W) { return W.nx64; }
+  static double2* nr(Work& W) { return W.nr64; }
+  static double2* nd(Work& W) { return W.nd64; }
+  static MgWork<double>& emg(Work& W) { return W.e64; }
+  static MgWork<double>& nmg(Work& W) { return W.n64; }
+};
+
+// X <- X - L phi with phi from `cycles` nodal V-cycles on L^* M L phi = L^* M X; at k = 0
+// the two constant edge fields are removed as well (Section 4).
+template <class T>
+void project(pbs_ctx* ctx, const pbs_opts& o, double2* X, int ncols, int cycles, cudaStream_t s) {
+  if (ncols <= 0) return;
+  Work& W = ctx->W;
+  const Hierarchy& H = ctx->H;
+  const KData& K = ctx->K;
+  const Level& L0 = H.lev[0];
+  const long N = L0.N(), D = L0.D();
+  cx<T>* rhs = (cx<T>*)Bufs<T>::nb(W);
+  cx<T>* phi = (cx<T>*)Bufs<T>::nx(W);
+  cx<T>* res = (cx<T>*)Bufs<T>::nr(W);
+  cx<T>* dphi = (cx<T>*)Bufs<T>::nd(W);
+  lift_adj_mass<T>(L0, K.d_ph, ncols, X, D, rhs, N, ncols, s);
+  nodal_vcycle<T>(H, K, Bufs<T>::nmg(W), 0, rhs, phi, N, ncols, o.nu_pre, o.nu_post, s);
+  for (int c = 1; c < cycles; ++c) {
+    apply_nodal<T>(L0, K.d_ph, ncols, phi, res, rhs, N, ncols, T(-1), T(1), s);
+    nodal_vcycle<T>(H, K, Bufs<T>::nmg(W), 0, res, dphi, N, ncols, o.nu_pre, o.nu_post, s);
+    k_axpy<T><<<nblocks(N * ncols), 256, 0, s>>>(phi, dphi, N * ncols);
+    PBS_CUDA(cudaGetLastError());
+  }
+  sub_lift<T>(L0, K.d_ph, ncols, phi, N, X, D, ncols, s);
+  if (K.gamma) deflate_constants(L0, X, D, ncols, W.parts, s);
+}
+
+// W = B R (one edge V-cycle per column, precision T)
+template <class T> void precondition(pbs_ctx* ctx, const pbs_opts& o, const double2* R, double2* Wout, int ncols,
+                                     cudaStream_t s);
+template <>
+void precondition<double>(pbs_ctx* ctx, const pbs_opts& o, const double2* R, double2* Wout, int ncols, cudaStream_t s) {
+  edge_vcycle<double>(ctx->H, ctx->K, ctx->W.e64, 0, R, Wout, ctx->W.D, ncols, o.nu_pre, o.nu_post, s);
+}
+template <>
+void precondition<float>(pbs_ctx* ctx, const pbs_opts& o, const double2* R, double2* Wout, int ncols, cudaStream_t s) {
+  Work& W = ctx->W;
+  convert_d2f(R, W.r32, W.D * ncols, s);
+  edge_vcycle<float>(ctx->H, ctx->K, W.e32, 0, W.r32, W.w32, W.D, ncols, o.nu_pre, o.nu_post, s);
+  convert_f2d(W.w32, Wout, W.D * ncols, s);
+}
+
+void project_dispatch(pbs_ctx* ctx, const pbs_opts& o, double2* X, int ncols, cudaStream_t s, int cycles = 0) {
+  if (cycles <= 0) cycles = o.nodal_cycles;
+  if (o.precision == PBS_MIXED) project<float>(ctx, o, X, ncols, cycles, s);
+  else project<double>(ctx, o, X, ncols, cycles, s);
+}
+
+// Nodal cycles for the iteration's projections.  The preconditioner maps a
+// gradient left in an iterate to about -(lambda/mu) times itself (A + mu M acts
+// as mu M on gradients), so iterates with large Rayleigh quotients need a more
+// accurate projection: one extra cycle (contraction about 0.1 each) per two
+// decades of lambda/mu.
+int projection_cycles(const pbs_opts& o, double theta_max, double mu) {
+  const double ratio = theta_max / mu;
+  const int extra = ratio > 1.0 ? (int)std::floor(std::log10(ratio) / 2.0) : 0;
+  return o.nodal_cycles + std::min(extra, 6);
+}
+void precondition_dispatch(pbs_ctx* ctx, const pbs_opts& o, const double2* R, double2* Wout, int ncols,
+                           cudaStream_t s) {
+  if (o.precision == PBS_MIXED) precondition<float>(ctx, o, R, Wout, ncols, s);
+  else precondition<double>(ctx, o, R, Wout, ncols, s);
+}
+
+// Rayleigh-Ritz on S[:, 0:q] -> E = S C (p columns, written to dst); theta on device.
+void rayleigh_ritz_step(pbs_ctx* ctx, const double2* S, int q, int p, double2* dst, cudaStream_t s) {
+  Work& W = ctx->W;
+  const Level& L0 = ctx->H.lev[0];
+  gram(L0, ctx->K.d_ph, q, S, W.D, q, W.GM, W.GA, W.gwork, W.gpart, W.gpart_n, s);
+  small_rr(W.GM, W.GA, q, p, W.C, W.theta, W.rr_scr, W.info, s);
+  int info[2] = {0, 0};
+  PBS_CUDA(cudaMemcpyAsync(info, W.info, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+  PBS_CUDA(cudaStreamSynchronize(s));
+  if (info[0] != 0) fail(PBS_ENUMERIC, info[0] == -2 ? "non-finite Gram matrix" : "trial space lost rank");
+  block_update(S, W.D, q, W.C, q, dst, W.D, p, nullptr, 0, W.D, s);
+}
+
+struct KResult {
+  std::vector<double> lam, res;
+  int iters = 0;
+  bool converged = false;
+};
+
+// The iteration at the current k (ctx->K set up) starting from the p columns in S[:, 0:p].
+KResult iterate(pbs_ctx* ctx, const pbs_opts& o, cudaStream_t s) {
+  Work& W = ctx->W;
+  const Level& L0 = ctx->H.lev[0];
+  const double* ph = ctx->K.d_ph;
+  const int p = o.block;
+  const long D = W.D;
+  double2* E = W.S;
+  double2* Wd = W.S + D * p;
+  double2* P = W.S + 2 * D * p;
+  bool have_p = false;
+  KResult out;
+  std::vector<double> h_norms(2 * p), h_lam(p);
+  double theta_max = ctx->last_theta_max;
+  const double mu = ctx->H.mu;
+  for (int it = 0;; ++it) {
+    // Rayleigh-Ritz prefers combinations whose leftover gradient lowers the
+    // quotient, so the new block (and the search direction) is cleaned before
+    // its residual is formed (Section 4, null-space elimination).
+    const int cyc = projection_cycles(o, theta_max, mu);
+    if (it > 0) {
+      project_dispatch(ctx, o, E, p, s, cyc);
+      if (have_p) project_dispatch(ctx, o, P, p, s, cyc);
+    }
+    // Rayleigh quotients in factored form, then the FP64 residual
+    rayleigh_parts(L0, ph, p, E, D, p, W.parts, W.rq, s);
+    k_rq<<<1, 64, 0, s>>>(W.rq, W.lam, p);
+    PBS_CUDA(cudaGetLastError());
+    residual(L0, ph, p, E, W.R, D, p, W.lam, W.parts, W.norms, s);
+    PBS_CUDA(cudaMemcpyAsync(h_norms.data(), W.norms, 2 * p * sizeof(double), cudaMemcpyDeviceToHost, s));
+    PBS_CUDA(cudaMemcpyAsync(h_lam.data(), W.lam, p * sizeof(double), cudaMemcpyDeviceToHost, s));
+    PBS_CUDA(cudaStreamSynchronize(s));
+    out.lam.assign(h_lam.begin(), h_lam.begin() + o.nev);
+    theta_max = 0.0;
+    for (int j = 0; j < p; ++j) theta_max = std::max(theta_max, std::fabs(h_lam[j]));
+    out.res.resize(o.nev);
+    bool conv = true;
+    for (int j = 0; j < o.nev; ++j) {
+      const double r = std::sqrt(h_norms[2 * j]) / (std::fabs(h_lam[j]) * std::sqrt(h_norms[2 * j + 1]));
+      if (!std::isfinite(r) || !std::isfinite(h_lam[j])) fail(PBS_ENUMERIC, "non-finite residual");
+      out.res[j] = r;
+      conv = conv && r <= o.tol;
+    }
+    out.iters = it;
+    if (verbose()) {
+      std::fprintf(stderr, "[pbs] k=(%.6f,%.6f) it=%d", ctx->K.k1, ctx->K.k2, it);
+      for (int j = 0; j < p; ++j)
+        std::fprintf(stderr, " %.10g/%.1e", h_lam[j],
+                     std::sqrt(h_norms[2 * j]) / (std::fabs(h_lam[j]) * std::sqrt(h_norms[2 * j + 1])));
+      std::fprintf(stderr, "\n");
+    }
+    if (conv) {
+      out.converged = true;
+      return out;
+    }
+    if (it >= o.max_iter) return out;
+    precondition_dispatch(ctx, o, W.R, Wd, p, s);
+    int q;
+    const double2* trial;
+    if (o.span == 1) {
+      k_sub_from<<<nblocks(D * p), 256, 0, s>>>(E, Wd, D * p);  // E_hat = E - B R
+      PBS_CUDA(cudaGetLastError());
+      project_dispatch(ctx, o, Wd, p, s, cyc);
+      q = p;
+      trial = Wd;
+    } else {
+      project_dispatch(ctx, o, Wd, p, s, cyc);
+      q = (o.span == 3 && have_p) ? 3 * p : 2 * p;
+      trial = E;  // [E, W, P] are contiguous
+    }
+    gram(L0, ph, q, trial, D, q, W.GM, W.GA, W.gwork, W.gpart, W.gpart_n, s);
+    small_rr(W.GM, W.GA, q, p, W.C, W.theta, W.rr_scr, W.info, s);
+    int info[2] = {0, 0};
+    PBS_CUDA(cudaMemcpyAsync(info, W.info, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    PBS_CUDA(cudaStreamSynchronize(s));
+    if (info[0] != 0) {
+      if (info[0] == -2) fail(PBS_ENUMERIC, "non-finite Gram matrix");
+      // rank loss in the LOBPCG basis: restart without the search direction
+      if (have_p) {
+        have_p = false;
+        q = 2 * p;
+        gram(L0, ph, q, trial, D, q, W.GM, W.GA, W.gwork, W.gpart, W.gpart_n, s);
+        small_rr(W.GM, W.GA, q, p, W.C, W.theta, W.rr_scr, W.info, s);
+        PBS_CUDA(cudaMemcpyAsync(info, W.info, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+        PBS_CUDA(cudaStreamSynchronize(s));
+      }
+      if (info[0] != 0) fail(PBS_ENUMERIC, "trial space lost rank");
+    }
+    double2* Enew = W.T2;
+    double2* Pnew = W.T2 + D * p;
+    if (o.span == 3) {
+      // P_new = [W, P] C[p:q], E_new = E C[0:p] + P_new
+      block_update(Wd, D, q - p, W.C + p, q, Pnew, D, p, nullptr, 0, D, s);
+      block_update(E, D, p, W.C, q, Enew, D, p, Pnew, D, D, s);
+      PBS_CUDA(cudaMemcpyAsync(E, Enew, sizeof(double2) * D * p, cudaMemcpyDeviceToDevice, s));
+      PBS_CUDA(cudaMemcpyAsync(P, Pnew, sizeof(double2) * D * p, cudaMemcpyDeviceToDevice, s));
+      have_p = true;
+    } else {
+      block_update(trial, D, q, W.C, q, Enew, D, p, nullptr, 0, D, s);
+      PBS_CUDA(cudaMemcpyAsync(E, Enew, sizeof(double2) * D * p, cudaMemcpyDeviceToDevice, s));
+    }
+  }
+}
+
+// Initial block: S[:, 0:p] from `init` (host), from the history (extrapolation), or random.
+void initial_block(pbs_ctx* ctx, const pbs_opts& o, const pbs_c64* init, int nhist, cudaStream_t s) {
+  Work& W = ctx->W;
+  const int p = o.block;
+  const long D = W.D;
+  if (nhist > 0) {
+    // S = [E_{k-1}, E_{k-2}, ...] as stored coefficient vectors (Section 6)
+    const int q = nhist * p;
+    PBS_CUDA(cudaMemcpyAsync(W.S, W.hist, sizeof(double2) * D * q, cudaMemcpyDeviceToDevice, s));
+    project_dispatch(ctx, o, W.S, q, s, projection_cycles(o, ctx->last_theta_max, ctx->H.mu));
+    rayleigh_ritz_step(ctx, W.S, q, p, W.T2, s);
+  } else {
+    if (init) PBS_CUDA(cudaMemcpyAsync(W.S, init, sizeof(double2) * D * p, cudaMemcpyHostToDevice, s));
+    else random_block(W.S, D, D, p, o.seed, s);
+    // A block with no relation to the spectrum has Rayleigh quotients near the top
+    // of it.  Two inverse-iteration steps E <- B M E (each followed by the
+    // projection and Rayleigh-Ritz) damp the high frequencies by about
+    // (lambda_low + mu) / (lambda_high + mu) before the iteration starts.
+    const int cyc = projection_cycles(o, 1e300, ctx->H.mu);
+    project_dispatch(ctx, o, W.S, p, s, cyc);
+    rayleigh_ritz_step(ctx, W.S, p, p, W.T2, s);
+    for (int step = 0; step < 2; ++step) {
+      apply_edge<double>(ctx->H.lev[0], ctx->K.d_ph, p, W.T2, W.R, nullptr, D, p, 0.0, 1.0, 0.0, nullptr, 0.0, s);
+      precondition_dispatch(ctx, o, W.R, W.S, p, s);
+      project_dispatch(ctx, o, W.S, p, s, cyc);
+      rayleigh_ritz_step(ctx, W.S, p, p, W.T2, s);
+    }
+  }
+  PBS_CUDA(cudaMemcpyAsync(W.S, W.T2, sizeof(double2) * D * p, cudaMemcpyDeviceToDevice, s));
+  // largest Ritz value of the start block, for the projection accuracy
+  std::vector<double> th(p);
+  PBS_CUDA(cudaMemcpyAsync(th.data(), W.theta, sizeof(double) * p, cudaMemcpyDeviceToHost, s));
+  PBS_CUDA(cudaStreamSynchronize(s));
+  ctx->last_theta_max = 0.0;
+  for (double t : th) ctx->last_theta_max = std::max(ctx->last_theta_max, std::fabs(t));
+}
+
+void set_k(pbs_ctx* ctx, double k1, double k2) { build_kdata(ctx->mem, ctx->H, ctx->K, k1, k2, ctx->stream); }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+
+namespace {
+int run_guarded_impl(const std::function<void()>& f) {
+  try {
+    g_last_error.clear();
+    f();
+    return PBS_OK;
+  } catch (const Error& e) {
+    g_last_error = e.what;
+    return e.status;
+  } catch (const std::bad_alloc&) {
+    g_last_error = "host allocation failed";
+    return PBS_ENOMEM;
+  } catch (...) {
+    g_last_error = "unexpected failure";
+    return PBS_ECUDA;
+  }
+}
+}  // namespace
+
+extern "C" {
+
+const char* pbs_strerror(int status) {
+  switch (status) {
+    case PBS_OK: return "ok";
+    case PBS_EINVAL: return "invalid argument";
+    case PBS_ENOMEM: return "out of device memory or over the budget";
+    case PBS_ENOCONV: return "not converged within max_iter";
+    case PBS_ENUMERIC: return "numerical breakdown";
+    case PBS_ETIMEOUT: return "device wait timed out";
+    case PBS_ECUDA: return "CUDA error";
+    default: return "unknown status";
+  }
+}
+
+const char* pbs_last_error(void) { return g_last_error.c_str(); }
+
+void pbs_default_opts(pbs_opts* o) {
+  if (!o) return;
+  o->nev = 4;
+  o->block = 6;
+  o->max_iter = 400;
+  o->precision = PBS_MIXED;
+  o->span = 3;
+  o->tol = 1e-8;
+  o->mu = 0.0;
+  o->nu_pre = 1;
+  o->nu_post = 1;
+  o->coarsest = 4;
+  o->nodal_cycles = 2;
+  o->extrap_depth = 3;
+  o->seed = 0;
+}
+
+int pbs_num_levels(int n, int m, int coarsest) {
+  if (n < 2 || m < 2 || coarsest < 2) return PBS_EINVAL;
+  return num_levels(n, m, coarsest);
+}
+
+int pbs_create(pbs_ctx** ctx, int device, size_t hbm_budget_bytes) {
+  if (!ctx) return PBS_EINVAL;
+  *ctx = nullptr;
+  return run_guarded_impl([&] {
+    int count = 0;
+    PBS_CUDA(cudaGetDeviceCount(&count));
+    if (device < 0 || device >= count) fail(PBS_EINVAL, "no such CUDA device");
+    DeviceGuard g(device);
+    std::unique_ptr<pbs_ctx> c(new pbs_ctx(hbm_budget_bytes));
+    c->device = device;
+    PBS_CUDA(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+    *ctx = c.release();
+  });
+}
+
+int pbs_destroy(pbs_ctx* ctx) {
+  if (!ctx) return PBS_OK;
+  return run_guarded_impl([&] {
+    DeviceGuard g(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    if (ctx->have_w) {
+      for (void* p : ctx->W.allocs) ctx->mem.free(p);
+      free_mg_work(ctx->mem, ctx->W.e32);
+      free_mg_work(ctx->mem, ctx->W.n32);
+      free_mg_work(ctx->mem, ctx->W.e64);
+      free_mg_work(ctx->mem, ctx->W.n64);
+    }
+    if (ctx->have_h) free_hierarchy(ctx->mem, ctx->H);
+    free_kdata(ctx->mem, ctx->K);
+    cudaStreamDestroy(ctx->stream);
+    delete ctx;
+  });
+}
+
+int pbs_solve_k(pbs_ctx* ctx, const pbs_geom* geom, const pbs_opts* opts, const double k[2], const pbs_c64* init,
+                double* eigvals, double* resid, int* iters, pbs_c64* evecs) {
+  if (!ctx || !geom || !opts || !k || !eigvals || !resid || !iters) return PBS_EINVAL;
+  int status = PBS_OK;
+  const int rc = run_guarded_impl([&] {
+    DeviceGuard g(ctx->device);
+    const pbs_opts& o = *opts;
+    validate_opts(o);
+    ensure_hierarchy_host(ctx, geom, effective_mu(o, geom->a, geom->b), o.coarsest);
+    ensure_work(ctx, o.block);
+    set_k(ctx, k[0], k[1]);
+    initial_block(ctx, o, init, 0, ctx->stream);
+    const KResult r = iterate(ctx, o, ctx->stream);
+    for (int j = 0; j < o.nev; ++j) {
+      eigvals[j] = r.lam[j];
+      resid[j] = r.res[j];
+    }
+    *iters = r.iters;
+    if (evecs) {
+      // M-normalise the returned columns
+      Work& W = ctx->W;
+      std::vector<double> rq(2 * o.block), sc(o.block);
+      rayleigh_parts(ctx->H.lev[0], ctx->K.d_ph, o.block, W.S, W.D, o.block, W.parts, W.rq, ctx->stream);
+      PBS_CUDA(cudaMemcpyAsync(rq.data(), W.rq, 2 * o.block * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+      PBS_CUDA(cudaStreamSynchronize(ctx->stream));
+      for (int j = 0; j < o.block; ++j) sc[j] = 1.0 / std::sqrt(rq[2 * j]);
+      PBS_CUDA(cudaMemcpyAsync(W.lam, sc.data(), o.block * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+      scale_columns(W.S, W.D, W.D, o.nev, W.lam, ctx->stream);
+      PBS_CUDA(cudaMemcpyAsync(evecs, W.S, sizeof(double2) * W.D * o.nev, cudaMemcpyDeviceToHost, ctx->stream));
+      PBS_CUDA(cudaStreamSynchronize(ctx->stream));
+    }
+    if (!r.converged) status = PBS_ENOCONV;
+  });
+  return rc != PBS_OK ? rc : status;
+}
+
+namespace {
+// Shared body of the two path entry points; ks/results on the host.
+int solve_path_impl(pbs_ctx* ctx, const pbs_opts& o, int nk, const double* ks, double* eigvals, double* resid,
+                    int* iters) {
+  int first_bad = PBS_OK;
+  Work& W = ctx->W;
+  const int p = o.block;
+  const long D = W.D;
+  int nhist = 0;
+  for (int t = 0; t < nk; ++t) {
+    set_k(ctx, ks[2 * t], ks[2 * t + 1]);
+    initial_block(ctx, o, nullptr, std::min(nhist, o.extrap_depth), ctx->stream);
+    KResult r = iterate(ctx, o, ctx->stream);
+    for (int j = 0; j < o.nev; ++j) {
+      eigvals[(long)t * o.nev + j] = r.lam[j];
+      resid[(long)t * o.nev + j] = r.res[j];
+    }
+    iters[t] = r.iters;
+    if (!r.converged && first_bad == PBS_OK) first_bad = PBS_ENOCONV;
+    // history ring: newest first
+    if (o.extrap_depth > 0) {
+      const int keep = std::min(nhist, 2);
+      if (keep > 0)
+        PBS_CUDA(cudaMemcpyAsync(W.hist + D * p, W.hist, sizeof(double2) * D * p * keep, cudaMemcpyDeviceToDevice,
+                                 ctx->stream));
+      PBS_CUDA(cudaMemcpyAsync(W.hist, W.S, sizeof(double2) * D * p, cudaMemcpyDeviceToDevice, ctx->stream));
+      nhist = std::min(nhist + 1, 3);
+    }
+  }
+  return first_bad;
+}
+}  // namespace
+
+int pbs_solve_path(pbs_ctx* ctx, const pbs_geom* geom, const pbs_opts* opts, int nk, const double* ks,
+                   double* eigvals, double* resid, int* iters) {
+  if (!ctx || !geom || !opts || nk < 0 || (nk > 0 && (!ks || !eigvals || !resid || !iters))) return PBS_EINVAL;
+  int status = PBS_OK;
+  const int rc = run_guarded_impl([&] {
+    DeviceGuard g(ctx->device);
+    validate_opts(*opts);
+    if (nk == 0) return;
+    ensure_hierarchy_host(ctx, geom, effective_mu(*opts, geom->a, geom->b), opts->coarsest);
+    ensure_work(ctx, opts->block);
+    status = solve_path_impl(ctx, *opts, nk, ks, eigvals, resid, iters);
+  });
+  return rc != PBS_OK ? rc : status;
+}
+
+int pbs_solve_path_device(pbs_ctx* ctx, double a, double b, int n, int m, const double* d_eps, const pbs_opts* opts,
+                          int nk, const double* d_ks, double* d_eigvals, double* d_resid, int* d_iters,
+                          void* cuda_stream) {
+  if (!ctx || !opts || nk < 0 || !d_eps || (nk > 0 && (!d_ks || !d_eigvals || !d_resid || !d_iters)))
+    return PBS_EINVAL;
+  int status = PBS_OK;
+  const int rc = run_guarded_impl([&] {
+    DeviceGuard g(ctx->device);
+    validate_opts(*opts);
+    validate_mesh(a, b, n, m);
+    cudaStream_t us = (cudaStream_t)cuda_stream;
+    // order the library stream after the caller's work on the inputs
+    cudaEvent_t ev;
+    PBS_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    PBS_CUDA(cudaEventRecord(ev, us));
+    PBS_CUDA(cudaStreamWaitEvent(ctx->stream, ev, 0));
+    if (nk == 0) {
+      cudaEventDestroy(ev);
+      return;
+    }
+    const uint64_t h = device_eps_hash(ctx, d_eps, (long)n * m);
+    ensure_hierarchy(ctx, a, b, n, m, d_eps, h, effective_mu(*opts, a, b), opts->coarsest);
+    ensure_work(ctx, opts->block);
+    std::vector<double> ks(2 * nk), ev_h((long)nk * opts->nev), rs_h((long)nk * opts->nev);
+    std::vector<int> it_h(nk);
+    PBS_CUDA(cudaMemcpyAsync(ks.data(), d_ks, sizeof(double) * 2 * nk, cudaMemcpyDeviceToHost, ctx->stream));
+    PBS_CUDA(cudaStreamSynchronize(ctx->stream));
+    status = solve_path_impl(ctx, *opts, nk, ks.data(), ev_h.data(), rs_h.data(), it_h.data());
+    PBS_CUDA(cudaMemcpyAsync(d_eigvals, ev_h.data(), sizeof(double) * ev_h.size(), cudaMemcpyHostToDevice, ctx->stream));
+    PBS_CUDA(cudaMemcpyAsync(d_resid, rs_h.data(), sizeof(double) * rs_h.size(), cudaMemcpyHostToDevice, ctx->stream));
+    PBS_CUDA(cudaMemcpyAsync(d_iters, it_h.data(), sizeof(int) * it_h.size(), cudaMemcpyHostToDevice, ctx->stream));
+    PBS_CUDA(cudaStreamSynchronize(ctx->stream));
+    cudaEventDestroy(ev);
+  });
+  return rc != PBS_OK ? rc : status;
+}
+
+int pbs_apply(pbs_ctx* ctx, const pbs_geom* geom, const pbs_opts* opts, int op, int level, const double k[2],
+              int ncols, const pbs_c64* x, pbs_c64* y, void* cuda_stream) {
+  if (!ctx || !geom || !opts || !k || ncols < 0) return PBS_EINVAL;
+  if (ncols > 0 && (!x || !y)) return PBS_EINVAL;
+  return run_guarded_impl([&] {
+    DeviceGuard g(ctx->device);
+    const pbs_opts& o = *opts;
+    if (o.precision != PBS_FP64 && o.precision != PBS_MIXED) fail(PBS_EINVAL, "unknown precision");
+    if (o.coarsest < 2 || o.nodal_cycles < 1 || o.nu_pre < 0 || o.nu_post < 0) fail(PBS_EINVAL, "bad multigrid options");
+    ensure_hierarchy_host(ctx, geom, effective_mu(o, geom->a, geom->b), o.coarsest);
+    const Hierarchy& H = ctx->H;
+    if (level < 0 || level >= H.nlev) fail(PBS_EINVAL, "level out of range");
+    const bool transfer = op == PBS_OP_PROLONG || op == PBS_OP_RESTRICT || op == PBS_OP_PROLONG_NODAL ||
+                          op == PBS_OP_RESTRICT_NODAL;
+    if (transfer && level + 1 >= H.nlev) fail(PBS_EINVAL, "no coarser level below `level`");
+    if (op < PBS_OP_A || op > PBS_OP_PROJECT) fail(PBS_EINVAL, "unknown operator");
+    if (op == PBS_OP_PROJECT && level != 0) fail(PBS_EINVAL, "PROJECT acts on level 0");
+    if (ncols == 0) return;
+    set_k(ctx, k[0], k[1]);
+    cudaStream_t us = (cudaStream_t)cuda_stream;
+    cudaStream_t s = ctx->stream;
+    cudaEvent_t ev;
+    PBS_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    PBS_CUDA(cudaEventRecord(ev, us));
+    PBS_CUDA(cudaStreamWaitEvent(s, ev, 0));
+    const Level& L = H.lev[level];
+    const KData& K = ctx->K;
+    const double mu = H.mu;
+    const double2* X = (const double2*)x;
+    double2* Y = (double2*)y;
+    const long D = L.D(), N = L.N();
+    const int cpg = ncols;
+    switch (op) {
+      case PBS_OP_A: apply_edge<double>(L, K.d_ph, cpg, X, Y, nullptr, D, ncols, 1.0, 0.0, 0.0, nullptr, 0.0, s); break;
+      case PBS_OP_M: apply_edge<double>(L, K.d_ph, cpg, X, Y, nullptr, D, ncols, 0.0, 1.0, 0.0, nullptr, 0.0, s); break;
+      case PBS_OP_A_MU_M: apply_edge<double>(L, K.d_ph, cpg, X, Y, nullptr, D, ncols, 1.0, mu, 0.0, nullptr, 0.0, s); break;
+      case PBS_OP_C: apply_curl<double>(L, K.d_ph, cpg, X, D, Y, N, ncols, s); break;
+      case PBS_OP_CH: apply_curl_adj<double>(L, K.d_ph, cpg, X, N, Y, D, ncols, s); break;
+      case PBS_OP_L: apply_lift<double>(L, K.d_ph, cpg, X, N, Y, D, ncols, s); break;
+      case PBS_OP_LH: apply_lift_adj<double>(L, K.d_ph, cpg, X, D, Y, N, ncols, s); break;
+      case PBS_OP_P_NODAL: apply_nodal<double>(L, K.d_ph, cpg, X, Y, nullptr, N, ncols, 1.0, 0.0, s); break;
+      case PBS_OP_PROLONG: {
+        const Level& C = H.lev[level + 1];
+        prolong_edge<double>(L, C, K.d_ph, cpg, X, C.D(), Y, D, ncols, false, s);
+        break;
+      }
+      case PBS_OP_RESTRICT: {
+        const Level& C = H.lev[level + 1];
+        restrict_edge<double>(L, C, K.d_ph, cpg, X, D, Y, C.D(), ncols, s);
+        break;
+      }
+      case PBS_OP_PROLONG_NODAL: {
+        const Level& C = H.lev[level + 1];
+        prolong_node<double>(L, C, K.d_ph, cpg, X, C.N(), Y, N, ncols, false, s);
+        break;
+      }
+      case PBS_OP_RESTRICT_NODAL: {
+        const Level& C = H.lev[level + 1];
+        restrict_node<double>(L, C, K.d_ph, cpg, X, N, Y, C.N(), ncols, s);
+        break;
+      }
+      case PBS_OP_VCYCLE_EDGE:
+      case PBS_OP_VCYCLE_NODAL:
+      case PBS_OP_PROJECT: {
+        // temporary multigrid workspace for ncols columns
+        const bool nodal = op == PBS_OP_VCYCLE_NODAL;
+        const long len = nodal ? N : D;
+        if (op == PBS_OP_PROJECT) {
+          // project a copy: needs the solver buffers for ncols columns
+          Work saved = ctx->W;
+          bool had = ctx->have_w;
+          ctx->have_w = false;
+          ctx->W = Work();
+          try {
+            ensure_work(ctx, std::max(1, (ncols + 2) / 3));
+            if (3 * ctx->W.p < ncols) fail(PBS_EINVAL, "too many columns");
+            PBS_CUDA(cudaMemcpyAsync(Y, X, sizeof(double2) * D * ncols, cudaMemcpyDeviceToDevice, s));
+            project_dispatch(ctx, o, Y, ncols, s);
+            PBS_CUDA(cudaStreamSynchronize(s));
+          } catch (...) {
+            for (void* q : ctx->W.allocs) ctx->mem.free(q);
+            free_mg_work(ctx->mem, ctx->W.e32); free_mg_work(ctx->mem, ctx->W.n32);
+            free_mg_work(ctx->mem, ctx->W.e64); free_mg_work(ctx->mem, ctx->W.n64);
+            ctx->W = saved;
+            ctx->have_w = had;
+            throw;
+          }
+          for (void* q : ctx->W.allocs) ctx->mem.free(q);
+          free_mg_work(ctx->mem, ctx->W.e32); free_mg_work(ctx->mem, ctx->W.n32);
+          free_mg_work(ctx->mem, ctx->W.e64); free_mg_work(ctx->mem, ctx->W.n64);
+          ctx->W = saved;
+          ctx->have_w = had;
+          break;
+        }
+        if (o.precision == PBS_MIXED) {
+          MgWork<float> w;
+          float2* xf = (float2*)ctx->mem.alloc(sizeof(float2) * len * ncols);
+          float2* yf = (float2*)ctx->mem.alloc(sizeof(float2) * len * ncols);
+          try {
+            alloc_mg_work<float>(ctx->mem, H, ncols, nodal, w);
+            convert_d2f(X, xf, len * ncols, s);
+            if (nodal) nodal_vcycle<float>(H, K, w, level, xf, yf, len, ncols, o.nu_pre, o.nu_post, s);
+            else edge_vcycle<float>(H, K, w, level, xf, yf, len, ncols, o.nu_pre, o.nu_post, s);
+            convert_f2d(yf, Y, len * ncols, s);
+            PBS_CUDA(cudaStreamSynchronize(s));
+          } catch (...) {
+            free_mg_work<float>(ctx->mem, w);
+            ctx->mem.free(xf);
+            ctx->mem.free(yf);
+            throw;
+          }
+          free_mg_work<float>(ctx->mem, w);
+          ctx->mem.free(xf);
+          ctx->mem.free(yf);
+        } else {
+          MgWork<double> w;
+          try {
+            alloc_mg_work<double>(ctx->mem, H, ncols, nodal, w);
+            if (nodal) nodal_vcycle<double>(H, K, w, level, X, Y, len, ncols, o.nu_pre, o.nu_post, s);
+            else edge_vcycle<double>(H, K, w, level, X, Y, len, ncols, o.nu_pre, o.nu_post, s);
+            PBS_CUDA(cudaStreamSynchronize(s));
+          } catch (...) {
+            free_mg_work<double>(ctx->mem, w);
+            throw;
+          }
+          free_mg_work<double>(ctx->mem, w);
+        }
+        break;
+      }
+      default: fail(PBS_EINVAL, "unknown operator");
+    }
+    // order the caller's stream after the library's work
+    PBS_CUDA(cudaEventRecord(ev, s));
+    PBS_CUDA(cudaStreamWaitEvent(us, ev, 0));
+    PBS_CUDA(cudaStreamSynchronize(s));
+    cudaEventDestroy(ev);
+  });
+}
+
+int pbs_gram(pbs_ctx* ctx, const pbs_geom* geom, const double k[2], int q, const pbs_c64* S, pbs_c64* GM, pbs_c64* GA,
+             void* cuda_stream) {
+  if (!ctx || !geom || !k || q < 0 || q > kMaxTrial) return PBS_EINVAL;
+  if (q > 0 && (!S || !GM || !GA)) return PBS_EINVAL;
+  return run_guarded_impl([&] {
+    DeviceGuard g(ctx->device);
+    if (q == 0) return;
+    pbs_opts o;
+    pbs_default_opts(&o);
+    ensure_hierarchy_host(ctx, geom, effective_mu(o, geom->a, geom->b), o.coarsest);
+    set_k(ctx, k[0], k[1]);
+    const Level& L0 = ctx->H.lev[0];
+    cudaStream_t s = ctx->stream;
+    cudaEvent_t ev;
+    PBS_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    PBS_CUDA(cudaEventRecord(ev, (cudaStream_t)cuda_stream));
+    PBS_CUDA(cudaStreamWaitEvent(s, ev, 0));
+    double2* work = (double2*)ctx->mem.alloc(sizeof(double2) * (L0.D() + L0.N()) * q);
+    const int npart = 2 * 152;
+    double2* part = (double2*)ctx->mem.alloc(sizeof(double2) * npart * (q * (q + 1) / 2));
+    try {
+      gram(L0, ctx->K.d_ph, q, (const double2*)S, L0.D(), q, (double2*)GM, (double2*)GA, work, part, npart, s);
+      PBS_CUDA(cudaStreamSynchronize(s));
+    } catch (...) {
+      ctx->mem.free(work);
+      ctx->mem.free(part);
+      cudaEventDestroy(ev);
+      throw;
+    }
+    ctx->mem.free(work);
+    ctx->mem.free(part);
+    cudaEventDestroy(ev);
+  });
+}
+
+int pbs_rayleigh_ritz(pbs_ctx* ctx, const pbs_geom* geom, const pbs_opts* opts, const double k[2], int q,
+                      const pbs_c64* S, int p, int project, double* theta, pbs_c64* X, void* cuda_stream) {
+  if (!ctx || !geom || !opts || !k || q < 1 || p < 1 || p > q || p > kMaxBlock || !S || !theta || !X)
+    return PBS_EINVAL;
+  return run_guarded_impl([&] {
+    DeviceGuard g(ctx->device);
+    const pbs_opts& o = *opts;
+    if (q > kMaxTrial) fail(PBS_EINVAL, "q too large");
+    ensure_hierarchy_host(ctx, geom, effective_mu(o, geom->a, geom->b), o.coarsest);
+    const int pw = std::max(p, (q + 2) / 3);
+    if (pw > kMaxBlock) fail(PBS_EINVAL, "q too large");
+    ensure_work(ctx, pw);
+    set_k(ctx, k[0], k[1]);
+    cudaStream_t s = ctx->stream;
+    cudaEvent_t ev;
+    PBS_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    PBS_CUDA(cudaEventRecord(ev, (cudaStream_t)cuda_stream));
+    PBS_CUDA(cudaStreamWaitEvent(s, ev, 0));
+    Work& W = ctx->W;
+    PBS_CUDA(cudaMemcpyAsync(W.S, S, sizeof(double2) * W.D * q, cudaMemcpyDeviceToDevice, s));
+    if (project) project_dispatch(ctx, o, W.S, q, s);
+    rayleigh_ritz_step(ctx, W.S, q, p, (double2*)X, s);
+    PBS_CUDA(cudaMemcpyAsync(theta, W.theta, sizeof(double) * p, cudaMemcpyDeviceToHost, s));
+    PBS_CUDA(cudaStreamSynchronize(s));
+    cudaEventDestroy(ev);
+  });
+}
+
+}  // extern "C"

@@ -1,0 +1,143 @@
+"""GPU parity of the eigensolver (Sections 4-6) against the CPU oracle.
+
+Eigenvalues: <= 1e-10 relative.  Eigenvectors: subspace angles <= 1e-6 per
+cluster of eigenvalues whose relative gap is below 1e-8 (degenerate
+eigenvalues have no unique eigenvectors; the cluster subspace is unique).
+Residuals: every wanted band below the requested tolerance.
+"""
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+torch = pytest.importorskip("torch")
+
+import paper_2304_00337_gb300 as pbs  # noqa: E402
+import pbs_inputs as gi  # noqa: E402
+from oracle import fem, eigen  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+PRECISIONS = [pbs.PBS_FP64, pbs.PBS_MIXED]
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import __graft_entry__ as ge
+    ge.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    with pbs.Context(0) as c:
+        yield c
+
+
+def _clusters(lam, rel=1e-8):
+    groups, cur = [], [0]
+    for i in range(1, len(lam)):
+        if abs(lam[i] - lam[i - 1]) <= rel * abs(lam[i]):
+            cur.append(i)
+        else:
+            groups.append(cur)
+            cur = [i]
+    groups.append(cur)
+    return groups
+
+
+def _max_angle(ops, X, Y):
+    """Largest principal angle between span(X) and span(Y) in the M inner product."""
+    M = ops["M"]
+    def orth(Z):
+        G = Z.conj().T @ (M @ Z)
+        R = np.linalg.cholesky(0.5 * (G + G.conj().T))
+        return Z @ np.linalg.inv(R).conj().T
+    Qx, Qy = orth(X), orth(Y)
+    s = np.linalg.svd(Qx.conj().T @ (M @ Qy), compute_uv=False)
+    return float(np.arccos(np.clip(s.min(), -1, 1)))
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_homogeneous_32_closed_form(ctx, precision):
+    # a = b = 1, eps = 1, 32 x 32, k = (pi/2, pi/4), 4 bands, block 4, random start from seed 0
+    n, k = 32, (np.pi / 2, np.pi / 4)
+    geom = pbs.Geometry(gi.const_eps(n, n))
+    init = gi.random_block(geom.D, 4, seed=0)
+    lam, res, iters, vec = ctx.solve_k(geom, dict(nev=4, block=4, precision=precision), k, init=init,
+                                       want_vectors=True)
+    want = eigen.closed_form_eps_const(1, 1, n, n, 1.0, k, 4)
+    assert np.max(np.abs(lam - want) / want) <= 1e-10
+    assert np.all(res <= 1e-8)
+    ops = fem.assemble(fem.Mesh(1, 1, n, n), np.ones((n, n)), k)
+    _, V = eigen.eigs_dense(ops, 4)
+    for g in _clusters(want):
+        assert _max_angle(ops, vec.T[:, g], V[:, g]) <= 1e-6
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+@pytest.mark.parametrize("k", [(0.4, -1.3), (0.0, 0.0), (np.pi, np.pi), (np.pi, 0.0), (0.05, 0.02)])
+def test_random_eps_vs_dense(ctx, precision, k):
+    n, m = 24, 16
+    eps = np.random.default_rng(3).uniform(1.0, 12.0, (m, n))
+    geom = pbs.Geometry(eps, 1.0, m / n)
+    lam, res, iters, vec = ctx.solve_k(geom, dict(nev=6, block=9, precision=precision, seed=5), k,
+                                       want_vectors=True)
+    ops = fem.assemble(fem.Mesh(1.0, m / n, n, m), eps, k)
+    want, V = eigen.eigs_dense(ops, 6)
+    assert np.max(np.abs(lam - want) / want) <= 1e-10
+    assert np.all(res <= 1e-8)
+    # vectors: angle bar applies to clusters separated from the rest of the spectrum
+    for g in _clusters(want):
+        assert _max_angle(ops, vec.T[:, g], V[:, g]) <= 1e-6
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_rod64_path_with_extrapolation(ctx, precision):
+    data = np.loadtxt(os.path.join(GOLDEN, "rod64_path31.txt"))
+    ks, want = data[:, :2], data[:, 2:]
+    geom = pbs.Geometry(gi.rod_eps(64, 64))
+    lam, res, iters = ctx.solve_path(geom, dict(nev=8, block=10, precision=precision), ks)
+    assert np.max(np.abs(lam - want) / want) <= 1e-10
+    assert np.all(res <= 1e-8)
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_rod256_path_full_size(ctx, precision):
+    path = os.path.join(GOLDEN, "rod256_path31.txt")
+    if not os.path.exists(path):
+        pytest.skip("golden values for the 256x256 path not generated")
+    data = np.loadtxt(path)
+    ks, want = data[:, :2], data[:, 2:]
+    geom = pbs.Geometry(gi.rod_eps(256, 256))
+    lam, res, iters = ctx.solve_path(geom, dict(nev=8, block=10, precision=precision), ks)
+    assert np.max(np.abs(lam - want) / want) <= 1e-10
+    assert np.all(res <= 1e-8)
+
+
+def test_device_path_matches_host_path(ctx):
+    n = 32
+    eps = gi.rod_eps(n, n)
+    ks = gi.gxmg_path(7)
+    o = dict(nev=4, block=6, precision=pbs.PBS_MIXED)
+    lam_h, res_h, it_h = ctx.solve_path(pbs.Geometry(eps), o, ks)
+    d_eps = torch.from_numpy(eps.copy()).cuda()
+    d_ks = torch.from_numpy(ks.copy()).cuda()
+    d_ev = torch.zeros((7, 4), dtype=torch.float64, device="cuda")
+    d_rs = torch.zeros((7, 4), dtype=torch.float64, device="cuda")
+    d_it = torch.zeros(7, dtype=torch.int32, device="cuda")
+    ctx.solve_path_device(1.0, 1.0, n, n, d_eps.data_ptr(), pbs.default_opts(**o), 7, d_ks.data_ptr(),
+                          d_ev.data_ptr(), d_rs.data_ptr(), d_it.data_ptr(), torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    assert np.array_equal(d_ev.cpu().numpy(), lam_h)
+    assert np.array_equal(d_it.cpu().numpy(), it_h)
+
+
+def test_span_variants_reach_the_same_eigenvalues(ctx):
+    n = 32
+    eps = gi.rod_eps(n, n)
+    geom = pbs.Geometry(eps)
+    k = (0.7, 0.3)
+    ops = fem.assemble(fem.Mesh(1, 1, n, n), eps, k)
+    want = eigen.eigs_sparse(ops, 4)[0]
+    for span in (1, 2, 3):
+        lam, res, iters, _ = ctx.solve_k(geom, dict(nev=4, block=7, span=span, precision=pbs.PBS_FP64), k)
+        assert np.max(np.abs(lam - want) / want) <= 1e-10, span

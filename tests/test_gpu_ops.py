@@ -1,0 +1,261 @@
+"""GPU parity of the operators, transfers, V-cycles, projection, Gram and Rayleigh-Ritz steps.
+
+Every call goes through the C ABI (``pbs_apply``, ``pbs_gram``,
+``pbs_rayleigh_ritz``) on seeded inputs; expected values come from the CPU
+oracle on the same inputs.  Bars: operator applications <= 1e-13 relative
+(2-norm per column), FP64 V-cycles and projection <= 1e-12 (same algorithm,
+different summation order), FP32 cycles <= 1e-5.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import paper_2304_00337_gb300 as pbs  # noqa: E402
+import pbs_inputs as gi  # noqa: E402
+from oracle import fem, multigrid as mg, extrapolation as ex, eigen  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+# (a, b, n, m, k): tiles of the kernels are 32 x 8 threads, so 48 x 20 leaves ragged tails
+CASES = [
+    (1.0, 1.0, 16, 16, (0.3, -0.2)),
+    (1.0, 20 / 48, 48, 20, (2.1, 0.7)),
+    (1.0, 1.0, 8, 8, (0.0, 0.0)),
+    (1.0, 1.0, 16, 16, (np.pi, np.pi)),
+    (1.3, 0.7, 24, 12, (-1.1, 3.0)),
+]
+MU = 0.7
+NCOLS = 3
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import __graft_entry__ as ge
+    ge.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    with pbs.Context(0) as c:
+        yield c
+
+
+def _eps(n, m, seed=11):
+    return np.random.default_rng(seed).uniform(1.0, 9.0, (m, n))
+
+
+def _block(ncols, size, seed):
+    r = np.random.default_rng(seed)
+    return r.standard_normal((ncols, size)) + 1j * r.standard_normal((ncols, size))
+
+
+def _dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def _apply(ctx, geom, op, x, out_len, k, level=0, **o):
+    xd = _dev(x)
+    yd = torch.zeros((x.shape[0], out_len), dtype=torch.complex128, device="cuda")
+    opts = pbs.default_opts(mu=MU, **o)
+    ctx.apply(geom, op, xd.data_ptr(), yd.data_ptr(), x.shape[0], k=k, level=level, opts=opts,
+              stream=torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    return yd.cpu().numpy()
+
+
+def _rel(got, want):
+    return np.max(np.linalg.norm(got - want, axis=1) / np.maximum(np.linalg.norm(want, axis=1), 1e-300))
+
+
+def _coarse_eps(eps):
+    inv = 1.0 / eps
+    return 1.0 / (0.25 * (inv[0::2, 0::2] + inv[1::2, 0::2] + inv[0::2, 1::2] + inv[1::2, 1::2]))
+
+
+@pytest.mark.parametrize("a,b,n,m,k", CASES)
+def test_edge_and_nodal_operators(ctx, a, b, n, m, k):
+    eps = _eps(n, m)
+    geom = pbs.Geometry(eps, a, b)
+    ops = fem.assemble(fem.Mesh(a, b, n, m), eps, k)
+    N, D = n * m, 2 * n * m
+    x = _block(NCOLS, D, 1)
+    xn = _block(NCOLS, N, 2)
+    A, M, C, L, P = ops["A"], ops["M"], ops["C"], ops["L"], ops["P"]
+    checks = [
+        ("A", x, D, A @ x.T),
+        ("M", x, D, M @ x.T),
+        ("A_MU_M", x, D, (A + MU * M) @ x.T),
+        ("C", x, N, C @ x.T),
+        ("CH", xn, D, C.conj().T @ xn.T),
+        ("L", xn, D, L @ xn.T),
+        ("LH", x, N, L.conj().T @ x.T),
+        ("P_NODAL", xn, N, P @ xn.T),
+    ]
+    for op, inp, olen, want in checks:
+        got = _apply(ctx, geom, op, inp, olen, k)
+        assert _rel(got, want.T) <= 1e-13, op
+
+
+@pytest.mark.parametrize("a,b,n,m,k", [CASES[0], CASES[1], CASES[3]])
+def test_transfers_and_coarse_level_operators(ctx, a, b, n, m, k):
+    eps = _eps(n, m)
+    geom = pbs.Geometry(eps, a, b)
+    fine = fem.Mesh(a, b, n, m)
+    coarse = fine.coarse()
+    Pe = fem.edge_prolongation(fine, coarse, k)
+    Pn = fem.nodal_prolongation(fine, coarse, k)
+    xc = _block(NCOLS, coarse.D, 3)
+    xf = _block(NCOLS, fine.D, 4)
+    assert _rel(_apply(ctx, geom, "PROLONG", xc, fine.D, k), (Pe @ xc.T).T) <= 1e-14
+    assert _rel(_apply(ctx, geom, "RESTRICT", xf, coarse.D, k), (Pe.conj().T @ xf.T).T) <= 1e-14
+    xcn = _block(NCOLS, coarse.N, 5)
+    xfn = _block(NCOLS, fine.N, 6)
+    assert _rel(_apply(ctx, geom, "PROLONG_NODAL", xcn, fine.N, k), (Pn @ xcn.T).T) <= 1e-14
+    assert _rel(_apply(ctx, geom, "RESTRICT_NODAL", xfn, coarse.N, k), (Pn.conj().T @ xfn.T).T) <= 1e-14
+    # level-1 operators = coarse assembly with the children's mean 1/eps
+    oc = fem.assemble(coarse, _coarse_eps(eps), k)
+    got = _apply(ctx, geom, "A_MU_M", xc, coarse.D, k, level=1)
+    assert _rel(got, ((oc["A"] + MU * oc["M"]) @ xc.T).T) <= 1e-13
+    got = _apply(ctx, geom, "P_NODAL", xcn, coarse.N, k, level=1)
+    assert _rel(got, (oc["P"] @ xcn.T).T) <= 1e-13
+
+
+@pytest.mark.parametrize("a,b,n,m,k", [CASES[0], CASES[1], CASES[2], CASES[3]])
+def test_vcycles_match_reference(ctx, a, b, n, m, k):
+    eps = _eps(n, m)
+    geom = pbs.Geometry(eps, a, b)
+    mesh = fem.Mesh(a, b, n, m)
+    levels = mg.edge_hierarchy(mesh, eps, k, MU, 4)
+    x = _block(2, mesh.D, 7)
+    want = np.stack([mg.edge_vcycle(levels, x[c]) for c in range(2)])
+    got = _apply(ctx, geom, "VCYCLE_EDGE", x, mesh.D, k, precision=pbs.PBS_FP64)
+    assert _rel(got, want) <= 1e-12
+    got32 = _apply(ctx, geom, "VCYCLE_EDGE", x, mesh.D, k, precision=pbs.PBS_MIXED)
+    assert _rel(got32, want) <= 1e-5
+    nlev = mg.nodal_hierarchy(mesh, eps, k, 4)
+    xn = _block(2, mesh.N, 8)
+    if fem.is_gamma(*fem.bloch_phases(k, a, b)):
+        xn -= xn.mean(axis=1, keepdims=True)
+    want = np.stack([mg.nodal_vcycle(nlev, xn[c]) for c in range(2)])
+    got = _apply(ctx, geom, "VCYCLE_NODAL", xn, mesh.N, k, precision=pbs.PBS_FP64)
+    assert _rel(got, want) <= 1e-12
+    got32 = _apply(ctx, geom, "VCYCLE_NODAL", xn, mesh.N, k, precision=pbs.PBS_MIXED)
+    assert _rel(got32, want) <= 1e-5
+
+
+@pytest.mark.parametrize("a,b,n,m,k", [CASES[0], CASES[2], CASES[4]])
+@pytest.mark.parametrize("cycles", [1, 3])
+def test_projection_matches_reference(ctx, a, b, n, m, k, cycles):
+    eps = _eps(n, m)
+    geom = pbs.Geometry(eps, a, b)
+    mesh = fem.Mesh(a, b, n, m)
+    ops = fem.assemble(mesh, eps, k)
+    nlev = mg.nodal_hierarchy(mesh, eps, k, 4)
+    x = _block(3, mesh.D, 9)
+    want = mg.project_approx(ops, nlev, x.T, cycles).T
+    got = _apply(ctx, geom, "PROJECT", x, mesh.D, k, precision=pbs.PBS_FP64, nodal_cycles=cycles)
+    assert _rel(got, want) <= 1e-12
+    got32 = _apply(ctx, geom, "PROJECT", x, mesh.D, k, precision=pbs.PBS_MIXED, nodal_cycles=cycles)
+    assert _rel(got32, want) <= 1e-5
+
+
+@pytest.mark.parametrize("a,b,n,m,k", [CASES[1], CASES[2]])
+def test_gram_matches_oracle(ctx, a, b, n, m, k):
+    eps = _eps(n, m)
+    geom = pbs.Geometry(eps, a, b)
+    ops = fem.assemble(fem.Mesh(a, b, n, m), eps, k)
+    q = 30
+    S = _block(q, geom.D, 10)
+    Sd = _dev(S)
+    GM = torch.zeros((q, q), dtype=torch.complex128, device="cuda")
+    GA = torch.zeros((q, q), dtype=torch.complex128, device="cuda")
+    ctx.gram(geom, k, q, Sd.data_ptr(), GM.data_ptr(), GA.data_ptr(), torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    gm = GM.cpu().numpy().T  # column-major on the device
+    ga = GA.cpu().numpy().T
+    wm, wa = ex.grams(ops, S.T)
+    assert np.abs(gm - wm).max() <= 1e-13 * np.abs(wm).max()
+    assert np.abs(ga - wa).max() <= 1e-13 * np.abs(wa).max()
+
+
+@pytest.mark.parametrize("k", [(0.3, 0.1), (0.0, 0.0)])
+def test_rayleigh_ritz_and_extrapolation(ctx, k):
+    n = 16
+    eps = gi.rod_eps(n, n)
+    geom = pbs.Geometry(eps)
+    ks = [np.array(k) + d for d in (np.array([0.2, 0.1]), np.array([0.4, 0.2]))]
+    prev = [eigen.solve_k(1, 1, n, n, eps, kk, 6, "dense")[1] for kk in ks]
+    ops = fem.assemble(fem.Mesh(1, 1, n, n), eps, k)
+    S = np.concatenate(prev, axis=1)  # (D, 12)
+    Sd = _dev(S.T)
+    X = torch.zeros((6, geom.D), dtype=torch.complex128, device="cuda")
+    # plain Rayleigh-Ritz on the span
+    th_want, _ = ex.rayleigh_ritz(ops, S, 6)
+    th = ctx.rayleigh_ritz(geom, pbs.default_opts(precision=pbs.PBS_FP64), k, 12, Sd.data_ptr(), 6, False,
+                           X.data_ptr(), torch.cuda.current_stream())
+    assert np.allclose(th, th_want, rtol=1e-11)
+    Xh = X.cpu().numpy().T
+    GM, GA = ex.grams(ops, Xh)
+    assert np.allclose(GM, np.eye(6), atol=1e-10)
+    assert np.allclose(np.real(np.diag(GA)), th_want, rtol=1e-10)
+    # extrapolation: projection off the gradients first (Section 6)
+    th_want, _ = ex.extrapolate(ops, prev, 6)
+    th = ctx.rayleigh_ritz(geom, pbs.default_opts(precision=pbs.PBS_FP64, nodal_cycles=14), k, 12, Sd.data_ptr(), 6,
+                           True, X.data_ptr(), torch.cuda.current_stream())
+    assert np.allclose(th, th_want, rtol=1e-10)
+
+
+def test_empty_and_invalid_calls(ctx):
+    geom = pbs.Geometry(_eps(16, 16))
+    x = torch.zeros((1, geom.D), dtype=torch.complex128, device="cuda")
+    ctx.apply(geom, "A", x.data_ptr(), x.data_ptr(), 0, k=(0.1, 0.2))  # ncols = 0: no-op
+    with pytest.raises(pbs.PbsError) as e:
+        ctx.apply(geom, "PROLONG", x.data_ptr(), x.data_ptr(), 1, level=2)  # no level below the coarsest
+    assert e.value.status == pbs.PBS_EINVAL
+    with pytest.raises(pbs.PbsError) as e:
+        ctx.solve_k(pbs.Geometry(_eps(15, 16)), dict(nev=2, block=4), (0.1, 0.1))  # odd side
+    assert e.value.status == pbs.PBS_EINVAL
+    bad = _eps(16, 16)
+    bad[3, 4] = -1.0
+    with pytest.raises(pbs.PbsError) as e:
+        ctx.solve_k(pbs.Geometry(bad), dict(nev=2, block=4), (0.1, 0.1))
+    assert e.value.status == pbs.PBS_EINVAL
+    with pytest.raises(pbs.PbsError) as e:
+        ctx.solve_k(geom, dict(nev=2, block=40), (0.1, 0.1))
+    assert e.value.status == pbs.PBS_EINVAL
+
+
+def test_max_size_operators_on_plane_waves(ctx):
+    # 4096 x 4096 (33.5M edges): a discrete Bloch plane wave with eps = 1 is a generalised
+    # eigenvector, A x = lambda M x, with lambda from the closed form; A L phi = 0 for any phi.
+    n = 4096
+    geom = pbs.Geometry(gi.const_eps(n, n, 1.0))
+    k = (0.37, -1.21)
+    p, q = 3, 5
+    h = 1.0 / n
+    t1, t2 = (k[0] + 2 * np.pi * p) * h, (k[1] + 2 * np.pi * q) * h
+    s1, s2 = np.sin(t1 / 2), np.sin(t2 / 2)
+    # rank-one curl-curl symbol 4w a a^T with a = (s2, -s1); eigenvector M^{-1} a of the pencil
+    mx, my = (2 + np.cos(t2)) / 3, (2 + np.cos(t1)) / 3
+    i = torch.arange(n, dtype=torch.float64, device="cuda")
+    J, I = torch.meshgrid(i, i, indexing="ij")
+    ex_ = (s2 / mx * torch.exp(1j * (t1 * (I + 0.5) + t2 * J))).reshape(-1)
+    ey_ = (-s1 / my * torch.exp(1j * (t1 * I + t2 * (J + 0.5)))).reshape(-1)
+    x = torch.cat([ex_, ey_]).reshape(1, -1).contiguous()
+    del ex_, ey_
+    lam = 6 * (1 - np.cos(t1)) / (h * h * (2 + np.cos(t1))) + 6 * (1 - np.cos(t2)) / (h * h * (2 + np.cos(t2)))
+    y = torch.empty_like(x)
+    z = torch.empty_like(x)
+    opts = pbs.default_opts(mu=MU)
+    ctx.apply(geom, "A", x.data_ptr(), y.data_ptr(), 1, k=k, opts=opts)
+    ctx.apply(geom, "M", x.data_ptr(), z.data_ptr(), 1, k=k, opts=opts)
+    torch.cuda.synchronize()
+    rel = (torch.linalg.vector_norm(y - lam * z) / torch.linalg.vector_norm(y)).item()
+    assert rel < 1e-9  # rounding of a 33.5M-entry stencil at lambda ~ 1e3
+    del y, z
+    phi = torch.exp(1j * (k[0] * I * h + k[1] * J * h)).reshape(1, -1).contiguous() * (1 + 0.5j)
+    g = torch.empty_like(x)
+    ctx.apply(geom, "L", phi.data_ptr(), g.data_ptr(), 1, k=k, opts=opts)
+    ag = torch.empty_like(x)
+    ctx.apply(geom, "A", g.data_ptr(), ag.data_ptr(), 1, k=k, opts=opts)
+    torch.cuda.synchronize()
+    assert (torch.linalg.vector_norm(ag) / torch.linalg.vector_norm(g)).item() < 1e-12 * 8 / h ** 2
