@@ -194,6 +194,24 @@ PBS_API int pbs_gram(pbs_ctx *ctx, const pbs_geom *geom, const double k[2], int 
 PBS_API int pbs_rayleigh_ritz(pbs_ctx *ctx, const pbs_geom *geom, const pbs_opts *opts, const double k[2], int q,
                       const pbs_c64 *S, int p, int project, double *theta, pbs_c64 *X, void *cuda_stream);
 
+/*
+ * Diagnostics: time every launch of the listed kernel classes with a pair of
+ * CUDA events on the stream it is launched on (the library's stream).
+ * `classes` is "all" or a comma-separated list of "edge_smooth",
+ * "node_smooth", "gram", "small_rr", "residual", "block_update",
+ * "lift_adj_mass"; NULL or "" switches timing off.  Enabling resets the
+ * counters.  pbs_profile_read returns, for one class, the summed device time
+ * (ms), the number of timed launches and their summed algorithmic work (bytes
+ * moved for the streaming kernels, flops for "gram", "small_rr" and
+ * "block_update") since then.
+ */
+PBS_API int pbs_profile_enable(pbs_ctx *ctx, const char *classes);
+PBS_API int pbs_profile_read(pbs_ctx *ctx, const char *kernel_class, double *total_ms, long *launches,
+                             double *work);
+
+/* Number of CUDA kernels the library has launched in this process. */
+PBS_API unsigned long long pbs_launch_count(void);
+
 /* Static description of a status code. */
 PBS_API const char *pbs_strerror(int status);
 

@@ -93,6 +93,10 @@ def lib() -> ct.CDLL:
         "pbs_gram": (ct.c_int, [P, ct.POINTER(pbs_geom), dp, ct.c_int, P, P, P, P]),
         "pbs_rayleigh_ritz": (ct.c_int, [P, ct.POINTER(pbs_geom), ct.POINTER(pbs_opts), dp, ct.c_int, P, ct.c_int,
                                          ct.c_int, dp, P, P]),
+        "pbs_profile_enable": (ct.c_int, [P, ct.c_char_p]),
+        "pbs_profile_read": (ct.c_int, [P, ct.c_char_p, ct.POINTER(ct.c_double), ct.POINTER(ct.c_long),
+                                        ct.POINTER(ct.c_double)]),
+        "pbs_launch_count": (ct.c_ulonglong, []),
         "pbs_strerror": (ct.c_char_p, [ct.c_int]),
         "pbs_last_error": (ct.c_char_p, []),
     }
@@ -102,6 +106,11 @@ def lib() -> ct.CDLL:
         f.argtypes = args
     _lib = L
     return L
+
+
+def launch_count() -> int:
+    """Kernels launched by the library in this process (``pbs_launch_count``)."""
+    return int(lib().pbs_launch_count())
 
 
 def strerror(status: int) -> str:
@@ -257,6 +266,19 @@ class Context:
         kk = np.asarray(k, dtype=np.float64)
         _check(lib().pbs_gram(self._ptr, geom.ref(), _dp(kk), q, s_ptr, gm_ptr, ga_ptr, _stream_ptr(stream)),
                "pbs_gram")
+
+    def profile_enable(self, classes: str | None):
+        """Time kernel classes with CUDA events on the library's stream (``pbs_profile_enable``)."""
+        _check(lib().pbs_profile_enable(self._ptr, (classes or "").encode()), "pbs_profile_enable")
+
+    def profile_read(self, kernel_class: str):
+        """``(total_ms, launches, work)`` of one timed kernel class (``pbs_profile_read``)."""
+        ms = ct.c_double(0.0)
+        n = ct.c_long(0)
+        w = ct.c_double(0.0)
+        _check(lib().pbs_profile_read(self._ptr, kernel_class.encode(), ct.byref(ms), ct.byref(n), ct.byref(w)),
+               "pbs_profile_read")
+        return ms.value, n.value, w.value
 
     def rayleigh_ritz(self, geom: Geometry, opts, k, q: int, s_ptr: int, p: int, project: bool, x_ptr: int,
                       stream=None):

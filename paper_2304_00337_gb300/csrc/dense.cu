@@ -593,12 +593,12 @@ inline unsigned blocks_for(long n, int per = 256, unsigned cap = 4096) {
 void convert_d2f(const double2* X, float2* Y, long n, cudaStream_t s) {
   if (n <= 0) return;
   k_d2f<<<blocks_for(n), 256, 0, s>>>(X, Y, n);
-  PBS_CUDA(cudaGetLastError());
+  PBS_LAUNCHED();
 }
 void convert_f2d(const float2* X, double2* Y, long n, cudaStream_t s) {
   if (n <= 0) return;
   k_f2d<<<blocks_for(n), 256, 0, s>>>(X, Y, n);
-  PBS_CUDA(cudaGetLastError());
+  PBS_LAUNCHED();
 }
 
 template <class T>
@@ -606,24 +606,26 @@ void sub_lift(const Level& L, const double* d_ph, int cpg, const cx<T>* Phi, lon
               cudaStream_t s) {
   if (ncols <= 0) return;
   k_sub_lift<T><<<grid2(L.n, L.m, ncols), dim3(kBX, kBY), 0, s>>>(L.n, L.m, d_ph, cpg, Phi, ldp, X, ldx);
-  PBS_CUDA(cudaGetLastError());
+  PBS_LAUNCHED();
 }
 
 template <class T>
 void lift_adj_mass(const Level& L, const double* d_ph, int cpg, const double2* X, long ldx, cx<T>* Rhs, long ldr,
                    int ncols, cudaStream_t s) {
   if (ncols <= 0) return;
+  timer_begin(KC_LIFT_ADJ_MASK, s, (16.0 * L.D() + 2.0 * sizeof(T) * L.N()) * ncols);
   k_lift_adj_mass<T><<<grid2(L.n, L.m, ncols), dim3(kBX, kBY), 0, s>>>(L.lvl<double>(), d_ph, cpg, X, ldx, Rhs, ldr);
-  PBS_CUDA(cudaGetLastError());
+  timer_end(KC_LIFT_ADJ_MASK, s);
+  PBS_LAUNCHED();
 }
 
 void deflate_constants(const Level& L, double2* X, long ld, int ncols, double* d_partials, cudaStream_t s) {
   if (ncols <= 0) return;
   const int nblk = 64;
   k_edge_sums<<<dim3(nblk, ncols), 256, 0, s>>>(L.N(), X, ld, d_partials, nblk);
-  PBS_CUDA(cudaGetLastError());
+  PBS_LAUNCHED();
   k_edge_sub_means<<<dim3(nblk, ncols), 256, 0, s>>>(L.N(), X, ld, d_partials, nblk);
-  PBS_CUDA(cudaGetLastError());
+  PBS_LAUNCHED();
 }
 
 void rayleigh_parts(const Level& L, const double* d_ph, int cpg, const double2* X, long ld, int ncols,
@@ -631,19 +633,21 @@ void rayleigh_parts(const Level& L, const double* d_ph, int cpg, const double2* 
   if (ncols <= 0) return;
   const dim3 g = grid2(L.n, L.m, ncols);
   k_rayleigh_parts<<<g, dim3(kBX, kBY), 0, s>>>(L.lvl<double>(), L.wts<double>(), d_ph, cpg, X, ld, d_partials);
-  PBS_CUDA(cudaGetLastError());
+  PBS_LAUNCHED();
   k_finalize2<<<ncols, 256, 0, s>>>(d_partials, g.x * g.y, d_out);
-  PBS_CUDA(cudaGetLastError());
+  PBS_LAUNCHED();
 }
 
 void residual(const Level& L, const double* d_ph, int cpg, const double2* E, double2* R, long ld, int ncols,
               const double* d_lam, double* d_partials, double* d_out, cudaStream_t s) {
   if (ncols <= 0) return;
   const dim3 g = grid2(L.n, L.m, ncols);
+  timer_begin(KC_RESIDUAL, s, 32.0 * L.D() * ncols);
   k_residual<<<g, dim3(kBX, kBY), 0, s>>>(L.lvl<double>(), L.wts<double>(), d_ph, cpg, E, R, ld, d_lam, d_partials);
-  PBS_CUDA(cudaGetLastError());
+  timer_end(KC_RESIDUAL, s);
+  PBS_LAUNCHED();
   k_finalize2<<<ncols, 256, 0, s>>>(d_partials, g.x * g.y, d_out);
-  PBS_CUDA(cudaGetLastError());
+  PBS_LAUNCHED();
 }
 
 int gram_partials(long rows) {
@@ -669,15 +673,19 @@ void gram(const Level& L, const double* d_ph, int cpg, const double2* S, long ld
   }
   const int ne = q * (q + 1) / 2;
   const int npM = std::min(npart, gram_partials(D));
+  timer_begin(KC_GRAM, s, 8.0 * ne * D);  // flops: one complex MAC per entry and row
   k_gram_ts<<<npM, 256, smem, s>>>(S, ld, MS, ld, q, D, nullptr, 0.0, d_partials);
-  PBS_CUDA(cudaGetLastError());
+  timer_end(KC_GRAM, s);
+  PBS_LAUNCHED();
   k_gram_finalize<<<(ne + 255) / 256, 256, 0, s>>>(d_partials, npM, q, GM, 0);
-  PBS_CUDA(cudaGetLastError());
+  PBS_LAUNCHED();
   const int npA = std::min(npart, gram_partials(N));
+  timer_begin(KC_GRAM, s, 8.0 * ne * N);
   k_gram_ts<<<npA, 256, smem, s>>>(CS, N, CS, N, q, N, L.winv64, 1.0 / (L.h1 * L.h2), d_partials);
-  PBS_CUDA(cudaGetLastError());
+  timer_end(KC_GRAM, s);
+  PBS_LAUNCHED();
   k_gram_finalize<<<(ne + 255) / 256, 256, 0, s>>>(d_partials, npA, q, GA, 0);
-  PBS_CUDA(cudaGetLastError());
+  PBS_LAUNCHED();
 }
 
 size_t small_rr_scratch(int q) { return (6ull * q * q + q) * sizeof(double2) + (size_t)q * sizeof(int) + 64; }
@@ -685,8 +693,10 @@ size_t small_rr_scratch(int q) { return (6ull * q * q + q) * sizeof(double2) + (
 void small_rr(const double2* GM, const double2* GA, int q, int p, double2* C, double* theta, double2* scratch,
               int* d_info, cudaStream_t s) {
   if (q > kMaxTrial || p > q || p < 1) fail(PBS_EINVAL, "small_rr: bad sizes");
+  timer_begin(KC_SMALL_RR, s, 8.0 * 6.0 * q * q * q);  // flops, order of magnitude
   k_small_rr<<<1, 256, 0, s>>>(GM, GA, q, p, C, theta, scratch, d_info);
-  PBS_CUDA(cudaGetLastError());
+  timer_end(KC_SMALL_RR, s);
+  PBS_LAUNCHED();
 }
 
 void block_update(const double2* X, long ldx, int q, const double2* C, int ldc, double2* Y, long ldy, int p,
@@ -700,20 +710,22 @@ void block_update(const double2* X, long ldx, int q, const double2* C, int ldc, 
                                   kMaxBlock * kMaxTrial * (int)sizeof(double2)));
     attr = true;
   }
+  timer_begin(KC_BLOCK_UPDATE, s, 8.0 * q * p * rows);  // flops
   k_block_update<<<blocks_for(rows, 256, 2 * 152 * 4), 256, smem, s>>>(X, ldx, q, C, ldc, Y, ldy, p, Z, ldz, rows);
-  PBS_CUDA(cudaGetLastError());
+  timer_end(KC_BLOCK_UPDATE, s);
+  PBS_LAUNCHED();
 }
 
 void random_block(double2* X, long ld, long rows, int ncols, uint64_t seed, cudaStream_t s) {
   if (ncols <= 0) return;
   k_random<<<dim3(blocks_for(rows, 256, 1024), ncols), 256, 0, s>>>(X, ld, rows, seed);
-  PBS_CUDA(cudaGetLastError());
+  PBS_LAUNCHED();
 }
 
 void scale_columns(double2* X, long ld, long rows, int ncols, const double* d_scale, cudaStream_t s) {
   if (ncols <= 0) return;
   k_scale_cols<<<dim3(blocks_for(rows, 256, 1024), ncols), 256, 0, s>>>(X, ld, rows, d_scale);
-  PBS_CUDA(cudaGetLastError());
+  PBS_LAUNCHED();
 }
 
 template void sub_lift<double>(const Level&, const double*, int, const double2*, long, double2*, long, int, cudaStream_t);

@@ -80,6 +80,39 @@ class DevMem {
 
 int num_levels(int n, int m, int coarsest);
 
+// Optional CUDA-event timing of kernel classes on the stream they are launched
+// on (enabled per context through pbs_profile_enable; off by default).  Each
+// timed launch also adds its algorithmic work (bytes for streaming kernels,
+// flops for arithmetic-bound ones) so the achieved rate can be derived.
+enum KernelClass {
+  KC_NONE = 0, KC_EDGE_SMOOTH, KC_NODE_SMOOTH, KC_GRAM, KC_SMALL_RR, KC_RESIDUAL, KC_BLOCK_UPDATE,
+  KC_LIFT_ADJ_MASK, KC_EDGE_APPLY, KC_COUNT
+};
+struct TimedLaunch {
+  int cls;
+  double work;
+  cudaEvent_t start, stop;
+};
+struct KernelTimer {
+  unsigned mask = 0;  // bit c set: class c is timed
+  double total_ms[KC_COUNT] = {};
+  double work[KC_COUNT] = {};
+  long launches[KC_COUNT] = {};
+  std::vector<TimedLaunch> pending;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pool;
+};
+extern thread_local KernelTimer* g_timer;
+void timer_begin(int cls, cudaStream_t s, double work);
+void timer_end(int cls, cudaStream_t s);
+void timer_collect();  // after a stream synchronisation
+// every kernel launch of the library is counted (process-wide)
+void count_launch();
+#define PBS_LAUNCHED()                 \
+  do {                                 \
+    ::pbs::count_launch();             \
+    PBS_CUDA(cudaGetLastError());      \
+  } while (0)
+
 // ---- hierarchy set-up (mg.cu) ---------------------------------------------
 void build_hierarchy(DevMem& mem, Hierarchy& H, const double* d_eps, int coarsest, cudaStream_t s);
 void free_hierarchy(DevMem& mem, Hierarchy& H);

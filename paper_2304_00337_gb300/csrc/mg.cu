@@ -256,6 +256,19 @@ template <class T> const T* k3_of(const Level& L);
 template <> const double* k3_of<double>(const Level& L) { return L.k3_64; }
 template <> const float* k3_of<float>(const Level& L) { return L.k3_32; }
 
+// Algorithmic bytes of one colour launch: every x value is read once (the
+// patch residuals need the neighbours), the colour's edges (half of them) read b
+// and write x, plus the colour's patch factors (6 reals per node) and 1/eps.
+template <class T> double smooth_bytes(const Level& L, int ncols) {
+  const double c = 2.0 * sizeof(T), D = (double)L.D(), N = (double)L.N();
+  return ncols * (c * D + 2 * c * D / 2) + 6.0 * sizeof(T) * N / 4 + sizeof(T) * N;
+}
+// point smoother: read x once, read b and write x on a quarter of the nodes
+template <class T> double node_smooth_bytes(const Level& L, int ncols) {
+  const double c = 2.0 * sizeof(T), N = (double)L.N();
+  return ncols * (c * N + 2 * c * N / 4);
+}
+
 inline dim3 half_grid(int n, int m, int ncols) {
   return dim3(((n + 1) / 2 + kBX - 1) / kBX, ((m + 1) / 2 + kBY - 1) / kBY, ncols);
 }
@@ -299,11 +312,11 @@ void build_hierarchy(DevMem& mem, Hierarchy& H, const double* d_eps, int coarses
       k_coarsen_w<<<dim3((n + kBX - 1) / kBX, (m + kBY - 1) / kBY), dim3(kBX, kBY), 0, s>>>(F.winv64, F.n, L.winv64,
                                                                                            L.winv32, n, m);
     }
-    PBS_CUDA(cudaGetLastError());
+    PBS_LAUNCHED();
     const double m1 = 2.0 / 3.0 * L.h2 / L.h1, m2 = 2.0 / 3.0 * L.h1 / L.h2;
     k_patch_factors<<<dim3((n + kBX - 1) / kBX, (m + kBY - 1) / kBY), dim3(kBX, kBY), 0, s>>>(
         L.winv64, n, m, 1.0 / (L.h1 * L.h2), m1, m2, H.mu, L.k3_64, L.k3_32);
-    PBS_CUDA(cudaGetLastError());
+    PBS_LAUNCHED();
     n /= 2;
     m /= 2;
   }
@@ -348,14 +361,14 @@ void build_kdata(DevMem& mem, const Hierarchy& H, KData& K, double k1, double k2
   int* d_info = (int*)mem.alloc(2 * sizeof(int));
   PBS_CUDA(cudaMemsetAsync(d_info, 0, 2 * sizeof(int), s));
   k_assemble_edge<<<dim3((Dc + 127) / 128, Dc), 128, 0, s>>>(C.lvl<double>(), C.wts<double>(), H.mu, K.d_ph, K.edge64);
-  PBS_CUDA(cudaGetLastError());
+  PBS_LAUNCHED();
   k_cholesky<<<1, 256, 0, s>>>(K.edge64, Dc, K.edge32, d_info);
-  PBS_CUDA(cudaGetLastError());
+  PBS_LAUNCHED();
   const double shift = K.gamma ? P_diag<double>(C.lvl<double>()) : 0.0;
   k_assemble_node<<<dim3((Nc + 127) / 128, Nc), 128, 0, s>>>(C.lvl<double>(), K.d_ph, shift, K.node64);
-  PBS_CUDA(cudaGetLastError());
+  PBS_LAUNCHED();
   k_cholesky<<<1, 256, 0, s>>>(K.node64, Nc, K.node32, d_info + 1);
-  PBS_CUDA(cudaGetLastError());
+  PBS_LAUNCHED();
   int info[2] = {0, 0};
   PBS_CUDA(cudaMemcpyAsync(info, d_info, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
   PBS_CUDA(cudaStreamSynchronize(s));
@@ -406,7 +419,7 @@ void edge_cycle(const Hierarchy& H, const KData& K, MgWork<T>& w, int l, const c
   const Level& L = H.lev[l];
   if (l == H.nlev - 1) {
     k_chol_solve<T><<<(ncols * 32 + 127) / 128, 128, 0, s>>>(edge_factor<T>(K), (int)L.D(), b, ld, x, ld, ncols);
-    PBS_CUDA(cudaGetLastError());
+    PBS_LAUNCHED();
     return;
   }
   for (int c = 0; c < ncols; ++c) PBS_CUDA(cudaMemsetAsync(x + c * ld, 0, L.D() * sizeof(cx<T>), s));
@@ -415,9 +428,11 @@ void edge_cycle(const Hierarchy& H, const KData& K, MgWork<T>& w, int l, const c
   const T mu = T(H.mu);
   for (int it = 0; it < nu_pre; ++it)
     for (int q = 0; q < 4; ++q) {
+      timer_begin(KC_EDGE_SMOOTH, s, smooth_bytes<T>(L, ncols));
       k_edge_smooth<T><<<half_grid(L.n, L.m, ncols), dim3(kBX, kBY), 0, s>>>(lv, wt, k3_of<T>(L), mu, K.d_ph, ncols, x,
                                                                              b, ld, kColours[q][0], kColours[q][1]);
-      PBS_CUDA(cudaGetLastError());
+      timer_end(KC_EDGE_SMOOTH, s);
+      PBS_LAUNCHED();
     }
   const Level& C = H.lev[l + 1];
   const long ldc = C.D();
@@ -427,9 +442,11 @@ void edge_cycle(const Hierarchy& H, const KData& K, MgWork<T>& w, int l, const c
   prolong_edge<T>(L, C, K.d_ph, ncols, w.x[l + 1], ldc, x, ld, ncols, true, s);
   for (int it = 0; it < nu_post; ++it)
     for (int q = 3; q >= 0; --q) {
+      timer_begin(KC_EDGE_SMOOTH, s, smooth_bytes<T>(L, ncols));
       k_edge_smooth<T><<<half_grid(L.n, L.m, ncols), dim3(kBX, kBY), 0, s>>>(lv, wt, k3_of<T>(L), mu, K.d_ph, ncols, x,
                                                                              b, ld, kColours[q][0], kColours[q][1]);
-      PBS_CUDA(cudaGetLastError());
+      timer_end(KC_EDGE_SMOOTH, s);
+      PBS_LAUNCHED();
     }
 }
 
@@ -439,16 +456,18 @@ void node_cycle(const Hierarchy& H, const KData& K, MgWork<T>& w, int l, const c
   const Level& L = H.lev[l];
   if (l == H.nlev - 1) {
     k_chol_solve<T><<<(ncols * 32 + 127) / 128, 128, 0, s>>>(node_factor<T>(K), (int)L.N(), b, ld, x, ld, ncols);
-    PBS_CUDA(cudaGetLastError());
+    PBS_LAUNCHED();
     return;
   }
   for (int c = 0; c < ncols; ++c) PBS_CUDA(cudaMemsetAsync(x + c * ld, 0, L.N() * sizeof(cx<T>), s));
   const Lvl<T> lv = L.lvl<T>();
   for (int it = 0; it < nu_pre; ++it)
     for (int q = 0; q < 4; ++q) {
+      timer_begin(KC_NODE_SMOOTH, s, node_smooth_bytes<T>(L, ncols));
       k_node_smooth<T><<<half_grid(L.n, L.m, ncols), dim3(kBX, kBY), 0, s>>>(lv, K.d_ph, ncols, x, b, ld,
                                                                              kColours[q][0], kColours[q][1]);
-      PBS_CUDA(cudaGetLastError());
+      timer_end(KC_NODE_SMOOTH, s);
+      PBS_LAUNCHED();
     }
   const Level& C = H.lev[l + 1];
   const long ldc = C.N();
@@ -458,9 +477,11 @@ void node_cycle(const Hierarchy& H, const KData& K, MgWork<T>& w, int l, const c
   prolong_node<T>(L, C, K.d_ph, ncols, w.x[l + 1], ldc, x, ld, ncols, true, s);
   for (int it = 0; it < nu_post; ++it)
     for (int q = 3; q >= 0; --q) {
+      timer_begin(KC_NODE_SMOOTH, s, node_smooth_bytes<T>(L, ncols));
       k_node_smooth<T><<<half_grid(L.n, L.m, ncols), dim3(kBX, kBY), 0, s>>>(lv, K.d_ph, ncols, x, b, ld,
                                                                              kColours[q][0], kColours[q][1]);
-      PBS_CUDA(cudaGetLastError());
+      timer_end(KC_NODE_SMOOTH, s);
+      PBS_LAUNCHED();
     }
 }
 

@@ -202,7 +202,7 @@ void apply_edge(const Level& L, const double* d_ph, int cpg, const cx<T>* X, cx<
   if (ncols <= 0) return;
   k_apply_edge<T><<<grid2(L.n, L.m, ncols), dim3(kBX, kBY), 0, s>>>(L.lvl<T>(), L.wts<T>(), d_ph, cpg, X, Y, B, ld,
                                                                       sA, sM, sL, lam, sB);
-  PBS_CUDA(cudaGetLastError());
+  PBS_LAUNCHED();
 }
 
 template <class T>
@@ -210,7 +210,7 @@ void apply_curl(const Level& L, const double* d_ph, int cpg, const cx<T>* X, lon
                 cudaStream_t s) {
   if (ncols <= 0) return;
   k_curl<T><<<grid2(L.n, L.m, ncols), dim3(kBX, kBY), 0, s>>>(L.lvl<T>(), d_ph, cpg, X, ldx, Y, ldy);
-  PBS_CUDA(cudaGetLastError());
+  PBS_LAUNCHED();
 }
 
 template <class T>
@@ -218,7 +218,7 @@ void apply_curl_adj(const Level& L, const double* d_ph, int cpg, const cx<T>* X,
                     int ncols, cudaStream_t s) {
   if (ncols <= 0) return;
   k_curl_adj<T><<<grid2(L.n, L.m, ncols), dim3(kBX, kBY), 0, s>>>(L.lvl<T>(), d_ph, cpg, X, ldx, Y, ldy);
-  PBS_CUDA(cudaGetLastError());
+  PBS_LAUNCHED();
 }
 
 template <class T>
@@ -226,7 +226,7 @@ void apply_lift(const Level& L, const double* d_ph, int cpg, const cx<T>* X, lon
                 cudaStream_t s) {
   if (ncols <= 0) return;
   k_lift<T><<<grid2(L.n, L.m, ncols), dim3(kBX, kBY), 0, s>>>(L.lvl<T>(), d_ph, cpg, X, ldx, Y, ldy);
-  PBS_CUDA(cudaGetLastError());
+  PBS_LAUNCHED();
 }
 
 template <class T>
@@ -234,7 +234,7 @@ void apply_lift_adj(const Level& L, const double* d_ph, int cpg, const cx<T>* X,
                     int ncols, cudaStream_t s) {
   if (ncols <= 0) return;
   k_lift_adj<T><<<grid2(L.n, L.m, ncols), dim3(kBX, kBY), 0, s>>>(L.lvl<T>(), d_ph, cpg, X, ldx, Y, ldy);
-  PBS_CUDA(cudaGetLastError());
+  PBS_LAUNCHED();
 }
 
 template <class T>
@@ -242,7 +242,7 @@ void apply_nodal(const Level& L, const double* d_ph, int cpg, const cx<T>* X, cx
                  int ncols, T sP, T sB, cudaStream_t s) {
   if (ncols <= 0) return;
   k_apply_nodal<T><<<grid2(L.n, L.m, ncols), dim3(kBX, kBY), 0, s>>>(L.lvl<T>(), d_ph, cpg, X, Y, B, ld, sP, sB);
-  PBS_CUDA(cudaGetLastError());
+  PBS_LAUNCHED();
 }
 
 template <class T>
@@ -251,7 +251,7 @@ void prolong_edge(const Level& f, const Level& c, const double* d_ph, int cpg, c
   if (ncols <= 0) return;
   k_prolong_edge<T><<<grid2(f.n, f.m, ncols), dim3(kBX, kBY), 0, s>>>(f.n, f.m, c.n, c.m, d_ph, cpg, Xc, ldc, Yf, ldf,
                                                                         accumulate ? 1 : 0);
-  PBS_CUDA(cudaGetLastError());
+  PBS_LAUNCHED();
 }
 
 template <class T>
@@ -260,7 +260,7 @@ void restrict_edge(const Level& f, const Level& c, const double* d_ph, int cpg, 
   if (ncols <= 0) return;
   k_restrict_edge<T><<<grid2(c.n, c.m, ncols), dim3(kBX, kBY), 0, s>>>(f.n, f.m, c.n, c.m, d_ph, cpg, Xf, ldf, Yc,
                                                                          ldc);
-  PBS_CUDA(cudaGetLastError());
+  PBS_LAUNCHED();
 }
 
 template <class T>
@@ -269,7 +269,7 @@ void prolong_node(const Level& f, const Level& c, const double* d_ph, int cpg, c
   if (ncols <= 0) return;
   k_prolong_node<T><<<grid2(f.n, f.m, ncols), dim3(kBX, kBY), 0, s>>>(f.n, f.m, c.n, c.m, d_ph, cpg, Xc, ldc, Yf, ldf,
                                                                         accumulate ? 1 : 0);
-  PBS_CUDA(cudaGetLastError());
+  PBS_LAUNCHED();
 }
 
 template <class T>
@@ -278,7 +278,7 @@ void restrict_node(const Level& f, const Level& c, const double* d_ph, int cpg, 
   if (ncols <= 0) return;
   k_restrict_node<T><<<grid2(c.n, c.m, ncols), dim3(kBX, kBY), 0, s>>>(f.n, f.m, c.n, c.m, d_ph, cpg, Xf, ldf, Yc,
                                                                          ldc);
-  PBS_CUDA(cudaGetLastError());
+  PBS_LAUNCHED();
 }
 
 #define PBS_INST_OPS(T)                                                                                             \

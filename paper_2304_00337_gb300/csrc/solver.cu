@@ -13,6 +13,7 @@
 // (E_hat, E^(m), E^(m-1)) with E_hat = E - W; using W and the implicit
 // direction P keeps the trial basis well conditioned.
 #include <algorithm>
+#include <atomic>
 #include <cstdlib>
 #include <cmath>
 #include <functional>
@@ -28,6 +29,46 @@
 namespace pbs {
 
 static thread_local std::string g_last_error;
+thread_local KernelTimer* g_timer = nullptr;
+static std::atomic<unsigned long long> g_launches{0};
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+void timer_begin(int cls, cudaStream_t s, double work) {
+  KernelTimer* t = g_timer;
+  if (!t || !(t->mask & (1u << cls))) return;
+  std::pair<cudaEvent_t, cudaEvent_t> ev;
+  if (!t->pool.empty()) {
+    ev = t->pool.back();
+    t->pool.pop_back();
+  } else {
+    PBS_CUDA(cudaEventCreate(&ev.first));
+    PBS_CUDA(cudaEventCreate(&ev.second));
+  }
+  PBS_CUDA(cudaEventRecord(ev.first, s));
+  t->pending.push_back(TimedLaunch{cls, work, ev.first, ev.second});
+}
+
+void timer_end(int cls, cudaStream_t s) {
+  KernelTimer* t = g_timer;
+  if (!t || !(t->mask & (1u << cls)) || t->pending.empty()) return;
+  PBS_CUDA(cudaEventRecord(t->pending.back().stop, s));
+}
+
+void timer_collect() {
+  KernelTimer* t = g_timer;
+  if (!t) return;
+  for (auto& l : t->pending) {
+    PBS_CUDA(cudaEventSynchronize(l.stop));
+    float ms = 0.f;
+    PBS_CUDA(cudaEventElapsedTime(&ms, l.start, l.stop));
+    t->total_ms[l.cls] += ms;
+    t->work[l.cls] += l.work;
+    t->launches[l.cls] += 1;
+    t->pool.push_back({l.start, l.stop});
+  }
+  t->pending.clear();
+}
 
 void fail(int status, const std::string& what) { throw Error{status, what}; }
 
@@ -145,6 +186,9 @@ struct pbs_ctx {
   Work W;
   bool have_w = false;
   double last_theta_max = 1e300;  // largest Ritz value of the latest start block
+  KernelTimer timer;
+  double* d_eps_in = nullptr;     // device copy of the latest host permittivity array
+  long d_eps_len = 0;
   explicit pbs_ctx(size_t budget) : mem(budget) {}
 };
 
@@ -158,6 +202,18 @@ struct DeviceGuard {
   }
   ~DeviceGuard() {
     if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+// Installs the context's kernel timer for the duration of an ABI call.
+struct TimerScope {
+  explicit TimerScope(pbs_ctx* ctx) { g_timer = ctx->timer.mask ? &ctx->timer : nullptr; }
+  ~TimerScope() {
+    try {
+      timer_collect();
+    } catch (...) {
+    }
+    g_timer = nullptr;
   }
 };
 
@@ -223,24 +279,18 @@ void ensure_hierarchy_host(pbs_ctx* ctx, const pbs_geom* g, double mu, int coars
   if (!g->eps) fail(PBS_EINVAL, "eps is NULL");
   const long N = (long)g->n * g->m;
   const uint64_t h = fnv1a(g->eps, N * sizeof(double));
-  uint64_t key = h;
-  key = fnv1a(&g->a, sizeof g->a, key);
-  key = fnv1a(&g->b, sizeof g->b, key);
-  key = fnv1a(&g->n, sizeof g->n, key);
-  key = fnv1a(&g->m, sizeof g->m, key);
-  key = fnv1a(&mu, sizeof mu, key);
-  key = fnv1a(&coarsest, sizeof coarsest, key);
-  if (ctx->have_h && ctx->H.key == key) return;
-  double* d_eps = (double*)ctx->mem.alloc(N * sizeof(double));
-  try {
-    PBS_CUDA(cudaMemcpyAsync(d_eps, g->eps, N * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
-    ensure_hierarchy(ctx, g->a, g->b, g->n, g->m, d_eps, h, mu, coarsest);
-  } catch (...) {
-    ctx->mem.free(d_eps);
-    throw;
+  // the permittivity is an input of every call: it is copied each time, and the
+  // resident hierarchy is rebuilt only when geometry, mu or coarsest changed
+  if (ctx->d_eps_len != N) {
+    ctx->mem.free(ctx->d_eps_in);
+    ctx->d_eps_in = nullptr;
+    ctx->d_eps_len = 0;
+    ctx->d_eps_in = (double*)ctx->mem.alloc(N * sizeof(double));
+    ctx->d_eps_len = N;
   }
+  PBS_CUDA(cudaMemcpyAsync(ctx->d_eps_in, g->eps, N * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  ensure_hierarchy(ctx, g->a, g->b, g->n, g->m, ctx->d_eps_in, h, mu, coarsest);
   PBS_CUDA(cudaStreamSynchronize(ctx->stream));
-  ctx->mem.free(d_eps);
 }
 
 uint64_t device_eps_hash(pbs_ctx* ctx, const double* d_eps, long N) {
@@ -248,7 +298,7 @@ uint64_t device_eps_hash(pbs_ctx* ctx, const double* d_eps, long N) {
   unsigned long long h = 0;
   PBS_CUDA(cudaMemsetAsync(d_h, 0, sizeof h, ctx->stream));
   k_hash_eps<<<nblocks(N), 256, 0, ctx->stream>>>(d_eps, N, d_h);
-  PBS_CUDA(cudaGetLastError());
+  PBS_LAUNCHED();
   PBS_CUDA(cudaMemcpyAsync(&h, d_h, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
   PBS_CUDA(cudaStreamSynchronize(ctx->stream));
   ctx->mem.free(d_h);
@@ -354,7 +404,7 @@ void project(pbs_ctx* ctx, const pbs_opts& o, double2* X, int ncols, int cycles,
     apply_nodal<T>(L0, K.d_ph, ncols, phi, res, rhs, N, ncols, T(-1), T(1), s);
     nodal_vcycle<T>(H, K, Bufs<T>::nmg(W), 0, res, dphi, N, ncols, o.nu_pre, o.nu_post, s);
     k_axpy<T><<<nblocks(N * ncols), 256, 0, s>>>(phi, dphi, N * ncols);
-    PBS_CUDA(cudaGetLastError());
+    PBS_LAUNCHED();
   }
   sub_lift<T>(L0, K.d_ph, ncols, phi, N, X, D, ncols, s);
   if (K.gamma) deflate_constants(L0, X, D, ncols, W.parts, s);
@@ -443,11 +493,12 @@ KResult iterate(pbs_ctx* ctx, const pbs_opts& o, cudaStream_t s) {
     // Rayleigh quotients in factored form, then the FP64 residual
     rayleigh_parts(L0, ph, p, E, D, p, W.parts, W.rq, s);
     k_rq<<<1, 64, 0, s>>>(W.rq, W.lam, p);
-    PBS_CUDA(cudaGetLastError());
+    PBS_LAUNCHED();
     residual(L0, ph, p, E, W.R, D, p, W.lam, W.parts, W.norms, s);
     PBS_CUDA(cudaMemcpyAsync(h_norms.data(), W.norms, 2 * p * sizeof(double), cudaMemcpyDeviceToHost, s));
     PBS_CUDA(cudaMemcpyAsync(h_lam.data(), W.lam, p * sizeof(double), cudaMemcpyDeviceToHost, s));
     PBS_CUDA(cudaStreamSynchronize(s));
+    timer_collect();
     out.lam.assign(h_lam.begin(), h_lam.begin() + o.nev);
     theta_max = 0.0;
     for (int j = 0; j < p; ++j) theta_max = std::max(theta_max, std::fabs(h_lam[j]));
@@ -477,7 +528,7 @@ KResult iterate(pbs_ctx* ctx, const pbs_opts& o, cudaStream_t s) {
     const double2* trial;
     if (o.span == 1) {
       k_sub_from<<<nblocks(D * p), 256, 0, s>>>(E, Wd, D * p);  // E_hat = E - B R
-      PBS_CUDA(cudaGetLastError());
+      PBS_LAUNCHED();
       project_dispatch(ctx, o, Wd, p, s, cyc);
       q = p;
       trial = Wd;
@@ -652,6 +703,11 @@ int pbs_destroy(pbs_ctx* ctx) {
     }
     if (ctx->have_h) free_hierarchy(ctx->mem, ctx->H);
     free_kdata(ctx->mem, ctx->K);
+    ctx->mem.free(ctx->d_eps_in);
+    for (auto& ev : ctx->timer.pool) {
+      cudaEventDestroy(ev.first);
+      cudaEventDestroy(ev.second);
+    }
     cudaStreamDestroy(ctx->stream);
     delete ctx;
   });
@@ -663,6 +719,7 @@ int pbs_solve_k(pbs_ctx* ctx, const pbs_geom* geom, const pbs_opts* opts, const 
   int status = PBS_OK;
   const int rc = run_guarded_impl([&] {
     DeviceGuard g(ctx->device);
+    TimerScope ts(ctx);
     const pbs_opts& o = *opts;
     validate_opts(o);
     ensure_hierarchy_host(ctx, geom, effective_mu(o, geom->a, geom->b), o.coarsest);
@@ -714,10 +771,11 @@ int solve_path_impl(pbs_ctx* ctx, const pbs_opts& o, int nk, const double* ks, d
     if (!r.converged && first_bad == PBS_OK) first_bad = PBS_ENOCONV;
     // history ring: newest first
     if (o.extrap_depth > 0) {
+      // shift the ring one slot (oldest first: source and destination never overlap)
       const int keep = std::min(nhist, 2);
-      if (keep > 0)
-        PBS_CUDA(cudaMemcpyAsync(W.hist + D * p, W.hist, sizeof(double2) * D * p * keep, cudaMemcpyDeviceToDevice,
-                                 ctx->stream));
+      for (int slot = keep; slot >= 1; --slot)
+        PBS_CUDA(cudaMemcpyAsync(W.hist + D * p * slot, W.hist + D * p * (slot - 1), sizeof(double2) * D * p,
+                                 cudaMemcpyDeviceToDevice, ctx->stream));
       PBS_CUDA(cudaMemcpyAsync(W.hist, W.S, sizeof(double2) * D * p, cudaMemcpyDeviceToDevice, ctx->stream));
       nhist = std::min(nhist + 1, 3);
     }
@@ -732,6 +790,7 @@ int pbs_solve_path(pbs_ctx* ctx, const pbs_geom* geom, const pbs_opts* opts, int
   int status = PBS_OK;
   const int rc = run_guarded_impl([&] {
     DeviceGuard g(ctx->device);
+    TimerScope ts(ctx);
     validate_opts(*opts);
     if (nk == 0) return;
     ensure_hierarchy_host(ctx, geom, effective_mu(*opts, geom->a, geom->b), opts->coarsest);
@@ -749,6 +808,7 @@ int pbs_solve_path_device(pbs_ctx* ctx, double a, double b, int n, int m, const 
   int status = PBS_OK;
   const int rc = run_guarded_impl([&] {
     DeviceGuard g(ctx->device);
+    TimerScope ts(ctx);
     validate_opts(*opts);
     validate_mesh(a, b, n, m);
     cudaStream_t us = (cudaStream_t)cuda_stream;
@@ -784,6 +844,7 @@ int pbs_apply(pbs_ctx* ctx, const pbs_geom* geom, const pbs_opts* opts, int op, 
   if (ncols > 0 && (!x || !y)) return PBS_EINVAL;
   return run_guarded_impl([&] {
     DeviceGuard g(ctx->device);
+    TimerScope ts(ctx);
     const pbs_opts& o = *opts;
     if (o.precision != PBS_FP64 && o.precision != PBS_MIXED) fail(PBS_EINVAL, "unknown precision");
     if (o.coarsest < 2 || o.nodal_cycles < 1 || o.nu_pre < 0 || o.nu_post < 0) fail(PBS_EINVAL, "bad multigrid options");
@@ -923,6 +984,7 @@ int pbs_gram(pbs_ctx* ctx, const pbs_geom* geom, const double k[2], int q, const
   if (q > 0 && (!S || !GM || !GA)) return PBS_EINVAL;
   return run_guarded_impl([&] {
     DeviceGuard g(ctx->device);
+    TimerScope ts(ctx);
     if (q == 0) return;
     pbs_opts o;
     pbs_default_opts(&o);
@@ -958,6 +1020,7 @@ int pbs_rayleigh_ritz(pbs_ctx* ctx, const pbs_geom* geom, const pbs_opts* opts, 
     return PBS_EINVAL;
   return run_guarded_impl([&] {
     DeviceGuard g(ctx->device);
+    TimerScope ts(ctx);
     const pbs_opts& o = *opts;
     if (q > kMaxTrial) fail(PBS_EINVAL, "q too large");
     ensure_hierarchy_host(ctx, geom, effective_mu(o, geom->a, geom->b), o.coarsest);
@@ -979,5 +1042,58 @@ int pbs_rayleigh_ritz(pbs_ctx* ctx, const pbs_geom* geom, const pbs_opts* opts, 
     cudaEventDestroy(ev);
   });
 }
+
+static const char* kClassNames[KC_COUNT] = {"", "edge_smooth", "node_smooth", "gram", "small_rr", "residual",
+                                             "block_update", "lift_adj_mass", "edge_apply"};
+
+static int class_of(const char* name) {
+  for (int c = 1; c < KC_COUNT; ++c)
+    if (std::strcmp(name, kClassNames[c]) == 0) return c;
+  return -1;
+}
+
+int pbs_profile_enable(pbs_ctx* ctx, const char* classes) {
+  if (!ctx) return PBS_EINVAL;
+  unsigned mask = 0;
+  if (classes && *classes) {
+    if (std::strcmp(classes, "all") == 0) {
+      mask = ((1u << KC_COUNT) - 1) & ~1u;
+    } else {
+      std::string list(classes);
+      size_t pos = 0;
+      while (pos <= list.size()) {
+        const size_t e = std::min(list.find(',', pos), list.size());
+        const std::string name = list.substr(pos, e - pos);
+        const int c = class_of(name.c_str());
+        if (c < 0) {
+          g_last_error = "unknown kernel class: " + name;
+          return PBS_EINVAL;
+        }
+        mask |= 1u << c;
+        pos = e + 1;
+      }
+    }
+  }
+  KernelTimer& t = ctx->timer;
+  t.mask = mask;
+  for (int c = 0; c < KC_COUNT; ++c) {
+    t.total_ms[c] = 0.0;
+    t.work[c] = 0.0;
+    t.launches[c] = 0;
+  }
+  return PBS_OK;
+}
+
+int pbs_profile_read(pbs_ctx* ctx, const char* kernel_class, double* total_ms, long* launches, double* work) {
+  if (!ctx || !kernel_class || !total_ms || !launches || !work) return PBS_EINVAL;
+  const int c = class_of(kernel_class);
+  if (c < 0) return PBS_EINVAL;
+  *total_ms = ctx->timer.total_ms[c];
+  *launches = ctx->timer.launches[c];
+  *work = ctx->timer.work[c];
+  return PBS_OK;
+}
+
+unsigned long long pbs_launch_count(void) { return g_launches.load(); }
 
 }  // extern "C"
