@@ -4,6 +4,7 @@
 // Reductions are two-stage with a fixed summation order (deterministic).
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 
 #include "internal.h"
 
@@ -269,30 +270,66 @@ __global__ void k_gram_finalize(const double2* __restrict__ part, int npart, int
 }
 
 // ---- small dense Rayleigh-Ritz (one block) -------------------------------
-// scratch layout (double2 unless noted), q <= kMaxTrial:
-//   G [q*q]  scaled M-Gram, overwritten by its Cholesky rows R (upper)
-//   A [q*q]  scaled A-Gram
-//   T [q*q]  R_K^{-1} (r x r, upper)
-//   Y [q*q]  work
-//   H [q*q]  T^* A_K T, diagonalised in place
-//   V [q*q]  Jacobi eigenvectors
-//   d [q] (double) column scales, keep [q] (int), theta [q] (double)
+// Given the Gram matrices GM = S^* M S and GA = S^* A S of a trial block S
+// (q columns), find the p smallest Ritz pairs (Section 4, eq. ritz_eigenvalue):
+//  1. scale to unit diagonal, Cholesky GM = R^* R dropping directions whose
+//     pivot falls below kDropTol (a span that lost rank);
+//  2. H = R^{-*} GA R^{-1} by two triangular solves;
+//  3. Householder reduction H = Q T Q^*, T Hermitian tridiagonal, made real by
+//     a diagonal unitary scaling;
+//  4. the p smallest eigenvalues of T by bisection on Sturm counts, their
+//     eigenvectors by inverse iteration (re-orthogonalised inside clusters);
+//  5. back-transformation and C = D R^{-1} Q U.
+// Everything runs in FP64 in one thread block (the problem is q x q, q <= 96).
 constexpr double kDropTol = 1e-12;  // relative pivot below which a trial direction is dropped
+constexpr int kRRThreads = 256;
 
-__device__ __forceinline__ double2 ldg2(const double2* p) { return *p; }
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double2 warp_sum2(double2 v) {
+  v.x = warp_sum(v.x);
+  v.y = warp_sum(v.y);
+  return v;
+}
 
-__global__ void __launch_bounds__(256) k_small_rr(const double2* __restrict__ GM, const double2* __restrict__ GA, int q,
-                                                  int p, double2* __restrict__ Cout, double* __restrict__ theta_out,
-                                                  double2* __restrict__ scr, int* __restrict__ info) {
-  const int tid = threadIdx.x, nt = blockDim.x;
+// number of eigenvalues of the real symmetric tridiagonal (a, e) below x
+__device__ int sturm_count(const double* a, const double* e2, int n, double x, double pivmin) {
+  int cnt = 0;
+  double d = a[0] - x;
+  if (fabs(d) < pivmin) d = -pivmin;
+  if (d < 0) ++cnt;
+  for (int i = 1; i < n; ++i) {
+    d = (a[i] - x) - e2[i - 1] / d;
+    if (fabs(d) < pivmin) d = -pivmin;
+    if (d < 0) ++cnt;
+  }
+  return cnt;
+}
+
+__global__ void __launch_bounds__(kRRThreads) k_small_rr(const double2* __restrict__ GM, const double2* __restrict__ GA,
+                                                         int q, int p, double2* __restrict__ Cout,
+                                                         double* __restrict__ theta_out, double2* __restrict__ scr,
+                                                         int* __restrict__ info, int in_smem) {
+  extern __shared__ double2 dsm[];
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
   const long qq = (long)q * q;
-  double2 *G = scr, *A = scr + qq, *T = scr + 2 * qq, *Y = scr + 3 * qq, *H = scr + 4 * qq, *V = scr + 5 * qq;
-  double* d = (double*)(scr + 6 * qq);
-  int* kidx = (int*)(d + q);
-  __shared__ int s_r, s_bad;
-  __shared__ double s_piv;
+  double2* G = in_smem ? dsm : scr;            // scaled M-Gram, then R (rows)
+  double2* H = G + qq;                          // scaled A-Gram, then H, then reflectors
+  double2* U = H + qq;                          // q x p eigenvectors
+  __shared__ double d[kMaxTrial];               // column scales
   __shared__ int s_keep[kMaxTrial];
-  // 1. scale to unit diagonal
+  __shared__ double ta[kMaxTrial], te[kMaxTrial], te2[kMaxTrial], tbeta[kMaxTrial];
+  __shared__ double2 talpha[kMaxTrial], tphase[kMaxTrial], tvec[kMaxTrial], tp[kMaxTrial];
+  __shared__ double lam[kMaxBlock];
+  __shared__ double Z[kMaxTrial * kMaxBlock];   // real eigenvectors of the tridiagonal, column j at j*r
+  __shared__ int s_r, s_bad;
+  __shared__ double s_piv, s_red[2 * kRRThreads / 32];
+  long long t_phase[8];
+  t_phase[0] = clock64();
+
+  // 1. scaling and load
   for (int i = tid; i < q; i += nt) {
     const double g = GM[(long)i * q + i].x;
     d[i] = (g > 0.0 && isfinite(g)) ? 1.0 / sqrt(g) : 0.0;
@@ -301,14 +338,16 @@ __global__ void __launch_bounds__(256) k_small_rr(const double2* __restrict__ GM
   __syncthreads();
   for (long t = tid; t < qq; t += nt) {
     const int i = int(t % q), j = int(t / q);
-    const double s = d[i] * d[j];
+    const double sc = d[i] * d[j];
     const double2 gm = GM[t], ga = GA[t];
     if (!isfinite(gm.x) || !isfinite(gm.y) || !isfinite(ga.x) || !isfinite(ga.y)) s_bad = 1;
-    G[t] = s * gm;
-    A[t] = s * ga;
+    G[t] = sc * gm;
+    H[t] = sc * ga;
   }
   __syncthreads();
-  // 2. Cholesky G = R^* R (R upper, rows stored in G) with dropping of dependent directions
+  // Cholesky with dropping: R row k stored in G[k][k:], i.e. G[j*q + k].  A dropped
+  // direction k becomes a decoupled unit row and column of R (so R^{-1} acts as the
+  // inverse of the kept block) and an isolated Ritz value above every kept one.
   for (int k = 0; k < q; ++k) {
     if (tid == 0) {
       const double pv = G[(long)k * q + k].x;
@@ -319,7 +358,7 @@ __global__ void __launch_bounds__(256) k_small_rr(const double2* __restrict__ GM
     __syncthreads();
     const double piv = s_piv;
     if (piv > 0.0) {
-      for (int j = k + tid; j < q; j += nt) {  // row k of R
+      for (int j = k + tid; j < q; j += nt) {
         const double2 v = G[(long)j * q + k];
         G[(long)j * q + k] = make_double2(v.x / piv, v.y / piv);
       }
@@ -328,195 +367,310 @@ __global__ void __launch_bounds__(256) k_small_rr(const double2* __restrict__ GM
       for (long t = tid; t < (long)rem * rem; t += nt) {
         const int ii = k + 1 + int(t % rem), jj = k + 1 + int(t / rem);
         if (ii > jj) continue;
-        // G[ii][jj] -= conj(R[k][ii]) R[k][jj]
-        const double2 rki = G[(long)ii * q + k], rkj = G[(long)jj * q + k];
-        G[(long)jj * q + ii] = G[(long)jj * q + ii] - cmulc(rki, rkj);
+        G[(long)jj * q + ii] = G[(long)jj * q + ii] - cmulc(G[(long)ii * q + k], G[(long)jj * q + k]);
       }
     } else {
-      for (int j = k + tid; j < q; j += nt) G[(long)j * q + k] = make_double2(0, 0);
+      for (int j = tid; j < q; j += nt) {
+        G[(long)j * q + k] = make_double2(j == k ? 1.0 : 0.0, 0.0);  // row k
+        if (j < k) G[(long)k * q + j] = make_double2(0, 0);          // column k above the diagonal
+        H[(long)j * q + k] = make_double2(0, 0);                       // decouple the A-Gram
+        H[(long)k * q + j] = make_double2(0, 0);
+      }
     }
     __syncthreads();
   }
   if (tid == 0) {
     int r = 0;
-    for (int k = 0; k < q; ++k)
-      if (s_keep[k]) kidx[r++] = k;
+    for (int k = 0; k < q; ++k) r += s_keep[k];
     s_r = r;
   }
   __syncthreads();
-  const int r = s_r;
-  if (r < p || s_bad) {
+  if (s_r < p || s_bad) {
     if (tid == 0) {
       info[0] = s_bad ? -2 : -1;
-      info[1] = r;
+      info[1] = s_r;
     }
     return;
   }
-  // 3. T = R_K^{-1}: columns in parallel, back substitution
-  for (int c = tid; c < r; c += nt) {
-    for (int i = r - 1; i >= 0; --i) {
-      double2 s = make_double2(i == c ? 1.0 : 0.0, 0.0);
-      for (int k = i + 1; k <= c; ++k) s = s - cmul(G[(long)kidx[k] * q + kidx[i]], T[(long)c * q + k]);
-      const double dii = G[(long)kidx[i] * q + kidx[i]].x;
-      T[(long)c * q + i] = i > c ? make_double2(0, 0) : make_double2(s.x / dii, s.y / dii);
+  t_phase[1] = clock64();
+  const int r = q;
+  // 2a. Y = A R^{-1}: row i of Y solves y R = a_i; column j in sequence, rows by warps
+  for (int j = 0; j < r; ++j) {
+    const double rjj = G[(long)j * q + j].x;
+    for (int i = warp; i < r; i += nw) {
+      double2 acc = make_double2(0, 0);
+      for (int k = lane; k < j; k += 32) acc = acc + cmul(H[(long)k * q + i], G[(long)j * q + k]);
+      acc = warp_sum2(acc);
+      if (lane == 0) {
+        const double2 v = H[(long)j * q + i] - acc;
+        H[(long)j * q + i] = make_double2(v.x / rjj, v.y / rjj);
+      }
     }
+    __syncthreads();
+  }
+  // 2b. H = R^{-*} Y: column c solves R^* h = y_c; row i in sequence, columns by warps
+  for (int i = 0; i < r; ++i) {
+    const double rii = G[(long)i * q + i].x;
+    for (int c = warp; c < r; c += nw) {
+      double2 acc = make_double2(0, 0);
+      for (int k = lane; k < i; k += 32) acc = acc + cmulc(G[(long)i * q + k], H[(long)c * q + k]);
+      acc = warp_sum2(acc);
+      if (lane == 0) {
+        const double2 v = H[(long)c * q + i] - acc;
+        H[(long)c * q + i] = make_double2(v.x / rii, v.y / rii);
+      }
+    }
+    __syncthreads();
+  }
+  // isolated value for dropped directions: twice the Gershgorin bound of the rest, plus one
+  if (tid == 0) {
+    double bound = 0.0;
+    for (int i = 0; i < r; ++i) {
+      if (!s_keep[i]) continue;
+      double rs = 0.0;
+      for (int j = 0; j < r; ++j) rs += sqrt(nrm2(H[(long)j * q + i]));
+      bound = fmax(bound, rs);
+    }
+    for (int i = 0; i < r; ++i)
+      if (!s_keep[i]) H[(long)i * q + i] = make_double2(2.0 * bound + 1.0, 0.0);
   }
   __syncthreads();
-  // 4. H = T^* A_K T
+  // exact Hermitian symmetry
   for (long t = tid; t < (long)r * r; t += nt) {
-    const int i = int(t % r), c = int(t / r);
-    double2 s = make_double2(0, 0);
-    for (int k = 0; k <= c; ++k) s = s + cmul(A[(long)kidx[k] * q + kidx[i]], T[(long)c * q + k]);
-    Y[(long)c * q + i] = s;
-  }
-  __syncthreads();
-  for (long t = tid; t < (long)r * r; t += nt) {
-    const int i = int(t % r), c = int(t / r);
-    double2 s = make_double2(0, 0);
-    for (int k = 0; k <= i; ++k) s = s + cmulc(T[(long)i * q + k], Y[(long)c * q + k]);
-    H[(long)c * q + i] = s;
-    V[(long)c * q + i] = make_double2(i == c ? 1.0 : 0.0, 0.0);
-  }
-  __syncthreads();
-  for (long t = tid; t < (long)r * r; t += nt) {  // exact Hermitian symmetry
     const int i = int(t % r), c = int(t / r);
     if (i < c) {
-      const double2 u = H[(long)c * q + i], l = H[(long)i * q + c];
-      H[(long)c * q + i] = make_double2(0.5 * (u.x + l.x), 0.5 * (u.y - l.y));
-      H[(long)i * q + c] = make_double2(0.5 * (u.x + l.x), -0.5 * (u.y - l.y));
+      const double2 up = H[(long)c * q + i], lo = H[(long)i * q + c];
+      const double2 m = make_double2(0.5 * (up.x + lo.x), 0.5 * (up.y - lo.y));
+      H[(long)c * q + i] = m;
+      H[(long)i * q + c] = conj(m);
     } else if (i == c) {
       H[(long)c * q + i].y = 0.0;
     }
   }
   __syncthreads();
-  // 5. cyclic Jacobi with a round-robin (parallel) ordering
-  __shared__ int s_pp[kMaxTrial / 2 + 1], s_qq[kMaxTrial / 2 + 1];
-  __shared__ double s_c[kMaxTrial / 2 + 1], s_s[kMaxTrial / 2 + 1];
-  __shared__ double2 s_w[kMaxTrial / 2 + 1];
-  __shared__ double s_off, s_dg;
-  __shared__ double s_poff[256], s_pdg[256];
-  const int rr = (r % 2) ? r + 1 : r;  // with a dummy player when r is odd
-  const int npair = rr / 2;
-  for (int sweep = 0; sweep < 60 && r > 1; ++sweep) {
-    // convergence test (fixed summation order: per-thread partials, then thread 0)
-    double off = 0, dg = 0;
-    for (long t = tid; t < (long)r * r; t += nt) {
-      const int i = int(t % r), c = int(t / r);
-      if (i < c) off += nrm2(H[(long)c * q + i]);
-      else if (i == c) dg += H[(long)c * q + i].x * H[(long)c * q + i].x;
-    }
-    s_poff[tid] = off;
-    s_pdg[tid] = dg;
+  t_phase[2] = clock64();
+  // 3. Householder tridiagonalisation; reflector k acts on rows/cols k+1..r-1 and is
+  //    stored in column k below the diagonal (v, with v_0 = x_0 - alpha) and tbeta[k]
+  for (int k = 0; k + 2 < r; ++k) {
+    const int m = r - k - 1;  // length of x
+    // sigma = ||x||
+    double s2 = 0.0;
+    for (int i = tid; i < m; i += nt) s2 += nrm2(H[(long)k * q + k + 1 + i]);
+    s2 = warp_sum(s2);
+    if (lane == 0) s_red[warp] = s2;
     __syncthreads();
     if (tid == 0) {
-      double so = 0, sd = 0;
-      for (int t = 0; t < nt; ++t) {
-        so += s_poff[t];
-        sd += s_pdg[t];
+      double tot = 0.0;
+      for (int w = 0; w < nw; ++w) tot += s_red[w];
+      const double sigma = sqrt(tot);
+      const double2 x0 = H[(long)k * q + k + 1];
+      const double ax0 = sqrt(nrm2(x0));
+      double2 ph = ax0 > 0.0 ? make_double2(x0.x / ax0, x0.y / ax0) : make_double2(1.0, 0.0);
+      if (sigma > 0.0 && tot > 1e-300) {
+        const double2 alpha = -sigma * ph;  // x -> alpha e_1
+        talpha[k] = alpha;
+        tbeta[k] = 1.0 / (sigma * (sigma + ax0));
+        H[(long)k * q + k + 1] = x0 - alpha;  // v_0
+      } else {
+        talpha[k] = x0;
+        tbeta[k] = 0.0;
       }
-      s_off = so;
-      s_dg = sd;
     }
     __syncthreads();
-    if (!(s_off > 1e-34 * s_dg)) break;
-    for (int step = 0; step < rr - 1; ++step) {
-      for (int k = tid; k < npair; k += nt) {
-        int a, b;
-        if (k == 0) { a = rr - 1; b = step; }
-        else { a = (step + k) % (rr - 1); b = (step - k + rr - 1) % (rr - 1); }
-        if (a > b) { const int t2 = a; a = b; b = t2; }
-        s_pp[k] = a;
-        s_qq[k] = b;
-        double c = 1.0, s = 0.0;
-        double2 w = make_double2(1, 0);
-        if (b < r) {
-          const double2 h = H[(long)b * q + a];
-          const double ah = sqrt(nrm2(h));
-          if (ah > 0.0) {
-            const double app = H[(long)a * q + a].x, aqq = H[(long)b * q + b].x;
-            const double th = (aqq - app) / (2.0 * ah);
-            const double t = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
-            c = 1.0 / sqrt(t * t + 1.0);
-            s = t * c;
-            w = make_double2(h.x / ah, -h.y / ah);  // conj(h)/|h|
-          }
-        }
-        s_c[k] = c;
-        s_s[k] = s;
-        s_w[k] = w;
+    const double beta = tbeta[k];
+    if (beta != 0.0) {
+      // p = beta * Hsub v (rows by warps)
+      for (int i = warp; i < m; i += nw) {
+        double2 acc = make_double2(0, 0);
+        for (int j = lane; j < m; j += 32) acc = acc + cmul(H[(long)(k + 1 + j) * q + k + 1 + i], H[(long)k * q + k + 1 + j]);
+        acc = warp_sum2(acc);
+        if (lane == 0) tp[i] = beta * acc;
       }
       __syncthreads();
-      // columns: H <- H J, V <- V J, J = [[c, s], [-s w, c w]] with w = conj(h)/|h|
-      for (long t = tid; t < (long)npair * r; t += nt) {
-        const int k = int(t / r), row = int(t % r);
-        const int a = s_pp[k], b = s_qq[k];
-        if (b >= r || s_s[k] == 0.0) continue;
-        const double c = s_c[k], s = s_s[k];
-        const double2 w = s_w[k];
-        const double2 ha = H[(long)a * q + row], hb = cmul(w, H[(long)b * q + row]);
-        H[(long)a * q + row] = c * ha - s * hb;
-        H[(long)b * q + row] = s * ha + c * hb;
-        const double2 va = V[(long)a * q + row], vb = cmul(w, V[(long)b * q + row]);
-        V[(long)a * q + row] = c * va - s * vb;
-        V[(long)b * q + row] = s * va + c * vb;
-      }
+      // K = beta/2 v^* p ; w = p - K v  (K is real for Hermitian H)
+      double kk = 0.0;
+      for (int i = tid; i < m; i += nt) kk += cmulc(H[(long)k * q + k + 1 + i], tp[i]).x;
+      kk = warp_sum(kk);
+      if (lane == 0) s_red[warp] = kk;
       __syncthreads();
-      // rows: H <- J^* H
-      for (long t = tid; t < (long)npair * r; t += nt) {
-        const int k = int(t / r), col = int(t % r);
-        const int a = s_pp[k], b = s_qq[k];
-        if (b >= r || s_s[k] == 0.0) continue;
-        const double c = s_c[k], s = s_s[k];
-        const double2 wc = conj(s_w[k]);
-        const double2 ha = H[(long)col * q + a], hb = cmul(wc, H[(long)col * q + b]);
-        H[(long)col * q + a] = c * ha - s * hb;
-        H[(long)col * q + b] = s * ha + c * hb;
-      }
+      double K = 0.0;
+      for (int w = 0; w < nw; ++w) K += s_red[w];
+      K *= 0.5 * beta;
+      for (int i = tid; i < m; i += nt) tvec[i] = tp[i] - K * H[(long)k * q + k + 1 + i];
       __syncthreads();
-      for (int k = tid; k < npair; k += nt) {
-        const int a = s_pp[k], b = s_qq[k];
-        if (b >= r || s_s[k] == 0.0) continue;
-        H[(long)b * q + a] = make_double2(0, 0);
-        H[(long)a * q + b] = make_double2(0, 0);
-        H[(long)a * q + a].y = 0.0;
-        H[(long)b * q + b].y = 0.0;
+      // Hsub -= v w^* + w v^*
+      for (long t = tid; t < (long)m * m; t += nt) {
+        const int i = int(t % m), j = int(t / m);
+        const double2 vi = H[(long)k * q + k + 1 + i], vj = H[(long)k * q + k + 1 + j];
+        const double2 wi = tvec[i], wj = tvec[j];
+        double2 h = H[(long)(k + 1 + j) * q + k + 1 + i];
+        h = h - cmul(vi, conj(wj)) - cmul(wi, conj(vj));
+        H[(long)(k + 1 + j) * q + k + 1 + i] = h;
       }
-      __syncthreads();
     }
+    __syncthreads();
   }
-  // 6. sort Ritz values ascending
-  __shared__ int s_ord[kMaxTrial];
+  // real tridiagonal: diag ta, off-diagonal te = |alpha| with the phase scaling tphase
   if (tid == 0) {
-    for (int i = 0; i < r; ++i) s_ord[i] = i;
-    for (int i = 1; i < r; ++i) {
-      const int v = s_ord[i];
-      const double key = H[(long)v * q + v].x;
-      int j = i - 1;
-      while (j >= 0 && H[(long)s_ord[j] * q + s_ord[j]].x > key) {
-        s_ord[j + 1] = s_ord[j];
-        --j;
+    double2 ph = make_double2(1.0, 0.0);
+    for (int k = 0; k < r; ++k) {
+      ta[k] = H[(long)k * q + k].x;
+      tphase[k] = ph;
+      if (k + 1 < r) {
+        const double2 al = (k + 2 < r) ? talpha[k] : H[(long)k * q + k + 1];
+        const double aa = sqrt(nrm2(al));
+        te[k] = aa;
+        te2[k] = aa * aa;
+        if (aa > 0.0) ph = cmul(ph, make_double2(al.x / aa, al.y / aa));
       }
-      s_ord[j + 1] = v;
     }
   }
   __syncthreads();
-  // 7. C[:, j] = D T V[:, ord[j]] (rows of dropped directions are zero)
-  for (long t = tid; t < (long)q * p; t += nt) {
-    const int row = int(t % q), j = int(t / q);
-    Cout[(long)j * q + row] = make_double2(0, 0);
+  t_phase[3] = clock64();
+  // 4a. bisection for the p smallest eigenvalues (one thread each)
+  double lo = 0.0, hi = 0.0, tnorm = 0.0;
+  for (int k = 0; k < r; ++k) {
+    const double rad = (k > 0 ? te[k - 1] : 0.0) + (k + 1 < r ? te[k] : 0.0);
+    lo = k == 0 ? ta[k] - rad : fmin(lo, ta[k] - rad);
+    hi = k == 0 ? ta[k] + rad : fmax(hi, ta[k] + rad);
+  }
+  tnorm = fmax(fabs(lo), fabs(hi));
+  const double pivmin = 1e-300 + 1e-30 * tnorm * tnorm;
+  if (tid < p) {
+    double a0 = lo - 1e-14 * tnorm - 1e-300, b0 = hi + 1e-14 * tnorm + 1e-300;
+    for (int it = 0; it < 200; ++it) {
+      const double mid = 0.5 * (a0 + b0);
+      if (mid <= a0 || mid >= b0 || b0 - a0 <= 4e-16 * fmax(fabs(a0), fabs(b0))) break;
+      if (sturm_count(ta, te2, r, mid, pivmin) > tid) b0 = mid;
+      else a0 = mid;
+    }
+    lam[tid] = 0.5 * (a0 + b0);
   }
   __syncthreads();
-  for (long t = tid; t < (long)r * p; t += nt) {
-    const int i = int(t % r), j = int(t / r);
-    const int col = s_ord[j];
-    double2 s = make_double2(0, 0);
-    for (int k = i; k < r; ++k) s = s + cmul(T[(long)k * q + i], V[(long)col * q + k]);
-    Cout[(long)j * q + kidx[i]] = d[kidx[i]] * s;
+  t_phase[4] = clock64();
+  // 4b. inverse iteration on T - lam_j I (Gaussian elimination with partial pivoting)
+  for (int sweep = 0; sweep < 3; ++sweep) {
+    if (tid < p) {
+      const int j = tid;
+      double* z = Z + j * r;
+      if (sweep == 0)
+        for (int i = 0; i < r; ++i) z[i] = 1.0 + 0.37 * sin(1.7 * (i + 1) * (j + 1));
+      const double shift = lam[j];
+      // factor and solve in local storage: rows hold (diag, super1, super2) after pivoting
+      double u0[kMaxTrial], u1[kMaxTrial], u2[kMaxTrial], mult[kMaxTrial];
+      bool swp[kMaxTrial];
+      double d0 = ta[0] - shift, s1 = r > 1 ? te[0] : 0.0;
+      for (int i = 0; i < r; ++i) {
+        const double below_sub = i + 1 < r ? te[i] : 0.0;
+        const double below_diag = i + 1 < r ? ta[i + 1] - shift : 0.0;
+        const double below_sup = i + 2 < r ? te[i + 1] : 0.0;
+        if (i + 1 < r && fabs(below_sub) > fabs(d0)) {
+          // swap rows i and i+1
+          swp[i] = true;
+          u0[i] = below_sub;
+          u1[i] = below_diag;
+          u2[i] = below_sup;
+          const double mlt = d0 / below_sub;
+          mult[i] = mlt;
+          d0 = s1 - mlt * below_diag;
+          s1 = -mlt * below_sup;
+        } else {
+          swp[i] = false;
+          double dd = d0;
+          if (fabs(dd) < pivmin) dd = dd < 0 ? -pivmin : pivmin;
+          u0[i] = dd;
+          u1[i] = s1;
+          u2[i] = 0.0;
+          const double mlt = i + 1 < r ? below_sub / dd : 0.0;
+          mult[i] = mlt;
+          d0 = below_diag - mlt * s1;
+          s1 = below_sup;
+        }
+      }
+      // forward: apply the row operations to z
+      for (int i = 0; i + 1 < r; ++i) {
+        if (swp[i]) {
+          const double t0 = z[i];
+          z[i] = z[i + 1];
+          z[i + 1] = t0 - mult[i] * z[i];
+        } else {
+          z[i + 1] -= mult[i] * z[i];
+        }
+      }
+      // backward substitution
+      for (int i = r - 1; i >= 0; --i) {
+        double v = z[i];
+        if (i + 1 < r) v -= u1[i] * z[i + 1];
+        if (i + 2 < r) v -= u2[i] * z[i + 2];
+        double dd = u0[i];
+        if (fabs(dd) < pivmin) dd = dd < 0 ? -pivmin : pivmin;
+        z[i] = v / dd;
+      }
+      double nrm = 0.0;
+      for (int i = 0; i < r; ++i) nrm += z[i] * z[i];
+      nrm = 1.0 / sqrt(nrm);
+      for (int i = 0; i < r; ++i) z[i] *= nrm;
+    }
+    __syncthreads();
+    // re-orthogonalise inside clusters of close eigenvalues (modified Gram-Schmidt)
+    if (tid == 0) {
+      for (int j = 1; j < p; ++j) {
+        int j0 = j;
+        while (j0 > 0 && lam[j] - lam[j0 - 1] <= 1e-7 * tnorm) --j0;
+        if (j0 == j) continue;
+        double* zj = Z + j * r;
+        for (int c = j0; c < j; ++c) {
+          const double* zc = Z + c * r;
+          double dot = 0.0;
+          for (int i = 0; i < r; ++i) dot += zc[i] * zj[i];
+          for (int i = 0; i < r; ++i) zj[i] -= dot * zc[i];
+        }
+        double nrm = 0.0;
+        for (int i = 0; i < r; ++i) nrm += zj[i] * zj[i];
+        nrm = 1.0 / sqrt(nrm);
+        for (int i = 0; i < r; ++i) zj[i] *= nrm;
+      }
+    }
+    __syncthreads();
   }
-  for (int j = tid; j < p; j += nt) theta_out[j] = H[(long)s_ord[j] * q + s_ord[j]].x;
+  t_phase[5] = clock64();
+  // 5. back-transformation u_j = Q (phase * z_j), one warp per vector
+  for (int j = warp; j < p; j += nw) {
+    double2* u = U + (long)j * q;
+    for (int i = lane; i < r; i += 32) u[i] = Z[j * r + i] * tphase[i];
+    __syncwarp();
+    for (int k = r - 3; k >= 0; --k) {
+      const double beta = tbeta[k];
+      if (beta == 0.0) continue;
+      const int m = r - k - 1;
+      double2 acc = make_double2(0, 0);
+      for (int i = lane; i < m; i += 32) acc = acc + cmulc(H[(long)k * q + k + 1 + i], u[k + 1 + i]);
+      acc = warp_sum2(acc);
+      const double2 f = beta * acc;
+      for (int i = lane; i < m; i += 32) u[k + 1 + i] = u[k + 1 + i] - cmul(H[(long)k * q + k + 1 + i], f);
+      __syncwarp();
+    }
+    // y = R^{-1} u (back substitution), then C[kidx[i], j] = d * y_i
+    for (int i = r - 1; i >= 0; --i) {
+      double2 acc = make_double2(0, 0);
+      for (int k = i + 1 + lane; k < r; k += 32) acc = acc + cmul(G[(long)k * q + i], u[k]);
+      acc = warp_sum2(acc);
+      if (lane == 0) {
+        const double rii = G[(long)i * q + i].x;
+        const double2 v = u[i] - acc;
+        u[i] = make_double2(v.x / rii, v.y / rii);
+      }
+      __syncwarp();
+    }
+    for (int i = lane; i < q; i += 32) Cout[(long)j * q + i] = s_keep[i] ? d[i] * u[i] : make_double2(0, 0);
+  }
+  for (int j = tid; j < p; j += nt) theta_out[j] = lam[j];
+  __syncthreads();
+  t_phase[6] = clock64();
   if (tid == 0) {
     info[0] = 0;
     info[1] = r;
+    for (int ph = 0; ph < 6; ++ph) info[2 + ph] = (int)((t_phase[ph + 1] - t_phase[ph]) / 1000);
   }
 }
 
@@ -688,15 +842,29 @@ void gram(const Level& L, const double* d_ph, int cpg, const double2* S, long ld
   PBS_LAUNCHED();
 }
 
-size_t small_rr_scratch(int q) { return (6ull * q * q + q) * sizeof(double2) + (size_t)q * sizeof(int) + 64; }
+size_t small_rr_scratch(int q) { return (2ull * q * q + (size_t)q * kMaxBlock) * sizeof(double2) + 64; }
 
 void small_rr(const double2* GM, const double2* GA, int q, int p, double2* C, double* theta, double2* scratch,
               int* d_info, cudaStream_t s) {
-  if (q > kMaxTrial || p > q || p < 1) fail(PBS_EINVAL, "small_rr: bad sizes");
-  timer_begin(KC_SMALL_RR, s, 8.0 * 6.0 * q * q * q);  // flops, order of magnitude
-  k_small_rr<<<1, 256, 0, s>>>(GM, GA, q, p, C, theta, scratch, d_info);
+  if (q > kMaxTrial || p > q || p < 1 || p > kMaxBlock) fail(PBS_EINVAL, "small_rr: bad sizes");
+  const size_t dyn = (2ull * q * q + (size_t)q * p) * sizeof(double2);
+  const int in_smem = dyn <= 150 * 1024 ? 1 : 0;
+  static bool attr = false;
+  if (!attr) {
+    PBS_CUDA(cudaFuncSetAttribute(k_small_rr, cudaFuncAttributeMaxDynamicSharedMemorySize, 150 * 1024));
+    attr = true;
+  }
+  timer_begin(KC_SMALL_RR, s, 8.0 * 3.0 * q * q * q);  // flops, order of magnitude
+  k_small_rr<<<1, kRRThreads, in_smem ? dyn : 0, s>>>(GM, GA, q, p, C, theta, scratch, d_info, in_smem);
   timer_end(KC_SMALL_RR, s);
   PBS_LAUNCHED();
+  if (verbose_enabled()) {
+    int h[8] = {};
+    PBS_CUDA(cudaMemcpyAsync(h, d_info, sizeof h, cudaMemcpyDeviceToHost, s));
+    PBS_CUDA(cudaStreamSynchronize(s));
+    std::fprintf(stderr, "[pbs] small_rr q=%d p=%d info=%d rank=%d kcycles: chol %d solves %d householder %d bisect %d invit %d back %d\n",
+                 q, p, h[0], h[1], h[2], h[3], h[4], h[5], h[6], h[7]);
+  }
 }
 
 void block_update(const double2* X, long ldx, int q, const double2* C, int ldc, double2* Y, long ldy, int p,

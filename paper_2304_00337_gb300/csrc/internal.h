@@ -107,6 +107,7 @@ void timer_end(int cls, cudaStream_t s);
 void timer_collect();  // after a stream synchronisation
 // every kernel launch of the library is counted (process-wide)
 void count_launch();
+bool verbose_enabled();  // PBS_VERBOSE set in the environment (diagnostic traces)
 #define PBS_LAUNCHED()                 \
   do {                                 \
     ::pbs::count_launch();             \

@@ -34,6 +34,11 @@ static std::atomic<unsigned long long> g_launches{0};
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
+bool verbose_enabled() {
+  static const bool v = std::getenv("PBS_VERBOSE") != nullptr;
+  return v;
+}
+
 void timer_begin(int cls, cudaStream_t s, double work) {
   KernelTimer* t = g_timer;
   if (!t || !(t->mask & (1u << cls))) return;
@@ -329,7 +334,7 @@ void ensure_work(pbs_ctx* ctx, int p) {
   };
   const long D = W.D, N = W.N;
   W.S = (double2*)A(sizeof(double2) * D * q);
-  W.T2 = (double2*)A(sizeof(double2) * D * 2 * p);
+  W.T2 = (double2*)A(sizeof(double2) * D * q);
   W.R = (double2*)A(sizeof(double2) * D * p);
   W.hist = (double2*)A(sizeof(double2) * D * 3 * p);
   W.gwork = (double2*)A(sizeof(double2) * (D + N) * q);
@@ -345,7 +350,7 @@ void ensure_work(pbs_ctx* ctx, int p) {
   W.parts = (double*)A(sizeof(double) * std::max<long>(2 * nblk * q, 4 * 64 * q));
   W.norms = (double*)A(sizeof(double) * 2 * q);
   W.rq = (double*)A(sizeof(double) * 2 * q);
-  W.info = (int*)A(sizeof(int) * 4);
+  W.info = (int*)A(sizeof(int) * 8);
   // preconditioner: p columns; projection: up to 3p columns (extrapolation spans)
   W.r32 = (float2*)A(sizeof(float2) * D * p);
   W.w32 = (float2*)A(sizeof(float2) * D * p);
@@ -468,28 +473,26 @@ struct KResult {
 
 // The iteration at the current k (ctx->K set up) starting from the p columns in S[:, 0:p].
 KResult iterate(pbs_ctx* ctx, const pbs_opts& o, cudaStream_t s) {
+  // Block layout in W.S: [E | P | W]; before the first search direction exists
+  // the preconditioned residual W sits in the P slot, so the trial block is
+  // always contiguous: [E, W] (q = 2p) or [E, P, W] (q = 3p).
   Work& W = ctx->W;
   const Level& L0 = ctx->H.lev[0];
   const double* ph = ctx->K.d_ph;
   const int p = o.block;
   const long D = W.D;
-  double2* E = W.S;
-  double2* Wd = W.S + D * p;
-  double2* P = W.S + 2 * D * p;
   bool have_p = false;
   KResult out;
   std::vector<double> h_norms(2 * p), h_lam(p);
   double theta_max = ctx->last_theta_max;
   const double mu = ctx->H.mu;
   for (int it = 0;; ++it) {
+    double2* E = W.S;
     // Rayleigh-Ritz prefers combinations whose leftover gradient lowers the
     // quotient, so the new block (and the search direction) is cleaned before
     // its residual is formed (Section 4, null-space elimination).
     const int cyc = projection_cycles(o, theta_max, mu);
-    if (it > 0) {
-      project_dispatch(ctx, o, E, p, s, cyc);
-      if (have_p) project_dispatch(ctx, o, P, p, s, cyc);
-    }
+    if (it > 0) project_dispatch(ctx, o, E, have_p ? 2 * p : p, s, cyc);
     // Rayleigh quotients in factored form, then the FP64 residual
     rayleigh_parts(L0, ph, p, E, D, p, W.parts, W.rq, s);
     k_rq<<<1, 64, 0, s>>>(W.rq, W.lam, p);
@@ -523,6 +526,8 @@ KResult iterate(pbs_ctx* ctx, const pbs_opts& o, cudaStream_t s) {
       return out;
     }
     if (it >= o.max_iter) return out;
+    const bool use_p = o.span == 3 && have_p;
+    double2* Wd = W.S + D * p * (use_p ? 2 : 1);
     precondition_dispatch(ctx, o, W.R, Wd, p, s);
     int q;
     const double2* trial;
@@ -534,8 +539,8 @@ KResult iterate(pbs_ctx* ctx, const pbs_opts& o, cudaStream_t s) {
       trial = Wd;
     } else {
       project_dispatch(ctx, o, Wd, p, s, cyc);
-      q = (o.span == 3 && have_p) ? 3 * p : 2 * p;
-      trial = E;  // [E, W, P] are contiguous
+      q = use_p ? 3 * p : 2 * p;
+      trial = E;
     }
     gram(L0, ph, q, trial, D, q, W.GM, W.GA, W.gwork, W.gpart, W.gpart_n, s);
     small_rr(W.GM, W.GA, q, p, W.C, W.theta, W.rr_scr, W.info, s);
@@ -544,30 +549,29 @@ KResult iterate(pbs_ctx* ctx, const pbs_opts& o, cudaStream_t s) {
     PBS_CUDA(cudaStreamSynchronize(s));
     if (info[0] != 0) {
       if (info[0] == -2) fail(PBS_ENUMERIC, "non-finite Gram matrix");
+      if (!use_p) fail(PBS_ENUMERIC, "trial space lost rank");
       // rank loss in the LOBPCG basis: restart without the search direction
-      if (have_p) {
-        have_p = false;
-        q = 2 * p;
-        gram(L0, ph, q, trial, D, q, W.GM, W.GA, W.gwork, W.gpart, W.gpart_n, s);
-        small_rr(W.GM, W.GA, q, p, W.C, W.theta, W.rr_scr, W.info, s);
-        PBS_CUDA(cudaMemcpyAsync(info, W.info, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
-        PBS_CUDA(cudaStreamSynchronize(s));
-      }
+      PBS_CUDA(cudaMemcpyAsync(W.S + D * p, Wd, sizeof(double2) * D * p, cudaMemcpyDeviceToDevice, s));
+      have_p = false;
+      q = 2 * p;
+      gram(L0, ph, q, trial, D, q, W.GM, W.GA, W.gwork, W.gpart, W.gpart_n, s);
+      small_rr(W.GM, W.GA, q, p, W.C, W.theta, W.rr_scr, W.info, s);
+      PBS_CUDA(cudaMemcpyAsync(info, W.info, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+      PBS_CUDA(cudaStreamSynchronize(s));
       if (info[0] != 0) fail(PBS_ENUMERIC, "trial space lost rank");
     }
+    // new block in the other buffer, then swap: T2 = [E_new | P_new | -]
     double2* Enew = W.T2;
     double2* Pnew = W.T2 + D * p;
     if (o.span == 3) {
-      // P_new = [W, P] C[p:q], E_new = E C[0:p] + P_new
-      block_update(Wd, D, q - p, W.C + p, q, Pnew, D, p, nullptr, 0, D, s);
+      // P_new = [P, W] C[p:q] (or W C[p:2p]), E_new = E C[0:p] + P_new
+      block_update(W.S + D * p, D, q - p, W.C + p, q, Pnew, D, p, nullptr, 0, D, s);
       block_update(E, D, p, W.C, q, Enew, D, p, Pnew, D, D, s);
-      PBS_CUDA(cudaMemcpyAsync(E, Enew, sizeof(double2) * D * p, cudaMemcpyDeviceToDevice, s));
-      PBS_CUDA(cudaMemcpyAsync(P, Pnew, sizeof(double2) * D * p, cudaMemcpyDeviceToDevice, s));
       have_p = true;
     } else {
       block_update(trial, D, q, W.C, q, Enew, D, p, nullptr, 0, D, s);
-      PBS_CUDA(cudaMemcpyAsync(E, Enew, sizeof(double2) * D * p, cudaMemcpyDeviceToDevice, s));
     }
+    std::swap(W.S, W.T2);
   }
 }
 
@@ -599,7 +603,7 @@ void initial_block(pbs_ctx* ctx, const pbs_opts& o, const pbs_c64* init, int nhi
       rayleigh_ritz_step(ctx, W.S, p, p, W.T2, s);
     }
   }
-  PBS_CUDA(cudaMemcpyAsync(W.S, W.T2, sizeof(double2) * D * p, cudaMemcpyDeviceToDevice, s));
+  std::swap(W.S, W.T2);
   // largest Ritz value of the start block, for the projection accuracy
   std::vector<double> th(p);
   PBS_CUDA(cudaMemcpyAsync(th.data(), W.theta, sizeof(double) * p, cudaMemcpyDeviceToHost, s));

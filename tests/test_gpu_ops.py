@@ -259,3 +259,23 @@ def test_max_size_operators_on_plane_waves(ctx):
     ctx.apply(geom, "A", g.data_ptr(), ag.data_ptr(), 1, k=k, opts=opts)
     torch.cuda.synchronize()
     assert (torch.linalg.vector_norm(ag) / torch.linalg.vector_norm(g)).item() < 1e-12 * 8 / h ** 2
+
+
+def test_rayleigh_ritz_drops_dependent_directions(ctx):
+    # a span given twice (second copy mixed by a random matrix) has rank 6: the
+    # Cholesky step must drop the dependent half and return the Ritz pairs of the span
+    n = 16
+    eps = gi.rod_eps(n, n)
+    geom = pbs.Geometry(eps)
+    k = (0.9, -0.4)
+    ops = fem.assemble(fem.Mesh(1, 1, n, n), eps, k)
+    r = np.random.default_rng(21)
+    V = eigen.eigs_dense(ops, 6)[1] + 1e-3 * (r.standard_normal((geom.D, 6)) + 1j * r.standard_normal((geom.D, 6)))
+    mix = r.standard_normal((6, 6)) + 1j * r.standard_normal((6, 6))
+    S = np.concatenate([V, V @ mix], axis=1)
+    want, _ = ex.rayleigh_ritz(ops, V, 6)
+    Sd = _dev(S.T)
+    X = torch.zeros((6, geom.D), dtype=torch.complex128, device="cuda")
+    th = ctx.rayleigh_ritz(geom, pbs.default_opts(precision=pbs.PBS_FP64), k, 12, Sd.data_ptr(), 6, False,
+                           X.data_ptr(), torch.cuda.current_stream())
+    assert np.allclose(th, want, rtol=1e-9)
