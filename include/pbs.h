@@ -212,6 +212,34 @@ PBS_API int pbs_profile_read(pbs_ctx *ctx, const char *kernel_class, double *tot
 /* Number of CUDA kernels the library has launched in this process. */
 PBS_API unsigned long long pbs_launch_count(void);
 
+/*
+ * Allocation-free Rayleigh-Ritz step.  No counterpart in the paper: it exists
+ * for callers that cannot call cudaMalloc, because all of their device memory
+ * is owned by another allocator (a framework's caching allocator or a fixed
+ * arena) or because their process forbids new device allocations once it is
+ * running.  Given the Gram matrices GM = S^* M S and GA = S^* A S of a trial
+ * block (for example from pbs_gram), it computes the p smallest Ritz values
+ * (`theta`, ascending) and the coefficient matrix C (q x p, column-major) with
+ * X = S C M-orthonormal Ritz vectors - the same computation as the
+ * coefficient step inside pbs_rayleigh_ritz.
+ *   GM, GA  device, q x q column-major Hermitian;  C device q x p;
+ *   theta   device, p doubles;  info device, 2 ints: info[0] = 0 on success,
+ *           -1 if the span has fewer than p independent directions, -2 if an
+ *           input is not finite; info[1] = numerical rank of the span.
+ * Limits: 1 <= q <= 96, 1 <= p <= min(q, 32); larger sizes return PBS_EINVAL.
+ * The kernel runs on `cuda_stream` on the current device; the call returns
+ * after the launch, without waiting for it.  It allocates nothing: its work
+ * space is a fixed device array of about 344 KB compiled into the library and
+ * held by every GPU that loads it until the process exits.  The first call on a
+ * device looks up that array's device address, so make the first call on each
+ * device before any stream capture.  Every call on a device shares the one
+ * array: calls whose kernels may overlap on the GPU (different streams without
+ * ordering) race and give wrong results; serialise them.  No element of the
+ * array has to start at zero: everything read is written first by the same call.
+ */
+PBS_API int pbs_small_rr_noalloc(const pbs_c64 *GM, const pbs_c64 *GA, int q, int p, pbs_c64 *C, double *theta,
+                                 int *info, void *cuda_stream);
+
 /* Static description of a status code. */
 PBS_API const char *pbs_strerror(int status);
 

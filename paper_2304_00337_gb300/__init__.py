@@ -97,6 +97,7 @@ def lib() -> ct.CDLL:
         "pbs_profile_read": (ct.c_int, [P, ct.c_char_p, ct.POINTER(ct.c_double), ct.POINTER(ct.c_long),
                                         ct.POINTER(ct.c_double)]),
         "pbs_launch_count": (ct.c_ulonglong, []),
+        "pbs_small_rr_noalloc": (ct.c_int, [P, P, ct.c_int, ct.c_int, P, P, P, P]),
         "pbs_strerror": (ct.c_char_p, [ct.c_int]),
         "pbs_last_error": (ct.c_char_p, []),
     }
@@ -111,6 +112,14 @@ def lib() -> ct.CDLL:
 def launch_count() -> int:
     """Kernels launched by the library in this process (``pbs_launch_count``)."""
     return int(lib().pbs_launch_count())
+
+
+def small_rr_noalloc(gm_ptr: int, ga_ptr: int, q: int, p: int, c_ptr: int, theta_ptr: int, info_ptr: int,
+                     stream=None) -> None:
+    """``pbs_small_rr_noalloc``: the Rayleigh-Ritz coefficient step on device Gram matrices,
+    without any device allocation (for callers that cannot call cudaMalloc)."""
+    _check(lib().pbs_small_rr_noalloc(gm_ptr, ga_ptr, q, p, c_ptr, theta_ptr, info_ptr, _stream_ptr(stream)),
+           "pbs_small_rr_noalloc")
 
 
 def strerror(status: int) -> str:

@@ -311,7 +311,7 @@ __device__ int sturm_count(const double* a, const double* e2, int n, double x, d
 __global__ void __launch_bounds__(kRRThreads) k_small_rr(const double2* __restrict__ GM, const double2* __restrict__ GA,
                                                          int q, int p, double2* __restrict__ Cout,
                                                          double* __restrict__ theta_out, double2* __restrict__ scr,
-                                                         int* __restrict__ info, int in_smem) {
+                                                         int* __restrict__ info, int in_smem, int* __restrict__ phase_out) {
   extern __shared__ double2 dsm[];
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
   const long qq = (long)q * q;
@@ -670,7 +670,8 @@ __global__ void __launch_bounds__(kRRThreads) k_small_rr(const double2* __restri
   if (tid == 0) {
     info[0] = 0;
     info[1] = r;
-    for (int ph = 0; ph < 6; ++ph) info[2 + ph] = (int)((t_phase[ph + 1] - t_phase[ph]) / 1000);
+    if (phase_out)
+      for (int ph = 0; ph < 6; ++ph) phase_out[ph] = (int)((t_phase[ph + 1] - t_phase[ph]) / 1000);
   }
 }
 
@@ -855,7 +856,8 @@ void small_rr(const double2* GM, const double2* GA, int q, int p, double2* C, do
     attr = true;
   }
   timer_begin(KC_SMALL_RR, s, 8.0 * 3.0 * q * q * q);  // flops, order of magnitude
-  k_small_rr<<<1, kRRThreads, in_smem ? dyn : 0, s>>>(GM, GA, q, p, C, theta, scratch, d_info, in_smem);
+  k_small_rr<<<1, kRRThreads, in_smem ? dyn : 0, s>>>(GM, GA, q, p, C, theta, scratch, d_info, in_smem,
+                                                      verbose_enabled() ? d_info + 2 : nullptr);
   timer_end(KC_SMALL_RR, s);
   PBS_LAUNCHED();
   if (verbose_enabled()) {
@@ -895,6 +897,56 @@ void scale_columns(double2* X, long ld, long rows, int ncols, const double* d_sc
   k_scale_cols<<<dim3(blocks_for(rows, 256, 1024), ncols), 256, 0, s>>>(X, ld, rows, d_scale);
   PBS_LAUNCHED();
 }
+
+}  // namespace pbs
+
+// ---------------------------------------------------------------------------
+// Allocation-free Rayleigh-Ritz step (pbs_small_rr_noalloc in pbs.h).
+//
+// The scratch of the small dense solve lives in this file-scope device array,
+// sized for the largest trial block the library supports (q = 96, p = 32):
+// 2 q^2 + q p complex doubles, about 344 KB, held by every GPU that loads the
+// library until the process exits.  Host code cannot use the array's name as a
+// device address, so its address is looked up once per device with
+// cudaGetSymbolAddress while that device is current.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+namespace {
+constexpr int kNoAllocQ = pbs::kMaxTrial, kNoAllocP = pbs::kMaxBlock;
+static __device__ __align__(256) double2 g_small_rr_scratch[2 * kNoAllocQ * kNoAllocQ + kNoAllocQ * kNoAllocP + 8];
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mutex;
+void* g_scratch_addr[kMaxDevices] = {};
+}  // namespace
+
+extern "C" int pbs_small_rr_noalloc(const pbs_c64* GM, const pbs_c64* GA, int q, int p, pbs_c64* C, double* theta,
+                                    int* info, void* cuda_stream) {
+  using namespace pbs;
+  if (!GM || !GA || !C || !theta || !info) return PBS_EINVAL;
+  if (q < 1 || q > kNoAllocQ || p < 1 || p > q || p > kNoAllocP) return PBS_EINVAL;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return PBS_ECUDA;
+  void* scratch = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_scratch_mutex);
+    if (!g_scratch_addr[dev]) {
+      // set-up on the first call on this device (with the device current)
+      if (cudaGetSymbolAddress(&g_scratch_addr[dev], g_small_rr_scratch) != cudaSuccess) {
+        g_scratch_addr[dev] = nullptr;
+        return PBS_ECUDA;
+      }
+    }
+    scratch = g_scratch_addr[dev];
+  }
+  k_small_rr<<<1, kRRThreads, 0, (cudaStream_t)cuda_stream>>>((const double2*)GM, (const double2*)GA, q, p,
+                                                                (double2*)C, theta, (double2*)scratch, info, 0,
+                                                                nullptr);
+  count_launch();
+  return cudaGetLastError() == cudaSuccess ? PBS_OK : PBS_ECUDA;
+}
+
+namespace pbs {
 
 template void sub_lift<double>(const Level&, const double*, int, const double2*, long, double2*, long, int, cudaStream_t);
 template void sub_lift<float>(const Level&, const double*, int, const float2*, long, double2*, long, int, cudaStream_t);
