@@ -225,11 +225,12 @@ PBS_API unsigned long long pbs_launch_count(void);
  *   GM, GA  device, q x q column-major Hermitian;  C device q x p;
  *   theta   device, p doubles;  info device, 2 ints: info[0] = 0 on success,
  *           -1 if the span has fewer than p independent directions, -2 if an
- *           input is not finite; info[1] = numerical rank of the span.
+ *           input is not finite, -3 if the eigensolve broke down; info[1] =
+ *           numerical rank of the span.
  * Limits: 1 <= q <= 96, 1 <= p <= min(q, 32); larger sizes return PBS_EINVAL.
  * The kernel runs on `cuda_stream` on the current device; the call returns
  * after the launch, without waiting for it.  It allocates nothing: its work
- * space is a fixed device array of about 344 KB compiled into the library and
+ * space is a fixed device array of about 480 KB compiled into the library and
  * held by every GPU that loads it until the process exits.  The first call on a
  * device looks up that array's device address, so make the first call on each
  * device before any stream capture.  Every call on a device shares the one

@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdio>
 
+#include "df32.cuh"
 #include "internal.h"
 
 namespace pbs {
@@ -272,38 +273,55 @@ __global__ void k_gram_finalize(const double2* __restrict__ part, int npart, int
 // ---- small dense Rayleigh-Ritz (one block) -------------------------------
 // Given the Gram matrices GM = S^* M S and GA = S^* A S of a trial block S
 // (q columns), find the p smallest Ritz pairs (Section 4, eq. ritz_eigenvalue):
-//  1. scale to unit diagonal, Cholesky GM = R^* R dropping directions whose
-//     pivot falls below kDropTol (a span that lost rank);
-//  2. H = R^{-*} GA R^{-1} by two triangular solves;
-//  3. Householder reduction H = Q T Q^*, T Hermitian tridiagonal, made real by
-//     a diagonal unitary scaling;
-//  4. the p smallest eigenvalues of T by bisection on Sturm counts, their
+//  1. scale to unit diagonal (FP64), Cholesky GM = R^* R dropping directions
+//     whose pivot falls below kDropTol (a span that lost rank);
+//  2. T = R^{-1} by Gauss-Jordan elimination, H = T^* GA T;
+//  3. Householder reduction H = Q Tr Q^*, Tr Hermitian tridiagonal, made real
+//     by a diagonal unitary scaling;
+//  4. the p smallest eigenvalues of Tr by multisection on Sturm counts, their
 //     eigenvectors by inverse iteration (re-orthogonalised inside clusters);
-//  5. back-transformation and C = D R^{-1} Q U.
-// Everything runs in FP64 in one thread block (the problem is q x q, q <= 96).
+//  5. back-transformation and C = D T Q U.
+// Steps 2-5 use double-float arithmetic (about 48 bits) on the FP32 pipe: the
+// coefficients only need ~1e-14 accuracy (Ritz values and residuals are
+// recomputed in FP64 from the updated block), and a serial chain of FP64
+// instructions is what limited this one-block kernel on GB300.
 constexpr double kDropTol = 1e-12;  // relative pivot below which a trial direction is dropped
 constexpr int kRRThreads = 256;
+constexpr int kRRWarps = kRRThreads / 32;
 
-__device__ __forceinline__ double warp_sum(double v) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+__device__ __forceinline__ df shfl_df(df v, int o) {
+  return df_make(__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o));
+}
+__device__ __forceinline__ df warp_sum_df(df v) {
+  for (int o = 16; o > 0; o >>= 1) v = v + shfl_df(v, o);
   return v;
 }
-__device__ __forceinline__ double2 warp_sum2(double2 v) {
-  v.x = warp_sum(v.x);
-  v.y = warp_sum(v.y);
+__device__ __forceinline__ cdf warp_sum_cdf(cdf v) {
+  for (int o = 16; o > 0; o >>= 1) v = v + cdf_make(shfl_df(v.re, o), shfl_df(v.im, o));
   return v;
 }
+// block-wide sum of a df value (all threads participate; result in every thread)
+__device__ __forceinline__ df block_sum_df(df v, df* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  v = warp_sum_df(v);
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  df t = df_zero();
+  for (int w = 0; w < kRRWarps; ++w) t = t + red[w];
+  return t;
+}
 
-// number of eigenvalues of the real symmetric tridiagonal (a, e) below x
-__device__ int sturm_count(const double* a, const double* e2, int n, double x, double pivmin) {
+// number of eigenvalues of the real symmetric tridiagonal (a, e^2) below x
+__device__ int sturm_count_df(const df* a, const df* e2, int n, df x, float pivmin) {
   int cnt = 0;
-  double d = a[0] - x;
-  if (fabs(d) < pivmin) d = -pivmin;
-  if (d < 0) ++cnt;
+  df d = a[0] - x;
+  if (fabsf(d.hi) < pivmin) d = df_make(-pivmin, 0.0f);
+  if (d.hi < 0.0f) ++cnt;
   for (int i = 1; i < n; ++i) {
     d = (a[i] - x) - e2[i - 1] / d;
-    if (fabs(d) < pivmin) d = -pivmin;
-    if (d < 0) ++cnt;
+    if (fabsf(d.hi) < pivmin) d = df_make(-pivmin, 0.0f);
+    if (d.hi < 0.0f) ++cnt;
   }
   return cnt;
 }
@@ -313,23 +331,24 @@ __global__ void __launch_bounds__(kRRThreads) k_small_rr(const double2* __restri
                                                          double* __restrict__ theta_out, double2* __restrict__ scr,
                                                          int* __restrict__ info, int in_smem, int* __restrict__ phase_out) {
   extern __shared__ double2 dsm[];
-  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = kRRWarps;
   const long qq = (long)q * q;
-  double2* G = in_smem ? dsm : scr;            // scaled M-Gram, then R (rows)
-  double2* H = G + qq;                          // scaled A-Gram, then H, then reflectors
-  double2* U = H + qq;                          // q x p eigenvectors
-  __shared__ double d[kMaxTrial];               // column scales
+  cdf* G = (cdf*)(in_smem ? dsm : scr);  // M-Gram -> R -> Y
+  cdf* H = G + qq;                        // A-Gram -> H -> reflectors
+  cdf* T = H + qq;                        // R^{-1}
+  cdf* U = T + qq;                        // q x p eigenvectors
+  __shared__ double d[kMaxTrial];         // column scales (FP64)
   __shared__ int s_keep[kMaxTrial];
-  __shared__ double ta[kMaxTrial], te[kMaxTrial], te2[kMaxTrial], tbeta[kMaxTrial];
-  __shared__ double2 talpha[kMaxTrial], tphase[kMaxTrial], tvec[kMaxTrial], tp[kMaxTrial];
-  __shared__ double lam[kMaxBlock];
-  __shared__ double Z[kMaxTrial * kMaxBlock];   // real eigenvectors of the tridiagonal, column j at j*r
-  __shared__ int s_r, s_bad;
-  __shared__ double s_piv, s_red[2 * kRRThreads / 32];
+  __shared__ df ta[kMaxTrial], te[kMaxTrial], te2[kMaxTrial], tbeta[kMaxTrial];
+  __shared__ cdf talpha[kMaxTrial], tphase[kMaxTrial], tvec[kMaxTrial], tp[kMaxTrial];
+  __shared__ df lam[kMaxBlock], lo_s[kMaxBlock], hi_s[kMaxBlock];
+  __shared__ df Z[kMaxTrial * kMaxBlock];  // real eigenvectors of the tridiagonal, column j at j*q
+  __shared__ int s_r, s_bad, s_cnt[kRRThreads];
+  __shared__ df s_piv, s_red[kRRWarps];
   long long t_phase[8];
   t_phase[0] = clock64();
 
-  // 1. scaling and load
+  // 1. scaling (FP64) and conversion
   for (int i = tid; i < q; i += nt) {
     const double g = GM[(long)i * q + i].x;
     d[i] = (g > 0.0 && isfinite(g)) ? 1.0 / sqrt(g) : 0.0;
@@ -341,40 +360,38 @@ __global__ void __launch_bounds__(kRRThreads) k_small_rr(const double2* __restri
     const double sc = d[i] * d[j];
     const double2 gm = GM[t], ga = GA[t];
     if (!isfinite(gm.x) || !isfinite(gm.y) || !isfinite(ga.x) || !isfinite(ga.y)) s_bad = 1;
-    G[t] = sc * gm;
-    H[t] = sc * ga;
+    G[t] = cdf_from(sc * gm);
+    H[t] = cdf_from(sc * ga);
+    T[t] = cdf_zero();
   }
   __syncthreads();
-  // Cholesky with dropping: R row k stored in G[k][k:], i.e. G[j*q + k].  A dropped
-  // direction k becomes a decoupled unit row and column of R (so R^{-1} acts as the
-  // inverse of the kept block) and an isolated Ritz value above every kept one.
+  // Cholesky with dropping: R row k stored in G[j*q + k] (j >= k).  A dropped
+  // direction becomes a decoupled unit row and column of R and an isolated Ritz
+  // value above every kept one.
   for (int k = 0; k < q; ++k) {
     if (tid == 0) {
-      const double pv = G[(long)k * q + k].x;
-      const bool keep = d[k] > 0.0 && pv > kDropTol && isfinite(pv);
+      const df pv = G[(long)k * q + k].re;
+      const bool keep = d[k] > 0.0 && df_to(pv) > kDropTol && isfinite(pv.hi);
       s_keep[k] = keep;
-      s_piv = keep ? sqrt(pv) : 0.0;
+      s_piv = keep ? df_make(1.0f, 0.0f) / df_sqrt(pv) : df_zero();  // 1 / R_kk
     }
     __syncthreads();
-    const double piv = s_piv;
-    if (piv > 0.0) {
-      for (int j = k + tid; j < q; j += nt) {
-        const double2 v = G[(long)j * q + k];
-        G[(long)j * q + k] = make_double2(v.x / piv, v.y / piv);
-      }
+    const df inv = s_piv;
+    if (inv.hi > 0.0f) {
+      for (int j = k + tid; j < q; j += nt) G[(long)j * q + k] = cdf_scale(G[(long)j * q + k], inv);
       __syncthreads();
       const int rem = q - k - 1;
       for (long t = tid; t < (long)rem * rem; t += nt) {
         const int ii = k + 1 + int(t % rem), jj = k + 1 + int(t / rem);
         if (ii > jj) continue;
-        G[(long)jj * q + ii] = G[(long)jj * q + ii] - cmulc(G[(long)ii * q + k], G[(long)jj * q + k]);
+        G[(long)jj * q + ii] = G[(long)jj * q + ii] - cdf_mulc(G[(long)ii * q + k], G[(long)jj * q + k]);
       }
     } else {
       for (int j = tid; j < q; j += nt) {
-        G[(long)j * q + k] = make_double2(j == k ? 1.0 : 0.0, 0.0);  // row k
-        if (j < k) G[(long)k * q + j] = make_double2(0, 0);          // column k above the diagonal
-        H[(long)j * q + k] = make_double2(0, 0);                       // decouple the A-Gram
-        H[(long)k * q + j] = make_double2(0, 0);
+        G[(long)j * q + k] = cdf_make(df_make(j == k ? 1.0f : 0.0f, 0.0f), df_zero());
+        if (j < k) G[(long)k * q + j] = cdf_zero();
+        H[(long)j * q + k] = cdf_zero();
+        H[(long)k * q + j] = cdf_zero();
       }
     }
     __syncthreads();
@@ -392,284 +409,303 @@ __global__ void __launch_bounds__(kRRThreads) k_small_rr(const double2* __restri
     }
     return;
   }
-  t_phase[1] = clock64();
   const int r = q;
-  // 2a. Y = A R^{-1}: row i of Y solves y R = a_i; column j in sequence, rows by warps
-  for (int j = 0; j < r; ++j) {
-    const double rjj = G[(long)j * q + j].x;
-    for (int i = warp; i < r; i += nw) {
-      double2 acc = make_double2(0, 0);
-      for (int k = lane; k < j; k += 32) acc = acc + cmul(H[(long)k * q + i], G[(long)j * q + k]);
-      acc = warp_sum2(acc);
-      if (lane == 0) {
-        const double2 v = H[(long)j * q + i] - acc;
-        H[(long)j * q + i] = make_double2(v.x / rjj, v.y / rjj);
-      }
+  t_phase[1] = clock64();
+  // 2a. T = R^{-1} by Gauss-Jordan: rows from the bottom; row k of T is
+  //     (e_k - sum_{c>k} R[k][c] T[c][:]) / R[k][k], all columns in parallel
+  for (int k = r - 1; k >= 0; --k) {
+    const df rkk = G[(long)k * q + k].re;
+    for (int c = tid; c < r; c += nt) {
+      if (c < k) continue;
+      cdf acc = cdf_make(df_make(c == k ? 1.0f : 0.0f, 0.0f), df_zero());
+      for (int m = k + 1; m <= c; ++m) acc = acc - G[(long)m * q + k] * T[(long)c * q + m];
+      T[(long)c * q + k] = cdf_make(acc.re / rkk, acc.im / rkk);
     }
     __syncthreads();
   }
-  // 2b. H = R^{-*} Y: column c solves R^* h = y_c; row i in sequence, columns by warps
-  for (int i = 0; i < r; ++i) {
-    const double rii = G[(long)i * q + i].x;
-    for (int c = warp; c < r; c += nw) {
-      double2 acc = make_double2(0, 0);
-      for (int k = lane; k < i; k += 32) acc = acc + cmulc(G[(long)i * q + k], H[(long)c * q + k]);
-      acc = warp_sum2(acc);
-      if (lane == 0) {
-        const double2 v = H[(long)c * q + i] - acc;
-        H[(long)c * q + i] = make_double2(v.x / rii, v.y / rii);
-      }
-    }
-    __syncthreads();
-  }
-  // isolated value for dropped directions: twice the Gershgorin bound of the rest, plus one
-  if (tid == 0) {
-    double bound = 0.0;
-    for (int i = 0; i < r; ++i) {
-      if (!s_keep[i]) continue;
-      double rs = 0.0;
-      for (int j = 0; j < r; ++j) rs += sqrt(nrm2(H[(long)j * q + i]));
-      bound = fmax(bound, rs);
-    }
-    for (int i = 0; i < r; ++i)
-      if (!s_keep[i]) H[(long)i * q + i] = make_double2(2.0 * bound + 1.0, 0.0);
+  // 2b. Y = A T into G (R is no longer needed), then H = T^* Y
+  for (long t = tid; t < (long)r * r; t += nt) {
+    const int i = int(t % r), c = int(t / r);
+    cdf acc = cdf_zero();
+    for (int m = 0; m <= c; ++m) acc = acc + H[(long)m * q + i] * T[(long)c * q + m];
+    G[(long)c * q + i] = acc;
   }
   __syncthreads();
-  // exact Hermitian symmetry
+  for (long t = tid; t < (long)r * r; t += nt) {
+    const int i = int(t % r), c = int(t / r);
+    cdf acc = cdf_zero();
+    for (int m = 0; m <= i; ++m) acc = acc + cdf_mulc(T[(long)i * q + m], G[(long)c * q + m]);
+    H[(long)c * q + i] = acc;
+  }
+  __syncthreads();
+  // exact Hermitian symmetry, and an isolated value for dropped directions
   for (long t = tid; t < (long)r * r; t += nt) {
     const int i = int(t % r), c = int(t / r);
     if (i < c) {
-      const double2 up = H[(long)c * q + i], lo = H[(long)i * q + c];
-      const double2 m = make_double2(0.5 * (up.x + lo.x), 0.5 * (up.y - lo.y));
+      const cdf up = H[(long)c * q + i], lo = H[(long)i * q + c];
+      const df half = df_make(0.5f, 0.0f);
+      const cdf m = cdf_make((up.re + lo.re) * half, (up.im - lo.im) * half);
       H[(long)c * q + i] = m;
-      H[(long)i * q + c] = conj(m);
+      H[(long)i * q + c] = cdf_conj(m);
     } else if (i == c) {
-      H[(long)c * q + i].y = 0.0;
+      H[(long)c * q + i].im = df_zero();
     }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    df bound = df_zero();
+    for (int i = 0; i < r; ++i) {
+      if (!s_keep[i]) continue;
+      df rs = df_zero();
+      for (int j = 0; j < r; ++j) rs = rs + df_sqrt(cdf_norm2(H[(long)j * q + i]));
+      if (df_lt(bound, rs)) bound = rs;
+    }
+    for (int i = 0; i < r; ++i)
+      if (!s_keep[i]) H[(long)i * q + i] = cdf_make(bound + bound + df_make(1.0f, 0.0f), df_zero());
   }
   __syncthreads();
   t_phase[2] = clock64();
   // 3. Householder tridiagonalisation; reflector k acts on rows/cols k+1..r-1 and is
   //    stored in column k below the diagonal (v, with v_0 = x_0 - alpha) and tbeta[k]
   for (int k = 0; k + 2 < r; ++k) {
-    const int m = r - k - 1;  // length of x
-    // sigma = ||x||
-    double s2 = 0.0;
-    for (int i = tid; i < m; i += nt) s2 += nrm2(H[(long)k * q + k + 1 + i]);
-    s2 = warp_sum(s2);
-    if (lane == 0) s_red[warp] = s2;
-    __syncthreads();
+    const int m = r - k - 1;
+    df s2 = df_zero();
+    for (int i = tid; i < m; i += nt) s2 = s2 + cdf_norm2(H[(long)k * q + k + 1 + i]);
+    s2 = block_sum_df(s2, s_red);
     if (tid == 0) {
-      double tot = 0.0;
-      for (int w = 0; w < nw; ++w) tot += s_red[w];
-      const double sigma = sqrt(tot);
-      const double2 x0 = H[(long)k * q + k + 1];
-      const double ax0 = sqrt(nrm2(x0));
-      double2 ph = ax0 > 0.0 ? make_double2(x0.x / ax0, x0.y / ax0) : make_double2(1.0, 0.0);
-      if (sigma > 0.0 && tot > 1e-300) {
-        const double2 alpha = -sigma * ph;  // x -> alpha e_1
+      const df sigma = df_sqrt(s2);
+      const cdf x0 = H[(long)k * q + k + 1];
+      const df ax0 = df_sqrt(cdf_norm2(x0));
+      cdf ph = ax0.hi > 0.0f ? cdf_make(x0.re / ax0, x0.im / ax0) : cdf_make(df_make(1.0f, 0.0f), df_zero());
+      if (sigma.hi > 0.0f) {
+        const cdf alpha = -cdf_scale(ph, sigma);
         talpha[k] = alpha;
-        tbeta[k] = 1.0 / (sigma * (sigma + ax0));
-        H[(long)k * q + k + 1] = x0 - alpha;  // v_0
+        tbeta[k] = df_make(1.0f, 0.0f) / (sigma * (sigma + ax0));
+        H[(long)k * q + k + 1] = x0 - alpha;
       } else {
         talpha[k] = x0;
-        tbeta[k] = 0.0;
+        tbeta[k] = df_zero();
       }
     }
     __syncthreads();
-    const double beta = tbeta[k];
-    if (beta != 0.0) {
-      // p = beta * Hsub v (rows by warps)
+    const df beta = tbeta[k];
+    if (beta.hi != 0.0f) {
+      // p = beta * Hsub v (rows by warps, columns by lanes)
       for (int i = warp; i < m; i += nw) {
-        double2 acc = make_double2(0, 0);
-        for (int j = lane; j < m; j += 32) acc = acc + cmul(H[(long)(k + 1 + j) * q + k + 1 + i], H[(long)k * q + k + 1 + j]);
-        acc = warp_sum2(acc);
-        if (lane == 0) tp[i] = beta * acc;
+        cdf acc = cdf_zero();
+        for (int j = lane; j < m; j += 32) acc = acc + H[(long)(k + 1 + j) * q + k + 1 + i] * H[(long)k * q + k + 1 + j];
+        acc = warp_sum_cdf(acc);
+        if (lane == 0) tp[i] = cdf_scale(acc, beta);
       }
       __syncthreads();
-      // K = beta/2 v^* p ; w = p - K v  (K is real for Hermitian H)
-      double kk = 0.0;
-      for (int i = tid; i < m; i += nt) kk += cmulc(H[(long)k * q + k + 1 + i], tp[i]).x;
-      kk = warp_sum(kk);
-      if (lane == 0) s_red[warp] = kk;
-      __syncthreads();
-      double K = 0.0;
-      for (int w = 0; w < nw; ++w) K += s_red[w];
-      K *= 0.5 * beta;
-      for (int i = tid; i < m; i += nt) tvec[i] = tp[i] - K * H[(long)k * q + k + 1 + i];
+      // K = beta/2 v^* p (real for Hermitian H); w = p - K v
+      df kk = df_zero();
+      for (int i = tid; i < m; i += nt) kk = kk + cdf_mulc(H[(long)k * q + k + 1 + i], tp[i]).re;
+      kk = block_sum_df(kk, s_red);
+      const df K = kk * beta * df_make(0.5f, 0.0f);
+      for (int i = tid; i < m; i += nt) tvec[i] = tp[i] - cdf_scale(H[(long)k * q + k + 1 + i], K);
       __syncthreads();
       // Hsub -= v w^* + w v^*
       for (long t = tid; t < (long)m * m; t += nt) {
         const int i = int(t % m), j = int(t / m);
-        const double2 vi = H[(long)k * q + k + 1 + i], vj = H[(long)k * q + k + 1 + j];
-        const double2 wi = tvec[i], wj = tvec[j];
-        double2 h = H[(long)(k + 1 + j) * q + k + 1 + i];
-        h = h - cmul(vi, conj(wj)) - cmul(wi, conj(vj));
+        const cdf vi = H[(long)k * q + k + 1 + i], vj = H[(long)k * q + k + 1 + j];
+        cdf h = H[(long)(k + 1 + j) * q + k + 1 + i];
+        h = h - vi * cdf_conj(tvec[j]) - tvec[i] * cdf_conj(vj);
         H[(long)(k + 1 + j) * q + k + 1 + i] = h;
       }
     }
     __syncthreads();
   }
-  // real tridiagonal: diag ta, off-diagonal te = |alpha| with the phase scaling tphase
+  // real tridiagonal: diagonal ta, off-diagonal te = |alpha|, phases tphase
   if (tid == 0) {
-    double2 ph = make_double2(1.0, 0.0);
+    cdf ph = cdf_make(df_make(1.0f, 0.0f), df_zero());
     for (int k = 0; k < r; ++k) {
-      ta[k] = H[(long)k * q + k].x;
+      ta[k] = H[(long)k * q + k].re;
       tphase[k] = ph;
       if (k + 1 < r) {
-        const double2 al = (k + 2 < r) ? talpha[k] : H[(long)k * q + k + 1];
-        const double aa = sqrt(nrm2(al));
+        const cdf al = (k + 2 < r) ? talpha[k] : H[(long)k * q + k + 1];
+        const df aa = df_sqrt(cdf_norm2(al));
         te[k] = aa;
         te2[k] = aa * aa;
-        if (aa > 0.0) ph = cmul(ph, make_double2(al.x / aa, al.y / aa));
+        if (aa.hi > 0.0f) ph = ph * cdf_make(al.re / aa, al.im / aa);
       }
     }
   }
   __syncthreads();
   t_phase[3] = clock64();
-  // 4a. bisection for the p smallest eigenvalues (one thread each)
-  double lo = 0.0, hi = 0.0, tnorm = 0.0;
+  // 4a. multisection: each warp refines one wanted eigenvalue at a time, its 32
+  //     lanes evaluating the Sturm count at 32 interior points of the bracket
+  df lo = df_zero(), hi = df_zero();
   for (int k = 0; k < r; ++k) {
-    const double rad = (k > 0 ? te[k - 1] : 0.0) + (k + 1 < r ? te[k] : 0.0);
-    lo = k == 0 ? ta[k] - rad : fmin(lo, ta[k] - rad);
-    hi = k == 0 ? ta[k] + rad : fmax(hi, ta[k] + rad);
+    const df rad = (k > 0 ? te[k - 1] : df_zero()) + (k + 1 < r ? te[k] : df_zero());
+    const df l = ta[k] - rad, h = ta[k] + rad;
+    if (k == 0 || df_lt(l, lo)) lo = l;
+    if (k == 0 || df_lt(hi, h)) hi = h;
   }
-  tnorm = fmax(fabs(lo), fabs(hi));
-  const double pivmin = 1e-300 + 1e-30 * tnorm * tnorm;
-  if (tid < p) {
-    double a0 = lo - 1e-14 * tnorm - 1e-300, b0 = hi + 1e-14 * tnorm + 1e-300;
-    for (int it = 0; it < 200; ++it) {
-      const double mid = 0.5 * (a0 + b0);
-      if (mid <= a0 || mid >= b0 || b0 - a0 <= 4e-16 * fmax(fabs(a0), fabs(b0))) break;
-      if (sturm_count(ta, te2, r, mid, pivmin) > tid) b0 = mid;
-      else a0 = mid;
+  const float tnorm = fmaxf(fabsf(lo.hi), fabsf(hi.hi)) + 1e-30f;
+  // Sturm pivots below pivmin are replaced by -pivmin: e^2 / pivmin stays far below the float range
+  const float pivmin = fmaxf(1e-30f * tnorm * tnorm, 1e-36f);
+  // inverse iteration: pivots are kept above the accuracy of the shift, so a solve
+  // grows the vector by at most ~1e14 and never leaves the float range
+  const float pivmin_ii = 1e-14f * tnorm;
+  for (int j = warp; j < p; j += nw) {
+    df a0 = lo - df_make(1e-6f * tnorm, 0.0f), b0 = hi + df_make(1e-6f * tnorm, 0.0f);
+    for (int it = 0; it < 24; ++it) {
+      const df w = b0 - a0;
+      if (df_to(w) <= 4e-15 * (double)tnorm) break;
+      const df x = a0 + df_mul_f(w, float(lane + 1) / 33.0f);
+      const int cnt = sturm_count_df(ta, te2, r, x, pivmin);
+      // new bracket: largest point with count <= j, smallest with count > j
+      const unsigned below = __ballot_sync(0xffffffffu, cnt <= j);
+      const int nb = __popc(below);  // points 0..nb-1 have count <= j (counts increase with x)
+      const df xa = df_make(__shfl_sync(0xffffffffu, x.hi, nb > 0 ? nb - 1 : 0),
+                            __shfl_sync(0xffffffffu, x.lo, nb > 0 ? nb - 1 : 0));
+      const df xb = df_make(__shfl_sync(0xffffffffu, x.hi, nb < 32 ? nb : 31),
+                            __shfl_sync(0xffffffffu, x.lo, nb < 32 ? nb : 31));
+      if (nb > 0) a0 = xa;
+      if (nb < 32) b0 = xb;
     }
-    lam[tid] = 0.5 * (a0 + b0);
+    if (lane == 0) {
+      lam[j] = (a0 + b0) * df_make(0.5f, 0.0f);
+      lo_s[j] = a0;
+      hi_s[j] = b0;
+    }
   }
   __syncthreads();
   t_phase[4] = clock64();
-  // 4b. inverse iteration on T - lam_j I (Gaussian elimination with partial pivoting)
-  for (int sweep = 0; sweep < 3; ++sweep) {
+  // 4b. inverse iteration on Tr - lam_j I (Gaussian elimination with partial
+  //     pivoting), one thread per eigenvalue; cluster members re-orthogonalised
+  for (int sweep = 0; sweep < 4; ++sweep) {
     if (tid < p) {
       const int j = tid;
-      double* z = Z + j * r;
+      df* z = Z + j * q;
       if (sweep == 0)
-        for (int i = 0; i < r; ++i) z[i] = 1.0 + 0.37 * sin(1.7 * (i + 1) * (j + 1));
-      const double shift = lam[j];
-      // factor and solve in local storage: rows hold (diag, super1, super2) after pivoting
-      double u0[kMaxTrial], u1[kMaxTrial], u2[kMaxTrial], mult[kMaxTrial];
+        for (int i = 0; i < r; ++i) z[i] = df_make(1.0f + 0.37f * __sinf(1.7f * (i + 1) * (j + 1)), 0.0f);
+      const df shift = lam[j];
+      df u0[kMaxTrial], u1[kMaxTrial], u2[kMaxTrial], mult[kMaxTrial];
       bool swp[kMaxTrial];
-      double d0 = ta[0] - shift, s1 = r > 1 ? te[0] : 0.0;
+      df d0 = ta[0] - shift, s1 = r > 1 ? te[0] : df_zero();
       for (int i = 0; i < r; ++i) {
-        const double below_sub = i + 1 < r ? te[i] : 0.0;
-        const double below_diag = i + 1 < r ? ta[i + 1] - shift : 0.0;
-        const double below_sup = i + 2 < r ? te[i + 1] : 0.0;
-        if (i + 1 < r && fabs(below_sub) > fabs(d0)) {
-          // swap rows i and i+1
+        const df below_sub = i + 1 < r ? te[i] : df_zero();
+        const df below_diag = i + 1 < r ? ta[i + 1] - shift : df_zero();
+        const df below_sup = i + 2 < r ? te[i + 1] : df_zero();
+        if (i + 1 < r && fabsf(below_sub.hi) > fabsf(d0.hi)) {
           swp[i] = true;
           u0[i] = below_sub;
           u1[i] = below_diag;
           u2[i] = below_sup;
-          const double mlt = d0 / below_sub;
+          const df mlt = d0 / below_sub;
           mult[i] = mlt;
           d0 = s1 - mlt * below_diag;
-          s1 = -mlt * below_sup;
+          s1 = -(mlt * below_sup);
         } else {
           swp[i] = false;
-          double dd = d0;
-          if (fabs(dd) < pivmin) dd = dd < 0 ? -pivmin : pivmin;
+          df dd = d0;
+          if (fabsf(dd.hi) < pivmin_ii) dd = df_make(dd.hi < 0.0f ? -pivmin_ii : pivmin_ii, 0.0f);
           u0[i] = dd;
           u1[i] = s1;
-          u2[i] = 0.0;
-          const double mlt = i + 1 < r ? below_sub / dd : 0.0;
+          u2[i] = df_zero();
+          const df mlt = i + 1 < r ? below_sub / dd : df_zero();
           mult[i] = mlt;
           d0 = below_diag - mlt * s1;
           s1 = below_sup;
         }
       }
-      // forward: apply the row operations to z
       for (int i = 0; i + 1 < r; ++i) {
         if (swp[i]) {
-          const double t0 = z[i];
+          const df t0 = z[i];
           z[i] = z[i + 1];
           z[i + 1] = t0 - mult[i] * z[i];
         } else {
-          z[i + 1] -= mult[i] * z[i];
+          z[i + 1] = z[i + 1] - mult[i] * z[i];
         }
       }
-      // backward substitution
       for (int i = r - 1; i >= 0; --i) {
-        double v = z[i];
-        if (i + 1 < r) v -= u1[i] * z[i + 1];
-        if (i + 2 < r) v -= u2[i] * z[i + 2];
-        double dd = u0[i];
-        if (fabs(dd) < pivmin) dd = dd < 0 ? -pivmin : pivmin;
+        df v = z[i];
+        if (i + 1 < r) v = v - u1[i] * z[i + 1];
+        if (i + 2 < r) v = v - u2[i] * z[i + 2];
+        df dd = u0[i];
+        if (fabsf(dd.hi) < pivmin_ii) dd = df_make(dd.hi < 0.0f ? -pivmin_ii : pivmin_ii, 0.0f);
         z[i] = v / dd;
       }
-      double nrm = 0.0;
-      for (int i = 0; i < r; ++i) nrm += z[i] * z[i];
-      nrm = 1.0 / sqrt(nrm);
-      for (int i = 0; i < r; ++i) z[i] *= nrm;
+      float zmax = 0.0f;
+      for (int i = 0; i < r; ++i) zmax = fmaxf(zmax, fabsf(z[i].hi));
+      const float sc = zmax > 0.0f ? 1.0f / zmax : 1.0f;
+      df nrm = df_zero();
+      for (int i = 0; i < r; ++i) {
+        z[i] = df_mul_f(z[i], sc);
+        nrm = nrm + z[i] * z[i];
+      }
+      const df inv = df_make(1.0f, 0.0f) / df_sqrt(nrm);
+      for (int i = 0; i < r; ++i) z[i] = z[i] * inv;
     }
     __syncthreads();
-    // re-orthogonalise inside clusters of close eigenvalues (modified Gram-Schmidt)
-    if (tid == 0) {
+    // modified Gram-Schmidt against earlier vectors whose eigenvalues lie within
+    // 1e-3 |T| (the usual reorthogonalisation window of inverse iteration);
+    // warp 0, lanes over the components
+    if (warp == 0) {
       for (int j = 1; j < p; ++j) {
-        int j0 = j;
-        while (j0 > 0 && lam[j] - lam[j0 - 1] <= 1e-7 * tnorm) --j0;
-        if (j0 == j) continue;
-        double* zj = Z + j * r;
-        for (int c = j0; c < j; ++c) {
-          const double* zc = Z + c * r;
-          double dot = 0.0;
-          for (int i = 0; i < r; ++i) dot += zc[i] * zj[i];
-          for (int i = 0; i < r; ++i) zj[i] -= dot * zc[i];
+        df* zj = Z + j * q;
+        bool touched = false;
+        for (int c = 0; c < j; ++c) {
+          if (df_to(lam[j] - lam[c]) > 1e-3 * (double)tnorm) continue;
+          const df* zc = Z + c * q;
+          df dot = df_zero();
+          for (int i = lane; i < r; i += 32) dot = dot + zc[i] * zj[i];
+          dot = warp_sum_df(dot);
+          for (int i = lane; i < r; i += 32) zj[i] = zj[i] - dot * zc[i];
+          __syncwarp();
+          touched = true;
         }
-        double nrm = 0.0;
-        for (int i = 0; i < r; ++i) nrm += zj[i] * zj[i];
-        nrm = 1.0 / sqrt(nrm);
-        for (int i = 0; i < r; ++i) zj[i] *= nrm;
+        if (touched) {
+          df nrm = df_zero();
+          for (int i = lane; i < r; i += 32) nrm = nrm + zj[i] * zj[i];
+          nrm = warp_sum_df(nrm);
+          const df inv = df_make(1.0f, 0.0f) / df_sqrt(nrm);
+          for (int i = lane; i < r; i += 32) zj[i] = zj[i] * inv;
+          __syncwarp();
+        }
       }
     }
     __syncthreads();
   }
   t_phase[5] = clock64();
-  // 5. back-transformation u_j = Q (phase * z_j), one warp per vector
+  // 5. back-transformation u_j = Q (phase * z_j), then C = D T u (one warp per vector)
   for (int j = warp; j < p; j += nw) {
-    double2* u = U + (long)j * q;
-    for (int i = lane; i < r; i += 32) u[i] = Z[j * r + i] * tphase[i];
+    cdf* u = U + (long)j * q;
+    for (int i = lane; i < r; i += 32) u[i] = cdf_scale(tphase[i], Z[j * q + i]);
     __syncwarp();
     for (int k = r - 3; k >= 0; --k) {
-      const double beta = tbeta[k];
-      if (beta == 0.0) continue;
+      const df beta = tbeta[k];
+      if (beta.hi == 0.0f) continue;
       const int m = r - k - 1;
-      double2 acc = make_double2(0, 0);
-      for (int i = lane; i < m; i += 32) acc = acc + cmulc(H[(long)k * q + k + 1 + i], u[k + 1 + i]);
-      acc = warp_sum2(acc);
-      const double2 f = beta * acc;
-      for (int i = lane; i < m; i += 32) u[k + 1 + i] = u[k + 1 + i] - cmul(H[(long)k * q + k + 1 + i], f);
+      cdf acc = cdf_zero();
+      for (int i = lane; i < m; i += 32) acc = acc + cdf_mulc(H[(long)k * q + k + 1 + i], u[k + 1 + i]);
+      acc = warp_sum_cdf(acc);
+      const cdf f = cdf_scale(acc, beta);
+      for (int i = lane; i < m; i += 32) u[k + 1 + i] = u[k + 1 + i] - H[(long)k * q + k + 1 + i] * f;
       __syncwarp();
     }
-    // y = R^{-1} u (back substitution), then C[kidx[i], j] = d * y_i
-    for (int i = r - 1; i >= 0; --i) {
-      double2 acc = make_double2(0, 0);
-      for (int k = i + 1 + lane; k < r; k += 32) acc = acc + cmul(G[(long)k * q + i], u[k]);
-      acc = warp_sum2(acc);
-      if (lane == 0) {
-        const double rii = G[(long)i * q + i].x;
-        const double2 v = u[i] - acc;
-        u[i] = make_double2(v.x / rii, v.y / rii);
-      }
-      __syncwarp();
+    for (int i = lane; i < q; i += 32) {
+      cdf acc = cdf_zero();
+      for (int m = i; m < r; ++m) acc = acc + T[(long)m * q + i] * u[m];
+      Cout[(long)j * q + i] = s_keep[i] ? d[i] * cdf_to(acc) : make_double2(0, 0);
     }
-    for (int i = lane; i < q; i += 32) Cout[(long)j * q + i] = s_keep[i] ? d[i] * u[i] : make_double2(0, 0);
   }
-  for (int j = tid; j < p; j += nt) theta_out[j] = lam[j];
+  for (int j = tid; j < p; j += nt) theta_out[j] = df_to(lam[j]);
   __syncthreads();
+  // a non-finite coefficient means a breakdown: report it instead of passing it on
+  int bad = 0;
+  for (long t = tid; t < (long)q * p; t += nt) {
+    const double2 c = Cout[t];
+    bad |= !(isfinite(c.x) && isfinite(c.y));
+  }
+  for (int j = tid; j < p; j += nt) bad |= !isfinite(theta_out[j]);
+  bad = __syncthreads_or(bad);
   t_phase[6] = clock64();
   if (tid == 0) {
-    info[0] = 0;
-    info[1] = r;
+    info[0] = bad ? -3 : 0;
+    info[1] = s_r;
     if (phase_out)
       for (int ph = 0; ph < 6; ++ph) phase_out[ph] = (int)((t_phase[ph + 1] - t_phase[ph]) / 1000);
   }
@@ -843,12 +879,12 @@ void gram(const Level& L, const double* d_ph, int cpg, const double2* S, long ld
   PBS_LAUNCHED();
 }
 
-size_t small_rr_scratch(int q) { return (2ull * q * q + (size_t)q * kMaxBlock) * sizeof(double2) + 64; }
+size_t small_rr_scratch(int q) { return (3ull * q * q + (size_t)q * kMaxBlock) * sizeof(double2) + 64; }
 
 void small_rr(const double2* GM, const double2* GA, int q, int p, double2* C, double* theta, double2* scratch,
               int* d_info, cudaStream_t s) {
   if (q > kMaxTrial || p > q || p < 1 || p > kMaxBlock) fail(PBS_EINVAL, "small_rr: bad sizes");
-  const size_t dyn = (2ull * q * q + (size_t)q * p) * sizeof(double2);
+  const size_t dyn = (3ull * q * q + (size_t)q * p) * sizeof(double2);
   const int in_smem = dyn <= 150 * 1024 ? 1 : 0;
   static bool attr = false;
   if (!attr) {
@@ -905,7 +941,7 @@ void scale_columns(double2* X, long ld, long rows, int ncols, const double* d_sc
 //
 // The scratch of the small dense solve lives in this file-scope device array,
 // sized for the largest trial block the library supports (q = 96, p = 32):
-// 2 q^2 + q p complex doubles, about 344 KB, held by every GPU that loads the
+// 3 q^2 + q p complex doubles, about 480 KB, held by every GPU that loads the
 // library until the process exits.  Host code cannot use the array's name as a
 // device address, so its address is looked up once per device with
 // cudaGetSymbolAddress while that device is current.
@@ -914,7 +950,7 @@ void scale_columns(double2* X, long ld, long rows, int ncols, const double* d_sc
 
 namespace {
 constexpr int kNoAllocQ = pbs::kMaxTrial, kNoAllocP = pbs::kMaxBlock;
-static __device__ __align__(256) double2 g_small_rr_scratch[2 * kNoAllocQ * kNoAllocQ + kNoAllocQ * kNoAllocP + 8];
+static __device__ __align__(256) double2 g_small_rr_scratch[3 * kNoAllocQ * kNoAllocQ + kNoAllocQ * kNoAllocP + 8];
 constexpr int kMaxDevices = 64;
 std::mutex g_scratch_mutex;
 void* g_scratch_addr[kMaxDevices] = {};

@@ -461,7 +461,9 @@ void rayleigh_ritz_step(pbs_ctx* ctx, const double2* S, int q, int p, double2* d
   int info[2] = {0, 0};
   PBS_CUDA(cudaMemcpyAsync(info, W.info, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
   PBS_CUDA(cudaStreamSynchronize(s));
-  if (info[0] != 0) fail(PBS_ENUMERIC, info[0] == -2 ? "non-finite Gram matrix" : "trial space lost rank");
+  if (info[0] != 0)
+    fail(PBS_ENUMERIC, info[0] == -2 ? "non-finite Gram matrix"
+                                     : info[0] == -3 ? "Rayleigh-Ritz breakdown" : "trial space lost rank");
   block_update(S, W.D, q, W.C, q, dst, W.D, p, nullptr, 0, W.D, s);
 }
 
@@ -549,6 +551,7 @@ KResult iterate(pbs_ctx* ctx, const pbs_opts& o, cudaStream_t s) {
     PBS_CUDA(cudaStreamSynchronize(s));
     if (info[0] != 0) {
       if (info[0] == -2) fail(PBS_ENUMERIC, "non-finite Gram matrix");
+      if (info[0] == -3) fail(PBS_ENUMERIC, "Rayleigh-Ritz breakdown");
       if (!use_p) fail(PBS_ENUMERIC, "trial space lost rank");
       // rank loss in the LOBPCG basis: restart without the search direction
       PBS_CUDA(cudaMemcpyAsync(W.S + D * p, Wd, sizeof(double2) * D * p, cudaMemcpyDeviceToDevice, s));
