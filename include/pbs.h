@@ -199,7 +199,8 @@ PBS_API int pbs_rayleigh_ritz(pbs_ctx *ctx, const pbs_geom *geom, const pbs_opts
  * CUDA events on the stream it is launched on (the library's stream).
  * `classes` is "all" or a comma-separated list of "edge_smooth",
  * "node_smooth", "gram", "small_rr", "residual", "block_update",
- * "lift_adj_mass"; NULL or "" switches timing off.  Enabling resets the
+ * "lift_adj_mass", optionally followed by "/N" to time only every N-th launch
+ * of each listed class; NULL or "" switches timing off.  Enabling resets the
  * counters.  pbs_profile_read returns, for one class, the summed device time
  * (ms), the number of timed launches and their summed algorithmic work (bytes
  * moved for the streaming kernels, flops for "gram", "small_rr" and

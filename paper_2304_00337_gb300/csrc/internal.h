@@ -95,6 +95,9 @@ struct TimedLaunch {
 };
 struct KernelTimer {
   unsigned mask = 0;  // bit c set: class c is timed
+  int every = 1;      // time every `every`-th launch of a timed class
+  long seen[KC_COUNT] = {};
+  bool open = false;  // the latest begin was recorded
   double total_ms[KC_COUNT] = {};
   double work[KC_COUNT] = {};
   long launches[KC_COUNT] = {};

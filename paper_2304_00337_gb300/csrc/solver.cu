@@ -42,6 +42,8 @@ bool verbose_enabled() {
 void timer_begin(int cls, cudaStream_t s, double work) {
   KernelTimer* t = g_timer;
   if (!t || !(t->mask & (1u << cls))) return;
+  t->open = (t->seen[cls]++ % t->every) == 0;
+  if (!t->open) return;
   std::pair<cudaEvent_t, cudaEvent_t> ev;
   if (!t->pool.empty()) {
     ev = t->pool.back();
@@ -56,7 +58,8 @@ void timer_begin(int cls, cudaStream_t s, double work) {
 
 void timer_end(int cls, cudaStream_t s) {
   KernelTimer* t = g_timer;
-  if (!t || !(t->mask & (1u << cls)) || t->pending.empty()) return;
+  if (!t || !(t->mask & (1u << cls)) || !t->open || t->pending.empty()) return;
+  t->open = false;
   PBS_CUDA(cudaEventRecord(t->pending.back().stop, s));
 }
 
@@ -1062,6 +1065,18 @@ static int class_of(const char* name) {
 int pbs_profile_enable(pbs_ctx* ctx, const char* classes) {
   if (!ctx) return PBS_EINVAL;
   unsigned mask = 0;
+  int every = 1;
+  std::string spec = classes ? classes : "";
+  const size_t slash = spec.find('/');
+  if (slash != std::string::npos) {
+    every = std::atoi(spec.c_str() + slash + 1);
+    spec = spec.substr(0, slash);
+    if (every < 1) {
+      g_last_error = "sampling interval must be >= 1";
+      return PBS_EINVAL;
+    }
+  }
+  classes = spec.c_str();
   if (classes && *classes) {
     if (std::strcmp(classes, "all") == 0) {
       mask = ((1u << KC_COUNT) - 1) & ~1u;
@@ -1083,7 +1098,10 @@ int pbs_profile_enable(pbs_ctx* ctx, const char* classes) {
   }
   KernelTimer& t = ctx->timer;
   t.mask = mask;
+  t.every = every;
+  t.open = false;
   for (int c = 0; c < KC_COUNT; ++c) {
+    t.seen[c] = 0;
     t.total_ms[c] = 0.0;
     t.work[c] = 0.0;
     t.launches[c] = 0;
