@@ -115,6 +115,10 @@ typedef struct {
   int nodal_cycles; /* nodal V-cycles per projection (default 2)                   */
   int extrap_depth; /* previous bases used for the initial guess along a path, 0..3 (default 3) */
   uint64_t seed;    /* seed of the random initial block when no guess is given     */
+  int kbatch;       /* Bloch vectors in flight along a path (default 1): the path is split
+                       into kbatch contiguous chains solved in lock-step, one block of
+                       `block` columns each, every launch covering all of them; each chain
+                       extrapolates along its own segment (Section 6)                 */
 } pbs_opts;
 
 /* Create a context on CUDA device `device`. `hbm_budget_bytes` caps the

@@ -62,7 +62,7 @@ class pbs_opts(ct.Structure):
     _fields_ = [("nev", ct.c_int), ("block", ct.c_int), ("max_iter", ct.c_int), ("precision", ct.c_int),
                 ("span", ct.c_int), ("tol", ct.c_double), ("mu", ct.c_double), ("nu_pre", ct.c_int),
                 ("nu_post", ct.c_int), ("coarsest", ct.c_int), ("nodal_cycles", ct.c_int),
-                ("extrap_depth", ct.c_int), ("seed", ct.c_uint64)]
+                ("extrap_depth", ct.c_int), ("seed", ct.c_uint64), ("kbatch", ct.c_int)]
 
 
 _lib = None

@@ -136,8 +136,10 @@ __global__ void k_sub_lift(int n, int m, const double* ph, int cpg, const cx<T>*
 }
 
 // per column sums of the x-edge and y-edge values (for the constant-field deflation at k = 0)
-__global__ void k_edge_sums(long N, const double2* __restrict__ X, long ld, double* __restrict__ part, int nblk) {
+__global__ void k_edge_sums(long N, const double2* __restrict__ X, long ld, double* __restrict__ part, int nblk,
+                            const int* __restrict__ gamma, int cpg) {
   const int c = blockIdx.y;
+  if (!gamma[c / cpg]) return;
   double sx_re = 0, sx_im = 0, sy_re = 0, sy_im = 0;
   for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < N; t += (long)gridDim.x * blockDim.x) {
     const double2 a = X[c * ld + t], b = X[c * ld + N + t];
@@ -152,8 +154,10 @@ __global__ void k_edge_sums(long N, const double2* __restrict__ X, long ld, doub
   }
 }
 
-__global__ void k_edge_sub_means(long N, double2* __restrict__ X, long ld, const double* __restrict__ part, int nblk) {
+__global__ void k_edge_sub_means(long N, double2* __restrict__ X, long ld, const double* __restrict__ part, int nblk,
+                                 const int* __restrict__ gamma, int cpg) {
   const int c = blockIdx.y;
+  if (!gamma[c / cpg]) return;
   __shared__ double mean[4];
   if (threadIdx.x < 4) {
     double s = 0;
@@ -178,95 +182,130 @@ __global__ void k_f2d(const float2* __restrict__ X, double2* __restrict__ Y, lon
     Y[t] = make_double2(double(X[t].x), double(X[t].y));
 }
 
-// ---- tall-skinny Gram: G[a][b] = sum_r conj(X[r][a]) wt[r] Y[r][b], a <= b ----
-constexpr int kGramRows = 32;
+// ---- block Gram matrices of a trial block, fused with the stencils ---------
+// For group g (blockIdx.y) and trial columns a, b (a <= b):
+//   GM[a][b] = sum_edges conj(s_a) (M s_b),   GA[a][b] = sum_cells w |..| conj(c_a) c_b,  c = C s
+// Each block takes chunks of kGramRows nodes; for every trial column it stages
+// the node's x- and y-edge values, (M s) at those edges and the curl of the
+// node's cell in shared memory, then accumulates its share of the q(q+1)/2
+// entries.  Trial column a of group g lives at roles.b[a / pr] + (g pr + a % pr) ld.
+constexpr int kGramRows = 16;
 constexpr int kGramAcc = 20;  // accumulators per thread: q(q+1)/2 <= 20 * 256 for q <= 100
 
-__global__ void __launch_bounds__(256) k_gram_ts(const double2* __restrict__ X, long ldx, const double2* __restrict__ Y,
-                                                 long ldy, int q, long rows, const double* __restrict__ winv,
-                                                 double wscale, double2* __restrict__ part) {
+__device__ __forceinline__ const double2* role_col(const Roles& R, int g, int a) {
+  return R.b[a / R.pr] + ((long)g * R.pr + a % R.pr) * R.ld;
+}
+
+__global__ void __launch_bounds__(256) k_gram_fused(Lvl<double> L, Wts<double> w, const double* ph, Roles roles, int q,
+                                                    double2* __restrict__ part, int npart) {
   extern __shared__ double2 sm[];
-  double2* xs = sm;                       // [q][kGramRows]
-  double2* ys = sm + q * kGramRows;       // [q][kGramRows]
+  const int g = blockIdx.y;
+  const long N = (long)L.n * L.m;
+  double2* sx = sm;                      // [q][kGramRows]
+  double2* sy = sx + q * kGramRows;
+  double2* mx = sy + q * kGramRows;
+  double2* my = mx + q * kGramRows;
+  double2* cc = my + q * kGramRows;      // w-scaled curl in cc_w, plain curl in cc
+  double2* cw = cc + q * kGramRows;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int ne = q * (q + 1) / 2;
+  const Ph<double> p = load_ph<double>(ph, g);
   int ea[kGramAcc], eb[kGramAcc];
-  double2 acc[kGramAcc];
+  double2 am[kGramAcc], aa[kGramAcc];
 #pragma unroll
   for (int k = 0; k < kGramAcc; ++k) {
-    acc[k] = make_double2(0, 0);
+    am[k] = make_double2(0, 0);
+    aa[k] = make_double2(0, 0);
     const int e = tid + k * nt;
-    int a = 0, b = 0;
+    int ai = 0, bi = 0;
     if (e < ne) {  // column-major upper triangle: e = b(b+1)/2 + a
-      b = int((sqrt(8.0 * e + 1.0) - 1.0) * 0.5);
-      while ((b + 1) * (b + 2) / 2 <= e) ++b;
-      while (b * (b + 1) / 2 > e) --b;
-      a = e - b * (b + 1) / 2;
+      bi = int((sqrt(8.0 * e + 1.0) - 1.0) * 0.5);
+      while ((bi + 1) * (bi + 2) / 2 <= e) ++bi;
+      while (bi * (bi + 1) / 2 > e) --bi;
+      ai = e - bi * (bi + 1) / 2;
     }
-    ea[k] = a;
-    eb[k] = b;
+    ea[k] = ai;
+    eb[k] = bi;
   }
-  const long nchunks = (rows + kGramRows - 1) / kGramRows;
+  const long nchunks = (N + kGramRows - 1) / kGramRows;
   for (long ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
     const long r0 = ch * kGramRows;
     __syncthreads();
     for (int t = tid; t < q * kGramRows; t += nt) {
       const int col = t / kGramRows, rr = t % kGramRows;
-      const long r = r0 + rr;
-      double2 xv = make_double2(0, 0), yv = make_double2(0, 0);
-      if (r < rows) {
-        xv = X[col * ldx + r];
-        yv = Y[col * ldy + r];
-        if (winv) yv = (wscale * winv[r]) * yv;
+      const long node = r0 + rr;
+      double2 vx = make_double2(0, 0), vy = vx, vmx = vx, vmy = vx, vc = vx, vcw = vx;
+      if (node < N) {
+        const int i = int(node % L.n), j = int(node / L.n);
+        const ERd<double> rd{role_col(roles, g, col), L.n, L.m, p};
+        vx = rd.x(i, j);
+        vy = rd.y(i, j);
+        vmx = M_x<double>(rd, L, i, j);
+        vmy = M_y<double>(rd, L, i, j);
+        vc = curl_at<double>(rd, i, j);
+        vcw = w(i, j) * vc;
       }
-      xs[col * kGramRows + rr] = xv;
-      ys[col * kGramRows + rr] = yv;
+      sx[col * kGramRows + rr] = vx;
+      sy[col * kGramRows + rr] = vy;
+      mx[col * kGramRows + rr] = vmx;
+      my[col * kGramRows + rr] = vmy;
+      cc[col * kGramRows + rr] = vc;
+      cw[col * kGramRows + rr] = vcw;
     }
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < kGramAcc; ++k) {
       if (tid + k * nt < ne) {
-        const double2* xa = xs + ea[k] * kGramRows;
-        const double2* yb = ys + eb[k] * kGramRows;
-        double2 s = acc[k];
-#pragma unroll 8
+        const int ia = ea[k] * kGramRows, ib = eb[k] * kGramRows;
+        double2 sM = am[k], sA = aa[k];
+#pragma unroll 4
         for (int rr = 0; rr < kGramRows; ++rr) {
-          const double2 u = xa[rr], v = yb[rr];
-          s.x = fma(u.x, v.x, fma(u.y, v.y, s.x));
-          s.y = fma(u.x, v.y, fma(-u.y, v.x, s.y));
+          const double2 u = sx[ia + rr], v = mx[ib + rr], u2 = sy[ia + rr], v2 = my[ib + rr];
+          sM.x = fma(u.x, v.x, fma(u.y, v.y, sM.x));
+          sM.y = fma(u.x, v.y, fma(-u.y, v.x, sM.y));
+          sM.x = fma(u2.x, v2.x, fma(u2.y, v2.y, sM.x));
+          sM.y = fma(u2.x, v2.y, fma(-u2.y, v2.x, sM.y));
+          const double2 c1 = cc[ia + rr], c2 = cw[ib + rr];
+          sA.x = fma(c1.x, c2.x, fma(c1.y, c2.y, sA.x));
+          sA.y = fma(c1.x, c2.y, fma(-c1.y, c2.x, sA.y));
         }
-        acc[k] = s;
+        am[k] = sM;
+        aa[k] = sA;
       }
     }
   }
+  double2* pm = part + ((long)g * npart + blockIdx.x) * 2 * ne;
 #pragma unroll
   for (int k = 0; k < kGramAcc; ++k) {
     const int e = tid + k * nt;
-    if (e < ne) part[(long)blockIdx.x * ne + e] = acc[k];
+    if (e < ne) {
+      pm[e] = am[k];
+      pm[ne + e] = aa[k];
+    }
   }
 }
 
-// sum partials in fixed order; write full Hermitian q x q (column-major), optionally accumulating
-__global__ void k_gram_finalize(const double2* __restrict__ part, int npart, int q, double2* __restrict__ G,
-                                int accumulate) {
+// sum partials in fixed order; write full Hermitian q x q (column-major) per group
+__global__ void k_gram_finalize(const double2* __restrict__ part, int npart, int q, double2* __restrict__ GM,
+                                double2* __restrict__ GA) {
+  const int g = blockIdx.y;
   const int ne = q * (q + 1) / 2;
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += gridDim.x * blockDim.x) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < 2 * ne; e += gridDim.x * blockDim.x) {
     double2 s = make_double2(0, 0);
-    for (int p = 0; p < npart; ++p) {
-      const double2 v = part[(long)p * ne + e];
+    for (int pp = 0; pp < npart; ++pp) {
+      const double2 v = part[((long)g * npart + pp) * 2 * ne + e];
       s.x += v.x;
       s.y += v.y;
     }
-    int b = int((sqrt(8.0 * e + 1.0) - 1.0) * 0.5);
-    while ((b + 1) * (b + 2) / 2 <= e) ++b;
-    while (b * (b + 1) / 2 > e) --b;
-    const int a = e - b * (b + 1) / 2;
-    if (accumulate) {
-      s = s + G[a + (long)b * q];
-    }
-    if (a == b) s.y = 0.0;
-    G[a + (long)b * q] = s;
-    G[b + (long)a * q] = conj(s);
+    const int ee = e < ne ? e : e - ne;
+    double2* G = (e < ne ? GM : GA) + (long)g * q * q;
+    int bi = int((sqrt(8.0 * ee + 1.0) - 1.0) * 0.5);
+    while ((bi + 1) * (bi + 2) / 2 <= ee) ++bi;
+    while (bi * (bi + 1) / 2 > ee) --bi;
+    const int ai = ee - bi * (bi + 1) / 2;
+    if (ai == bi) s.y = 0.0;
+    G[ai + (long)bi * q] = s;
+    G[bi + (long)ai * q] = conj(s);
   }
 }
 
@@ -329,8 +368,19 @@ __device__ int sturm_count_df(const df* a, const df* e2, int n, df x, float pivm
 __global__ void __launch_bounds__(kRRThreads) k_small_rr(const double2* __restrict__ GM, const double2* __restrict__ GA,
                                                          int q, int p, double2* __restrict__ Cout,
                                                          double* __restrict__ theta_out, double2* __restrict__ scr,
-                                                         int* __restrict__ info, int in_smem, int* __restrict__ phase_out) {
+                                                         int* __restrict__ info, int in_smem, int* __restrict__ phase_out,
+                                                         long scr_stride) {
   extern __shared__ double2 dsm[];
+  {  // group blockIdx.x: its own Gram matrices, outputs and scratch
+    const long g = blockIdx.x;
+    GM += g * q * q;
+    GA += g * q * q;
+    Cout += g * q * p;
+    theta_out += g * p;
+    scr += g * scr_stride;
+    info += 8 * g;
+    if (phase_out) phase_out += 8 * g;
+  }
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = kRRWarps;
   const long qq = (long)q * q;
   cdf* G = (cdf*)(in_smem ? dsm : scr);  // M-Gram -> R -> Y
@@ -711,20 +761,25 @@ __global__ void __launch_bounds__(kRRThreads) k_small_rr(const double2* __restri
   }
 }
 
-// Y[:, j] = sum_i X[:, i] C[i, j] (+ Z[:, j])
-__global__ void __launch_bounds__(256) k_block_update(const double2* __restrict__ X, long ldx, int q,
-                                                      const double2* __restrict__ C, int ldc, double2* __restrict__ Y,
-                                                      long ldy, int p, const double2* __restrict__ Z, long ldz,
-                                                      long rows) {
+// Y[:, j] = sum_i X[:, i] C[i, j] (+ Z[:, j]) for group blockIdx.y: trial column i
+// of the group at role_col(X, g, i); output column j at Y + (g p + j) ldy;
+// C of group g at C + g cgs (column-major, leading dimension ldc).
+__global__ void __launch_bounds__(256) k_block_update(Roles X, int q, const double2* __restrict__ C, int ldc, long cgs,
+                                                      double2* __restrict__ Y, long ldy, int p,
+                                                      const double2* __restrict__ Z, long ldz, long rows) {
   extern __shared__ double2 cs[];  // [p][q]
-  for (int t = threadIdx.x; t < p * q; t += blockDim.x) cs[t] = C[(long)(t / q) * ldc + (t % q)];
+  const int g = blockIdx.y;
+  const double2* Cg = C + g * cgs;
+  for (int t = threadIdx.x; t < p * q; t += blockDim.x) cs[t] = Cg[(long)(t / q) * ldc + (t % q)];
   __syncthreads();
+  double2* Yg = Y + (long)g * p * ldy;
+  const double2* Zg = Z ? Z + (long)g * p * ldz : nullptr;
   for (long r = blockIdx.x * (long)blockDim.x + threadIdx.x; r < rows; r += (long)gridDim.x * blockDim.x) {
     double2 acc[kMaxBlock];
 #pragma unroll
     for (int j = 0; j < kMaxBlock; ++j) acc[j] = make_double2(0, 0);
     for (int i = 0; i < q; ++i) {
-      const double2 x = X[(long)i * ldx + r];
+      const double2 x = role_col(X, g, i)[r];
 #pragma unroll
       for (int j = 0; j < kMaxBlock; ++j) {
         if (j < p) {
@@ -738,8 +793,8 @@ __global__ void __launch_bounds__(256) k_block_update(const double2* __restrict_
     for (int j = 0; j < kMaxBlock; ++j) {
       if (j < p) {
         double2 v = acc[j];
-        if (Z) v = v + Z[(long)j * ldz + r];
-        Y[(long)j * ldy + r] = v;
+        if (Zg) v = v + Zg[(long)j * ldz + r];
+        Yg[(long)j * ldy + r] = v;
       }
     }
   }
@@ -810,12 +865,13 @@ void lift_adj_mass(const Level& L, const double* d_ph, int cpg, const double2* X
   PBS_LAUNCHED();
 }
 
-void deflate_constants(const Level& L, double2* X, long ld, int ncols, double* d_partials, cudaStream_t s) {
+void deflate_constants(const Level& L, double2* X, long ld, int ncols, const int* d_gamma, int cpg,
+                       double* d_partials, cudaStream_t s) {
   if (ncols <= 0) return;
   const int nblk = 64;
-  k_edge_sums<<<dim3(nblk, ncols), 256, 0, s>>>(L.N(), X, ld, d_partials, nblk);
+  k_edge_sums<<<dim3(nblk, ncols), 256, 0, s>>>(L.N(), X, ld, d_partials, nblk, d_gamma, cpg);
   PBS_LAUNCHED();
-  k_edge_sub_means<<<dim3(nblk, ncols), 256, 0, s>>>(L.N(), X, ld, d_partials, nblk);
+  k_edge_sub_means<<<dim3(nblk, ncols), 256, 0, s>>>(L.N(), X, ld, d_partials, nblk, d_gamma, cpg);
   PBS_LAUNCHED();
 }
 
@@ -841,49 +897,45 @@ void residual(const Level& L, const double* d_ph, int cpg, const double2* E, dou
   PBS_LAUNCHED();
 }
 
-int gram_partials(long rows) {
-  long b = (rows + kGramRows - 1) / kGramRows;
-  return (int)(b < 2 * 152 ? b : 2 * 152);
+int gram_partials(long rows, int ngroups) {
+  const long chunks = (rows + kGramRows - 1) / kGramRows;
+  long per = (2 * 152 + ngroups - 1) / ngroups;
+  if (per < 8) per = 8;
+  return (int)(chunks < per ? chunks : per);
 }
 
-void gram(const Level& L, const double* d_ph, int cpg, const double2* S, long ld, int q, double2* GM, double2* GA,
-          double2* work, double2* d_partials, int npart, cudaStream_t s) {
-  if (q <= 0) return;
+void gram_groups(const Level& L, const double* d_ph, Roles roles, int q, int ngroups, double2* GM, double2* GA,
+                 double2* d_partials, long partial_capacity, cudaStream_t s) {
+  if (q <= 0 || ngroups <= 0) return;
   if (q > kMaxTrial) fail(PBS_EINVAL, "trial block too wide");
-  const long D = L.D(), N = L.N();
-  double2* MS = work;            // D x q
-  double2* CS = work + D * q;    // N x q
-  apply_edge<double>(L, d_ph, cpg, S, MS, nullptr, ld, q, 0.0, 1.0, 0.0, nullptr, 0.0, s);
-  // MS uses stride ld (same as S); CS stride N
-  apply_curl<double>(L, d_ph, cpg, S, ld, CS, N, q, s);
-  const size_t smem = 2ull * q * kGramRows * sizeof(double2);
+  const int npart = gram_partials(L.N(), ngroups);
+  const int ne = q * (q + 1) / 2;
+  if ((long)ngroups * npart * 2 * ne > partial_capacity) fail(PBS_EINVAL, "gram partials buffer too small");
+  const size_t smem = 6ull * q * kGramRows * sizeof(double2);
   static bool attr = false;
   if (!attr) {
-    PBS_CUDA(cudaFuncSetAttribute(k_gram_ts, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * kMaxTrial * kGramRows * (int)sizeof(double2)));
+    PBS_CUDA(cudaFuncSetAttribute(k_gram_fused, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  6 * kMaxTrial * kGramRows * (int)sizeof(double2)));
     attr = true;
   }
-  const int ne = q * (q + 1) / 2;
-  const int npM = std::min(npart, gram_partials(D));
-  timer_begin(KC_GRAM, s, 8.0 * ne * D);  // flops: one complex MAC per entry and row
-  k_gram_ts<<<npM, 256, smem, s>>>(S, ld, MS, ld, q, D, nullptr, 0.0, d_partials);
+  timer_begin(KC_GRAM, s, 8.0 * ne * 3.0 * L.N() * ngroups);  // flops: three complex MACs per entry and node
+  k_gram_fused<<<dim3(npart, ngroups), 256, smem, s>>>(L.lvl<double>(), L.wts<double>(), d_ph, roles, q, d_partials,
+                                                        npart);
   timer_end(KC_GRAM, s);
   PBS_LAUNCHED();
-  k_gram_finalize<<<(ne + 255) / 256, 256, 0, s>>>(d_partials, npM, q, GM, 0);
+  k_gram_finalize<<<dim3((2 * ne + 255) / 256, ngroups), 256, 0, s>>>(d_partials, npart, q, GM, GA);
   PBS_LAUNCHED();
-  const int npA = std::min(npart, gram_partials(N));
-  timer_begin(KC_GRAM, s, 8.0 * ne * N);
-  k_gram_ts<<<npA, 256, smem, s>>>(CS, N, CS, N, q, N, L.winv64, 1.0 / (L.h1 * L.h2), d_partials);
-  timer_end(KC_GRAM, s);
-  PBS_LAUNCHED();
-  k_gram_finalize<<<(ne + 255) / 256, 256, 0, s>>>(d_partials, npA, q, GA, 0);
-  PBS_LAUNCHED();
+}
+
+long gram_partials_size(long rows, int q, int ngroups) {
+  return (long)ngroups * gram_partials(rows, ngroups) * q * (q + 1);
 }
 
 size_t small_rr_scratch(int q) { return (3ull * q * q + (size_t)q * kMaxBlock) * sizeof(double2) + 64; }
 
 void small_rr(const double2* GM, const double2* GA, int q, int p, double2* C, double* theta, double2* scratch,
-              int* d_info, cudaStream_t s) {
-  if (q > kMaxTrial || p > q || p < 1 || p > kMaxBlock) fail(PBS_EINVAL, "small_rr: bad sizes");
+              int* d_info, int ngroups, cudaStream_t s) {
+  if (q > kMaxTrial || p > q || p < 1 || p > kMaxBlock || ngroups < 1) fail(PBS_EINVAL, "small_rr: bad sizes");
   const size_t dyn = (3ull * q * q + (size_t)q * p) * sizeof(double2);
   const int in_smem = dyn <= 150 * 1024 ? 1 : 0;
   static bool attr = false;
@@ -891,23 +943,24 @@ void small_rr(const double2* GM, const double2* GA, int q, int p, double2* C, do
     PBS_CUDA(cudaFuncSetAttribute(k_small_rr, cudaFuncAttributeMaxDynamicSharedMemorySize, 150 * 1024));
     attr = true;
   }
-  timer_begin(KC_SMALL_RR, s, 8.0 * 3.0 * q * q * q);  // flops, order of magnitude
-  k_small_rr<<<1, kRRThreads, in_smem ? dyn : 0, s>>>(GM, GA, q, p, C, theta, scratch, d_info, in_smem,
-                                                      verbose_enabled() ? d_info + 2 : nullptr);
+  const long stride = (long)(small_rr_scratch(q) / sizeof(double2));
+  timer_begin(KC_SMALL_RR, s, 8.0 * 3.0 * q * q * q * ngroups);  // flops, order of magnitude
+  k_small_rr<<<ngroups, kRRThreads, in_smem ? dyn : 0, s>>>(GM, GA, q, p, C, theta, scratch, d_info, in_smem,
+                                                            verbose_enabled() ? d_info + 2 : nullptr, stride);
   timer_end(KC_SMALL_RR, s);
   PBS_LAUNCHED();
   if (verbose_enabled()) {
     int h[8] = {};
     PBS_CUDA(cudaMemcpyAsync(h, d_info, sizeof h, cudaMemcpyDeviceToHost, s));
     PBS_CUDA(cudaStreamSynchronize(s));
-    std::fprintf(stderr, "[pbs] small_rr q=%d p=%d info=%d rank=%d kcycles: chol %d solves %d householder %d bisect %d invit %d back %d\n",
-                 q, p, h[0], h[1], h[2], h[3], h[4], h[5], h[6], h[7]);
+    std::fprintf(stderr, "[pbs] small_rr q=%d p=%d groups=%d info=%d rank=%d kcycles: chol %d solves %d householder %d bisect %d invit %d back %d\n",
+                 q, p, ngroups, h[0], h[1], h[2], h[3], h[4], h[5], h[6], h[7]);
   }
 }
 
-void block_update(const double2* X, long ldx, int q, const double2* C, int ldc, double2* Y, long ldy, int p,
-                  const double2* Z, long ldz, long rows, cudaStream_t s) {
-  if (p <= 0 || rows <= 0) return;
+void block_update(Roles X, int q, const double2* C, int ldc, long cgs, double2* Y, long ldy, int p,
+                  const double2* Z, long ldz, long rows, int ngroups, cudaStream_t s) {
+  if (p <= 0 || rows <= 0 || ngroups <= 0) return;
   if (p > kMaxBlock) fail(PBS_EINVAL, "block_update: p too large");
   const size_t smem = (size_t)p * q * sizeof(double2);
   static bool attr = false;
@@ -916,8 +969,10 @@ void block_update(const double2* X, long ldx, int q, const double2* C, int ldc, 
                                   kMaxBlock * kMaxTrial * (int)sizeof(double2)));
     attr = true;
   }
-  timer_begin(KC_BLOCK_UPDATE, s, 8.0 * q * p * rows);  // flops
-  k_block_update<<<blocks_for(rows, 256, 2 * 152 * 4), 256, smem, s>>>(X, ldx, q, C, ldc, Y, ldy, p, Z, ldz, rows);
+  long per = blocks_for(rows, 256, 2 * 152 * 4);
+  per = std::max<long>(1, per / ngroups);
+  timer_begin(KC_BLOCK_UPDATE, s, 8.0 * q * p * rows * ngroups);  // flops
+  k_block_update<<<dim3((unsigned)per, ngroups), 256, smem, s>>>(X, q, C, ldc, cgs, Y, ldy, p, Z, ldz, rows);
   timer_end(KC_BLOCK_UPDATE, s);
   PBS_LAUNCHED();
 }
@@ -977,7 +1032,7 @@ extern "C" int pbs_small_rr_noalloc(const pbs_c64* GM, const pbs_c64* GA, int q,
   }
   k_small_rr<<<1, kRRThreads, 0, (cudaStream_t)cuda_stream>>>((const double2*)GM, (const double2*)GA, q, p,
                                                                 (double2*)C, theta, (double2*)scratch, info, 0,
-                                                                nullptr);
+                                                                nullptr, 0);
   count_launch();
   return cudaGetLastError() == cudaSuccess ? PBS_OK : PBS_ECUDA;
 }

@@ -52,19 +52,29 @@ struct Hierarchy {
   std::vector<void*> allocs;
 };
 
-// Per-Bloch-vector data: phases and the factored coarsest systems.
+// Per-Bloch-vector data of `ngroups` groups (one Bloch vector each): phases,
+// k = 0 flags and the factored coarsest systems.  The device phase and flag
+// tables repeat the per-group entries three times, so that column c of any
+// role-major block [E_all | P_all | W_all] with `cpg` columns per group finds
+// its group's entry at c / cpg.
 struct KData {
-  double k1 = 0, k2 = 0;
-  double ph[4] = {1, 0, 1, 0};  // alpha, beta (host copy)
-  bool gamma = false;
-  double* d_ph = nullptr;       // device copy (4 doubles)
+  int ngroups = 0;
   int Dc = 0, Nc = 0;
-  double2* edge64 = nullptr;    // Cholesky factor (lower, column-major Dc x Dc) of A_c + mu M_c
+  double* d_ph = nullptr;      // 3 * ngroups entries of (alpha.re, alpha.im, beta.re, beta.im)
+  int* d_gamma = nullptr;      // 3 * ngroups flags: 1 when both phases equal one (k = 0)
+  double2* edge64 = nullptr;   // ngroups Cholesky factors (lower, column-major Dc x Dc) of A_c + mu M_c
   float2* edge32 = nullptr;
-  double2* node64 = nullptr;    // Cholesky factor of P_c (+ constant-mode term at k = 0)
+  double2* node64 = nullptr;   // ngroups factors of P_c (+ a constant-mode term at k = 0), Nc x Nc
   float2* node32 = nullptr;
+  std::vector<double> k1, k2;  // host mirror
+  std::vector<char> gamma;
+  bool owner = true;
+  bool any_gamma() const {
+    for (char g : gamma)
+      if (g) return true;
+    return false;
+  }
 };
-
 // Device allocator with a byte budget.
 class DevMem {
  public:
@@ -120,7 +130,9 @@ bool verbose_enabled();  // PBS_VERBOSE set in the environment (diagnostic trace
 // ---- hierarchy set-up (mg.cu) ---------------------------------------------
 void build_hierarchy(DevMem& mem, Hierarchy& H, const double* d_eps, int coarsest, cudaStream_t s);
 void free_hierarchy(DevMem& mem, Hierarchy& H);
-void build_kdata(DevMem& mem, const Hierarchy& H, KData& K, double k1, double k2, cudaStream_t s);
+void alloc_kdata(DevMem& mem, const Hierarchy& H, KData& K, int ngroups);
+void set_group_k(DevMem& mem, const Hierarchy& H, KData& K, int g, double k1, double k2, cudaStream_t s);
+KData kdata_view(const KData& K, int g);  // non-owning single-group view of group g
 void free_kdata(DevMem& mem, KData& K);
 
 // ---- operators (ops.cu); X, Y device blocks of ncols columns with stride ld ----
@@ -169,12 +181,13 @@ template <class T> struct MgWork {
 template <class T> void alloc_mg_work(DevMem& mem, const Hierarchy& H, int ncols, bool nodal, MgWork<T>& w);
 template <class T> void free_mg_work(DevMem& mem, MgWork<T>& w);
 // Y = B X: one edge V-cycle for A + mu M started from zero (x, y on level `l0`).
+// `cpg` columns per group: column c uses group (c / cpg) of the tables.
 template <class T>
 void edge_vcycle(const Hierarchy& H, const KData& K, MgWork<T>& w, int l0, const cx<T>* X, cx<T>* Y, long ld,
-                 int ncols, int nu_pre, int nu_post, cudaStream_t s);
+                 int ncols, int cpg, int nu_pre, int nu_post, cudaStream_t s);
 template <class T>
 void nodal_vcycle(const Hierarchy& H, const KData& K, MgWork<T>& w, int l0, const cx<T>* X, cx<T>* Y, long ld,
-                  int ncols, int nu_pre, int nu_post, cudaStream_t s);
+                  int ncols, int cpg, int nu_pre, int nu_post, cudaStream_t s);
 
 // ---- dense block kernels (dense.cu) ---------------------------------------
 void convert_d2f(const double2* X, float2* Y, long n, cudaStream_t s);
@@ -187,25 +200,36 @@ void sub_lift(const Level& L, const double* d_ph, int cpg, const cx<T>* Phi, lon
 template <class T>
 void lift_adj_mass(const Level& L, const double* d_ph, int cpg, const double2* X, long ldx, cx<T>* Rhs, long ldr,
                    int ncols, cudaStream_t s);
-// subtract the x-edge mean and the y-edge mean of every column (k = 0 deflation)
-void deflate_constants(const Level& L, double2* X, long ld, int ncols, double* d_partials, cudaStream_t s);
+// subtract the x-edge mean and the y-edge mean of every column of a k = 0 group
+// (flags d_gamma[c / cpg]; the deflation of the two constant fields)
+void deflate_constants(const Level& L, double2* X, long ld, int ncols, const int* d_gamma, int cpg,
+                       double* d_partials, cudaStream_t s);
 // per column: out[2c] = e^* M e, out[2c+1] = (C e)^* W (C e)
 void rayleigh_parts(const Level& L, const double* d_ph, int cpg, const double2* X, long ld, int ncols,
                     double* d_partials, double* d_out, cudaStream_t s);
 // R = A E - lam M E; per column out[2c] = |R|^2, out[2c+1] = |M E|^2
 void residual(const Level& L, const double* d_ph, int cpg, const double2* E, double2* R, long ld, int ncols,
               const double* d_lam, double* d_partials, double* d_out, cudaStream_t s);
-// GM = S^* M S, GA = (C S)^* W (C S)  (q x q, column-major); work: D*q + N*q double2
-void gram(const Level& L, const double* d_ph, int cpg, const double2* S, long ld, int q, double2* GM, double2* GA,
-          double2* work, double2* d_partials, int npart, cudaStream_t s);
-int gram_partials(long rows);
-// Rayleigh-Ritz in coefficient space: C (q x p) and theta (p); status in d_info[0]
+// Columns of trial blocks held in up to three role arrays: column a of group g is
+// b[a / pr] + (g * pr + a % pr) * ld.
+struct Roles {
+  const double2* b[3];
+  int pr;
+  long ld;
+};
+// Per group g (phases from entry g of d_ph): GM_g = S^* M S, GA_g = (C S)^* W (C S), q x q
+// column-major at GM + g q^2, GA + g q^2.
+void gram_groups(const Level& L, const double* d_ph, Roles roles, int q, int ngroups, double2* GM, double2* GA,
+                 double2* d_partials, long partial_capacity, cudaStream_t s);
+long gram_partials_size(long rows, int q, int ngroups);  // double2 elements
+// Rayleigh-Ritz in coefficient space for ngroups groups: C (q x p per group), theta (p per
+// group), status in d_info[8 g], scratch small_rr_scratch(q) bytes per group
 void small_rr(const double2* GM, const double2* GA, int q, int p, double2* C, double* theta, double2* scratch,
-              int* d_info, cudaStream_t s);
+              int* d_info, int ngroups, cudaStream_t s);
 size_t small_rr_scratch(int q);
-// Y[:, j] = sum_i X[:, i] C[i, j] (+ Z[:, j]); X: rows x q, C: q x p column-major (device)
-void block_update(const double2* X, long ldx, int q, const double2* C, int ldc, double2* Y, long ldy, int p,
-                  const double2* Z, long ldz, long rows, cudaStream_t s);
+// Y_g[:, j] = sum_i X_g[:, i] C_g[i, j] (+ Z_g[:, j]) for each group
+void block_update(Roles X, int q, const double2* C, int ldc, long cgs, double2* Y, long ldy, int p,
+                  const double2* Z, long ldz, long rows, int ngroups, cudaStream_t s);
 void random_block(double2* X, long ld, long rows, int ncols, uint64_t seed, cudaStream_t s);
 void scale_columns(double2* X, long ld, long rows, int ncols, const double* d_scale, cudaStream_t s);
 

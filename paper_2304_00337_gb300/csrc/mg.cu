@@ -97,7 +97,7 @@ __global__ void k_patch_factors(const double* __restrict__ winv, int n, int m, d
 }
 
 // Dense coarsest-level matrices, column-major: column `col` = operator applied to unit vector `col`.
-__global__ void k_assemble_edge(Lvl<double> L, Wts<double> w, double mu, const double* ph, double2* K) {
+__global__ void k_assemble_edge(Lvl<double> L, Wts<double> w, double mu, const double* ph, double2* K) {  // ph: the group's entry
   const int Nc = L.n * L.m, Dc = 2 * Nc;
   const int row = blockIdx.x * blockDim.x + threadIdx.x, col = blockIdx.y;
   if (row >= Dc || col >= Dc) return;
@@ -158,10 +158,11 @@ __global__ void k_cholesky(double2* A, int n, float2* A32, int* info) {
 
 // Solve L L^* x = b for each column (one warp per column).
 template <class T>
-__global__ void k_chol_solve(const cx<T>* __restrict__ Lf, int n, const cx<T>* __restrict__ B, long ldb,
-                             cx<T>* __restrict__ X, long ldx, int ncols) {
+__global__ void k_chol_solve(const cx<T>* __restrict__ Lbase, int n, const cx<T>* __restrict__ B, long ldb,
+                             cx<T>* __restrict__ X, long ldx, int ncols, int cpg, int ngroups) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (warp >= ncols) return;
+  const cx<T>* __restrict__ Lf = Lbase + (long)((warp / cpg) % ngroups) * n * n;
   const cx<T>* b = B + warp * ldb;
   cx<T>* x = X + warp * ldx;
   // forward: L y = b  (y stored in x)
@@ -334,57 +335,91 @@ void free_hierarchy(DevMem& mem, Hierarchy& H) {
   H.nlev = 0;
 }
 
-void build_kdata(DevMem& mem, const Hierarchy& H, KData& K, double k1, double k2, cudaStream_t s) {
-  K.k1 = k1;
-  K.k2 = k2;
-  K.ph[0] = std::cos(k1 * H.a);
-  K.ph[1] = std::sin(k1 * H.a);
-  K.ph[2] = std::cos(k2 * H.b);
-  K.ph[3] = std::sin(k2 * H.b);
-  K.gamma = std::hypot(K.ph[0] - 1.0, K.ph[1]) < 1e-14 && std::hypot(K.ph[2] - 1.0, K.ph[3]) < 1e-14;
-  if (K.gamma) {  // use the exact phases at the lattice points
-    K.ph[0] = 1.0; K.ph[1] = 0.0; K.ph[2] = 1.0; K.ph[3] = 0.0;
-  }
+void alloc_kdata(DevMem& mem, const Hierarchy& H, KData& K, int ngroups) {
   const Level& C = H.lev[H.nlev - 1];
   const int Dc = (int)C.D(), Nc = (int)C.N();
-  if (!K.d_ph || K.Dc != Dc) {
-    free_kdata(mem, K);
-    K.d_ph = (double*)mem.alloc(4 * sizeof(double));
-    K.edge64 = (double2*)mem.alloc((size_t)Dc * Dc * sizeof(double2));
-    K.edge32 = (float2*)mem.alloc((size_t)Dc * Dc * sizeof(float2));
-    K.node64 = (double2*)mem.alloc((size_t)Nc * Nc * sizeof(double2));
-    K.node32 = (float2*)mem.alloc((size_t)Nc * Nc * sizeof(float2));
-    K.Dc = Dc;
-    K.Nc = Nc;
+  if (K.ngroups == ngroups && K.Dc == Dc && K.d_ph) return;
+  free_kdata(mem, K);
+  K.ngroups = ngroups;
+  K.Dc = Dc;
+  K.Nc = Nc;
+  K.owner = true;
+  K.d_ph = (double*)mem.alloc(12ull * ngroups * sizeof(double));
+  K.d_gamma = (int*)mem.alloc(3ull * ngroups * sizeof(int));
+  K.edge64 = (double2*)mem.alloc((size_t)ngroups * Dc * Dc * sizeof(double2));
+  K.edge32 = (float2*)mem.alloc((size_t)ngroups * Dc * Dc * sizeof(float2));
+  K.node64 = (double2*)mem.alloc((size_t)ngroups * Nc * Nc * sizeof(double2));
+  K.node32 = (float2*)mem.alloc((size_t)ngroups * Nc * Nc * sizeof(float2));
+  K.k1.assign(ngroups, 0.0);
+  K.k2.assign(ngroups, 0.0);
+  K.gamma.assign(ngroups, 0);
+}
+
+void set_group_k(DevMem& mem, const Hierarchy& H, KData& K, int g, double k1, double k2, cudaStream_t s) {
+  if (g < 0 || g >= K.ngroups) fail(PBS_EINVAL, "group out of range");
+  double ph[4] = {std::cos(k1 * H.a), std::sin(k1 * H.a), std::cos(k2 * H.b), std::sin(k2 * H.b)};
+  const bool gamma = std::hypot(ph[0] - 1.0, ph[1]) < 1e-14 && std::hypot(ph[2] - 1.0, ph[3]) < 1e-14;
+  if (gamma) {  // the exact phases at the lattice points
+    ph[0] = 1.0; ph[1] = 0.0; ph[2] = 1.0; ph[3] = 0.0;
   }
-  PBS_CUDA(cudaMemcpyAsync(K.d_ph, K.ph, 4 * sizeof(double), cudaMemcpyHostToDevice, s));
+  K.k1[g] = k1;
+  K.k2[g] = k2;
+  K.gamma[g] = gamma;
+  const int gi = gamma ? 1 : 0;
+  for (int rep = 0; rep < 3; ++rep) {
+    const long e = (long)rep * K.ngroups + g;
+    PBS_CUDA(cudaMemcpyAsync(K.d_ph + 4 * e, ph, 4 * sizeof(double), cudaMemcpyHostToDevice, s));
+    PBS_CUDA(cudaMemcpyAsync(K.d_gamma + e, &gi, sizeof(int), cudaMemcpyHostToDevice, s));
+  }
+  const Level& C = H.lev[H.nlev - 1];
+  const int Dc = K.Dc, Nc = K.Nc;
+  double2* e64 = K.edge64 + (size_t)g * Dc * Dc;
+  float2* e32 = K.edge32 + (size_t)g * Dc * Dc;
+  double2* n64 = K.node64 + (size_t)g * Nc * Nc;
+  float2* n32 = K.node32 + (size_t)g * Nc * Nc;
+  const double* gph = K.d_ph + 4 * g;
   int* d_info = (int*)mem.alloc(2 * sizeof(int));
   PBS_CUDA(cudaMemsetAsync(d_info, 0, 2 * sizeof(int), s));
-  k_assemble_edge<<<dim3((Dc + 127) / 128, Dc), 128, 0, s>>>(C.lvl<double>(), C.wts<double>(), H.mu, K.d_ph, K.edge64);
+  k_assemble_edge<<<dim3((Dc + 127) / 128, Dc), 128, 0, s>>>(C.lvl<double>(), C.wts<double>(), H.mu, gph, e64);
   PBS_LAUNCHED();
-  k_cholesky<<<1, 256, 0, s>>>(K.edge64, Dc, K.edge32, d_info);
+  k_cholesky<<<1, 256, 0, s>>>(e64, Dc, e32, d_info);
   PBS_LAUNCHED();
-  const double shift = K.gamma ? P_diag<double>(C.lvl<double>()) : 0.0;
-  k_assemble_node<<<dim3((Nc + 127) / 128, Nc), 128, 0, s>>>(C.lvl<double>(), K.d_ph, shift, K.node64);
+  const double shift = gamma ? P_diag<double>(C.lvl<double>()) : 0.0;
+  k_assemble_node<<<dim3((Nc + 127) / 128, Nc), 128, 0, s>>>(C.lvl<double>(), gph, shift, n64);
   PBS_LAUNCHED();
-  k_cholesky<<<1, 256, 0, s>>>(K.node64, Nc, K.node32, d_info + 1);
+  k_cholesky<<<1, 256, 0, s>>>(n64, Nc, n32, d_info + 1);
   PBS_LAUNCHED();
   int info[2] = {0, 0};
   PBS_CUDA(cudaMemcpyAsync(info, d_info, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
   PBS_CUDA(cudaStreamSynchronize(s));
   mem.free(d_info);
-  if (info[0] || info[1]) fail(-4, "coarsest-level Cholesky factorisation failed");
+  if (info[0] || info[1]) fail(PBS_ENUMERIC, "coarsest-level Cholesky factorisation failed");
+}
+
+KData kdata_view(const KData& K, int g) {
+  KData v;
+  v.ngroups = 1;
+  v.Dc = K.Dc;
+  v.Nc = K.Nc;
+  v.d_ph = K.d_ph + 4 * g;
+  v.d_gamma = K.d_gamma + g;
+  v.edge64 = K.edge64 + (size_t)g * K.Dc * K.Dc;
+  v.edge32 = K.edge32 + (size_t)g * K.Dc * K.Dc;
+  v.node64 = K.node64 + (size_t)g * K.Nc * K.Nc;
+  v.node32 = K.node32 + (size_t)g * K.Nc * K.Nc;
+  v.k1 = {K.k1[g]};
+  v.k2 = {K.k2[g]};
+  v.gamma = {K.gamma[g]};
+  v.owner = false;
+  return v;
 }
 
 void free_kdata(DevMem& mem, KData& K) {
-  for (void* p : {(void*)K.d_ph, (void*)K.edge64, (void*)K.edge32, (void*)K.node64, (void*)K.node32})
-    if (p) mem.free(p);
-  K.d_ph = nullptr;
-  K.edge64 = nullptr;
-  K.edge32 = nullptr;
-  K.node64 = nullptr;
-  K.node32 = nullptr;
-  K.Dc = K.Nc = 0;
+  if (K.owner)
+    for (void* p : {(void*)K.d_ph, (void*)K.d_gamma, (void*)K.edge64, (void*)K.edge32, (void*)K.node64,
+                    (void*)K.node32})
+      if (p) mem.free(p);
+  K = KData();
 }
 
 template <class T> void alloc_mg_work(DevMem& mem, const Hierarchy& H, int ncols, bool nodal, MgWork<T>& w) {
@@ -415,10 +450,11 @@ namespace {
 
 template <class T>
 void edge_cycle(const Hierarchy& H, const KData& K, MgWork<T>& w, int l, const cx<T>* b, cx<T>* x, long ld, int ncols,
-                int nu_pre, int nu_post, cudaStream_t s) {
+                int cpg, int nu_pre, int nu_post, cudaStream_t s) {
   const Level& L = H.lev[l];
   if (l == H.nlev - 1) {
-    k_chol_solve<T><<<(ncols * 32 + 127) / 128, 128, 0, s>>>(edge_factor<T>(K), (int)L.D(), b, ld, x, ld, ncols);
+    k_chol_solve<T><<<(ncols * 32 + 127) / 128, 128, 0, s>>>(edge_factor<T>(K), (int)L.D(), b, ld, x, ld, ncols, cpg,
+                                                             K.ngroups);
     PBS_LAUNCHED();
     return;
   }
@@ -429,21 +465,21 @@ void edge_cycle(const Hierarchy& H, const KData& K, MgWork<T>& w, int l, const c
   for (int it = 0; it < nu_pre; ++it)
     for (int q = 0; q < 4; ++q) {
       timer_begin(KC_EDGE_SMOOTH, s, smooth_bytes<T>(L, ncols));
-      k_edge_smooth<T><<<half_grid(L.n, L.m, ncols), dim3(kBX, kBY), 0, s>>>(lv, wt, k3_of<T>(L), mu, K.d_ph, ncols, x,
+      k_edge_smooth<T><<<half_grid(L.n, L.m, ncols), dim3(kBX, kBY), 0, s>>>(lv, wt, k3_of<T>(L), mu, K.d_ph, cpg, x,
                                                                              b, ld, kColours[q][0], kColours[q][1]);
       timer_end(KC_EDGE_SMOOTH, s);
       PBS_LAUNCHED();
     }
   const Level& C = H.lev[l + 1];
   const long ldc = C.D();
-  apply_edge<T>(L, K.d_ph, ncols, x, w.r[l], b, ld, ncols, T(-1), -mu, T(0), nullptr, T(1), s);
-  restrict_edge<T>(L, C, K.d_ph, ncols, w.r[l], ld, w.b[l + 1], ldc, ncols, s);
-  edge_cycle<T>(H, K, w, l + 1, w.b[l + 1], w.x[l + 1], ldc, ncols, nu_pre, nu_post, s);
-  prolong_edge<T>(L, C, K.d_ph, ncols, w.x[l + 1], ldc, x, ld, ncols, true, s);
+  apply_edge<T>(L, K.d_ph, cpg, x, w.r[l], b, ld, ncols, T(-1), -mu, T(0), nullptr, T(1), s);
+  restrict_edge<T>(L, C, K.d_ph, cpg, w.r[l], ld, w.b[l + 1], ldc, ncols, s);
+  edge_cycle<T>(H, K, w, l + 1, w.b[l + 1], w.x[l + 1], ldc, ncols, cpg, nu_pre, nu_post, s);
+  prolong_edge<T>(L, C, K.d_ph, cpg, w.x[l + 1], ldc, x, ld, ncols, true, s);
   for (int it = 0; it < nu_post; ++it)
     for (int q = 3; q >= 0; --q) {
       timer_begin(KC_EDGE_SMOOTH, s, smooth_bytes<T>(L, ncols));
-      k_edge_smooth<T><<<half_grid(L.n, L.m, ncols), dim3(kBX, kBY), 0, s>>>(lv, wt, k3_of<T>(L), mu, K.d_ph, ncols, x,
+      k_edge_smooth<T><<<half_grid(L.n, L.m, ncols), dim3(kBX, kBY), 0, s>>>(lv, wt, k3_of<T>(L), mu, K.d_ph, cpg, x,
                                                                              b, ld, kColours[q][0], kColours[q][1]);
       timer_end(KC_EDGE_SMOOTH, s);
       PBS_LAUNCHED();
@@ -452,10 +488,11 @@ void edge_cycle(const Hierarchy& H, const KData& K, MgWork<T>& w, int l, const c
 
 template <class T>
 void node_cycle(const Hierarchy& H, const KData& K, MgWork<T>& w, int l, const cx<T>* b, cx<T>* x, long ld, int ncols,
-                int nu_pre, int nu_post, cudaStream_t s) {
+                int cpg, int nu_pre, int nu_post, cudaStream_t s) {
   const Level& L = H.lev[l];
   if (l == H.nlev - 1) {
-    k_chol_solve<T><<<(ncols * 32 + 127) / 128, 128, 0, s>>>(node_factor<T>(K), (int)L.N(), b, ld, x, ld, ncols);
+    k_chol_solve<T><<<(ncols * 32 + 127) / 128, 128, 0, s>>>(node_factor<T>(K), (int)L.N(), b, ld, x, ld, ncols, cpg,
+                                                             K.ngroups);
     PBS_LAUNCHED();
     return;
   }
@@ -464,21 +501,21 @@ void node_cycle(const Hierarchy& H, const KData& K, MgWork<T>& w, int l, const c
   for (int it = 0; it < nu_pre; ++it)
     for (int q = 0; q < 4; ++q) {
       timer_begin(KC_NODE_SMOOTH, s, node_smooth_bytes<T>(L, ncols));
-      k_node_smooth<T><<<half_grid(L.n, L.m, ncols), dim3(kBX, kBY), 0, s>>>(lv, K.d_ph, ncols, x, b, ld,
+      k_node_smooth<T><<<half_grid(L.n, L.m, ncols), dim3(kBX, kBY), 0, s>>>(lv, K.d_ph, cpg, x, b, ld,
                                                                              kColours[q][0], kColours[q][1]);
       timer_end(KC_NODE_SMOOTH, s);
       PBS_LAUNCHED();
     }
   const Level& C = H.lev[l + 1];
   const long ldc = C.N();
-  apply_nodal<T>(L, K.d_ph, ncols, x, w.r[l], b, ld, ncols, T(-1), T(1), s);
-  restrict_node<T>(L, C, K.d_ph, ncols, w.r[l], ld, w.b[l + 1], ldc, ncols, s);
-  node_cycle<T>(H, K, w, l + 1, w.b[l + 1], w.x[l + 1], ldc, ncols, nu_pre, nu_post, s);
-  prolong_node<T>(L, C, K.d_ph, ncols, w.x[l + 1], ldc, x, ld, ncols, true, s);
+  apply_nodal<T>(L, K.d_ph, cpg, x, w.r[l], b, ld, ncols, T(-1), T(1), s);
+  restrict_node<T>(L, C, K.d_ph, cpg, w.r[l], ld, w.b[l + 1], ldc, ncols, s);
+  node_cycle<T>(H, K, w, l + 1, w.b[l + 1], w.x[l + 1], ldc, ncols, cpg, nu_pre, nu_post, s);
+  prolong_node<T>(L, C, K.d_ph, cpg, w.x[l + 1], ldc, x, ld, ncols, true, s);
   for (int it = 0; it < nu_post; ++it)
     for (int q = 3; q >= 0; --q) {
       timer_begin(KC_NODE_SMOOTH, s, node_smooth_bytes<T>(L, ncols));
-      k_node_smooth<T><<<half_grid(L.n, L.m, ncols), dim3(kBX, kBY), 0, s>>>(lv, K.d_ph, ncols, x, b, ld,
+      k_node_smooth<T><<<half_grid(L.n, L.m, ncols), dim3(kBX, kBY), 0, s>>>(lv, K.d_ph, cpg, x, b, ld,
                                                                              kColours[q][0], kColours[q][1]);
       timer_end(KC_NODE_SMOOTH, s);
       PBS_LAUNCHED();
@@ -489,27 +526,27 @@ void node_cycle(const Hierarchy& H, const KData& K, MgWork<T>& w, int l, const c
 
 template <class T>
 void edge_vcycle(const Hierarchy& H, const KData& K, MgWork<T>& w, int l0, const cx<T>* X, cx<T>* Y, long ld,
-                 int ncols, int nu_pre, int nu_post, cudaStream_t s) {
+                 int ncols, int cpg, int nu_pre, int nu_post, cudaStream_t s) {
   if (ncols <= 0) return;
   if (ncols > w.ncols) fail(-1, "multigrid workspace too small");
-  edge_cycle<T>(H, K, w, l0, X, Y, ld, ncols, nu_pre, nu_post, s);
+  edge_cycle<T>(H, K, w, l0, X, Y, ld, ncols, cpg, nu_pre, nu_post, s);
 }
 
 template <class T>
 void nodal_vcycle(const Hierarchy& H, const KData& K, MgWork<T>& w, int l0, const cx<T>* X, cx<T>* Y, long ld,
-                  int ncols, int nu_pre, int nu_post, cudaStream_t s) {
+                  int ncols, int cpg, int nu_pre, int nu_post, cudaStream_t s) {
   if (ncols <= 0) return;
   if (ncols > w.ncols) fail(-1, "multigrid workspace too small");
-  node_cycle<T>(H, K, w, l0, X, Y, ld, ncols, nu_pre, nu_post, s);
+  node_cycle<T>(H, K, w, l0, X, Y, ld, ncols, cpg, nu_pre, nu_post, s);
 }
 
 #define PBS_INST_MG(T)                                                                                            \
   template void alloc_mg_work<T>(DevMem&, const Hierarchy&, int, bool, MgWork<T>&);                               \
   template void free_mg_work<T>(DevMem&, MgWork<T>&);                                                             \
   template void edge_vcycle<T>(const Hierarchy&, const KData&, MgWork<T>&, int, const cx<T>*, cx<T>*, long, int, \
-                               int, int, cudaStream_t);                                                           \
+                               int, int, int, cudaStream_t);                                                      \
   template void nodal_vcycle<T>(const Hierarchy&, const KData&, MgWork<T>&, int, const cx<T>*, cx<T>*, long, int, \
-                                int, int, cudaStream_t);
+                                int, int, int, cudaStream_t);
 PBS_INST_MG(double)
 PBS_INST_MG(float)
 

@@ -162,21 +162,26 @@ inline unsigned nblocks(long n) { return (unsigned)std::min<long>(std::max<long>
 
 }  // namespace
 
-// Solver workspace for one (hierarchy, block width) pair.
+// Batched solver workspace: G groups (Bloch vectors in flight) of p columns.
+// The block lives role-major, S = [E_all | P_all | W_all], group g's columns of
+// each role at g*p; S2 receives the next block.
 struct Work {
-  int p = 0;
+  int G = 0, p = 0;
   long D = 0, N = 0;
-  double2 *S = nullptr, *T2 = nullptr, *R = nullptr, *hist = nullptr, *gwork = nullptr;
+  double2 *S = nullptr, *S2 = nullptr, *R = nullptr, *init = nullptr, *hist = nullptr;
   double2 *GM = nullptr, *GA = nullptr, *C = nullptr, *rr_scr = nullptr, *gpart = nullptr;
+  long gpart_cap = 0;
   double *theta = nullptr, *lam = nullptr, *parts = nullptr, *norms = nullptr, *rq = nullptr;
   int* info = nullptr;
-  int gpart_n = 0;
-  // preconditioner / projection buffers (FP32 and FP64 variants)
-  float2 *r32 = nullptr, *w32 = nullptr, *nb32 = nullptr, *nx32 = nullptr, *nr32 = nullptr, *nd32 = nullptr;
+  float2 *r32 = nullptr, *w32 = nullptr;
+  float2 *nb32 = nullptr, *nx32 = nullptr, *nr32 = nullptr, *nd32 = nullptr;
   double2 *nb64 = nullptr, *nx64 = nullptr, *nr64 = nullptr, *nd64 = nullptr;
   MgWork<float> e32, n32;
   MgWork<double> e64, n64;
   std::vector<void*> allocs;
+  double2* E() const { return S; }
+  double2* P() const { return S + (long)G * p * D; }
+  double2* W() const { return S + 2L * G * p * D; }
 };
 
 }  // namespace pbs
@@ -193,9 +198,8 @@ struct pbs_ctx {
   KData K;
   Work W;
   bool have_w = false;
-  double last_theta_max = 1e300;  // largest Ritz value of the latest start block
   KernelTimer timer;
-  double* d_eps_in = nullptr;     // device copy of the latest host permittivity array
+  double* d_eps_in = nullptr;  // device copy of the latest host permittivity array
   long d_eps_len = 0;
   explicit pbs_ctx(size_t budget) : mem(budget) {}
 };
@@ -225,6 +229,17 @@ struct TimerScope {
   }
 };
 
+void free_work(pbs_ctx* ctx) {
+  if (!ctx->have_w) return;
+  for (void* p : ctx->W.allocs) ctx->mem.free(p);
+  free_mg_work(ctx->mem, ctx->W.e32);
+  free_mg_work(ctx->mem, ctx->W.n32);
+  free_mg_work(ctx->mem, ctx->W.e64);
+  free_mg_work(ctx->mem, ctx->W.n64);
+  ctx->W = Work();
+  ctx->have_w = false;
+}
+
 void validate_opts(const pbs_opts& o) {
   if (o.nev < 1 || o.block < o.nev || o.block > kMaxBlock) fail(PBS_EINVAL, "need 1 <= nev <= block <= 32");
   if (o.max_iter < 0) fail(PBS_EINVAL, "max_iter must be >= 0");
@@ -235,6 +250,7 @@ void validate_opts(const pbs_opts& o) {
   if (o.coarsest < 2) fail(PBS_EINVAL, "coarsest must be >= 2");
   if (o.nodal_cycles < 1) fail(PBS_EINVAL, "nodal_cycles must be >= 1");
   if (o.extrap_depth < 0 || o.extrap_depth > 3) fail(PBS_EINVAL, "extrap_depth must be 0..3");
+  if (o.kbatch < 1 || o.kbatch > 256) fail(PBS_EINVAL, "kbatch must be 1..256");
 }
 
 void validate_mesh(double a, double b, int n, int m) {
@@ -256,16 +272,7 @@ void ensure_hierarchy(pbs_ctx* ctx, double a, double b, int n, int m, const doub
   key = fnv1a(&mu, sizeof mu, key);
   key = fnv1a(&coarsest, sizeof coarsest, key);
   if (ctx->have_h && ctx->H.key == key) return;
-  if (ctx->have_w) {
-    // workspaces depend on the hierarchy sizes
-    for (void* p : ctx->W.allocs) ctx->mem.free(p);
-    free_mg_work(ctx->mem, ctx->W.e32);
-    free_mg_work(ctx->mem, ctx->W.n32);
-    free_mg_work(ctx->mem, ctx->W.e64);
-    free_mg_work(ctx->mem, ctx->W.n64);
-    ctx->W = Work();
-    ctx->have_w = false;
-  }
+  free_work(ctx);  // workspaces depend on the hierarchy sizes
   if (ctx->have_h) free_hierarchy(ctx->mem, ctx->H);
   free_kdata(ctx->mem, ctx->K);
   ctx->have_h = false;
@@ -313,19 +320,13 @@ uint64_t device_eps_hash(pbs_ctx* ctx, const double* d_eps, long N) {
   return h;
 }
 
-void ensure_work(pbs_ctx* ctx, int p) {
+
+void ensure_work(pbs_ctx* ctx, int p, int G) {
   Work& W = ctx->W;
-  if (ctx->have_w && W.p == p) return;
-  if (ctx->have_w) {
-    for (void* q : W.allocs) ctx->mem.free(q);
-    free_mg_work(ctx->mem, W.e32);
-    free_mg_work(ctx->mem, W.n32);
-    free_mg_work(ctx->mem, W.e64);
-    free_mg_work(ctx->mem, W.n64);
-    W = Work();
-    ctx->have_w = false;
-  }
+  if (ctx->have_w && W.p == p && W.G == G) return;
+  free_work(ctx);
   const Hierarchy& H = ctx->H;
+  W.G = G;
   W.p = p;
   W.D = H.lev[0].D();
   W.N = H.lev[0].N();
@@ -335,40 +336,42 @@ void ensure_work(pbs_ctx* ctx, int p) {
     W.allocs.push_back(ptr);
     return ptr;
   };
-  const long D = W.D, N = W.N;
-  W.S = (double2*)A(sizeof(double2) * D * q);
-  W.T2 = (double2*)A(sizeof(double2) * D * q);
-  W.R = (double2*)A(sizeof(double2) * D * p);
-  W.hist = (double2*)A(sizeof(double2) * D * 3 * p);
-  W.gwork = (double2*)A(sizeof(double2) * (D + N) * q);
-  W.GM = (double2*)A(sizeof(double2) * q * q);
-  W.GA = (double2*)A(sizeof(double2) * q * q);
-  W.C = (double2*)A(sizeof(double2) * q * p);
-  W.rr_scr = (double2*)A(small_rr_scratch(q));
-  W.gpart_n = 2 * 152;
-  W.gpart = (double2*)A(sizeof(double2) * W.gpart_n * (q * (q + 1) / 2));
-  W.theta = (double*)A(sizeof(double) * q);
-  W.lam = (double*)A(sizeof(double) * q);
+  const long D = W.D, N = W.N, Gp = (long)G * p;
+  W.S = (double2*)A(sizeof(double2) * D * 3 * Gp);
+  W.S2 = (double2*)A(sizeof(double2) * D * 3 * Gp);
+  W.R = (double2*)A(sizeof(double2) * D * Gp);
+  W.init = (double2*)A(sizeof(double2) * D * q);
+  W.hist = (double2*)A(sizeof(double2) * D * 3 * Gp);
+  W.GM = (double2*)A(sizeof(double2) * q * q * G);
+  W.GA = (double2*)A(sizeof(double2) * q * q * G);
+  W.C = (double2*)A(sizeof(double2) * q * p * G);
+  W.rr_scr = (double2*)A(small_rr_scratch(q) * G);
+  W.gpart_cap = std::max(gram_partials_size(N, q, G), gram_partials_size(N, q, 1));
+  W.gpart = (double2*)A(sizeof(double2) * W.gpart_cap);
+  W.theta = (double*)A(sizeof(double) * q * G);
+  W.lam = (double*)A(sizeof(double) * std::max<long>(Gp, q));
+  const long ncol = std::max<long>(3 * Gp, q);
   const long nblk = ((H.lev[0].n + 31) / 32) * ((H.lev[0].m + 7) / 8);
-  W.parts = (double*)A(sizeof(double) * std::max<long>(2 * nblk * q, 4 * 64 * q));
-  W.norms = (double*)A(sizeof(double) * 2 * q);
-  W.rq = (double*)A(sizeof(double) * 2 * q);
-  W.info = (int*)A(sizeof(int) * 8);
-  // preconditioner: p columns; projection: up to 3p columns (extrapolation spans)
-  W.r32 = (float2*)A(sizeof(float2) * D * p);
-  W.w32 = (float2*)A(sizeof(float2) * D * p);
-  W.nb32 = (float2*)A(sizeof(float2) * N * q);
-  W.nx32 = (float2*)A(sizeof(float2) * N * q);
-  W.nr32 = (float2*)A(sizeof(float2) * N * q);
-  W.nd32 = (float2*)A(sizeof(float2) * N * q);
-  W.nb64 = (double2*)A(sizeof(double2) * N * q);
-  W.nx64 = (double2*)A(sizeof(double2) * N * q);
-  W.nr64 = (double2*)A(sizeof(double2) * N * q);
-  W.nd64 = (double2*)A(sizeof(double2) * N * q);
-  alloc_mg_work<float>(ctx->mem, H, p, false, W.e32);
-  alloc_mg_work<float>(ctx->mem, H, q, true, W.n32);
-  alloc_mg_work<double>(ctx->mem, H, p, false, W.e64);
-  alloc_mg_work<double>(ctx->mem, H, q, true, W.n64);
+  W.parts = (double*)A(sizeof(double) * std::max<long>(2 * nblk * ncol, 4 * 64 * ncol));
+  W.norms = (double*)A(sizeof(double) * 2 * ncol);
+  W.rq = (double*)A(sizeof(double) * 2 * ncol);
+  W.info = (int*)A(sizeof(int) * 8 * G);
+  W.r32 = (float2*)A(sizeof(float2) * D * Gp);
+  W.w32 = (float2*)A(sizeof(float2) * D * Gp);
+  W.nb32 = (float2*)A(sizeof(float2) * N * ncol);
+  W.nx32 = (float2*)A(sizeof(float2) * N * ncol);
+  W.nr32 = (float2*)A(sizeof(float2) * N * ncol);
+  W.nd32 = (float2*)A(sizeof(float2) * N * ncol);
+  W.nb64 = (double2*)A(sizeof(double2) * N * ncol);
+  W.nx64 = (double2*)A(sizeof(double2) * N * ncol);
+  W.nr64 = (double2*)A(sizeof(double2) * N * ncol);
+  W.nd64 = (double2*)A(sizeof(double2) * N * ncol);
+  alloc_mg_work<float>(ctx->mem, H, (int)std::max<long>(Gp, p), false, W.e32);
+  alloc_mg_work<float>(ctx->mem, H, (int)ncol, true, W.n32);
+  alloc_mg_work<double>(ctx->mem, H, (int)std::max<long>(Gp, p), false, W.e64);
+  alloc_mg_work<double>(ctx->mem, H, (int)ncol, true, W.n64);
+  PBS_CUDA(cudaMemsetAsync(W.S, 0, sizeof(double2) * D * 3 * Gp, ctx->stream));
+  PBS_CUDA(cudaMemsetAsync(W.S2, 0, sizeof(double2) * D * 3 * Gp, ctx->stream));
   ctx->have_w = true;
 }
 
@@ -392,51 +395,51 @@ template <> struct Bufs<double> {
   static MgWork<double>& nmg(Work& W) { return W.n64; }
 };
 
-// X <- X - L phi with phi from `cycles` nodal V-cycles on L^* M L phi = L^* M X; at k = 0
-// the two constant edge fields are removed as well (Section 4).
+// X <- X - L phi with phi from `cycles` nodal V-cycles on L^* M L phi = L^* M X; the
+// constant edge fields of k = 0 groups are removed as well (Section 4).  Column c
+// belongs to group c / cpg of K.
 template <class T>
-void project(pbs_ctx* ctx, const pbs_opts& o, double2* X, int ncols, int cycles, cudaStream_t s) {
+void project(pbs_ctx* ctx, const pbs_opts& o, const KData& K, double2* X, int ncols, int cpg, int cycles,
+             cudaStream_t s) {
   if (ncols <= 0) return;
   Work& W = ctx->W;
   const Hierarchy& H = ctx->H;
-  const KData& K = ctx->K;
   const Level& L0 = H.lev[0];
   const long N = L0.N(), D = L0.D();
   cx<T>* rhs = (cx<T>*)Bufs<T>::nb(W);
   cx<T>* phi = (cx<T>*)Bufs<T>::nx(W);
   cx<T>* res = (cx<T>*)Bufs<T>::nr(W);
   cx<T>* dphi = (cx<T>*)Bufs<T>::nd(W);
-  lift_adj_mass<T>(L0, K.d_ph, ncols, X, D, rhs, N, ncols, s);
-  nodal_vcycle<T>(H, K, Bufs<T>::nmg(W), 0, rhs, phi, N, ncols, o.nu_pre, o.nu_post, s);
+  lift_adj_mass<T>(L0, K.d_ph, cpg, X, D, rhs, N, ncols, s);
+  nodal_vcycle<T>(H, K, Bufs<T>::nmg(W), 0, rhs, phi, N, ncols, cpg, o.nu_pre, o.nu_post, s);
   for (int c = 1; c < cycles; ++c) {
-    apply_nodal<T>(L0, K.d_ph, ncols, phi, res, rhs, N, ncols, T(-1), T(1), s);
-    nodal_vcycle<T>(H, K, Bufs<T>::nmg(W), 0, res, dphi, N, ncols, o.nu_pre, o.nu_post, s);
+    apply_nodal<T>(L0, K.d_ph, cpg, phi, res, rhs, N, ncols, T(-1), T(1), s);
+    nodal_vcycle<T>(H, K, Bufs<T>::nmg(W), 0, res, dphi, N, ncols, cpg, o.nu_pre, o.nu_post, s);
     k_axpy<T><<<nblocks(N * ncols), 256, 0, s>>>(phi, dphi, N * ncols);
     PBS_LAUNCHED();
   }
-  sub_lift<T>(L0, K.d_ph, ncols, phi, N, X, D, ncols, s);
-  if (K.gamma) deflate_constants(L0, X, D, ncols, W.parts, s);
+  sub_lift<T>(L0, K.d_ph, cpg, phi, N, X, D, ncols, s);
+  if (K.any_gamma()) deflate_constants(L0, X, D, ncols, K.d_gamma, cpg, W.parts, s);
 }
 
-// W = B R (one edge V-cycle per column, precision T)
-template <class T> void precondition(pbs_ctx* ctx, const pbs_opts& o, const double2* R, double2* Wout, int ncols,
-                                     cudaStream_t s);
-template <>
-void precondition<double>(pbs_ctx* ctx, const pbs_opts& o, const double2* R, double2* Wout, int ncols, cudaStream_t s) {
-  edge_vcycle<double>(ctx->H, ctx->K, ctx->W.e64, 0, R, Wout, ctx->W.D, ncols, o.nu_pre, o.nu_post, s);
-}
-template <>
-void precondition<float>(pbs_ctx* ctx, const pbs_opts& o, const double2* R, double2* Wout, int ncols, cudaStream_t s) {
-  Work& W = ctx->W;
-  convert_d2f(R, W.r32, W.D * ncols, s);
-  edge_vcycle<float>(ctx->H, ctx->K, W.e32, 0, W.r32, W.w32, W.D, ncols, o.nu_pre, o.nu_post, s);
-  convert_f2d(W.w32, Wout, W.D * ncols, s);
-}
-
-void project_dispatch(pbs_ctx* ctx, const pbs_opts& o, double2* X, int ncols, cudaStream_t s, int cycles = 0) {
+void project_dispatch(pbs_ctx* ctx, const pbs_opts& o, const KData& K, double2* X, int ncols, int cpg, int cycles,
+                      cudaStream_t s) {
   if (cycles <= 0) cycles = o.nodal_cycles;
-  if (o.precision == PBS_MIXED) project<float>(ctx, o, X, ncols, cycles, s);
-  else project<double>(ctx, o, X, ncols, cycles, s);
+  if (o.precision == PBS_MIXED) project<float>(ctx, o, K, X, ncols, cpg, cycles, s);
+  else project<double>(ctx, o, K, X, ncols, cpg, cycles, s);
+}
+
+// W = B R (one edge V-cycle per column)
+void precondition_dispatch(pbs_ctx* ctx, const pbs_opts& o, const KData& K, const double2* R, double2* Wout, int ncols,
+                           int cpg, cudaStream_t s) {
+  Work& W = ctx->W;
+  if (o.precision == PBS_MIXED) {
+    convert_d2f(R, W.r32, W.D * ncols, s);
+    edge_vcycle<float>(ctx->H, K, W.e32, 0, W.r32, W.w32, W.D, ncols, cpg, o.nu_pre, o.nu_post, s);
+    convert_f2d(W.w32, Wout, W.D * ncols, s);
+  } else {
+    edge_vcycle<double>(ctx->H, K, W.e64, 0, R, Wout, W.D, ncols, cpg, o.nu_pre, o.nu_post, s);
+  }
 }
 
 // Nodal cycles for the iteration's projections.  The preconditioner maps a
@@ -449,182 +452,265 @@ int projection_cycles(const pbs_opts& o, double theta_max, double mu) {
   const int extra = ratio > 1.0 ? (int)std::floor(std::log10(ratio) / 2.0) : 0;
   return o.nodal_cycles + std::min(extra, 6);
 }
-void precondition_dispatch(pbs_ctx* ctx, const pbs_opts& o, const double2* R, double2* Wout, int ncols,
-                           cudaStream_t s) {
-  if (o.precision == PBS_MIXED) precondition<float>(ctx, o, R, Wout, ncols, s);
-  else precondition<double>(ctx, o, R, Wout, ncols, s);
-}
 
-// Rayleigh-Ritz on S[:, 0:q] -> E = S C (p columns, written to dst); theta on device.
-void rayleigh_ritz_step(pbs_ctx* ctx, const double2* S, int q, int p, double2* dst, cudaStream_t s) {
+// Rayleigh-Ritz of one group's pencil (view Kv) on the q contiguous columns S:
+// the p lowest Ritz vectors go to dst; returns the largest |theta|.
+double rr_single(pbs_ctx* ctx, const KData& Kv, const double2* S, int q, int p, double2* dst, cudaStream_t s) {
   Work& W = ctx->W;
   const Level& L0 = ctx->H.lev[0];
-  gram(L0, ctx->K.d_ph, q, S, W.D, q, W.GM, W.GA, W.gwork, W.gpart, W.gpart_n, s);
-  small_rr(W.GM, W.GA, q, p, W.C, W.theta, W.rr_scr, W.info, s);
+  const Roles R{{S, S, S}, q, W.D};
+  gram_groups(L0, Kv.d_ph, R, q, 1, W.GM, W.GA, W.gpart, W.gpart_cap, s);
+  small_rr(W.GM, W.GA, q, p, W.C, W.theta, W.rr_scr, W.info, 1, s);
   int info[2] = {0, 0};
+  std::vector<double> th(p);
   PBS_CUDA(cudaMemcpyAsync(info, W.info, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+  PBS_CUDA(cudaMemcpyAsync(th.data(), W.theta, p * sizeof(double), cudaMemcpyDeviceToHost, s));
   PBS_CUDA(cudaStreamSynchronize(s));
   if (info[0] != 0)
     fail(PBS_ENUMERIC, info[0] == -2 ? "non-finite Gram matrix"
                                      : info[0] == -3 ? "Rayleigh-Ritz breakdown" : "trial space lost rank");
-  block_update(S, W.D, q, W.C, q, dst, W.D, p, nullptr, 0, W.D, s);
+  block_update(R, q, W.C, q, (long)q * p, dst, W.D, p, nullptr, 0, W.D, 1, s);
+  double tm = 0.0;
+  for (double t : th) tm = std::max(tm, std::fabs(t));
+  return tm;
 }
 
-struct KResult {
-  std::vector<double> lam, res;
-  int iters = 0;
-  bool converged = false;
+// Host-side state of one group (one Bloch vector in flight, one chain of the path).
+struct Group {
+  int first = 0, last = -1;  // indices of its chain in the k list
+  int pos = 0;               // index being solved
+  int it = 0;
+  bool have_p = false, active = false, need_init = false;
+  int nhist = 0;
+  double theta_max = 1e300;
 };
 
-// The iteration at the current k (ctx->K set up) starting from the p columns in S[:, 0:p].
-KResult iterate(pbs_ctx* ctx, const pbs_opts& o, cudaStream_t s) {
-  // Block layout in W.S: [E | P | W]; before the first search direction exists
-  // the preconditioned residual W sits in the P slot, so the trial block is
-  // always contiguous: [E, W] (q = 2p) or [E, P, W] (q = 3p).
+// Start block of group g into E_g (P_g zeroed): extrapolation from the group's history,
+// else `init` (host, D x p) or a seeded random block smoothed by two steps E <- B M E.
+void init_group(pbs_ctx* ctx, const pbs_opts& o, Group& gr, int g, const pbs_c64* init, cudaStream_t s) {
+  Work& W = ctx->W;
+  const int p = o.block;
+  const long D = W.D;
+  const KData Kv = kdata_view(ctx->K, g);
+  double2* Eg = W.E() + (long)g * p * D;
+  double2* Pg = W.P() + (long)g * p * D;
+  const int depth = std::min(gr.nhist, o.extrap_depth);
+  double tm;
+  if (depth > 0) {
+    // S = [E_{k-1}, E_{k-2}, ...] as stored coefficient vectors (Section 6)
+    const int q = depth * p;
+    PBS_CUDA(cudaMemcpyAsync(W.init, W.hist + (long)g * 3 * p * D, sizeof(double2) * D * q, cudaMemcpyDeviceToDevice,
+                             s));
+    project_dispatch(ctx, o, Kv, W.init, q, q, projection_cycles(o, gr.theta_max, ctx->H.mu), s);
+    tm = rr_single(ctx, Kv, W.init, q, p, Eg, s);
+  } else {
+    double2* X0 = W.init;           // p columns
+    double2* X1 = W.init + D * p;   // p columns
+    if (init) PBS_CUDA(cudaMemcpyAsync(X0, init, sizeof(double2) * D * p, cudaMemcpyHostToDevice, s));
+    else random_block(X0, D, D, p, o.seed, s);
+    // A block unrelated to the spectrum has Rayleigh quotients near its top: two
+    // inverse-iteration steps E <- B M E (each followed by the projection and
+    // Rayleigh-Ritz) damp the high frequencies before the iteration starts.
+    const int cyc = projection_cycles(o, 1e300, ctx->H.mu);
+    project_dispatch(ctx, o, Kv, X0, p, p, cyc, s);
+    rr_single(ctx, Kv, X0, p, p, X1, s);
+    double2* Rg = W.R + (long)g * p * D;
+    for (int step = 0; step < 2; ++step) {
+      apply_edge<double>(ctx->H.lev[0], Kv.d_ph, p, X1, Rg, nullptr, D, p, 0.0, 1.0, 0.0, nullptr, 0.0, s);
+      precondition_dispatch(ctx, o, Kv, Rg, X0, p, p, s);
+      project_dispatch(ctx, o, Kv, X0, p, p, cyc, s);
+      tm = rr_single(ctx, Kv, X0, p, p, step == 1 ? Eg : X1, s);
+    }
+  }
+  PBS_CUDA(cudaMemsetAsync(Pg, 0, sizeof(double2) * D * p, s));
+  gr.theta_max = tm;
+  gr.it = 0;
+  gr.have_p = false;
+  gr.need_init = false;
+}
+
+struct PathResult {
+  std::vector<double> lam, res;  // nk x nev
+  std::vector<int> iters;
+  bool all_converged = true;
+};
+
+// Solve the Bloch vectors ks[0..nk) as `nchains` contiguous chains, one group per
+// chain iterating in lock-step (Algorithm 2 for every group at once); each k of a
+// chain after its first starts from the extrapolation of that chain's previous
+// bases (Section 6).  A group whose k converged records it and restarts on the next
+// k of its chain while the other groups keep iterating.
+PathResult solve_chains(pbs_ctx* ctx, const pbs_opts& o, int nk, const double* ks, int nchains, const pbs_c64* init) {
+  cudaStream_t s = ctx->stream;
+  const int p = o.block, G = std::max(1, std::min(nchains, nk));
+  alloc_kdata(ctx->mem, ctx->H, ctx->K, G);
+  ensure_work(ctx, p, G);
   Work& W = ctx->W;
   const Level& L0 = ctx->H.lev[0];
-  const double* ph = ctx->K.d_ph;
-  const int p = o.block;
-  const long D = W.D;
-  bool have_p = false;
-  KResult out;
-  std::vector<double> h_norms(2 * p), h_lam(p);
-  double theta_max = ctx->last_theta_max;
+  const long D = W.D, Gp = (long)G * p;
   const double mu = ctx->H.mu;
-  for (int it = 0;; ++it) {
-    double2* E = W.S;
-    // Rayleigh-Ritz prefers combinations whose leftover gradient lowers the
-    // quotient, so the new block (and the search direction) is cleaned before
-    // its residual is formed (Section 4, null-space elimination).
-    const int cyc = projection_cycles(o, theta_max, mu);
-    if (it > 0) project_dispatch(ctx, o, E, have_p ? 2 * p : p, s, cyc);
+  PathResult out;
+  out.lam.assign((long)nk * o.nev, 0.0);
+  out.res.assign((long)nk * o.nev, 0.0);
+  out.iters.assign(nk, 0);
+  std::vector<Group> gr(G);
+  for (int g = 0; g < G; ++g) {
+    gr[g].first = (int)((long)nk * g / G);
+    gr[g].last = (int)((long)nk * (g + 1) / G) - 1;
+    gr[g].pos = gr[g].first;
+    gr[g].active = true;
+    set_group_k(ctx->mem, ctx->H, ctx->K, g, ks[2 * gr[g].pos], ks[2 * gr[g].pos + 1], s);
+    init_group(ctx, o, gr[g], g, g == 0 ? init : nullptr, s);
+  }
+  std::vector<double> h_norms(2 * Gp), h_lam(Gp);
+  std::vector<int> h_info(8 * G);
+  const int q = 3 * p;
+  for (int round = 0;; ++round) {
+    bool any = false;
+    for (auto& x : gr) any = any || x.active;
+    if (!any) break;
+    int cyc = o.nodal_cycles;
+    for (auto& x : gr)
+      if (x.active) cyc = std::max(cyc, projection_cycles(o, x.theta_max, mu));
+    // Rayleigh-Ritz prefers combinations whose leftover gradient lowers the quotient,
+    // so E and P are cleaned before the residual (Section 4, null-space elimination)
+    if (round > 0) project_dispatch(ctx, o, ctx->K, W.E(), 2 * (int)Gp, p, cyc, s);
     // Rayleigh quotients in factored form, then the FP64 residual
-    rayleigh_parts(L0, ph, p, E, D, p, W.parts, W.rq, s);
-    k_rq<<<1, 64, 0, s>>>(W.rq, W.lam, p);
+    rayleigh_parts(L0, ctx->K.d_ph, p, W.E(), D, (int)Gp, W.parts, W.rq, s);
+    k_rq<<<nblocks(Gp), 256, 0, s>>>(W.rq, W.lam, (int)Gp);
     PBS_LAUNCHED();
-    residual(L0, ph, p, E, W.R, D, p, W.lam, W.parts, W.norms, s);
-    PBS_CUDA(cudaMemcpyAsync(h_norms.data(), W.norms, 2 * p * sizeof(double), cudaMemcpyDeviceToHost, s));
-    PBS_CUDA(cudaMemcpyAsync(h_lam.data(), W.lam, p * sizeof(double), cudaMemcpyDeviceToHost, s));
+    residual(L0, ctx->K.d_ph, p, W.E(), W.R, D, (int)Gp, W.lam, W.parts, W.norms, s);
+    PBS_CUDA(cudaMemcpyAsync(h_norms.data(), W.norms, 2 * Gp * sizeof(double), cudaMemcpyDeviceToHost, s));
+    PBS_CUDA(cudaMemcpyAsync(h_lam.data(), W.lam, Gp * sizeof(double), cudaMemcpyDeviceToHost, s));
     PBS_CUDA(cudaStreamSynchronize(s));
     timer_collect();
-    out.lam.assign(h_lam.begin(), h_lam.begin() + o.nev);
-    theta_max = 0.0;
-    for (int j = 0; j < p; ++j) theta_max = std::max(theta_max, std::fabs(h_lam[j]));
-    out.res.resize(o.nev);
-    bool conv = true;
-    for (int j = 0; j < o.nev; ++j) {
-      const double r = std::sqrt(h_norms[2 * j]) / (std::fabs(h_lam[j]) * std::sqrt(h_norms[2 * j + 1]));
-      if (!std::isfinite(r) || !std::isfinite(h_lam[j])) fail(PBS_ENUMERIC, "non-finite residual");
-      out.res[j] = r;
-      conv = conv && r <= o.tol;
+    std::vector<char> cont(G, 0);
+    for (int g = 0; g < G; ++g) {
+      Group& x = gr[g];
+      if (!x.active) continue;
+      bool conv = true;
+      double tm = 0.0;
+      std::vector<double> res(o.nev);
+      for (int j = 0; j < p; ++j) tm = std::max(tm, std::fabs(h_lam[(long)g * p + j]));
+      for (int j = 0; j < o.nev; ++j) {
+        const long c = (long)g * p + j;
+        const double r = std::sqrt(h_norms[2 * c]) / (std::fabs(h_lam[c]) * std::sqrt(h_norms[2 * c + 1]));
+        if (!std::isfinite(r) || !std::isfinite(h_lam[c])) fail(PBS_ENUMERIC, "non-finite residual");
+        res[j] = r;
+        conv = conv && r <= o.tol;
+      }
+      x.theta_max = tm;
+      if (verbose()) {
+        std::fprintf(stderr, "[pbs] g=%d k=(%.6f,%.6f) it=%d", g, ctx->K.k1[g], ctx->K.k2[g], x.it);
+        for (int j = 0; j < p; ++j) {
+          const long c = (long)g * p + j;
+          std::fprintf(stderr, " %.10g/%.1e", h_lam[c],
+                       std::sqrt(h_norms[2 * c]) / (std::fabs(h_lam[c]) * std::sqrt(h_norms[2 * c + 1])));
+        }
+        std::fprintf(stderr, "\n");
+      }
+      if (conv || x.it >= o.max_iter) {
+        for (int j = 0; j < o.nev; ++j) {
+          out.lam[(long)x.pos * o.nev + j] = h_lam[(long)g * p + j];
+          out.res[(long)x.pos * o.nev + j] = res[j];
+        }
+        out.iters[x.pos] = x.it;
+        if (!conv) out.all_converged = false;
+        // history ring of the chain (newest first; oldest slot first, so no copy overlaps)
+        if (o.extrap_depth > 0 && x.pos < x.last) {
+          double2* hg = W.hist + (long)g * 3 * p * D;
+          const int keep = std::min(x.nhist, 2);
+          for (int slot = keep; slot >= 1; --slot)
+            PBS_CUDA(cudaMemcpyAsync(hg + D * p * slot, hg + D * p * (slot - 1), sizeof(double2) * D * p,
+                                     cudaMemcpyDeviceToDevice, s));
+          PBS_CUDA(cudaMemcpyAsync(hg, W.E() + (long)g * p * D, sizeof(double2) * D * p, cudaMemcpyDeviceToDevice, s));
+          x.nhist = std::min(x.nhist + 1, 3);
+        }
+        if (x.pos < x.last) {
+          x.pos += 1;
+          x.need_init = true;
+        } else {
+          x.active = false;
+        }
+      } else {
+        cont[g] = 1;
+      }
     }
-    out.iters = it;
-    if (verbose()) {
-      std::fprintf(stderr, "[pbs] k=(%.6f,%.6f) it=%d", ctx->K.k1, ctx->K.k2, it);
-      for (int j = 0; j < p; ++j)
-        std::fprintf(stderr, " %.10g/%.1e", h_lam[j],
-                     std::sqrt(h_norms[2 * j]) / (std::fabs(h_lam[j]) * std::sqrt(h_norms[2 * j + 1])));
-      std::fprintf(stderr, "\n");
-    }
-    if (conv) {
-      out.converged = true;
-      return out;
-    }
-    if (it >= o.max_iter) return out;
-    const bool use_p = o.span == 3 && have_p;
-    double2* Wd = W.S + D * p * (use_p ? 2 : 1);
-    precondition_dispatch(ctx, o, W.R, Wd, p, s);
-    int q;
-    const double2* trial;
-    if (o.span == 1) {
-      k_sub_from<<<nblocks(D * p), 256, 0, s>>>(E, Wd, D * p);  // E_hat = E - B R
-      PBS_LAUNCHED();
-      project_dispatch(ctx, o, Wd, p, s, cyc);
-      q = p;
-      trial = Wd;
-    } else {
-      project_dispatch(ctx, o, Wd, p, s, cyc);
-      q = use_p ? 3 * p : 2 * p;
-      trial = E;
-    }
-    gram(L0, ph, q, trial, D, q, W.GM, W.GA, W.gwork, W.gpart, W.gpart_n, s);
-    small_rr(W.GM, W.GA, q, p, W.C, W.theta, W.rr_scr, W.info, s);
-    int info[2] = {0, 0};
-    PBS_CUDA(cudaMemcpyAsync(info, W.info, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
-    PBS_CUDA(cudaStreamSynchronize(s));
-    if (info[0] != 0) {
-      if (info[0] == -2) fail(PBS_ENUMERIC, "non-finite Gram matrix");
-      if (info[0] == -3) fail(PBS_ENUMERIC, "Rayleigh-Ritz breakdown");
-      if (!use_p) fail(PBS_ENUMERIC, "trial space lost rank");
-      // rank loss in the LOBPCG basis: restart without the search direction
-      PBS_CUDA(cudaMemcpyAsync(W.S + D * p, Wd, sizeof(double2) * D * p, cudaMemcpyDeviceToDevice, s));
-      have_p = false;
-      q = 2 * p;
-      gram(L0, ph, q, trial, D, q, W.GM, W.GA, W.gwork, W.gpart, W.gpart_n, s);
-      small_rr(W.GM, W.GA, q, p, W.C, W.theta, W.rr_scr, W.info, s);
-      PBS_CUDA(cudaMemcpyAsync(info, W.info, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    bool any_cont = false;
+    for (char c : cont) any_cont = any_cont || c;
+    if (any_cont) {
+      // W = B R, projected; Gram matrices of [E, P, W] per group; Rayleigh-Ritz; update
+      double2* Wd = W.W();
+      precondition_dispatch(ctx, o, ctx->K, W.R, Wd, (int)Gp, p, s);
+      if (o.span == 1) {  // PINVIT (Algorithm 1): the trial block is E_hat = E - B R alone
+        k_sub_from<<<nblocks(D * Gp), 256, 0, s>>>(W.E(), Wd, D * Gp);
+        PBS_LAUNCHED();
+      }
+      project_dispatch(ctx, o, ctx->K, Wd, (int)Gp, p, cyc, s);
+      // trial block per group: [E, P, W] (span 3; P = 0 until a search direction
+      // exists, and always for span 2, so its columns are dropped) or [E_hat] (span 1)
+      const Roles trial = o.span == 1 ? Roles{{Wd, Wd, Wd}, p, D} : Roles{{W.E(), W.P(), W.W()}, p, D};
+      const int qt = o.span == 1 ? p : q;
+      gram_groups(L0, ctx->K.d_ph, trial, qt, G, W.GM, W.GA, W.gpart, W.gpart_cap, s);
+      small_rr(W.GM, W.GA, qt, p, W.C, W.theta, W.rr_scr, W.info, G, s);
+      PBS_CUDA(cudaMemcpyAsync(h_info.data(), W.info, sizeof(int) * 8 * G, cudaMemcpyDeviceToHost, s));
       PBS_CUDA(cudaStreamSynchronize(s));
-      if (info[0] != 0) fail(PBS_ENUMERIC, "trial space lost rank");
+      for (int g = 0; g < G; ++g) {
+        if (!cont[g] || h_info[8 * g] == 0) continue;
+        if (h_info[8 * g] == -2) fail(PBS_ENUMERIC, "non-finite Gram matrix");
+        if (h_info[8 * g] == -3) fail(PBS_ENUMERIC, "Rayleigh-Ritz breakdown");
+        if (o.span != 3 || !gr[g].have_p) fail(PBS_ENUMERIC, "trial space lost rank");
+        // rank loss in the LOBPCG basis: restart this group without the search direction
+        PBS_CUDA(cudaMemsetAsync(W.P() + (long)g * p * D, 0, sizeof(double2) * D * p, s));
+        const KData Kv = kdata_view(ctx->K, g);
+        const Roles tg{{W.E() + (long)g * p * D, W.P() + (long)g * p * D, W.W() + (long)g * p * D}, p, D};
+        double2* GMg = W.GM + (long)g * q * q;
+        double2* GAg = W.GA + (long)g * q * q;
+        gram_groups(L0, Kv.d_ph, tg, q, 1, GMg, GAg, W.gpart, W.gpart_cap, s);
+        small_rr(GMg, GAg, q, p, W.C + (long)g * q * p, W.theta + (long)g * q, W.rr_scr, W.info + 8 * g, 1, s);
+        int inf2[2];
+        PBS_CUDA(cudaMemcpyAsync(inf2, W.info + 8 * g, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+        PBS_CUDA(cudaStreamSynchronize(s));
+        if (inf2[0] != 0) fail(PBS_ENUMERIC, "trial space lost rank");
+      }
+      double2* E2 = W.S2;
+      double2* P2 = W.S2 + Gp * D;
+      if (o.span == 1) {
+        // E_new = E_hat C
+        block_update(trial, p, W.C, p, (long)p * p, E2, D, p, nullptr, 0, D, G, s);
+        PBS_CUDA(cudaMemsetAsync(P2, 0, sizeof(double2) * D * Gp, s));
+      } else {
+        // P_new = [P, W] C[p:q], E_new = E C[0:p] + P_new   (into S2, then swap)
+        const Roles pw{{W.P(), W.W(), W.W()}, p, D};
+        block_update(pw, 2 * p, W.C + p, q, (long)q * p, P2, D, p, nullptr, 0, D, G, s);
+        const Roles ee{{W.E(), W.E(), W.E()}, p, D};
+        block_update(ee, p, W.C, q, (long)q * p, E2, D, p, P2, D, D, G, s);
+        if (o.span == 2) PBS_CUDA(cudaMemsetAsync(P2, 0, sizeof(double2) * D * Gp, s));  // gradient method: no P
+      }
+      std::swap(W.S, W.S2);
+      for (int g = 0; g < G; ++g)
+        if (cont[g]) {
+          gr[g].have_p = true;
+          gr[g].it += 1;
+        }
     }
-    // new block in the other buffer, then swap: T2 = [E_new | P_new | -]
-    double2* Enew = W.T2;
-    double2* Pnew = W.T2 + D * p;
-    if (o.span == 3) {
-      // P_new = [P, W] C[p:q] (or W C[p:2p]), E_new = E C[0:p] + P_new
-      block_update(W.S + D * p, D, q - p, W.C + p, q, Pnew, D, p, nullptr, 0, D, s);
-      block_update(E, D, p, W.C, q, Enew, D, p, Pnew, D, D, s);
-      have_p = true;
-    } else {
-      block_update(trial, D, q, W.C, q, Enew, D, p, nullptr, 0, D, s);
+    // groups that moved to their next Bloch vector
+    for (int g = 0; g < G; ++g) {
+      if (!gr[g].need_init) continue;
+      set_group_k(ctx->mem, ctx->H, ctx->K, g, ks[2 * gr[g].pos], ks[2 * gr[g].pos + 1], s);
+      init_group(ctx, o, gr[g], g, nullptr, s);
     }
-    std::swap(W.S, W.T2);
   }
+  return out;
 }
 
-// Initial block: S[:, 0:p] from `init` (host), from the history (extrapolation), or random.
-void initial_block(pbs_ctx* ctx, const pbs_opts& o, const pbs_c64* init, int nhist, cudaStream_t s) {
-  Work& W = ctx->W;
-  const int p = o.block;
-  const long D = W.D;
-  if (nhist > 0) {
-    // S = [E_{k-1}, E_{k-2}, ...] as stored coefficient vectors (Section 6)
-    const int q = nhist * p;
-    PBS_CUDA(cudaMemcpyAsync(W.S, W.hist, sizeof(double2) * D * q, cudaMemcpyDeviceToDevice, s));
-    project_dispatch(ctx, o, W.S, q, s, projection_cycles(o, ctx->last_theta_max, ctx->H.mu));
-    rayleigh_ritz_step(ctx, W.S, q, p, W.T2, s);
-  } else {
-    if (init) PBS_CUDA(cudaMemcpyAsync(W.S, init, sizeof(double2) * D * p, cudaMemcpyHostToDevice, s));
-    else random_block(W.S, D, D, p, o.seed, s);
-    // A block with no relation to the spectrum has Rayleigh quotients near the top
-    // of it.  Two inverse-iteration steps E <- B M E (each followed by the
-    // projection and Rayleigh-Ritz) damp the high frequencies by about
-    // (lambda_low + mu) / (lambda_high + mu) before the iteration starts.
-    const int cyc = projection_cycles(o, 1e300, ctx->H.mu);
-    project_dispatch(ctx, o, W.S, p, s, cyc);
-    rayleigh_ritz_step(ctx, W.S, p, p, W.T2, s);
-    for (int step = 0; step < 2; ++step) {
-      apply_edge<double>(ctx->H.lev[0], ctx->K.d_ph, p, W.T2, W.R, nullptr, D, p, 0.0, 1.0, 0.0, nullptr, 0.0, s);
-      precondition_dispatch(ctx, o, W.R, W.S, p, s);
-      project_dispatch(ctx, o, W.S, p, s, cyc);
-      rayleigh_ritz_step(ctx, W.S, p, p, W.T2, s);
-    }
-  }
-  std::swap(W.S, W.T2);
-  // largest Ritz value of the start block, for the projection accuracy
-  std::vector<double> th(p);
-  PBS_CUDA(cudaMemcpyAsync(th.data(), W.theta, sizeof(double) * p, cudaMemcpyDeviceToHost, s));
-  PBS_CUDA(cudaStreamSynchronize(s));
-  ctx->last_theta_max = 0.0;
-  for (double t : th) ctx->last_theta_max = std::max(ctx->last_theta_max, std::fabs(t));
+// single-group tables for the operator entry points
+void set_single_k(pbs_ctx* ctx, double k1, double k2) {
+  alloc_kdata(ctx->mem, ctx->H, ctx->K, 1);
+  set_group_k(ctx->mem, ctx->H, ctx->K, 0, k1, k2, ctx->stream);
 }
-
-void set_k(pbs_ctx* ctx, double k1, double k2) { build_kdata(ctx->mem, ctx->H, ctx->K, k1, k2, ctx->stream); }
 
 }  // namespace
-
-// ---------------------------------------------------------------------------
-// C ABI
-// ---------------------------------------------------------------------------
 
 namespace {
 int run_guarded_impl(const std::function<void()>& f) {
@@ -677,6 +763,7 @@ void pbs_default_opts(pbs_opts* o) {
   o->nodal_cycles = 2;
   o->extrap_depth = 3;
   o->seed = 0;
+  o->kbatch = 1;
 }
 
 int pbs_num_levels(int n, int m, int coarsest) {
@@ -704,13 +791,7 @@ int pbs_destroy(pbs_ctx* ctx) {
   return run_guarded_impl([&] {
     DeviceGuard g(ctx->device);
     cudaStreamSynchronize(ctx->stream);
-    if (ctx->have_w) {
-      for (void* p : ctx->W.allocs) ctx->mem.free(p);
-      free_mg_work(ctx->mem, ctx->W.e32);
-      free_mg_work(ctx->mem, ctx->W.n32);
-      free_mg_work(ctx->mem, ctx->W.e64);
-      free_mg_work(ctx->mem, ctx->W.n64);
-    }
+    free_work(ctx);
     if (ctx->have_h) free_hierarchy(ctx->mem, ctx->H);
     free_kdata(ctx->mem, ctx->K);
     ctx->mem.free(ctx->d_eps_in);
@@ -723,6 +804,7 @@ int pbs_destroy(pbs_ctx* ctx) {
   });
 }
 
+
 int pbs_solve_k(pbs_ctx* ctx, const pbs_geom* geom, const pbs_opts* opts, const double k[2], const pbs_c64* init,
                 double* eigvals, double* resid, int* iters, pbs_c64* evecs) {
   if (!ctx || !geom || !opts || !k || !eigvals || !resid || !iters) return PBS_EINVAL;
@@ -730,69 +812,32 @@ int pbs_solve_k(pbs_ctx* ctx, const pbs_geom* geom, const pbs_opts* opts, const 
   const int rc = run_guarded_impl([&] {
     DeviceGuard g(ctx->device);
     TimerScope ts(ctx);
-    const pbs_opts& o = *opts;
+    pbs_opts o = *opts;
     validate_opts(o);
     ensure_hierarchy_host(ctx, geom, effective_mu(o, geom->a, geom->b), o.coarsest);
-    ensure_work(ctx, o.block);
-    set_k(ctx, k[0], k[1]);
-    initial_block(ctx, o, init, 0, ctx->stream);
-    const KResult r = iterate(ctx, o, ctx->stream);
+    const PathResult r = solve_chains(ctx, o, 1, k, 1, init);
     for (int j = 0; j < o.nev; ++j) {
       eigvals[j] = r.lam[j];
       resid[j] = r.res[j];
     }
-    *iters = r.iters;
+    *iters = r.iters[0];
     if (evecs) {
       // M-normalise the returned columns
       Work& W = ctx->W;
       std::vector<double> rq(2 * o.block), sc(o.block);
-      rayleigh_parts(ctx->H.lev[0], ctx->K.d_ph, o.block, W.S, W.D, o.block, W.parts, W.rq, ctx->stream);
+      rayleigh_parts(ctx->H.lev[0], ctx->K.d_ph, o.block, W.E(), W.D, o.block, W.parts, W.rq, ctx->stream);
       PBS_CUDA(cudaMemcpyAsync(rq.data(), W.rq, 2 * o.block * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
       PBS_CUDA(cudaStreamSynchronize(ctx->stream));
       for (int j = 0; j < o.block; ++j) sc[j] = 1.0 / std::sqrt(rq[2 * j]);
       PBS_CUDA(cudaMemcpyAsync(W.lam, sc.data(), o.block * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
-      scale_columns(W.S, W.D, W.D, o.nev, W.lam, ctx->stream);
-      PBS_CUDA(cudaMemcpyAsync(evecs, W.S, sizeof(double2) * W.D * o.nev, cudaMemcpyDeviceToHost, ctx->stream));
+      scale_columns(W.E(), W.D, W.D, o.nev, W.lam, ctx->stream);
+      PBS_CUDA(cudaMemcpyAsync(evecs, W.E(), sizeof(double2) * W.D * o.nev, cudaMemcpyDeviceToHost, ctx->stream));
       PBS_CUDA(cudaStreamSynchronize(ctx->stream));
     }
-    if (!r.converged) status = PBS_ENOCONV;
+    if (!r.all_converged) status = PBS_ENOCONV;
   });
   return rc != PBS_OK ? rc : status;
 }
-
-namespace {
-// Shared body of the two path entry points; ks/results on the host.
-int solve_path_impl(pbs_ctx* ctx, const pbs_opts& o, int nk, const double* ks, double* eigvals, double* resid,
-                    int* iters) {
-  int first_bad = PBS_OK;
-  Work& W = ctx->W;
-  const int p = o.block;
-  const long D = W.D;
-  int nhist = 0;
-  for (int t = 0; t < nk; ++t) {
-    set_k(ctx, ks[2 * t], ks[2 * t + 1]);
-    initial_block(ctx, o, nullptr, std::min(nhist, o.extrap_depth), ctx->stream);
-    KResult r = iterate(ctx, o, ctx->stream);
-    for (int j = 0; j < o.nev; ++j) {
-      eigvals[(long)t * o.nev + j] = r.lam[j];
-      resid[(long)t * o.nev + j] = r.res[j];
-    }
-    iters[t] = r.iters;
-    if (!r.converged && first_bad == PBS_OK) first_bad = PBS_ENOCONV;
-    // history ring: newest first
-    if (o.extrap_depth > 0) {
-      // shift the ring one slot (oldest first: source and destination never overlap)
-      const int keep = std::min(nhist, 2);
-      for (int slot = keep; slot >= 1; --slot)
-        PBS_CUDA(cudaMemcpyAsync(W.hist + D * p * slot, W.hist + D * p * (slot - 1), sizeof(double2) * D * p,
-                                 cudaMemcpyDeviceToDevice, ctx->stream));
-      PBS_CUDA(cudaMemcpyAsync(W.hist, W.S, sizeof(double2) * D * p, cudaMemcpyDeviceToDevice, ctx->stream));
-      nhist = std::min(nhist + 1, 3);
-    }
-  }
-  return first_bad;
-}
-}  // namespace
 
 int pbs_solve_path(pbs_ctx* ctx, const pbs_geom* geom, const pbs_opts* opts, int nk, const double* ks,
                    double* eigvals, double* resid, int* iters) {
@@ -804,8 +849,11 @@ int pbs_solve_path(pbs_ctx* ctx, const pbs_geom* geom, const pbs_opts* opts, int
     validate_opts(*opts);
     if (nk == 0) return;
     ensure_hierarchy_host(ctx, geom, effective_mu(*opts, geom->a, geom->b), opts->coarsest);
-    ensure_work(ctx, opts->block);
-    status = solve_path_impl(ctx, *opts, nk, ks, eigvals, resid, iters);
+    const PathResult r = solve_chains(ctx, *opts, nk, ks, opts->kbatch, nullptr);
+    std::copy(r.lam.begin(), r.lam.end(), eigvals);
+    std::copy(r.res.begin(), r.res.end(), resid);
+    std::copy(r.iters.begin(), r.iters.end(), iters);
+    if (!r.all_converged) status = PBS_ENOCONV;
   });
   return rc != PBS_OK ? rc : status;
 }
@@ -827,23 +875,19 @@ int pbs_solve_path_device(pbs_ctx* ctx, double a, double b, int n, int m, const 
     PBS_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
     PBS_CUDA(cudaEventRecord(ev, us));
     PBS_CUDA(cudaStreamWaitEvent(ctx->stream, ev, 0));
-    if (nk == 0) {
-      cudaEventDestroy(ev);
-      return;
-    }
+    cudaEventDestroy(ev);
+    if (nk == 0) return;
     const uint64_t h = device_eps_hash(ctx, d_eps, (long)n * m);
     ensure_hierarchy(ctx, a, b, n, m, d_eps, h, effective_mu(*opts, a, b), opts->coarsest);
-    ensure_work(ctx, opts->block);
-    std::vector<double> ks(2 * nk), ev_h((long)nk * opts->nev), rs_h((long)nk * opts->nev);
-    std::vector<int> it_h(nk);
+    std::vector<double> ks(2 * nk);
     PBS_CUDA(cudaMemcpyAsync(ks.data(), d_ks, sizeof(double) * 2 * nk, cudaMemcpyDeviceToHost, ctx->stream));
     PBS_CUDA(cudaStreamSynchronize(ctx->stream));
-    status = solve_path_impl(ctx, *opts, nk, ks.data(), ev_h.data(), rs_h.data(), it_h.data());
-    PBS_CUDA(cudaMemcpyAsync(d_eigvals, ev_h.data(), sizeof(double) * ev_h.size(), cudaMemcpyHostToDevice, ctx->stream));
-    PBS_CUDA(cudaMemcpyAsync(d_resid, rs_h.data(), sizeof(double) * rs_h.size(), cudaMemcpyHostToDevice, ctx->stream));
-    PBS_CUDA(cudaMemcpyAsync(d_iters, it_h.data(), sizeof(int) * it_h.size(), cudaMemcpyHostToDevice, ctx->stream));
+    const PathResult r = solve_chains(ctx, *opts, nk, ks.data(), opts->kbatch, nullptr);
+    PBS_CUDA(cudaMemcpyAsync(d_eigvals, r.lam.data(), sizeof(double) * r.lam.size(), cudaMemcpyHostToDevice, ctx->stream));
+    PBS_CUDA(cudaMemcpyAsync(d_resid, r.res.data(), sizeof(double) * r.res.size(), cudaMemcpyHostToDevice, ctx->stream));
+    PBS_CUDA(cudaMemcpyAsync(d_iters, r.iters.data(), sizeof(int) * r.iters.size(), cudaMemcpyHostToDevice, ctx->stream));
     PBS_CUDA(cudaStreamSynchronize(ctx->stream));
-    cudaEventDestroy(ev);
+    if (!r.all_converged) status = PBS_ENOCONV;
   });
   return rc != PBS_OK ? rc : status;
 }
@@ -867,7 +911,7 @@ int pbs_apply(pbs_ctx* ctx, const pbs_geom* geom, const pbs_opts* opts, int op, 
     if (op < PBS_OP_A || op > PBS_OP_PROJECT) fail(PBS_EINVAL, "unknown operator");
     if (op == PBS_OP_PROJECT && level != 0) fail(PBS_EINVAL, "PROJECT acts on level 0");
     if (ncols == 0) return;
-    set_k(ctx, k[0], k[1]);
+    set_single_k(ctx, k[0], k[1]);
     cudaStream_t us = (cudaStream_t)cuda_stream;
     cudaStream_t s = ctx->stream;
     cudaEvent_t ev;
@@ -917,30 +961,12 @@ int pbs_apply(pbs_ctx* ctx, const pbs_geom* geom, const pbs_opts* opts, int op, 
         const bool nodal = op == PBS_OP_VCYCLE_NODAL;
         const long len = nodal ? N : D;
         if (op == PBS_OP_PROJECT) {
-          // project a copy: needs the solver buffers for ncols columns
-          Work saved = ctx->W;
-          bool had = ctx->have_w;
-          ctx->have_w = false;
-          ctx->W = Work();
-          try {
-            ensure_work(ctx, std::max(1, (ncols + 2) / 3));
-            if (3 * ctx->W.p < ncols) fail(PBS_EINVAL, "too many columns");
-            PBS_CUDA(cudaMemcpyAsync(Y, X, sizeof(double2) * D * ncols, cudaMemcpyDeviceToDevice, s));
-            project_dispatch(ctx, o, Y, ncols, s);
-            PBS_CUDA(cudaStreamSynchronize(s));
-          } catch (...) {
-            for (void* q : ctx->W.allocs) ctx->mem.free(q);
-            free_mg_work(ctx->mem, ctx->W.e32); free_mg_work(ctx->mem, ctx->W.n32);
-            free_mg_work(ctx->mem, ctx->W.e64); free_mg_work(ctx->mem, ctx->W.n64);
-            ctx->W = saved;
-            ctx->have_w = had;
-            throw;
-          }
-          for (void* q : ctx->W.allocs) ctx->mem.free(q);
-          free_mg_work(ctx->mem, ctx->W.e32); free_mg_work(ctx->mem, ctx->W.n32);
-          free_mg_work(ctx->mem, ctx->W.e64); free_mg_work(ctx->mem, ctx->W.n64);
-          ctx->W = saved;
-          ctx->have_w = had;
+          const int pw = std::max(1, (ncols + 2) / 3);
+          if (pw > kMaxBlock) fail(PBS_EINVAL, "too many columns");
+          ensure_work(ctx, pw, 1);
+          PBS_CUDA(cudaMemcpyAsync(Y, X, sizeof(double2) * D * ncols, cudaMemcpyDeviceToDevice, s));
+          project_dispatch(ctx, o, K, Y, ncols, ncols, o.nodal_cycles, s);
+          PBS_CUDA(cudaStreamSynchronize(s));
           break;
         }
         if (o.precision == PBS_MIXED) {
@@ -950,8 +976,8 @@ int pbs_apply(pbs_ctx* ctx, const pbs_geom* geom, const pbs_opts* opts, int op, 
           try {
             alloc_mg_work<float>(ctx->mem, H, ncols, nodal, w);
             convert_d2f(X, xf, len * ncols, s);
-            if (nodal) nodal_vcycle<float>(H, K, w, level, xf, yf, len, ncols, o.nu_pre, o.nu_post, s);
-            else edge_vcycle<float>(H, K, w, level, xf, yf, len, ncols, o.nu_pre, o.nu_post, s);
+            if (nodal) nodal_vcycle<float>(H, K, w, level, xf, yf, len, ncols, ncols, o.nu_pre, o.nu_post, s);
+            else edge_vcycle<float>(H, K, w, level, xf, yf, len, ncols, ncols, o.nu_pre, o.nu_post, s);
             convert_f2d(yf, Y, len * ncols, s);
             PBS_CUDA(cudaStreamSynchronize(s));
           } catch (...) {
@@ -967,8 +993,8 @@ int pbs_apply(pbs_ctx* ctx, const pbs_geom* geom, const pbs_opts* opts, int op, 
           MgWork<double> w;
           try {
             alloc_mg_work<double>(ctx->mem, H, ncols, nodal, w);
-            if (nodal) nodal_vcycle<double>(H, K, w, level, X, Y, len, ncols, o.nu_pre, o.nu_post, s);
-            else edge_vcycle<double>(H, K, w, level, X, Y, len, ncols, o.nu_pre, o.nu_post, s);
+            if (nodal) nodal_vcycle<double>(H, K, w, level, X, Y, len, ncols, ncols, o.nu_pre, o.nu_post, s);
+            else edge_vcycle<double>(H, K, w, level, X, Y, len, ncols, ncols, o.nu_pre, o.nu_post, s);
             PBS_CUDA(cudaStreamSynchronize(s));
           } catch (...) {
             free_mg_work<double>(ctx->mem, w);
@@ -999,28 +1025,25 @@ int pbs_gram(pbs_ctx* ctx, const pbs_geom* geom, const double k[2], int q, const
     pbs_opts o;
     pbs_default_opts(&o);
     ensure_hierarchy_host(ctx, geom, effective_mu(o, geom->a, geom->b), o.coarsest);
-    set_k(ctx, k[0], k[1]);
+    set_single_k(ctx, k[0], k[1]);
     const Level& L0 = ctx->H.lev[0];
     cudaStream_t s = ctx->stream;
     cudaEvent_t ev;
     PBS_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
     PBS_CUDA(cudaEventRecord(ev, (cudaStream_t)cuda_stream));
     PBS_CUDA(cudaStreamWaitEvent(s, ev, 0));
-    double2* work = (double2*)ctx->mem.alloc(sizeof(double2) * (L0.D() + L0.N()) * q);
-    const int npart = 2 * 152;
-    double2* part = (double2*)ctx->mem.alloc(sizeof(double2) * npart * (q * (q + 1) / 2));
+    cudaEventDestroy(ev);
+    const long cap = gram_partials_size(L0.N(), q, 1);
+    double2* part = (double2*)ctx->mem.alloc(sizeof(double2) * cap);
     try {
-      gram(L0, ctx->K.d_ph, q, (const double2*)S, L0.D(), q, (double2*)GM, (double2*)GA, work, part, npart, s);
+      const Roles R{{(const double2*)S, (const double2*)S, (const double2*)S}, q, L0.D()};
+      gram_groups(L0, ctx->K.d_ph, R, q, 1, (double2*)GM, (double2*)GA, part, cap, s);
       PBS_CUDA(cudaStreamSynchronize(s));
     } catch (...) {
-      ctx->mem.free(work);
       ctx->mem.free(part);
-      cudaEventDestroy(ev);
       throw;
     }
-    ctx->mem.free(work);
     ctx->mem.free(part);
-    cudaEventDestroy(ev);
   });
 }
 
@@ -1036,20 +1059,21 @@ int pbs_rayleigh_ritz(pbs_ctx* ctx, const pbs_geom* geom, const pbs_opts* opts, 
     ensure_hierarchy_host(ctx, geom, effective_mu(o, geom->a, geom->b), o.coarsest);
     const int pw = std::max(p, (q + 2) / 3);
     if (pw > kMaxBlock) fail(PBS_EINVAL, "q too large");
-    ensure_work(ctx, pw);
-    set_k(ctx, k[0], k[1]);
+    ensure_work(ctx, pw, 1);
+    set_single_k(ctx, k[0], k[1]);
     cudaStream_t s = ctx->stream;
     cudaEvent_t ev;
     PBS_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
     PBS_CUDA(cudaEventRecord(ev, (cudaStream_t)cuda_stream));
     PBS_CUDA(cudaStreamWaitEvent(s, ev, 0));
+    cudaEventDestroy(ev);
     Work& W = ctx->W;
-    PBS_CUDA(cudaMemcpyAsync(W.S, S, sizeof(double2) * W.D * q, cudaMemcpyDeviceToDevice, s));
-    if (project) project_dispatch(ctx, o, W.S, q, s);
-    rayleigh_ritz_step(ctx, W.S, q, p, (double2*)X, s);
+    PBS_CUDA(cudaMemcpyAsync(W.init, S, sizeof(double2) * W.D * q, cudaMemcpyDeviceToDevice, s));
+    const KData Kv = kdata_view(ctx->K, 0);
+    if (project) project_dispatch(ctx, o, Kv, W.init, q, q, o.nodal_cycles, s);
+    rr_single(ctx, Kv, W.init, q, p, (double2*)X, s);
     PBS_CUDA(cudaMemcpyAsync(theta, W.theta, sizeof(double) * p, cudaMemcpyDeviceToHost, s));
     PBS_CUDA(cudaStreamSynchronize(s));
-    cudaEventDestroy(ev);
   });
 }
 

@@ -29,7 +29,7 @@ def test_exports_every_declared_symbol(built):
 def test_default_opts_and_strerror(built):
     o = pbs.default_opts()
     assert (o.nev, o.block, o.span, o.precision, o.coarsest, o.nodal_cycles, o.extrap_depth) == (4, 6, 3, 1, 4, 2, 3)
-    assert o.tol == 1e-8 and o.max_iter == 400
+    assert o.tol == 1e-8 and o.max_iter == 400 and o.kbatch == 1
     assert pbs.strerror(pbs.PBS_EINVAL) == "invalid argument"
     assert pbs.strerror(12345) == "unknown status"
 
@@ -50,6 +50,6 @@ def test_null_arguments_are_rejected(built):
 
 
 def test_struct_layout_matches_header(built):
-    # pbs_opts: 5 ints, 2 doubles, 5 ints, 1 uint64 with natural alignment
-    assert ct.sizeof(pbs.pbs_opts) == 72
+    # pbs_opts: 5 ints, 2 doubles, 5 ints, 1 uint64, 1 int with natural alignment
+    assert ct.sizeof(pbs.pbs_opts) == 80
     assert ct.sizeof(pbs.pbs_geom) == 32

@@ -141,3 +141,24 @@ def test_span_variants_reach_the_same_eigenvalues(ctx):
     for span in (1, 2, 3):
         lam, res, iters, _ = ctx.solve_k(geom, dict(nev=4, block=7, span=span, precision=pbs.PBS_FP64), k)
         assert np.max(np.abs(lam - want) / want) <= 1e-10, span
+
+
+@pytest.mark.parametrize("kbatch", [3, 8, 31])
+def test_rod64_path_with_k_points_in_flight(ctx, kbatch):
+    # several chains of the path iterate in lock-step (every launch covers all of them);
+    # with kbatch = 31 every Bloch vector is its own chain (no extrapolation)
+    data = np.loadtxt(os.path.join(GOLDEN, "rod64_path31.txt"))
+    ks, want = data[:, :2], data[:, 2:]
+    geom = pbs.Geometry(gi.rod_eps(64, 64))
+    lam, res, iters = ctx.solve_path(geom, dict(nev=8, block=10, precision=pbs.PBS_MIXED, kbatch=kbatch), ks)
+    assert np.max(np.abs(lam - want) / want) <= 1e-10
+    assert np.all(res <= 1e-8)
+
+
+def test_batched_path_is_deterministic(ctx):
+    ks = gi.gxmg_path(13)
+    geom = pbs.Geometry(gi.rod_eps(32, 32))
+    o = dict(nev=4, block=6, kbatch=3)
+    a = ctx.solve_path(geom, o, ks)[0]
+    b = ctx.solve_path(geom, o, ks)[0]
+    assert np.array_equal(a, b)
