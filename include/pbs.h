@@ -60,9 +60,11 @@ extern "C" {
 
 /* ---- precision policies (Section 4/5 preconditioner precision) -------- */
 #define PBS_FP64 0  /* every kernel in FP64 ("plain")                         */
-#define PBS_MIXED 1 /* FP32 multigrid V-cycles and nodal cycles; FP64 residual,
-                       Gram matrices, Rayleigh-Ritz, projection right-hand side
-                       and update                                              */
+#define PBS_MIXED 1 /* FP32 multigrid V-cycles and nodal cycles; residual,
+                       Rayleigh quotients, Gram matrices, projection right-hand
+                       side and update in double-float arithmetic on the FP32
+                       pipe (FP64 storage, about 2^-47 relative rounding); the
+                       small Rayleigh-Ritz eigensolve in double-float too      */
 
 /* ---- operators for pbs_apply ----------------------------------------- */
 #define PBS_OP_A 0             /* edge -> edge: y = A x  (Section 3)            */
@@ -183,10 +185,13 @@ PBS_API int pbs_apply(pbs_ctx *ctx, const pbs_geom *geom, const pbs_opts *opts, 
 /*
  * Block Gram matrices of the pencil at k (Section 4, used by Rayleigh-Ritz):
  * GM = S^* M S and GA = (C S)^* W (C S) = S^* A S, W = diag(1/(eps_c h1 h2)).
- * S: device D x q; GM, GA: device q x q column-major.
+ * S: device D x q; GM, GA: device q x q column-major.  `precision` selects the
+ * arithmetic: PBS_FP64, or PBS_MIXED = double-float on the FP32 pipe (about
+ * 2^-47 relative rounding, compensated sums), the arithmetic the mixed policy
+ * uses inside the solver.  Inputs and outputs are FP64 either way.
  */
 PBS_API int pbs_gram(pbs_ctx *ctx, const pbs_geom *geom, const double k[2], int q, const pbs_c64 *S, pbs_c64 *GM,
-             pbs_c64 *GA, void *cuda_stream);
+             pbs_c64 *GA, int precision, void *cuda_stream);
 
 /*
  * Rayleigh-Ritz of the pencil on span(S) (Section 4, eq. ritz_eigenvalue):

@@ -90,7 +90,7 @@ def lib() -> ct.CDLL:
                                              ct.POINTER(pbs_opts), ct.c_int, P, P, P, P, P]),
         "pbs_apply": (ct.c_int, [P, ct.POINTER(pbs_geom), ct.POINTER(pbs_opts), ct.c_int, ct.c_int, dp, ct.c_int,
                                  P, P, P]),
-        "pbs_gram": (ct.c_int, [P, ct.POINTER(pbs_geom), dp, ct.c_int, P, P, P, P]),
+        "pbs_gram": (ct.c_int, [P, ct.POINTER(pbs_geom), dp, ct.c_int, P, P, P, ct.c_int, P]),
         "pbs_rayleigh_ritz": (ct.c_int, [P, ct.POINTER(pbs_geom), ct.POINTER(pbs_opts), dp, ct.c_int, P, ct.c_int,
                                          ct.c_int, dp, P, P]),
         "pbs_profile_enable": (ct.c_int, [P, ct.c_char_p]),
@@ -271,10 +271,11 @@ class Context:
         _check(lib().pbs_apply(self._ptr, geom.ref(), ct.byref(o), opc, level, _dp(kk), ncols, x_ptr, y_ptr,
                                _stream_ptr(stream)), f"pbs_apply({op})")
 
-    def gram(self, geom: Geometry, k, q: int, s_ptr: int, gm_ptr: int, ga_ptr: int, stream=None):
+    def gram(self, geom: Geometry, k, q: int, s_ptr: int, gm_ptr: int, ga_ptr: int, stream=None,
+             precision: int = PBS_FP64):
         kk = np.asarray(k, dtype=np.float64)
-        _check(lib().pbs_gram(self._ptr, geom.ref(), _dp(kk), q, s_ptr, gm_ptr, ga_ptr, _stream_ptr(stream)),
-               "pbs_gram")
+        _check(lib().pbs_gram(self._ptr, geom.ref(), _dp(kk), q, s_ptr, gm_ptr, ga_ptr, precision,
+                              _stream_ptr(stream)), "pbs_gram")
 
     def profile_enable(self, classes: str | None):
         """Time kernel classes with CUDA events on the library's stream (``pbs_profile_enable``)."""

@@ -19,11 +19,14 @@
 #include <cuda_runtime.h>
 #include <cstdint>
 
+#include "df32.cuh"
+
 namespace pbs {
 
 template <class T> struct cx_of;
 template <> struct cx_of<double> { using type = double2; };
 template <> struct cx_of<float> { using type = float2; };
+template <> struct cx_of<df> { using type = dcx; };
 template <class T> using cx = typename cx_of<T>::type;
 
 template <class T> __host__ __device__ __forceinline__ cx<T> mk(T r, T i) {
@@ -67,10 +70,11 @@ template <class T> __device__ __forceinline__ cx<T> to_cx(float2 v) { return mk<
 template <class T> struct Ph {
   cx<T> al, be;
 };
+template <class T> __device__ __forceinline__ cx<T> ph_as(double re, double im);
 template <class T> __device__ __forceinline__ Ph<T> load_ph(const double* ph, int group) {
   Ph<T> p;
-  p.al = mk<T>(T(ph[4 * group + 0]), T(ph[4 * group + 1]));
-  p.be = mk<T>(T(ph[4 * group + 2]), T(ph[4 * group + 3]));
+  p.al = ph_as<T>(ph[4 * group + 0], ph[4 * group + 1]);
+  p.be = ph_as<T>(ph[4 * group + 2], ph[4 * group + 3]);
   return p;
 }
 
@@ -101,6 +105,81 @@ __device__ __forceinline__ cx<T> gread(const cx<T>* __restrict__ f, int i, int j
   cx<T> v = f[(long)j * n + i];
   return w ? cmul(v, ph) : v;
 }
+
+// FP64 storage read in arithmetic T (double: as is; df: split by integer operations;
+// float: rounded).
+template <class T> __device__ __forceinline__ cx<T> ld_as(const double2* p);
+template <> __device__ __forceinline__ double2 ld_as<double>(const double2* p) { return *p; }
+template <> __device__ __forceinline__ dcx ld_as<df>(const double2* p) { return dcx_split(*p); }
+template <> __device__ __forceinline__ float2 ld_as<float>(const double2* p) {
+  const double2 v = *p;
+  return make_float2(float(v.x), float(v.y));
+}
+template <class T> __device__ __forceinline__ T ld_scalar(double d);
+template <> __device__ __forceinline__ double ld_scalar<double>(double d) { return d; }
+template <> __device__ __forceinline__ df ld_scalar<df>(double d) { return df_split(d); }
+__device__ __forceinline__ double2 to_d2(double2 v) { return v; }
+__device__ __forceinline__ double2 to_d2(dcx v) { return dcx_to(v); }
+__device__ __forceinline__ double to_double(double v) { return v; }
+__device__ __forceinline__ double to_double(df v) { return df_to(v); }
+template <class T> __device__ __forceinline__ T narrow(double v) { return T(v); }
+template <class T> __device__ __forceinline__ T narrow(df v);
+template <> __device__ __forceinline__ float narrow<float>(df v) { return df_to_float(v); }
+template <> __device__ __forceinline__ double narrow<double>(df v) { return df_to(v); }
+// exact widening of a stored value to the arithmetic type
+template <class T> __device__ __forceinline__ cx<T> widen(float2 v);
+template <> __device__ __forceinline__ double2 widen<double>(float2 v) { return make_double2(v.x, v.y); }
+template <> __device__ __forceinline__ dcx widen<df>(float2 v) {
+  return dcx_make(df_make(v.x, 0.0f), df_make(v.y, 0.0f));
+}
+template <class T> __device__ __forceinline__ cx<T> widen(double2 v);
+template <> __device__ __forceinline__ double2 widen<double>(double2 v) { return v; }
+template <> __device__ __forceinline__ dcx widen<df>(double2 v) { return dcx_split(v); }
+
+// Phases in the arithmetic of a kernel
+template <class T> __device__ __forceinline__ cx<T> ph_as(double re, double im);
+template <> __device__ __forceinline__ double2 ph_as<double>(double re, double im) { return make_double2(re, im); }
+template <> __device__ __forceinline__ float2 ph_as<float>(double re, double im) {
+  return make_float2(float(re), float(im));
+}
+template <> __device__ __forceinline__ dcx ph_as<df>(double re, double im) {
+  return dcx_make(df_split(re), df_split(im));
+}
+
+// gread of FP64 storage in arithmetic T
+template <class T>
+__device__ __forceinline__ cx<T> gread_d(const double2* __restrict__ f, int i, int j, int n, int m, const Ph<T>& p) {
+  bool w = false;
+  cx<T> ph = mk<T>(T(1.0), T(0.0));
+  if (i < 0) {
+    i += n;
+    ph = conj(p.al);
+    w = true;
+  } else if (i >= n) {
+    i -= n;
+    ph = p.al;
+    w = true;
+  }
+  if (j < 0) {
+    j += m;
+    ph = cmul(ph, conj(p.be));
+    w = true;
+  } else if (j >= m) {
+    j -= m;
+    ph = cmul(ph, p.be);
+    w = true;
+  }
+  const cx<T> v = ld_as<T>(f + (long)j * n + i);
+  return w ? cmul(v, ph) : v;
+}
+// Reader of an FP64 edge vector in arithmetic T
+template <class T> struct ERdD {
+  const double2* __restrict__ X;
+  int n, m;
+  Ph<T> p;
+  __device__ __forceinline__ cx<T> x(int i, int j) const { return gread_d<T>(X, i, j, n, m, p); }
+  __device__ __forceinline__ cx<T> y(int i, int j) const { return gread_d<T>(X + (long)n * m, i, j, n, m, p); }
+};
 
 // Reader of one edge vector from memory (x-edges at X, y-edges at X + n*m).
 template <class T> struct ERd {
@@ -138,6 +217,18 @@ template <class T> struct Wts {
   }
 };
 
+// The same weights as double-floats, pre-scaled by 1 / (h1 h2) (level 0 only).
+struct WtsDF {
+  const float2* __restrict__ w;  // (hi, lo) per cell
+  int n, m;
+  __device__ __forceinline__ df operator()(int i, int j) const {
+    if (i < 0) i += n; else if (i >= n) i -= n;
+    if (j < 0) j += m; else if (j >= m) j -= m;
+    const float2 v = w[(long)j * n + i];
+    return df_make(v.x, v.y);
+  }
+};
+
 // Level geometry constants.
 template <class T> struct Lvl {
   int n, m;
@@ -149,11 +240,11 @@ template <class T, class R> __device__ __forceinline__ cx<T> curl_at(const R& r,
   return r.x(i, j + 1) - r.x(i, j) - r.y(i + 1, j) + r.y(i, j);
 }
 // (A u) at x-edge (i,j): top of cell (i,j-1), bottom of cell (i,j)
-template <class T, class R> __device__ __forceinline__ cx<T> A_x(const R& r, const Wts<T>& w, int i, int j) {
+template <class T, class R, class W> __device__ __forceinline__ cx<T> A_x(const R& r, const W& w, int i, int j) {
   return w(i, j - 1) * curl_at<T>(r, i, j - 1) - w(i, j) * curl_at<T>(r, i, j);
 }
 // (A u) at y-edge (i,j): right of cell (i-1,j), left of cell (i,j)
-template <class T, class R> __device__ __forceinline__ cx<T> A_y(const R& r, const Wts<T>& w, int i, int j) {
+template <class T, class R, class W> __device__ __forceinline__ cx<T> A_y(const R& r, const W& w, int i, int j) {
   return w(i, j) * curl_at<T>(r, i, j) - w(i - 1, j) * curl_at<T>(r, i - 1, j);
 }
 template <class T, class R> __device__ __forceinline__ cx<T> M_x(const R& r, const Lvl<T>& L, int i, int j) {

@@ -41,6 +41,34 @@ __device__ __forceinline__ void block_sum2(double& a, double& b) {
   }
 }
 
+__device__ __forceinline__ df shfl_df(df v, int o) {
+  return df_make(__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o));
+}
+
+// Block-wide sum of two double-floats (fixed order); result valid in thread 0.
+__device__ __forceinline__ void block_sum2(df& a, df& b) {
+  __shared__ df sa[32], sb[32];
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  for (int o = 16; o > 0; o >>= 1) {
+    a = a + df_make(__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o));
+    b = b + df_make(__shfl_xor_sync(0xffffffffu, b.hi, o), __shfl_xor_sync(0xffffffffu, b.lo, o));
+  }
+  if (lane == 0) {
+    sa[wid] = a;
+    sb[wid] = b;
+  }
+  __syncthreads();
+  const int nw = (blockDim.x * blockDim.y + 31) >> 5;
+  if (wid == 0) {
+    a = lane < nw ? sa[lane] : df_zero();
+    b = lane < nw ? sb[lane] : df_zero();
+    for (int o = 16; o > 0; o >>= 1) {
+      a = a + df_make(__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o));
+      b = b + df_make(__shfl_xor_sync(0xffffffffu, b.hi, o), __shfl_xor_sync(0xffffffffu, b.lo, o));
+    }
+  }
+}
+
 // partials: [ncols][nblk][2] -> out [ncols][2], fixed order
 __global__ void k_finalize2(const double* __restrict__ part, int nblk, double* __restrict__ out) {
   const int c = blockIdx.x;
@@ -56,25 +84,34 @@ __global__ void k_finalize2(const double* __restrict__ part, int nblk, double* _
   }
 }
 
-__global__ void k_rayleigh_parts(Lvl<double> L, Wts<double> w, const double* ph, int cpg, const double2* __restrict__ X,
-                                 long ld, double* __restrict__ part) {
+// The kernels below read and write FP64 blocks; V is the arithmetic: double
+// (plain FP64) or df (double-float on the FP32 pipe, about 2^-47 relative).
+
+template <class V, class W>
+__global__ void k_rayleigh_parts(Lvl<V> L, W w, const double* ph, int cpg, const double2* __restrict__ X, long ld,
+                                 double* __restrict__ part) {
   const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y, c = blockIdx.z;
-  double den = 0, num = 0;
+  V den = V(0.0), num = V(0.0);
   if (i < L.n && j < L.m) {
-    const ERd<double> r{X + c * ld, L.n, L.m, load_ph<double>(ph, c / cpg)};
-    const double2 mx = M_x<double>(r, L, i, j), my = M_y<double>(r, L, i, j);
-    const double2 ex = r.x(i, j), ey = r.y(i, j);
+    const ERdD<V> r{X + c * ld, L.n, L.m, load_ph<V>(ph, c / cpg)};
+    const cx<V> mx = M_x<V>(r, L, i, j), my = M_y<V>(r, L, i, j);
+    const cx<V> ex = r.x(i, j), ey = r.y(i, j);
     den = ex.x * mx.x + ex.y * mx.y + ey.x * my.x + ey.y * my.y;
-    num = w(i, j) * nrm2(curl_at<double>(r, i, j));
+    num = w(i, j) * nrm2(curl_at<V>(r, i, j));
   }
   block_sum2(den, num);
   if (threadIdx.x == 0 && threadIdx.y == 0) {
     const int nblk = gridDim.x * gridDim.y, b = blockIdx.y * gridDim.x + blockIdx.x;
-    part[((long)c * nblk + b) * 2] = den;
-    part[((long)c * nblk + b) * 2 + 1] = num;
+    part[((long)c * nblk + b) * 2] = to_double(den);
+    part[((long)c * nblk + b) * 2 + 1] = to_double(num);
   }
 }
 
+// R = A E - lam M E in FP64 in every precision policy: the iterate enters through
+// a stencil whose terms are up to lambda_max / lambda larger than the result, so
+// a perturbation of the stored vector of relative size eta moves the relative
+// residual by about eta lambda_max / lambda (1.6e7 at 256 x 256 next to Gamma),
+// which only FP64's 1.1e-16 keeps well under a tolerance of 1e-8.
 __global__ void k_residual(Lvl<double> L, Wts<double> w, const double* ph, int cpg, const double2* __restrict__ E,
                            double2* __restrict__ R, long ld, const double* __restrict__ lam, double* __restrict__ part) {
   const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y, c = blockIdx.z;
@@ -98,19 +135,20 @@ __global__ void k_residual(Lvl<double> L, Wts<double> w, const double* ph, int c
   }
 }
 
-// rhs(i,j) = (L^* M x)(i,j) = (Mx)_x(i-1,j) - (Mx)_x(i,j) + (Mx)_y(i,j-1) - (Mx)_y(i,j)
-template <class T>
-__global__ void k_lift_adj_mass(Lvl<double> L, const double* ph, int cpg, const double2* __restrict__ X, long ldx,
+// rhs(i,j) = (L^* M x)(i,j) = (Mx)_x(i-1,j) - (Mx)_x(i,j) + (Mx)_y(i,j-1) - (Mx)_y(i,j),
+// computed in V and stored in T
+template <class V, class T>
+__global__ void k_lift_adj_mass(Lvl<V> L, const double* ph, int cpg, const double2* __restrict__ X, long ldx,
                                 cx<T>* __restrict__ Y, long ldy) {
   const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y, c = blockIdx.z;
   if (i >= L.n || j >= L.m) return;
-  const ERd<double> r{X + c * ldx, L.n, L.m, load_ph<double>(ph, c / cpg)};
-  const double2 v = M_x<double>(r, L, i - 1, j) - M_x<double>(r, L, i, j) + M_y<double>(r, L, i, j - 1) -
-                    M_y<double>(r, L, i, j);
-  Y[c * ldy + (long)j * L.n + i] = mk<T>(T(v.x), T(v.y));
+  const ERdD<V> r{X + c * ldx, L.n, L.m, load_ph<V>(ph, c / cpg)};
+  const cx<V> v = M_x<V>(r, L, i - 1, j) - M_x<V>(r, L, i, j) + M_y<V>(r, L, i, j - 1) - M_y<V>(r, L, i, j);
+  Y[c * ldy + (long)j * L.n + i] = mk<T>(narrow<T>(v.x), narrow<T>(v.y));
 }
 
-// x <- x - L phi
+// x <- x - L phi, in FP64 in every precision policy (it writes the iterate; see
+// k_residual); phi differences of FP32 values are exact in FP64
 template <class T>
 __global__ void k_sub_lift(int n, int m, const double* ph, int cpg, const cx<T>* __restrict__ Phi, long ldp,
                            double2* __restrict__ X, long ldx) {
@@ -193,7 +231,9 @@ constexpr int kGramRows = 16;
 constexpr int kGramAcc = 20;  // accumulators per thread: q(q+1)/2 <= 20 * 256 for q <= 100
 
 __device__ __forceinline__ const double2* role_col(const Roles& R, int g, int a) {
-  return R.b[a / R.pr] + ((long)g * R.pr + a % R.pr) * R.ld;
+  const int r = a / R.pr;  // selects rather than an indexed load keep R out of local memory
+  const double2* base = r == 0 ? R.b[0] : (r == 1 ? R.b[1] : R.b[2]);
+  return base + ((long)g * R.pr + a % R.pr) * R.ld;
 }
 
 __global__ void __launch_bounds__(256) k_gram_fused(Lvl<double> L, Wts<double> w, const double* ph, Roles roles, int q,
@@ -285,6 +325,125 @@ __global__ void __launch_bounds__(256) k_gram_fused(Lvl<double> L, Wts<double> w
   }
 }
 
+// The same partial sums in double-float on the FP32 pipe.  Trial columns are
+// padded to qp = 3 ceil(q/3) and taken in tiles of three; thread (slot, phase)
+// accumulates the 3 x 3 tile `slot` (tiles I <= J, J-major; blockIdx.z selects
+// which 256/P tiles this block holds) of GM and GA over rows phase, phase + P, ...
+// of each staged chunk, with Dot2 accumulators folded once per chunk.  The P
+// phases of a tile sit in one warp and are combined by shuffles in a fixed order.
+constexpr int kGdRows = 16;
+
+__device__ __forceinline__ void mac_conj(acc2& re, acc2& im, const dcx& a, const dcx& b) {
+  // += conj(a) b
+  dot2(re, a.x, b.x);
+  dot2(re, a.y, b.y);
+  dot2(im, a.x, b.y);
+  dot2_neg(im, a.y, b.x);
+}
+
+template <int P>
+__global__ void __launch_bounds__(256) k_gram_df(Lvl<df> L, WtsDF w, const double* ph, Roles roles, int q, int qp,
+                                                 double2* __restrict__ part, int npart) {
+  extern __shared__ float4 smf[];
+  dcx* sx = reinterpret_cast<dcx*>(smf);  // [kGdRows][qp] each
+  dcx* sy = sx + kGdRows * qp;
+  dcx* mx = sy + kGdRows * qp;
+  dcx* my = mx + kGdRows * qp;
+  dcx* cc = my + kGdRows * qp;
+  dcx* cw = cc + kGdRows * qp;
+  const int g = blockIdx.y;
+  const int tid = threadIdx.x;
+  const int T3 = qp / 3, ntile = T3 * (T3 + 1) / 2;
+  const int slot = blockIdx.z * (256 / P) + tid / P, phase = tid % P;
+  const bool active = slot < ntile;
+  int I = 0, J = 0;
+  if (active) {
+    J = int((sqrtf(8.0f * slot + 1.0f) - 1.0f) * 0.5f);
+    while ((J + 1) * (J + 2) / 2 <= slot) ++J;
+    while (J * (J + 1) / 2 > slot) --J;
+    I = slot - J * (J + 1) / 2;
+  }
+  const dcx z = dcx_make(df_zero(), df_zero());
+  for (int t = tid; t < kGdRows * (qp - q); t += blockDim.x) {
+    const int e = (t / (qp - q)) * qp + q + t % (qp - q);
+    sx[e] = z; sy[e] = z; mx[e] = z; my[e] = z; cc[e] = z; cw[e] = z;
+  }
+  acc2 mre[9], mim[9], are[9], aim[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    mre[k] = acc2_zero(); mim[k] = acc2_zero(); are[k] = acc2_zero(); aim[k] = acc2_zero();
+  }
+  const Ph<df> p = load_ph<df>(ph, g);
+  const long N = (long)L.n * L.m;
+  const long nchunks = (N + kGdRows - 1) / kGdRows;
+  for (long ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+    const long r0 = ch * kGdRows;
+    __syncthreads();
+    for (int t = tid; t < q * kGdRows; t += blockDim.x) {
+      const int col = t / kGdRows, rr = t % kGdRows;
+      const long node = r0 + rr;
+      dcx vx = z, vy = z, vmx = z, vmy = z, vc = z, vcw = z;
+      if (node < N) {
+        const int i = int(node % L.n), j = int(node / L.n);
+        const ERdD<df> rd{role_col(roles, g, col), L.n, L.m, p};
+        vx = rd.x(i, j);
+        vy = rd.y(i, j);
+        vmx = M_x<df>(rd, L, i, j);
+        vmy = M_y<df>(rd, L, i, j);
+        vc = curl_at<df>(rd, i, j);
+        vcw = w(i, j) * vc;
+      }
+      const int e = rr * qp + col;
+      sx[e] = vx; sy[e] = vy; mx[e] = vmx; my[e] = vmy; cc[e] = vc; cw[e] = vcw;
+    }
+    __syncthreads();
+    if (active) {
+      for (int rr = phase; rr < kGdRows; rr += P) {
+        const int ra = rr * qp + 3 * I, rb = rr * qp + 3 * J;
+        dcx a[3], b[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) { a[k] = sx[ra + k]; b[k] = mx[rb + k]; }
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+          for (int l = 0; l < 3; ++l) mac_conj(mre[3 * k + l], mim[3 * k + l], a[k], b[l]);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) { a[k] = sy[ra + k]; b[k] = my[rb + k]; }
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+          for (int l = 0; l < 3; ++l) mac_conj(mre[3 * k + l], mim[3 * k + l], a[k], b[l]);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) { a[k] = cc[ra + k]; b[k] = cw[rb + k]; }
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+          for (int l = 0; l < 3; ++l) mac_conj(are[3 * k + l], aim[3 * k + l], a[k], b[l]);
+      }
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+        dot2_fold(mre[k]); dot2_fold(mim[k]); dot2_fold(are[k]); dot2_fold(aim[k]);
+      }
+    }
+  }
+  const int ne = q * (q + 1) / 2;
+  double2* pm = part + ((long)g * npart + blockIdx.x) * 2 * ne;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    df v[4] = {acc2_df(mre[k]), acc2_df(mim[k]), acc2_df(are[k]), acc2_df(aim[k])};
+#pragma unroll
+    for (int o = 1; o < P; o <<= 1)
+#pragma unroll
+      for (int t = 0; t < 4; ++t) v[t] = v[t] + shfl_df(v[t], o);
+    const int a = 3 * I + k / 3, b = 3 * J + k % 3;
+    if (active && phase == 0 && a < q && b < q && a <= b) {
+      const int e = b * (b + 1) / 2 + a;
+      pm[e] = make_double2(df_to(v[0]), df_to(v[1]));
+      pm[ne + e] = make_double2(df_to(v[2]), df_to(v[3]));
+    }
+  }
+}
+
 // sum partials in fixed order; write full Hermitian q x q (column-major) per group
 __global__ void k_gram_finalize(const double2* __restrict__ part, int npart, int q, double2* __restrict__ GM,
                                 double2* __restrict__ GA) {
@@ -328,9 +487,6 @@ constexpr double kDropTol = 1e-12;  // relative pivot below which a trial direct
 constexpr int kRRThreads = 256;
 constexpr int kRRWarps = kRRThreads / 32;
 
-__device__ __forceinline__ df shfl_df(df v, int o) {
-  return df_make(__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o));
-}
 __device__ __forceinline__ df warp_sum_df(df v) {
   for (int o = 16; o > 0; o >>= 1) v = v + shfl_df(v, o);
   return v;
@@ -857,10 +1013,12 @@ void sub_lift(const Level& L, const double* d_ph, int cpg, const cx<T>* Phi, lon
 
 template <class T>
 void lift_adj_mass(const Level& L, const double* d_ph, int cpg, const double2* X, long ldx, cx<T>* Rhs, long ldr,
-                   int ncols, cudaStream_t s) {
+                   int ncols, bool dfa, cudaStream_t s) {
   if (ncols <= 0) return;
   timer_begin(KC_LIFT_ADJ_MASK, s, (16.0 * L.D() + 2.0 * sizeof(T) * L.N()) * ncols);
-  k_lift_adj_mass<T><<<grid2(L.n, L.m, ncols), dim3(kBX, kBY), 0, s>>>(L.lvl<double>(), d_ph, cpg, X, ldx, Rhs, ldr);
+  const dim3 g = grid2(L.n, L.m, ncols);
+  if (dfa) k_lift_adj_mass<df, T><<<g, dim3(kBX, kBY), 0, s>>>(L.lvl<df>(), d_ph, cpg, X, ldx, Rhs, ldr);
+  else k_lift_adj_mass<double, T><<<g, dim3(kBX, kBY), 0, s>>>(L.lvl<double>(), d_ph, cpg, X, ldx, Rhs, ldr);
   timer_end(KC_LIFT_ADJ_MASK, s);
   PBS_LAUNCHED();
 }
@@ -876,10 +1034,14 @@ void deflate_constants(const Level& L, double2* X, long ld, int ncols, const int
 }
 
 void rayleigh_parts(const Level& L, const double* d_ph, int cpg, const double2* X, long ld, int ncols,
-                    double* d_partials, double* d_out, cudaStream_t s) {
+                    double* d_partials, double* d_out, bool dfa, cudaStream_t s) {
   if (ncols <= 0) return;
   const dim3 g = grid2(L.n, L.m, ncols);
-  k_rayleigh_parts<<<g, dim3(kBX, kBY), 0, s>>>(L.lvl<double>(), L.wts<double>(), d_ph, cpg, X, ld, d_partials);
+  if (dfa)
+    k_rayleigh_parts<df><<<g, dim3(kBX, kBY), 0, s>>>(L.lvl<df>(), L.wts_df(), d_ph, cpg, X, ld, d_partials);
+  else
+    k_rayleigh_parts<double><<<g, dim3(kBX, kBY), 0, s>>>(L.lvl<double>(), L.wts<double>(), d_ph, cpg, X, ld,
+                                                         d_partials);
   PBS_LAUNCHED();
   k_finalize2<<<ncols, 256, 0, s>>>(d_partials, g.x * g.y, d_out);
   PBS_LAUNCHED();
@@ -904,23 +1066,44 @@ int gram_partials(long rows, int ngroups) {
   return (int)(chunks < per ? chunks : per);
 }
 
+template <int P> void launch_gram_df(const Level& L, const double* d_ph, Roles roles, int q, int qp, int ngroups,
+                                     int npart, double2* d_partials, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    PBS_CUDA(cudaFuncSetAttribute(k_gram_df<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  6 * kMaxTrial * kGdRows * (int)sizeof(dcx)));
+    attr = true;
+  }
+  const int T3 = qp / 3, ntile = T3 * (T3 + 1) / 2, per = 256 / P;
+  const size_t smem = 6ull * qp * kGdRows * sizeof(dcx);
+  k_gram_df<P><<<dim3(npart, ngroups, (ntile + per - 1) / per), 256, smem, s>>>(L.lvl<df>(), L.wts_df(), d_ph, roles,
+                                                                                q, qp, d_partials, npart);
+}
+
 void gram_groups(const Level& L, const double* d_ph, Roles roles, int q, int ngroups, double2* GM, double2* GA,
-                 double2* d_partials, long partial_capacity, cudaStream_t s) {
+                 double2* d_partials, long partial_capacity, bool dfa, cudaStream_t s) {
   if (q <= 0 || ngroups <= 0) return;
   if (q > kMaxTrial) fail(PBS_EINVAL, "trial block too wide");
   const int npart = gram_partials(L.N(), ngroups);
   const int ne = q * (q + 1) / 2;
   if ((long)ngroups * npart * 2 * ne > partial_capacity) fail(PBS_EINVAL, "gram partials buffer too small");
-  const size_t smem = 6ull * q * kGramRows * sizeof(double2);
-  static bool attr = false;
-  if (!attr) {
-    PBS_CUDA(cudaFuncSetAttribute(k_gram_fused, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  6 * kMaxTrial * kGramRows * (int)sizeof(double2)));
-    attr = true;
-  }
   timer_begin(KC_GRAM, s, 8.0 * ne * 3.0 * L.N() * ngroups);  // flops: three complex MACs per entry and node
-  k_gram_fused<<<dim3(npart, ngroups), 256, smem, s>>>(L.lvl<double>(), L.wts<double>(), d_ph, roles, q, d_partials,
-                                                        npart);
+  if (dfa) {
+    const int qp = 3 * ((q + 2) / 3), T3 = qp / 3, ntile = T3 * (T3 + 1) / 2;
+    if (ntile <= 16) launch_gram_df<16>(L, d_ph, roles, q, qp, ngroups, npart, d_partials, s);
+    else if (ntile <= 32) launch_gram_df<8>(L, d_ph, roles, q, qp, ngroups, npart, d_partials, s);
+    else launch_gram_df<4>(L, d_ph, roles, q, qp, ngroups, npart, d_partials, s);
+  } else {
+    static bool attr = false;
+    if (!attr) {
+      PBS_CUDA(cudaFuncSetAttribute(k_gram_fused, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    6 * kMaxTrial * kGramRows * (int)sizeof(double2)));
+      attr = true;
+    }
+    const size_t smem = 6ull * q * kGramRows * sizeof(double2);
+    k_gram_fused<<<dim3(npart, ngroups), 256, smem, s>>>(L.lvl<double>(), L.wts<double>(), d_ph, roles, q, d_partials,
+                                                          npart);
+  }
   timer_end(KC_GRAM, s);
   PBS_LAUNCHED();
   k_gram_finalize<<<dim3((2 * ne + 255) / 256, ngroups), 256, 0, s>>>(d_partials, npart, q, GM, GA);
@@ -962,15 +1145,15 @@ void block_update(Roles X, int q, const double2* C, int ldc, long cgs, double2* 
                   const double2* Z, long ldz, long rows, int ngroups, cudaStream_t s) {
   if (p <= 0 || rows <= 0 || ngroups <= 0) return;
   if (p > kMaxBlock) fail(PBS_EINVAL, "block_update: p too large");
-  const size_t smem = (size_t)p * q * sizeof(double2);
+  long per = blocks_for(rows, 256, 2 * 152 * 4);
+  per = std::max<long>(1, per / ngroups);
   static bool attr = false;
   if (!attr) {
     PBS_CUDA(cudaFuncSetAttribute(k_block_update, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   kMaxBlock * kMaxTrial * (int)sizeof(double2)));
     attr = true;
   }
-  long per = blocks_for(rows, 256, 2 * 152 * 4);
-  per = std::max<long>(1, per / ngroups);
+  const size_t smem = (size_t)p * q * sizeof(double2);
   timer_begin(KC_BLOCK_UPDATE, s, 8.0 * q * p * rows * ngroups);  // flops
   k_block_update<<<dim3((unsigned)per, ngroups), 256, smem, s>>>(X, q, C, ldc, cgs, Y, ldy, p, Z, ldz, rows);
   timer_end(KC_BLOCK_UPDATE, s);
@@ -1039,11 +1222,13 @@ extern "C" int pbs_small_rr_noalloc(const pbs_c64* GM, const pbs_c64* GA, int q,
 
 namespace pbs {
 
-template void sub_lift<double>(const Level&, const double*, int, const double2*, long, double2*, long, int, cudaStream_t);
-template void sub_lift<float>(const Level&, const double*, int, const float2*, long, double2*, long, int, cudaStream_t);
-template void lift_adj_mass<double>(const Level&, const double*, int, const double2*, long, double2*, long, int,
+template void sub_lift<double>(const Level&, const double*, int, const double2*, long, double2*, long, int,
+                               cudaStream_t);
+template void sub_lift<float>(const Level&, const double*, int, const float2*, long, double2*, long, int,
+                              cudaStream_t);
+template void lift_adj_mass<double>(const Level&, const double*, int, const double2*, long, double2*, long, int, bool,
                                     cudaStream_t);
-template void lift_adj_mass<float>(const Level&, const double*, int, const double2*, long, float2*, long, int,
+template void lift_adj_mass<float>(const Level&, const double*, int, const double2*, long, float2*, long, int, bool,
                                    cudaStream_t);
 
 }  // namespace pbs

@@ -13,6 +13,9 @@ namespace pbs {
 
 struct df {
   float hi, lo;
+  df() = default;
+  // rounding of a double to hi + lo; meant for constants (folded at compile time)
+  __host__ __device__ constexpr explicit df(double d) : hi((float)d), lo((float)(d - (double)(float)d)) {}
 };
 
 __device__ __forceinline__ df df_make(float h, float l) {
@@ -88,6 +91,95 @@ __device__ __forceinline__ df df_sqrt(df a) {
 __device__ __forceinline__ bool df_lt(df a, df b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
 __device__ __forceinline__ df df_abs(df a) { return a.hi < 0.0f ? -a : a; }
 __device__ __forceinline__ df df_zero() { return df_make(0.0f, 0.0f); }
+
+// FP64 -> df with integer operations only (no FP64 instruction): hi keeps the
+// leading 24 significand bits of d (truncated), lo the next 24 rounded to nearest,
+// so |d - (hi + lo)| <= 2^-47 |d|.  Magnitudes below 2^-100 give 0; magnitudes of
+// 2^127 and above (and inf / NaN) take the FP64 conversion, which keeps them.
+__device__ __forceinline__ df df_split(double d) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(d);
+  const unsigned hw = (unsigned)(u >> 32), lw = (unsigned)u;
+  const int e = (int)((hw >> 20) & 0x7FFu) - 1023;
+  if (e < -100) return df_make(0.0f, 0.0f);
+  if (e > 126) return df_make((float)d, 0.0f);
+  const unsigned sgn = hw & 0x80000000u;
+  const float hi = __uint_as_float(sgn | ((unsigned)(e + 127) << 23) | ((hw & 0xFFFFFu) << 3) | (lw >> 29));
+  // the remaining 29 bits r scaled by 2^(e-52): round to 23 bits and place them under
+  // the implicit bit of 2^(e-23); a carry out of the 23 bits moves into the exponent,
+  // which is still the right value.  The subtraction is exact (Sterbenz).
+  const unsigned base = sgn | ((unsigned)(e + 104) << 23);
+  const unsigned r = lw & 0x1FFFFFFFu;
+  const float lo = __fsub_rn(__uint_as_float(base + ((r + 32u) >> 6)), __uint_as_float(base));
+  return quick_two_sum(hi, lo);
+}
+
+// Streaming arithmetic: a + b with one two-sum on the leading parts and a plain
+// float sum of the trailing parts; its error is about 2^-47 (|a| + |b|), which is
+// the measure every stencil and block kernel needs (errors relative to the
+// vectors' norms, not to a cancelled result).
+__device__ __forceinline__ df dfs_add(df a, df b) {
+  df s = two_sum(a.hi, b.hi);
+  s.lo = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
+  return quick_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ df dfs_sub(df a, df b) { return dfs_add(a, df_make(-b.hi, -b.lo)); }
+__device__ __forceinline__ float df_to_float(df a) { return __fadd_rn(a.hi, a.lo); }
+
+// Complex value of the streaming kernels (members x = re, y = im, like float2 /
+// double2, so the templated stencils instantiate with it).
+struct dcx {
+  df x, y;
+};
+__device__ __forceinline__ dcx dcx_make(df r, df i) {
+  dcx z;
+  z.x = r;
+  z.y = i;
+  return z;
+}
+__device__ __forceinline__ dcx operator+(dcx a, dcx b) { return dcx_make(dfs_add(a.x, b.x), dfs_add(a.y, b.y)); }
+__device__ __forceinline__ dcx operator-(dcx a, dcx b) { return dcx_make(dfs_sub(a.x, b.x), dfs_sub(a.y, b.y)); }
+__device__ __forceinline__ dcx operator-(dcx a) { return dcx_make(-a.x, -a.y); }
+__device__ __forceinline__ dcx operator*(df s, dcx a) { return dcx_make(s * a.x, s * a.y); }
+__device__ __forceinline__ dcx cmul(dcx a, dcx b) {
+  return dcx_make(dfs_sub(a.x * b.x, a.y * b.y), dfs_add(a.x * b.y, a.y * b.x));
+}
+__device__ __forceinline__ dcx conj(dcx a) { return dcx_make(a.x, -a.y); }
+__device__ __forceinline__ df nrm2(dcx a) { return dfs_add(a.x * a.x, a.y * a.y); }
+__device__ __forceinline__ dcx dcx_split(double2 v) { return dcx_make(df_split(v.x), df_split(v.y)); }
+__device__ __forceinline__ double2 dcx_to(dcx v) { return make_double2(df_to(v.x), df_to(v.y)); }
+
+// Compensated dot-product accumulator (the Dot2 scheme of Ogita, Rump and Oishi,
+// 2005, with df operands): s collects the leading products by two-sums, c the
+// rounding errors of those sums and products and the cross terms with the
+// trailing parts.  s + c carries about twice the float precision as long as c is
+// folded back (dot2_fold) every few dozen terms.
+struct acc2 {
+  float s, c;
+};
+__device__ __forceinline__ acc2 acc2_zero() {
+  acc2 a;
+  a.s = 0.0f;
+  a.c = 0.0f;
+  return a;
+}
+// a += x * y
+__device__ __forceinline__ void dot2(acc2& a, df x, df y) {
+  const float p = __fmul_rn(x.hi, y.hi);
+  const float pe = __fmaf_rn(x.hi, y.hi, -p);
+  const float t = __fadd_rn(a.s, p);
+  const float z = __fsub_rn(t, a.s);
+  const float se = __fadd_rn(__fsub_rn(a.s, __fsub_rn(t, z)), __fsub_rn(p, z));
+  a.s = t;
+  a.c = __fmaf_rn(x.hi, y.lo, __fmaf_rn(x.lo, y.hi, __fadd_rn(a.c, __fadd_rn(pe, se))));
+}
+// a -= x * y
+__device__ __forceinline__ void dot2_neg(acc2& a, df x, df y) { dot2(a, df_make(-x.hi, -x.lo), y); }
+__device__ __forceinline__ void dot2_fold(acc2& a) {
+  const df r = two_sum(a.s, a.c);
+  a.s = r.hi;
+  a.c = r.lo;
+}
+__device__ __forceinline__ df acc2_df(acc2 a) { return two_sum(a.s, a.c); }
 
 // complex double-float
 struct cdf {

@@ -35,7 +35,9 @@ struct Level {
   float* winv32 = nullptr;
   double* k3_64 = nullptr;   // per node: 6 entries of the inverse 3x3 patch block, SoA [6][N]
   float* k3_32 = nullptr;
+  float2* wdf = nullptr;     // level 0: w = (1/eps) / (h1 h2) as double-float (hi, lo) per cell
   long N() const { return (long)n * m; }
+  WtsDF wts_df() const { return WtsDF{wdf, n, m}; }
   long D() const { return 2L * n * m; }
   template <class T> Lvl<T> lvl() const { return Lvl<T>{n, m, T(h2 / h1), T(h1 / h2)}; }
   template <class T> Wts<T> wts() const;
@@ -190,6 +192,12 @@ void nodal_vcycle(const Hierarchy& H, const KData& K, MgWork<T>& w, int l0, cons
                   int ncols, int cpg, int nu_pre, int nu_post, cudaStream_t s);
 
 // ---- dense block kernels (dense.cu) ---------------------------------------
+// Every kernel below reads and writes FP64 blocks.  Where a `dfa` flag is given it
+// selects the arithmetic: false = FP64, true = double-float on the FP32 pipe
+// (about 2^-47 relative; the mixed-precision policy).  Kernels that write the
+// iterate or difference it through the curl-curl stencil (residual, block update,
+// x - L phi) have no flag: a relative perturbation eta of the iterate moves the
+// relative residual by about eta lambda_max / lambda, so they stay in FP64.
 void convert_d2f(const double2* X, float2* Y, long n, cudaStream_t s);
 void convert_f2d(const float2* X, double2* Y, long n, cudaStream_t s);
 // x <- x - L phi (FP64 x, phi in T), level 0
@@ -199,14 +207,14 @@ void sub_lift(const Level& L, const double* d_ph, int cpg, const cx<T>* Phi, lon
 // rhs = L^* M x  (FP64), stored in T
 template <class T>
 void lift_adj_mass(const Level& L, const double* d_ph, int cpg, const double2* X, long ldx, cx<T>* Rhs, long ldr,
-                   int ncols, cudaStream_t s);
+                   int ncols, bool dfa, cudaStream_t s);
 // subtract the x-edge mean and the y-edge mean of every column of a k = 0 group
 // (flags d_gamma[c / cpg]; the deflation of the two constant fields)
 void deflate_constants(const Level& L, double2* X, long ld, int ncols, const int* d_gamma, int cpg,
                        double* d_partials, cudaStream_t s);
 // per column: out[2c] = e^* M e, out[2c+1] = (C e)^* W (C e)
 void rayleigh_parts(const Level& L, const double* d_ph, int cpg, const double2* X, long ld, int ncols,
-                    double* d_partials, double* d_out, cudaStream_t s);
+                    double* d_partials, double* d_out, bool dfa, cudaStream_t s);
 // R = A E - lam M E; per column out[2c] = |R|^2, out[2c+1] = |M E|^2
 void residual(const Level& L, const double* d_ph, int cpg, const double2* E, double2* R, long ld, int ncols,
               const double* d_lam, double* d_partials, double* d_out, cudaStream_t s);
@@ -220,7 +228,7 @@ struct Roles {
 // Per group g (phases from entry g of d_ph): GM_g = S^* M S, GA_g = (C S)^* W (C S), q x q
 // column-major at GM + g q^2, GA + g q^2.
 void gram_groups(const Level& L, const double* d_ph, Roles roles, int q, int ngroups, double2* GM, double2* GA,
-                 double2* d_partials, long partial_capacity, cudaStream_t s);
+                 double2* d_partials, long partial_capacity, bool dfa, cudaStream_t s);
 long gram_partials_size(long rows, int q, int ngroups);  // double2 elements
 // Rayleigh-Ritz in coefficient space for ngroups groups: C (q x p per group), theta (p per
 // group), status in d_info[8 g], scratch small_rr_scratch(q) bytes per group

@@ -39,6 +39,14 @@ namespace {
 constexpr int kBX = 32, kBY = 8;
 constexpr int kColours[4][2] = {{0, 0}, {1, 0}, {0, 1}, {1, 1}};
 
+// w = (1/eps) / (h1 h2) as a double-float pair per cell
+__global__ void k_weights_df(const double* __restrict__ winv, double scale, float2* __restrict__ w, long N) {
+  const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (t >= N) return;
+  const df v = df_from(scale * winv[t]);
+  w[t] = make_float2(v.hi, v.lo);
+}
+
 __global__ void k_inv_eps(const double* __restrict__ eps, double* __restrict__ w64, float* __restrict__ w32, long N,
                           int* __restrict__ bad) {
   const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
@@ -314,6 +322,12 @@ void build_hierarchy(DevMem& mem, Hierarchy& H, const double* d_eps, int coarses
                                                                                            L.winv32, n, m);
     }
     PBS_LAUNCHED();
+    if (l == 0) {
+      L.wdf = (float2*)mem.alloc(N * sizeof(float2));
+      H.allocs.push_back(L.wdf);
+      k_weights_df<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(L.winv64, 1.0 / (L.h1 * L.h2), L.wdf, N);
+      PBS_LAUNCHED();
+    }
     const double m1 = 2.0 / 3.0 * L.h2 / L.h1, m2 = 2.0 / 3.0 * L.h1 / L.h2;
     k_patch_factors<<<dim3((n + kBX - 1) / kBX, (m + kBY - 1) / kBY), dim3(kBX, kBY), 0, s>>>(
         L.winv64, n, m, 1.0 / (L.h1 * L.h2), m1, m2, H.mu, L.k3_64, L.k3_32);

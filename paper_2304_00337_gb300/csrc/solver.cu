@@ -410,7 +410,8 @@ void project(pbs_ctx* ctx, const pbs_opts& o, const KData& K, double2* X, int nc
   cx<T>* phi = (cx<T>*)Bufs<T>::nx(W);
   cx<T>* res = (cx<T>*)Bufs<T>::nr(W);
   cx<T>* dphi = (cx<T>*)Bufs<T>::nd(W);
-  lift_adj_mass<T>(L0, K.d_ph, cpg, X, D, rhs, N, ncols, s);
+  const bool dfa = o.precision == PBS_MIXED;
+  lift_adj_mass<T>(L0, K.d_ph, cpg, X, D, rhs, N, ncols, dfa, s);
   nodal_vcycle<T>(H, K, Bufs<T>::nmg(W), 0, rhs, phi, N, ncols, cpg, o.nu_pre, o.nu_post, s);
   for (int c = 1; c < cycles; ++c) {
     apply_nodal<T>(L0, K.d_ph, cpg, phi, res, rhs, N, ncols, T(-1), T(1), s);
@@ -455,11 +456,12 @@ int projection_cycles(const pbs_opts& o, double theta_max, double mu) {
 
 // Rayleigh-Ritz of one group's pencil (view Kv) on the q contiguous columns S:
 // the p lowest Ritz vectors go to dst; returns the largest |theta|.
-double rr_single(pbs_ctx* ctx, const KData& Kv, const double2* S, int q, int p, double2* dst, cudaStream_t s) {
+double rr_single(pbs_ctx* ctx, const KData& Kv, const double2* S, int q, int p, double2* dst, bool dfa,
+                 cudaStream_t s) {
   Work& W = ctx->W;
   const Level& L0 = ctx->H.lev[0];
   const Roles R{{S, S, S}, q, W.D};
-  gram_groups(L0, Kv.d_ph, R, q, 1, W.GM, W.GA, W.gpart, W.gpart_cap, s);
+  gram_groups(L0, Kv.d_ph, R, q, 1, W.GM, W.GA, W.gpart, W.gpart_cap, dfa, s);
   small_rr(W.GM, W.GA, q, p, W.C, W.theta, W.rr_scr, W.info, 1, s);
   int info[2] = {0, 0};
   std::vector<double> th(p);
@@ -502,7 +504,7 @@ void init_group(pbs_ctx* ctx, const pbs_opts& o, Group& gr, int g, const pbs_c64
     PBS_CUDA(cudaMemcpyAsync(W.init, W.hist + (long)g * 3 * p * D, sizeof(double2) * D * q, cudaMemcpyDeviceToDevice,
                              s));
     project_dispatch(ctx, o, Kv, W.init, q, q, projection_cycles(o, gr.theta_max, ctx->H.mu), s);
-    tm = rr_single(ctx, Kv, W.init, q, p, Eg, s);
+    tm = rr_single(ctx, Kv, W.init, q, p, Eg, o.precision == PBS_MIXED, s);
   } else {
     double2* X0 = W.init;           // p columns
     double2* X1 = W.init + D * p;   // p columns
@@ -513,13 +515,13 @@ void init_group(pbs_ctx* ctx, const pbs_opts& o, Group& gr, int g, const pbs_c64
     // Rayleigh-Ritz) damp the high frequencies before the iteration starts.
     const int cyc = projection_cycles(o, 1e300, ctx->H.mu);
     project_dispatch(ctx, o, Kv, X0, p, p, cyc, s);
-    rr_single(ctx, Kv, X0, p, p, X1, s);
+    rr_single(ctx, Kv, X0, p, p, X1, o.precision == PBS_MIXED, s);
     double2* Rg = W.R + (long)g * p * D;
     for (int step = 0; step < 2; ++step) {
       apply_edge<double>(ctx->H.lev[0], Kv.d_ph, p, X1, Rg, nullptr, D, p, 0.0, 1.0, 0.0, nullptr, 0.0, s);
       precondition_dispatch(ctx, o, Kv, Rg, X0, p, p, s);
       project_dispatch(ctx, o, Kv, X0, p, p, cyc, s);
-      tm = rr_single(ctx, Kv, X0, p, p, step == 1 ? Eg : X1, s);
+      tm = rr_single(ctx, Kv, X0, p, p, step == 1 ? Eg : X1, o.precision == PBS_MIXED, s);
     }
   }
   PBS_CUDA(cudaMemsetAsync(Pg, 0, sizeof(double2) * D * p, s));
@@ -542,6 +544,7 @@ struct PathResult {
 // k of its chain while the other groups keep iterating.
 PathResult solve_chains(pbs_ctx* ctx, const pbs_opts& o, int nk, const double* ks, int nchains, const pbs_c64* init) {
   cudaStream_t s = ctx->stream;
+  const bool dfa = o.precision == PBS_MIXED;
   const int p = o.block, G = std::max(1, std::min(nchains, nk));
   alloc_kdata(ctx->mem, ctx->H, ctx->K, G);
   ensure_work(ctx, p, G);
@@ -576,7 +579,7 @@ PathResult solve_chains(pbs_ctx* ctx, const pbs_opts& o, int nk, const double* k
     // so E and P are cleaned before the residual (Section 4, null-space elimination)
     if (round > 0) project_dispatch(ctx, o, ctx->K, W.E(), 2 * (int)Gp, p, cyc, s);
     // Rayleigh quotients in factored form, then the FP64 residual
-    rayleigh_parts(L0, ctx->K.d_ph, p, W.E(), D, (int)Gp, W.parts, W.rq, s);
+    rayleigh_parts(L0, ctx->K.d_ph, p, W.E(), D, (int)Gp, W.parts, W.rq, dfa, s);
     k_rq<<<nblocks(Gp), 256, 0, s>>>(W.rq, W.lam, (int)Gp);
     PBS_LAUNCHED();
     residual(L0, ctx->K.d_ph, p, W.E(), W.R, D, (int)Gp, W.lam, W.parts, W.norms, s);
@@ -651,7 +654,7 @@ PathResult solve_chains(pbs_ctx* ctx, const pbs_opts& o, int nk, const double* k
       // exists, and always for span 2, so its columns are dropped) or [E_hat] (span 1)
       const Roles trial = o.span == 1 ? Roles{{Wd, Wd, Wd}, p, D} : Roles{{W.E(), W.P(), W.W()}, p, D};
       const int qt = o.span == 1 ? p : q;
-      gram_groups(L0, ctx->K.d_ph, trial, qt, G, W.GM, W.GA, W.gpart, W.gpart_cap, s);
+      gram_groups(L0, ctx->K.d_ph, trial, qt, G, W.GM, W.GA, W.gpart, W.gpart_cap, dfa, s);
       small_rr(W.GM, W.GA, qt, p, W.C, W.theta, W.rr_scr, W.info, G, s);
       PBS_CUDA(cudaMemcpyAsync(h_info.data(), W.info, sizeof(int) * 8 * G, cudaMemcpyDeviceToHost, s));
       PBS_CUDA(cudaStreamSynchronize(s));
@@ -666,7 +669,7 @@ PathResult solve_chains(pbs_ctx* ctx, const pbs_opts& o, int nk, const double* k
         const Roles tg{{W.E() + (long)g * p * D, W.P() + (long)g * p * D, W.W() + (long)g * p * D}, p, D};
         double2* GMg = W.GM + (long)g * q * q;
         double2* GAg = W.GA + (long)g * q * q;
-        gram_groups(L0, Kv.d_ph, tg, q, 1, GMg, GAg, W.gpart, W.gpart_cap, s);
+        gram_groups(L0, Kv.d_ph, tg, q, 1, GMg, GAg, W.gpart, W.gpart_cap, dfa, s);
         small_rr(GMg, GAg, q, p, W.C + (long)g * q * p, W.theta + (long)g * q, W.rr_scr, W.info + 8 * g, 1, s);
         int inf2[2];
         PBS_CUDA(cudaMemcpyAsync(inf2, W.info + 8 * g, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -825,7 +828,8 @@ int pbs_solve_k(pbs_ctx* ctx, const pbs_geom* geom, const pbs_opts* opts, const 
       // M-normalise the returned columns
       Work& W = ctx->W;
       std::vector<double> rq(2 * o.block), sc(o.block);
-      rayleigh_parts(ctx->H.lev[0], ctx->K.d_ph, o.block, W.E(), W.D, o.block, W.parts, W.rq, ctx->stream);
+      rayleigh_parts(ctx->H.lev[0], ctx->K.d_ph, o.block, W.E(), W.D, o.block, W.parts, W.rq, o.precision == PBS_MIXED,
+                     ctx->stream);
       PBS_CUDA(cudaMemcpyAsync(rq.data(), W.rq, 2 * o.block * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
       PBS_CUDA(cudaStreamSynchronize(ctx->stream));
       for (int j = 0; j < o.block; ++j) sc[j] = 1.0 / std::sqrt(rq[2 * j]);
@@ -1015,8 +1019,9 @@ int pbs_apply(pbs_ctx* ctx, const pbs_geom* geom, const pbs_opts* opts, int op, 
 }
 
 int pbs_gram(pbs_ctx* ctx, const pbs_geom* geom, const double k[2], int q, const pbs_c64* S, pbs_c64* GM, pbs_c64* GA,
-             void* cuda_stream) {
+             int precision, void* cuda_stream) {
   if (!ctx || !geom || !k || q < 0 || q > kMaxTrial) return PBS_EINVAL;
+  if (precision != PBS_FP64 && precision != PBS_MIXED) return PBS_EINVAL;
   if (q > 0 && (!S || !GM || !GA)) return PBS_EINVAL;
   return run_guarded_impl([&] {
     DeviceGuard g(ctx->device);
@@ -1037,7 +1042,7 @@ int pbs_gram(pbs_ctx* ctx, const pbs_geom* geom, const double k[2], int q, const
     double2* part = (double2*)ctx->mem.alloc(sizeof(double2) * cap);
     try {
       const Roles R{{(const double2*)S, (const double2*)S, (const double2*)S}, q, L0.D()};
-      gram_groups(L0, ctx->K.d_ph, R, q, 1, (double2*)GM, (double2*)GA, part, cap, s);
+      gram_groups(L0, ctx->K.d_ph, R, q, 1, (double2*)GM, (double2*)GA, part, cap, precision == PBS_MIXED, s);
       PBS_CUDA(cudaStreamSynchronize(s));
     } catch (...) {
       ctx->mem.free(part);
@@ -1071,7 +1076,7 @@ int pbs_rayleigh_ritz(pbs_ctx* ctx, const pbs_geom* geom, const pbs_opts* opts, 
     PBS_CUDA(cudaMemcpyAsync(W.init, S, sizeof(double2) * W.D * q, cudaMemcpyDeviceToDevice, s));
     const KData Kv = kdata_view(ctx->K, 0);
     if (project) project_dispatch(ctx, o, Kv, W.init, q, q, o.nodal_cycles, s);
-    rr_single(ctx, Kv, W.init, q, p, (double2*)X, s);
+    rr_single(ctx, Kv, W.init, q, p, (double2*)X, o.precision == PBS_MIXED, s);
     PBS_CUDA(cudaMemcpyAsync(theta, W.theta, sizeof(double) * p, cudaMemcpyDeviceToHost, s));
     PBS_CUDA(cudaStreamSynchronize(s));
   });

@@ -158,8 +158,9 @@ def test_projection_matches_reference(ctx, a, b, n, m, k, cycles):
     assert _rel(got32, want) <= 1e-5
 
 
+@pytest.mark.parametrize("precision", [pbs.PBS_FP64, pbs.PBS_MIXED])
 @pytest.mark.parametrize("a,b,n,m,k", [CASES[1], CASES[2]])
-def test_gram_matches_oracle(ctx, a, b, n, m, k):
+def test_gram_matches_oracle(ctx, a, b, n, m, k, precision):
     eps = _eps(n, m)
     geom = pbs.Geometry(eps, a, b)
     ops = fem.assemble(fem.Mesh(a, b, n, m), eps, k)
@@ -168,17 +169,22 @@ def test_gram_matches_oracle(ctx, a, b, n, m, k):
     Sd = _dev(S)
     GM = torch.zeros((q, q), dtype=torch.complex128, device="cuda")
     GA = torch.zeros((q, q), dtype=torch.complex128, device="cuda")
-    ctx.gram(geom, k, q, Sd.data_ptr(), GM.data_ptr(), GA.data_ptr(), torch.cuda.current_stream())
+    ctx.gram(geom, k, q, Sd.data_ptr(), GM.data_ptr(), GA.data_ptr(), torch.cuda.current_stream(),
+             precision=precision)
     torch.cuda.synchronize()
     gm = GM.cpu().numpy().T  # column-major on the device
     ga = GA.cpu().numpy().T
     wm, wa = ex.grams(ops, S.T)
+    # FP64: rounding ~1e-16 per term; double-float: inputs split to 2^-47 relative,
+    # stencils and compensated sums add a few units of that
     assert np.abs(gm - wm).max() <= 1e-13 * np.abs(wm).max()
     assert np.abs(ga - wa).max() <= 1e-13 * np.abs(wa).max()
+    assert np.array_equal(gm, gm.conj().T) and np.array_equal(ga, ga.conj().T)
 
 
+@pytest.mark.parametrize("precision", [pbs.PBS_FP64, pbs.PBS_MIXED])
 @pytest.mark.parametrize("k", [(0.3, 0.1), (0.0, 0.0)])
-def test_rayleigh_ritz_and_extrapolation(ctx, k):
+def test_rayleigh_ritz_and_extrapolation(ctx, k, precision):
     n = 16
     eps = gi.rod_eps(n, n)
     geom = pbs.Geometry(eps)
@@ -190,7 +196,7 @@ def test_rayleigh_ritz_and_extrapolation(ctx, k):
     X = torch.zeros((6, geom.D), dtype=torch.complex128, device="cuda")
     # plain Rayleigh-Ritz on the span
     th_want, _ = ex.rayleigh_ritz(ops, S, 6)
-    th = ctx.rayleigh_ritz(geom, pbs.default_opts(precision=pbs.PBS_FP64), k, 12, Sd.data_ptr(), 6, False,
+    th = ctx.rayleigh_ritz(geom, pbs.default_opts(precision=precision), k, 12, Sd.data_ptr(), 6, False,
                            X.data_ptr(), torch.cuda.current_stream())
     assert np.allclose(th, th_want, rtol=1e-11)
     Xh = X.cpu().numpy().T
@@ -199,9 +205,11 @@ def test_rayleigh_ritz_and_extrapolation(ctx, k):
     assert np.allclose(np.real(np.diag(GA)), th_want, rtol=1e-10)
     # extrapolation: projection off the gradients first (Section 6)
     th_want, _ = ex.extrapolate(ops, prev, 6)
-    th = ctx.rayleigh_ritz(geom, pbs.default_opts(precision=pbs.PBS_FP64, nodal_cycles=14), k, 12, Sd.data_ptr(), 6,
+    th = ctx.rayleigh_ritz(geom, pbs.default_opts(precision=precision, nodal_cycles=14), k, 12, Sd.data_ptr(), 6,
                            True, X.data_ptr(), torch.cuda.current_stream())
-    assert np.allclose(th, th_want, rtol=1e-10)
+    # mixed: the nodal cycles run in FP32 and leave ~1e-7 of the gradient part,
+    # which moves the Ritz values at second order
+    assert np.allclose(th, th_want, rtol=1e-10 if precision == pbs.PBS_FP64 else 1e-9)
 
 
 def test_empty_and_invalid_calls(ctx):
@@ -261,7 +269,8 @@ def test_max_size_operators_on_plane_waves(ctx):
     assert (torch.linalg.vector_norm(ag) / torch.linalg.vector_norm(g)).item() < 1e-12 * 8 / h ** 2
 
 
-def test_rayleigh_ritz_drops_dependent_directions(ctx):
+@pytest.mark.parametrize("precision", [pbs.PBS_FP64, pbs.PBS_MIXED])
+def test_rayleigh_ritz_drops_dependent_directions(ctx, precision):
     # a span given twice (second copy mixed by a random matrix) has rank 6: the
     # Cholesky step must drop the dependent half and return the Ritz pairs of the span
     n = 16
@@ -276,6 +285,6 @@ def test_rayleigh_ritz_drops_dependent_directions(ctx):
     want, _ = ex.rayleigh_ritz(ops, V, 6)
     Sd = _dev(S.T)
     X = torch.zeros((6, geom.D), dtype=torch.complex128, device="cuda")
-    th = ctx.rayleigh_ritz(geom, pbs.default_opts(precision=pbs.PBS_FP64), k, 12, Sd.data_ptr(), 6, False,
+    th = ctx.rayleigh_ritz(geom, pbs.default_opts(precision=precision), k, 12, Sd.data_ptr(), 6, False,
                            X.data_ptr(), torch.cuda.current_stream())
     assert np.allclose(th, want, rtol=1e-9)
