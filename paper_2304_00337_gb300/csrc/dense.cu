@@ -956,6 +956,61 @@ __global__ void __launch_bounds__(256) k_block_update(Roles X, int q, const doub
   }
 }
 
+// The same product in double-float (compensated Dot2 sums, folded every 8 trial
+// columns; PB >= p accumulator pairs per thread).  Used for the search direction
+// P = [P, W] C only: its rounding, 2^-47 |P|, reaches the iterate through
+// E C + P, where it is 2^-47 |P| / |E| relative, far below the FP64 rounding of
+// E C once the steps have become small.
+template <int PB>
+__global__ void __launch_bounds__(256) k_block_update_df(Roles X, int q, const double2* __restrict__ C, int ldc,
+                                                         long cgs, double2* __restrict__ Y, long ldy, int p,
+                                                         const double2* __restrict__ Z, long ldz, long rows) {
+  extern __shared__ float4 csf[];
+  dcx* cs = reinterpret_cast<dcx*>(csf);  // [p][q]
+  const int g = blockIdx.y;
+  const double2* Cg = C + g * cgs;
+  for (int t = threadIdx.x; t < p * q; t += blockDim.x) cs[t] = dcx_split(Cg[(long)(t / q) * ldc + (t % q)]);
+  __syncthreads();
+  double2* Yg = Y + (long)g * p * ldy;
+  const double2* Zg = Z ? Z + (long)g * p * ldz : nullptr;
+  for (long r = blockIdx.x * (long)blockDim.x + threadIdx.x; r < rows; r += (long)gridDim.x * blockDim.x) {
+    acc2 re[PB], im[PB];
+#pragma unroll
+    for (int j = 0; j < PB; ++j) {
+      re[j] = acc2_zero();
+      im[j] = acc2_zero();
+    }
+    for (int i = 0; i < q; ++i) {
+      const dcx x = dcx_split(role_col(X, g, i)[r]);
+#pragma unroll
+      for (int j = 0; j < PB; ++j) {
+        if (j < p) {
+          const dcx c = cs[j * q + i];
+          dot2(re[j], x.x, c.x);
+          dot2_neg(re[j], x.y, c.y);
+          dot2(im[j], x.x, c.y);
+          dot2(im[j], x.y, c.x);
+        }
+      }
+      if ((i & 7) == 7) {
+#pragma unroll
+        for (int j = 0; j < PB; ++j) {
+          dot2_fold(re[j]);
+          dot2_fold(im[j]);
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < PB; ++j) {
+      if (j < p) {
+        dcx v = dcx_make(acc2_df(re[j]), acc2_df(im[j]));
+        if (Zg) v = v + dcx_split(Zg[(long)j * ldz + r]);
+        Yg[(long)j * ldy + r] = dcx_to(v);
+      }
+    }
+  }
+}
+
 __device__ __forceinline__ uint64_t mix64(uint64_t z) {
   z += 0x9e3779b97f4a7c15ull;
   z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
@@ -1141,21 +1196,39 @@ void small_rr(const double2* GM, const double2* GA, int q, int p, double2* C, do
   }
 }
 
+template <int PB> void launch_update_df(Roles X, int q, const double2* C, int ldc, long cgs, double2* Y, long ldy,
+                                        int p, const double2* Z, long ldz, long rows, dim3 grid, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    PBS_CUDA(cudaFuncSetAttribute(k_block_update_df<PB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  kMaxBlock * kMaxTrial * (int)sizeof(dcx)));
+    attr = true;
+  }
+  k_block_update_df<PB><<<grid, 256, (size_t)p * q * sizeof(dcx), s>>>(X, q, C, ldc, cgs, Y, ldy, p, Z, ldz, rows);
+}
+
 void block_update(Roles X, int q, const double2* C, int ldc, long cgs, double2* Y, long ldy, int p,
-                  const double2* Z, long ldz, long rows, int ngroups, cudaStream_t s) {
+                  const double2* Z, long ldz, long rows, int ngroups, bool dfa, cudaStream_t s) {
   if (p <= 0 || rows <= 0 || ngroups <= 0) return;
   if (p > kMaxBlock) fail(PBS_EINVAL, "block_update: p too large");
   long per = blocks_for(rows, 256, 2 * 152 * 4);
   per = std::max<long>(1, per / ngroups);
-  static bool attr = false;
-  if (!attr) {
-    PBS_CUDA(cudaFuncSetAttribute(k_block_update, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  kMaxBlock * kMaxTrial * (int)sizeof(double2)));
-    attr = true;
-  }
-  const size_t smem = (size_t)p * q * sizeof(double2);
+  const dim3 grid((unsigned)per, ngroups);
   timer_begin(KC_BLOCK_UPDATE, s, 8.0 * q * p * rows * ngroups);  // flops
-  k_block_update<<<dim3((unsigned)per, ngroups), 256, smem, s>>>(X, q, C, ldc, cgs, Y, ldy, p, Z, ldz, rows);
+  if (dfa) {
+    if (p <= 8) launch_update_df<8>(X, q, C, ldc, cgs, Y, ldy, p, Z, ldz, rows, grid, s);
+    else if (p <= 16) launch_update_df<16>(X, q, C, ldc, cgs, Y, ldy, p, Z, ldz, rows, grid, s);
+    else launch_update_df<32>(X, q, C, ldc, cgs, Y, ldy, p, Z, ldz, rows, grid, s);
+  } else {
+    static bool attr = false;
+    if (!attr) {
+      PBS_CUDA(cudaFuncSetAttribute(k_block_update, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    kMaxBlock * kMaxTrial * (int)sizeof(double2)));
+      attr = true;
+    }
+    const size_t smem = (size_t)p * q * sizeof(double2);
+    k_block_update<<<grid, 256, smem, s>>>(X, q, C, ldc, cgs, Y, ldy, p, Z, ldz, rows);
+  }
   timer_end(KC_BLOCK_UPDATE, s);
   PBS_LAUNCHED();
 }

@@ -98,7 +98,7 @@ int num_levels(int n, int m, int coarsest);
 // flops for arithmetic-bound ones) so the achieved rate can be derived.
 enum KernelClass {
   KC_NONE = 0, KC_EDGE_SMOOTH, KC_NODE_SMOOTH, KC_GRAM, KC_SMALL_RR, KC_RESIDUAL, KC_BLOCK_UPDATE,
-  KC_LIFT_ADJ_MASK, KC_EDGE_APPLY, KC_COUNT
+  KC_LIFT_ADJ_MASK, KC_EDGE_APPLY, KC_EDGE_TAIL, KC_NODE_TAIL, KC_COUNT
 };
 struct TimedLaunch {
   int cls;
@@ -194,10 +194,10 @@ void nodal_vcycle(const Hierarchy& H, const KData& K, MgWork<T>& w, int l0, cons
 // ---- dense block kernels (dense.cu) ---------------------------------------
 // Every kernel below reads and writes FP64 blocks.  Where a `dfa` flag is given it
 // selects the arithmetic: false = FP64, true = double-float on the FP32 pipe
-// (about 2^-47 relative; the mixed-precision policy).  Kernels that write the
-// iterate or difference it through the curl-curl stencil (residual, block update,
-// x - L phi) have no flag: a relative perturbation eta of the iterate moves the
-// relative residual by about eta lambda_max / lambda, so they stay in FP64.
+// (about 2^-47 relative; the mixed-precision policy).  What writes the iterate or
+// differences it through the curl-curl stencil (residual, E C, x - L phi) stays in
+// FP64: a relative perturbation eta of the iterate moves the relative residual by
+// about eta lambda_max / lambda.
 void convert_d2f(const double2* X, float2* Y, long n, cudaStream_t s);
 void convert_f2d(const float2* X, double2* Y, long n, cudaStream_t s);
 // x <- x - L phi (FP64 x, phi in T), level 0
@@ -236,8 +236,9 @@ void small_rr(const double2* GM, const double2* GA, int q, int p, double2* C, do
               int* d_info, int ngroups, cudaStream_t s);
 size_t small_rr_scratch(int q);
 // Y_g[:, j] = sum_i X_g[:, i] C_g[i, j] (+ Z_g[:, j]) for each group
+// (dfa: double-float, for the search direction only; the iterate's update is FP64)
 void block_update(Roles X, int q, const double2* C, int ldc, long cgs, double2* Y, long ldy, int p,
-                  const double2* Z, long ldz, long rows, int ngroups, cudaStream_t s);
+                  const double2* Z, long ldz, long rows, int ngroups, bool dfa, cudaStream_t s);
 void random_block(double2* X, long ld, long rows, int ncols, uint64_t seed, cudaStream_t s);
 void scale_columns(double2* X, long ld, long rows, int ncols, const double* d_scale, cudaStream_t s);
 

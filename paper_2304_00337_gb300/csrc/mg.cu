@@ -31,6 +31,7 @@
 #include <cstring>
 
 #include "internal.h"
+#include "mgpoint.cuh"
 
 namespace pbs {
 
@@ -170,39 +171,8 @@ __global__ void k_chol_solve(const cx<T>* __restrict__ Lbase, int n, const cx<T>
                              cx<T>* __restrict__ X, long ldx, int ncols, int cpg, int ngroups) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (warp >= ncols) return;
-  const cx<T>* __restrict__ Lf = Lbase + (long)((warp / cpg) % ngroups) * n * n;
-  const cx<T>* b = B + warp * ldb;
-  cx<T>* x = X + warp * ldx;
-  // forward: L y = b  (y stored in x)
-  for (int i = 0; i < n; ++i) {
-    cx<T> acc = czero<T>();
-    for (int k = lane; k < i; k += 32) acc = acc + cmul(Lf[(long)k * n + i], x[k]);
-    for (int o = 16; o > 0; o >>= 1) {
-      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
-      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
-    }
-    if (lane == 0) {
-      const T d = Lf[(long)i * n + i].x;
-      const cx<T> v = b[i] - acc;
-      x[i] = mk<T>(v.x / d, v.y / d);
-    }
-    __syncwarp();
-  }
-  // backward: L^* x = y
-  for (int i = n - 1; i >= 0; --i) {
-    cx<T> acc = czero<T>();
-    for (int k = i + 1 + lane; k < n; k += 32) acc = acc + cmulc(Lf[(long)i * n + k], x[k]);
-    for (int o = 16; o > 0; o >>= 1) {
-      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
-      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
-    }
-    if (lane == 0) {
-      const T d = Lf[(long)i * n + i].x;
-      const cx<T> v = x[i] - acc;
-      x[i] = mk<T>(v.x / d, v.y / d);
-    }
-    __syncwarp();
-  }
+  const cx<T>* Lf = Lbase + (long)((warp / cpg) % ngroups) * n * n;
+  chol_solve_warp<T>(Lf, n, B + warp * ldb, X + warp * ldx, lane);
 }
 
 // One colour of the node-patch block Gauss-Seidel sweep for A + mu M.
@@ -215,31 +185,7 @@ __global__ void k_edge_smooth(Lvl<T> L, Wts<T> w, const T* __restrict__ k3, T mu
   const Ph<T> p = load_ph<T>(ph, c / cpg);
   const ERd<T> r{X + c * ld, L.n, L.m, p};
   const ERd<T> rb{B + c * ld, L.n, L.m, p};
-  // residual b - (A + mu M) x on the patch, in ghost coordinates
-  const cx<T> rL = rb.x(i - 1, j) - (A_x<T>(r, w, i - 1, j) + mu * M_x<T>(r, L, i - 1, j));
-  const cx<T> rR = rb.x(i, j) - (A_x<T>(r, w, i, j) + mu * M_x<T>(r, L, i, j));
-  const cx<T> rB = rb.y(i, j - 1) - (A_y<T>(r, w, i, j - 1) + mu * M_y<T>(r, L, i, j - 1));
-  const cx<T> rT = rb.y(i, j) - (A_y<T>(r, w, i, j) + mu * M_y<T>(r, L, i, j));
-  const T m1 = T(2.0 / 3.0) * L.mx, m2 = T(2.0 / 3.0) * L.my;
-  const cx<T> s0 = (T(1) / (mu * T(2) * (m1 + m2))) * (rL - rR + rB - rT);
-  const cx<T> ya = rL + rR, yb = rB + rT, yc = m2 * (rL - rR) + m1 * (rT - rB);
-  const long N = (long)L.n * L.m, e = (long)j * L.n + i;
-  const T K00 = k3[e], K01 = k3[N + e], K02 = k3[2 * N + e], K11 = k3[3 * N + e], K12 = k3[4 * N + e],
-          K22 = k3[5 * N + e];
-  const cx<T> za = K00 * ya + K01 * yb + K02 * yc;
-  const cx<T> zb = K01 * ya + K11 * yb + K12 * yc;
-  const cx<T> zc = K02 * ya + K12 * yb + K22 * yc;
-  const cx<T> dL = s0 + za + m2 * zc, dR = za - m2 * zc - s0;
-  const cx<T> dB = s0 + zb - m1 * zc, dT = zb + m1 * zc - s0;
-  cx<T>* Xx = X + c * ld;
-  cx<T>* Xy = Xx + N;
-  Xx[e] = Xx[e] + dR;
-  Xy[e] = Xy[e] + dT;
-  // a ghost-coordinate change d of an edge read as conj(alpha) x is alpha d in storage
-  if (i > 0) Xx[e - 1] = Xx[e - 1] + dL;
-  else Xx[(long)j * L.n + L.n - 1] = Xx[(long)j * L.n + L.n - 1] + cmul(p.al, dL);
-  if (j > 0) Xy[e - L.n] = Xy[e - L.n] + dB;
-  else Xy[(long)(L.m - 1) * L.n + i] = Xy[(long)(L.m - 1) * L.n + i] + cmul(p.be, dB);
+  edge_smooth_at<T>(L, w, k3, mu, p, r, rb, X + c * ld, i, j);
 }
 
 // One colour of point Gauss-Seidel for P = L^* M L.
@@ -250,9 +196,168 @@ __global__ void k_node_smooth(Lvl<T> L, const double* ph, int cpg, cx<T>* X, con
   const int c = blockIdx.z;
   if (i >= L.n || j >= L.m) return;
   const NRd<T> r{X + c * ld, L.n, L.m, load_ph<T>(ph, c / cpg)};
-  const long e = (long)j * L.n + i;
-  const cx<T> res = B[c * ld + e] - P_at<T>(r, L, i, j);
-  X[c * ld + e] = X[c * ld + e] + (T(1) / P_diag<T>(L)) * res;
+  node_smooth_at<T>(L, r, X + c * ld, B + c * ld, i, j);
+}
+
+// ---- fused coarse-level V-cycles ---------------------------------------------
+// The levels from `top` down to the coarsest run as one kernel: one CTA per
+// column walks the rest of the V-cycle (zero, pre-smoothing by colour, residual
+// and restriction on the way down; the coarsest triangular solves; prolongation
+// and post-smoothing on the way up) with block-wide barriers between the steps.
+// Every point update is the function the one-launch-per-step kernels call, in
+// the same colour order, so the result is the one of the unfused V-cycle.
+template <class T> struct TailLevel {
+  Lvl<T> L;
+  Wts<T> w;     // edge cycles only
+  const T* k3;  // edge cycles only
+  cx<T>* x;     // level work vectors (columns of `len` at stride `len`); x, b unused at the top
+  cx<T>* b;
+  cx<T>* r;
+  long len;
+};
+template <class T> struct TailArgs {
+  int nl;  // levels in the tail, the last one the coarsest
+  TailLevel<T> lev[kMaxLevels];
+  const cx<T>* b0;  // top level right-hand sides and solutions, columns at stride ld0
+  cx<T>* x0;
+  long ld0;
+  const double* ph;
+  int cpg;
+  const cx<T>* factor;  // per-group coarsest Cholesky factors (nfac x nfac)
+  int nfac, ngroups;
+  T mu;
+  int nu_pre, nu_post;
+};
+constexpr int kTailThreads = 512;
+constexpr long kTailMaxNodes = 4096;  // a level joins the tail when it has at most this many nodes
+
+template <class T> __device__ __forceinline__ cx<T>* tail_x(const TailArgs<T>& a, int l, int c) {
+  return l == 0 ? a.x0 + c * a.ld0 : a.lev[l].x + c * a.lev[l].len;
+}
+template <class T> __device__ __forceinline__ const cx<T>* tail_b(const TailArgs<T>& a, int l, int c) {
+  return l == 0 ? a.b0 + c * a.ld0 : a.lev[l].b + c * a.lev[l].len;
+}
+
+// colour q of the 2 x 2 node colouring on an n x m grid: node t of the colour
+__device__ __forceinline__ int colour_count(int n, int m, int ci, int cj) {
+  return ((n - ci + 1) / 2) * ((m - cj + 1) / 2);
+}
+
+template <class T>
+__global__ void __launch_bounds__(kTailThreads) k_node_tail(TailArgs<T> a) {
+  const int c = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+  const Ph<T> p = load_ph<T>(a.ph, c / a.cpg);
+  auto sweep = [&](const Lvl<T>& L, cx<T>* x, const cx<T>* b, int q) {
+    const int ci = q & 1, cj = q >> 1, nh = (L.n - ci + 1) / 2;  // colour q of (0,0), (1,0), (0,1), (1,1)
+    const NRdPlain<T> rx{x, L.n, L.m, p};
+    for (int t = tid; t < colour_count(L.n, L.m, ci, cj); t += nt)
+      node_smooth_at<T>(L, rx, x, b, ci + 2 * (t % nh), cj + 2 * (t / nh));
+    __syncthreads();
+  };
+  for (int l = 0; l < a.nl - 1; ++l) {
+    const Lvl<T> L = a.lev[l].L;
+    const int N = L.n * L.m;
+    cx<T>* x = tail_x(a, l, c);
+    const cx<T>* b = tail_b(a, l, c);
+    for (int t = tid; t < N; t += nt) x[t] = czero<T>();
+    __syncthreads();
+    for (int it = 0; it < a.nu_pre; ++it)
+      for (int q = 0; q < 4; ++q) sweep(L, x, b, q);
+    cx<T>* r = a.lev[l].r + c * a.lev[l].len;
+    const NRdPlain<T> rx{x, L.n, L.m, p};
+    for (int t = tid; t < N; t += nt) r[t] = apply_nodal_at<T>(L, rx, b, T(-1), T(1), t % L.n, t / L.n);
+    __syncthreads();
+    const Lvl<T> C = a.lev[l + 1].L;
+    cx<T>* bc = a.lev[l + 1].b + c * a.lev[l + 1].len;
+    const NRdPlain<T> rr{r, L.n, L.m, p};
+    for (int t = tid; t < C.n * C.m; t += nt) bc[t] = restrict_node_at<T>(rr, t % C.n, t / C.n);
+    __syncthreads();
+  }
+  if (tid < 32) {
+    const int l = a.nl - 1;
+    chol_solve_warp<T>(a.factor + (long)((c / a.cpg) % a.ngroups) * a.nfac * a.nfac, a.nfac, tail_b(a, l, c),
+                       tail_x(a, l, c), tid);
+  }
+  __syncthreads();
+  for (int l = a.nl - 2; l >= 0; --l) {
+    const Lvl<T> L = a.lev[l].L, C = a.lev[l + 1].L;
+    cx<T>* x = tail_x(a, l, c);
+    const cx<T>* b = tail_b(a, l, c);
+    const NRdPlain<T> rc{tail_x(a, l + 1, c), C.n, C.m, p};
+    for (int t = tid; t < L.n * L.m; t += nt) x[t] = x[t] + prolong_node_at<T>(rc, t % L.n, t / L.n);
+    __syncthreads();
+    for (int it = 0; it < a.nu_post; ++it)
+      for (int q = 3; q >= 0; --q) sweep(L, x, b, q);
+  }
+}
+
+template <class T>
+__global__ void __launch_bounds__(kTailThreads) k_edge_tail(TailArgs<T> a) {
+  const int c = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+  const Ph<T> p = load_ph<T>(a.ph, c / a.cpg);
+  auto sweep = [&](const TailLevel<T>& TL, cx<T>* x, const cx<T>* b, int q) {
+    const Lvl<T>& L = TL.L;
+    const int ci = q & 1, cj = q >> 1, nh = (L.n - ci + 1) / 2;  // colour q of (0,0), (1,0), (0,1), (1,1)
+    const ERdPlain<T> rx{x, L.n, L.m, p};
+    const ERdPlain<T> rb{b, L.n, L.m, p};
+    for (int t = tid; t < colour_count(L.n, L.m, ci, cj); t += nt)
+      edge_smooth_at<T>(L, TL.w, TL.k3, a.mu, p, rx, rb, x, ci + 2 * (t % nh), cj + 2 * (t / nh));
+    __syncthreads();
+  };
+  for (int l = 0; l < a.nl - 1; ++l) {
+    const TailLevel<T> TL = a.lev[l];
+    const Lvl<T> L = TL.L;
+    const int N = L.n * L.m;
+    cx<T>* x = tail_x(a, l, c);
+    const cx<T>* b = tail_b(a, l, c);
+    for (int t = tid; t < 2 * N; t += nt) x[t] = czero<T>();
+    __syncthreads();
+    for (int it = 0; it < a.nu_pre; ++it)
+      for (int q = 0; q < 4; ++q) sweep(TL, x, b, q);
+    cx<T>* r = TL.r + c * TL.len;
+    const ERdPlain<T> rx{x, L.n, L.m, p};
+    for (int t = tid; t < N; t += nt) {
+      cx<T> yx, yy;
+      apply_edge_at<T>(L, TL.w, rx, b, T(-1), -a.mu, T(1), t % L.n, t / L.n, yx, yy);
+      r[t] = yx;
+      r[N + t] = yy;
+    }
+    __syncthreads();
+    const Lvl<T> C = a.lev[l + 1].L;
+    const int Nc = C.n * C.m;
+    cx<T>* bc = a.lev[l + 1].b + c * a.lev[l + 1].len;
+    const ERdPlain<T> rr{r, L.n, L.m, p};
+    for (int t = tid; t < Nc; t += nt) {
+      cx<T> vx, vy;
+      restrict_edge_at<T>(rr, t % C.n, t / C.n, vx, vy);
+      bc[t] = vx;
+      bc[Nc + t] = vy;
+    }
+    __syncthreads();
+  }
+  if (tid < 32) {
+    const int l = a.nl - 1;
+    chol_solve_warp<T>(a.factor + (long)((c / a.cpg) % a.ngroups) * a.nfac * a.nfac, a.nfac, tail_b(a, l, c),
+                       tail_x(a, l, c), tid);
+  }
+  __syncthreads();
+  for (int l = a.nl - 2; l >= 0; --l) {
+    const TailLevel<T> TL = a.lev[l];
+    const Lvl<T> L = TL.L, C = a.lev[l + 1].L;
+    const int N = L.n * L.m;
+    cx<T>* x = tail_x(a, l, c);
+    const cx<T>* b = tail_b(a, l, c);
+    const ERdPlain<T> rc{tail_x(a, l + 1, c), C.n, C.m, p};
+    for (int t = tid; t < N; t += nt) {
+      cx<T> vx, vy;
+      prolong_edge_at<T>(rc, t % L.n, t / L.n, vx, vy);
+      x[t] = x[t] + vx;
+      x[N + t] = x[N + t] + vy;
+    }
+    __syncthreads();
+    for (int it = 0; it < a.nu_post; ++it)
+      for (int q = 3; q >= 0; --q) sweep(TL, x, b, q);
+  }
 }
 
 template <class T> const cx<T>* edge_factor(const KData& K);
@@ -462,6 +567,64 @@ template <class T> void free_mg_work(DevMem& mem, MgWork<T>& w) {
 
 namespace {
 
+// Columns of `len` values at stride ld set to zero (one call when they are contiguous).
+template <class T> void zero_columns(cx<T>* x, long ld, long len, int ncols, cudaStream_t s) {
+  if (ld == len) {
+    PBS_CUDA(cudaMemsetAsync(x, 0, (size_t)len * ncols * sizeof(cx<T>), s));
+  } else {
+    for (int c = 0; c < ncols; ++c) PBS_CUDA(cudaMemsetAsync(x + c * ld, 0, len * sizeof(cx<T>), s));
+  }
+}
+
+// The fused tail covers level l and everything below when l is not the coarsest
+// and has at most kTailMaxNodes nodes.
+inline bool tail_from(const Hierarchy& H, int l) { return l < H.nlev - 1 && H.lev[l].N() <= kTailMaxNodes; }
+
+// Algorithmic bytes of a fused tail: its smoothing sweeps as counted for the
+// per-step kernels, plus one read and one write of a level vector for each of the
+// residual, restriction and prolongation.
+template <class T> double tail_bytes(const Hierarchy& H, int l, int ncols, int nu, bool nodal) {
+  double b = 0.0;
+  for (int k = l; k < H.nlev - 1; ++k) {
+    const Level& L = H.lev[k];
+    const double len = nodal ? (double)L.N() : (double)L.D();
+    b += 4.0 * nu * (nodal ? node_smooth_bytes<T>(L, ncols) : smooth_bytes<T>(L, ncols));
+    b += 6.0 * len * ncols * sizeof(cx<T>);
+  }
+  return b;
+}
+
+template <class T>
+TailArgs<T> tail_args(const Hierarchy& H, const KData& K, MgWork<T>& w, int l, const cx<T>* b, cx<T>* x, long ld,
+                      int cpg, int nu_pre, int nu_post, bool nodal) {
+  TailArgs<T> a{};
+  a.nl = H.nlev - l;
+  for (int k = 0; k < a.nl; ++k) {
+    const Level& L = H.lev[l + k];
+    TailLevel<T>& t = a.lev[k];
+    t.L = L.lvl<T>();
+    t.w = L.wts<T>();
+    t.k3 = k3_of<T>(L);
+    t.x = w.x[l + k];
+    t.b = w.b[l + k];
+    t.r = w.r[l + k];
+    t.len = nodal ? L.N() : L.D();
+  }
+  a.b0 = b;
+  a.x0 = x;
+  a.ld0 = ld;
+  a.ph = K.d_ph;
+  a.cpg = cpg;
+  const Level& Cst = H.lev[H.nlev - 1];
+  a.factor = nodal ? node_factor<T>(K) : edge_factor<T>(K);
+  a.nfac = (int)(nodal ? Cst.N() : Cst.D());
+  a.ngroups = K.ngroups;
+  a.mu = T(H.mu);
+  a.nu_pre = nu_pre;
+  a.nu_post = nu_post;
+  return a;
+}
+
 template <class T>
 void edge_cycle(const Hierarchy& H, const KData& K, MgWork<T>& w, int l, const cx<T>* b, cx<T>* x, long ld, int ncols,
                 int cpg, int nu_pre, int nu_post, cudaStream_t s) {
@@ -472,7 +635,14 @@ void edge_cycle(const Hierarchy& H, const KData& K, MgWork<T>& w, int l, const c
     PBS_LAUNCHED();
     return;
   }
-  for (int c = 0; c < ncols; ++c) PBS_CUDA(cudaMemsetAsync(x + c * ld, 0, L.D() * sizeof(cx<T>), s));
+  if (tail_from(H, l)) {
+    timer_begin(KC_EDGE_TAIL, s, tail_bytes<T>(H, l, ncols, nu_pre + nu_post, false));
+    k_edge_tail<T><<<ncols, kTailThreads, 0, s>>>(tail_args<T>(H, K, w, l, b, x, ld, cpg, nu_pre, nu_post, false));
+    timer_end(KC_EDGE_TAIL, s);
+    PBS_LAUNCHED();
+    return;
+  }
+  zero_columns<T>(x, ld, L.D(), ncols, s);
   const Lvl<T> lv = L.lvl<T>();
   const Wts<T> wt = L.wts<T>();
   const T mu = T(H.mu);
@@ -510,7 +680,14 @@ void node_cycle(const Hierarchy& H, const KData& K, MgWork<T>& w, int l, const c
     PBS_LAUNCHED();
     return;
   }
-  for (int c = 0; c < ncols; ++c) PBS_CUDA(cudaMemsetAsync(x + c * ld, 0, L.N() * sizeof(cx<T>), s));
+  if (tail_from(H, l)) {
+    timer_begin(KC_NODE_TAIL, s, tail_bytes<T>(H, l, ncols, nu_pre + nu_post, true));
+    k_node_tail<T><<<ncols, kTailThreads, 0, s>>>(tail_args<T>(H, K, w, l, b, x, ld, cpg, nu_pre, nu_post, true));
+    timer_end(KC_NODE_TAIL, s);
+    PBS_LAUNCHED();
+    return;
+  }
+  zero_columns<T>(x, ld, L.N(), ncols, s);
   const Lvl<T> lv = L.lvl<T>();
   for (int it = 0; it < nu_pre; ++it)
     for (int q = 0; q < 4; ++q) {

@@ -3,6 +3,7 @@
 // index (i, j) and column; a column's Bloch phases come from its group
 // (column / cpg) in the phase table.
 #include "internal.h"
+#include "mgpoint.cuh"
 
 namespace pbs {
 
@@ -21,19 +22,8 @@ __global__ void k_apply_edge(Lvl<T> L, Wts<T> w, const double* ph, int cpg, cons
   const ERd<T> r{X + c * ld, L.n, L.m, load_ph<T>(ph, c / cpg)};
   const long N = (long)L.n * L.m, e = (long)j * L.n + i;
   const T s = sM + (lam ? sL * lam[c] : T(0));
-  cx<T> yx = czero<T>(), yy = czero<T>();
-  if (sA != T(0)) {
-    yx = sA * A_x<T>(r, w, i, j);
-    yy = sA * A_y<T>(r, w, i, j);
-  }
-  if (s != T(0)) {
-    yx = yx + s * M_x<T>(r, L, i, j);
-    yy = yy + s * M_y<T>(r, L, i, j);
-  }
-  if (B) {
-    yx = yx + sB * B[c * ld + e];
-    yy = yy + sB * B[c * ld + N + e];
-  }
+  cx<T> yx, yy;
+  apply_edge_at<T>(L, w, r, B ? B + c * ld : nullptr, sA, s, sB, i, j, yx, yy);
   Y[c * ld + e] = yx;
   Y[c * ld + N + e] = yy;
 }
@@ -91,10 +81,7 @@ __global__ void k_apply_nodal(Lvl<T> L, const double* ph, int cpg, const cx<T>* 
   const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y, c = blockIdx.z;
   if (i >= L.n || j >= L.m) return;
   const NRd<T> r{X + c * ld, L.n, L.m, load_ph<T>(ph, c / cpg)};
-  const long e = (long)j * L.n + i;
-  cx<T> y = sP * P_at<T>(r, L, i, j);
-  if (B) y = y + sB * B[c * ld + e];
-  Y[c * ld + e] = y;
+  Y[c * ld + (long)j * L.n + i] = apply_nodal_at<T>(L, r, B ? B + c * ld : nullptr, sP, sB, i, j);
 }
 
 // Natural embedding of coarse edges (Section 5): a fine edge lying on a coarse
@@ -106,21 +93,10 @@ __global__ void k_prolong_edge(int nf, int mf, int nc, int mc, const double* ph,
                                int accumulate) {
   const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y, c = blockIdx.z;
   if (i >= nf || j >= mf) return;
-  const Ph<T> p = load_ph<T>(ph, c / cpg);
-  const cx<T>* xc = Xc + c * ldc;
-  const cx<T>* yc = xc + (long)nc * mc;
+  const ERd<T> rc{Xc + c * ldc, nc, mc, load_ph<T>(ph, c / cpg)};
   const long Nf = (long)nf * mf, e = (long)j * nf + i;
   cx<T> vx, vy;
-  {
-    const int I = i >> 1;
-    if ((j & 1) == 0) vx = T(0.5) * xc[(long)(j >> 1) * nc + I];
-    else vx = T(0.25) * (xc[(long)(j >> 1) * nc + I] + gread<T>(xc, I, (j >> 1) + 1, nc, mc, p));
-  }
-  {
-    const int J = j >> 1;
-    if ((i & 1) == 0) vy = T(0.5) * yc[(long)J * nc + (i >> 1)];
-    else vy = T(0.25) * (yc[(long)J * nc + (i >> 1)] + gread<T>(yc, (i >> 1) + 1, J, nc, mc, p));
-  }
+  prolong_edge_at<T>(rc, i, j, vx, vy);
   cx<T>* yf = Yf + c * ldf;
   if (accumulate) {
     yf[e] = yf[e] + vx;
@@ -137,13 +113,9 @@ __global__ void k_restrict_edge(int nf, int mf, int nc, int mc, const double* ph
                                 const cx<T>* __restrict__ Xf, long ldf, cx<T>* __restrict__ Yc, long ldc) {
   const int I = blockIdx.x * kBX + threadIdx.x, J = blockIdx.y * kBY + threadIdx.y, c = blockIdx.z;
   if (I >= nc || J >= mc) return;
-  const Ph<T> p = load_ph<T>(ph, c / cpg);
-  const ERd<T> r{Xf + c * ldf, nf, mf, p};
-  const int i = 2 * I, j = 2 * J;
-  const cx<T> vx = T(0.5) * (r.x(i, j) + r.x(i + 1, j)) +
-                   T(0.25) * (r.x(i, j + 1) + r.x(i + 1, j + 1) + r.x(i, j - 1) + r.x(i + 1, j - 1));
-  const cx<T> vy = T(0.5) * (r.y(i, j) + r.y(i, j + 1)) +
-                   T(0.25) * (r.y(i + 1, j) + r.y(i + 1, j + 1) + r.y(i - 1, j) + r.y(i - 1, j + 1));
+  const ERd<T> r{Xf + c * ldf, nf, mf, load_ph<T>(ph, c / cpg)};
+  cx<T> vx, vy;
+  restrict_edge_at<T>(r, I, J, vx, vy);
   const long Nc = (long)nc * mc, e = (long)J * nc + I;
   Yc[c * ldc + e] = vx;
   Yc[c * ldc + Nc + e] = vy;
@@ -156,20 +128,8 @@ __global__ void k_prolong_node(int nf, int mf, int nc, int mc, const double* ph,
                                int accumulate) {
   const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y, c = blockIdx.z;
   if (i >= nf || j >= mf) return;
-  const Ph<T> p = load_ph<T>(ph, c / cpg);
-  const cx<T>* xc = Xc + c * ldc;
-  const int I = i >> 1, J = j >> 1;
-  cx<T> v;
-  if (!(i & 1) && !(j & 1)) {
-    v = xc[(long)J * nc + I];
-  } else if ((i & 1) && !(j & 1)) {
-    v = T(0.5) * (xc[(long)J * nc + I] + gread<T>(xc, I + 1, J, nc, mc, p));
-  } else if (!(i & 1) && (j & 1)) {
-    v = T(0.5) * (xc[(long)J * nc + I] + gread<T>(xc, I, J + 1, nc, mc, p));
-  } else {
-    v = T(0.25) * (xc[(long)J * nc + I] + gread<T>(xc, I + 1, J, nc, mc, p) + gread<T>(xc, I, J + 1, nc, mc, p) +
-                   gread<T>(xc, I + 1, J + 1, nc, mc, p));
-  }
+  const NRd<T> rc{Xc + c * ldc, nc, mc, load_ph<T>(ph, c / cpg)};
+  const cx<T> v = prolong_node_at<T>(rc, i, j);
   const long e = (long)j * nf + i;
   cx<T>* yf = Yf + c * ldf;
   yf[e] = accumulate ? yf[e] + v : v;
@@ -180,18 +140,8 @@ __global__ void k_restrict_node(int nf, int mf, int nc, int mc, const double* ph
                                 const cx<T>* __restrict__ Xf, long ldf, cx<T>* __restrict__ Yc, long ldc) {
   const int I = blockIdx.x * kBX + threadIdx.x, J = blockIdx.y * kBY + threadIdx.y, c = blockIdx.z;
   if (I >= nc || J >= mc) return;
-  const Ph<T> p = load_ph<T>(ph, c / cpg);
-  const cx<T>* xf = Xf + c * ldf;
-  cx<T> acc = czero<T>();
-#pragma unroll
-  for (int dj = -1; dj <= 1; ++dj) {
-#pragma unroll
-    for (int di = -1; di <= 1; ++di) {
-      const T wgt = (di == 0 ? T(1) : T(0.5)) * (dj == 0 ? T(1) : T(0.5));
-      acc = acc + wgt * gread<T>(xf, 2 * I + di, 2 * J + dj, nf, mf, p);
-    }
-  }
-  Yc[c * ldc + (long)J * nc + I] = acc;
+  const NRd<T> rf{Xf + c * ldf, nf, mf, load_ph<T>(ph, c / cpg)};
+  Yc[c * ldc + (long)J * nc + I] = restrict_node_at<T>(rf, I, J);
 }
 
 }  // namespace

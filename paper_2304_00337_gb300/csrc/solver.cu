@@ -471,7 +471,7 @@ double rr_single(pbs_ctx* ctx, const KData& Kv, const double2* S, int q, int p, 
   if (info[0] != 0)
     fail(PBS_ENUMERIC, info[0] == -2 ? "non-finite Gram matrix"
                                      : info[0] == -3 ? "Rayleigh-Ritz breakdown" : "trial space lost rank");
-  block_update(R, q, W.C, q, (long)q * p, dst, W.D, p, nullptr, 0, W.D, 1, s);
+  block_update(R, q, W.C, q, (long)q * p, dst, W.D, p, nullptr, 0, W.D, 1, false, s);
   double tm = 0.0;
   for (double t : th) tm = std::max(tm, std::fabs(t));
   return tm;
@@ -680,14 +680,14 @@ PathResult solve_chains(pbs_ctx* ctx, const pbs_opts& o, int nk, const double* k
       double2* P2 = W.S2 + Gp * D;
       if (o.span == 1) {
         // E_new = E_hat C
-        block_update(trial, p, W.C, p, (long)p * p, E2, D, p, nullptr, 0, D, G, s);
+        block_update(trial, p, W.C, p, (long)p * p, E2, D, p, nullptr, 0, D, G, false, s);
         PBS_CUDA(cudaMemsetAsync(P2, 0, sizeof(double2) * D * Gp, s));
       } else {
         // P_new = [P, W] C[p:q], E_new = E C[0:p] + P_new   (into S2, then swap)
         const Roles pw{{W.P(), W.W(), W.W()}, p, D};
-        block_update(pw, 2 * p, W.C + p, q, (long)q * p, P2, D, p, nullptr, 0, D, G, s);
+        block_update(pw, 2 * p, W.C + p, q, (long)q * p, P2, D, p, nullptr, 0, D, G, dfa, s);
         const Roles ee{{W.E(), W.E(), W.E()}, p, D};
-        block_update(ee, p, W.C, q, (long)q * p, E2, D, p, P2, D, D, G, s);
+        block_update(ee, p, W.C, q, (long)q * p, E2, D, p, P2, D, D, G, false, s);
         if (o.span == 2) PBS_CUDA(cudaMemsetAsync(P2, 0, sizeof(double2) * D * Gp, s));  // gradient method: no P
       }
       std::swap(W.S, W.S2);
@@ -1083,7 +1083,8 @@ int pbs_rayleigh_ritz(pbs_ctx* ctx, const pbs_geom* geom, const pbs_opts* opts, 
 }
 
 static const char* kClassNames[KC_COUNT] = {"", "edge_smooth", "node_smooth", "gram", "small_rr", "residual",
-                                             "block_update", "lift_adj_mass", "edge_apply"};
+                                             "block_update", "lift_adj_mass", "edge_apply", "edge_tail",
+                                             "node_tail"};
 
 static int class_of(const char* name) {
   for (int c = 1; c < KC_COUNT; ++c)

@@ -4,7 +4,9 @@ Every call goes through the C ABI (``pbs_apply``, ``pbs_gram``,
 ``pbs_rayleigh_ritz``) on seeded inputs; expected values come from the CPU
 oracle on the same inputs.  Bars: operator applications <= 1e-13 relative
 (2-norm per column), FP64 V-cycles and projection <= 1e-12 (same algorithm,
-different summation order), FP32 cycles <= 1e-5.
+different summation order), FP32 cycles <= 1e-5; on larger grids the V-cycle
+bars grow with the rounding amplification the oracle itself shows under a
+one-ulp input perturbation.
 """
 import numpy as np
 import pytest
@@ -66,6 +68,18 @@ def _rel(got, want):
     return np.max(np.linalg.norm(got - want, axis=1) / np.maximum(np.linalg.norm(want, axis=1), 1e-300))
 
 
+def _bars(fn, x):
+    """FP64 and FP32 bars for a linear solver step.  The oracle's own output is
+    moved by a one-ulp (2^-53) relative perturbation of its input; that change
+    divided by 2^-53 is the rounding amplification of the step, which grows with
+    the condition of the level operators.  Bars: 1e-12 (FP64) and 1e-5 (FP32), or
+    twice the amplification times the unit roundoff, whichever is larger."""
+    y = fn(x)
+    d = x * (1 + 2.0 ** -53 * np.random.default_rng(99).standard_normal(x.shape))
+    amp = np.linalg.norm(fn(d) - y) / np.linalg.norm(y) / 2.0 ** -53
+    return max(1e-12, 2 * amp * 2.0 ** -53), max(1e-5, 2 * amp * 2.0 ** -24)
+
+
 def _coarse_eps(eps):
     inv = 1.0 / eps
     return 1.0 / (0.25 * (inv[0::2, 0::2] + inv[1::2, 0::2] + inv[0::2, 1::2] + inv[1::2, 1::2]))
@@ -119,7 +133,9 @@ def test_transfers_and_coarse_level_operators(ctx, a, b, n, m, k):
     assert _rel(got, (oc["P"] @ xcn.T).T) <= 1e-13
 
 
-@pytest.mark.parametrize("a,b,n,m,k", [CASES[0], CASES[1], CASES[2], CASES[3]])
+# levels with at most 4096 nodes run as one fused kernel; 96 x 48 (4608 nodes) runs
+# its top level step by step and the rest fused, the smaller cases fused throughout
+@pytest.mark.parametrize("a,b,n,m,k", [CASES[0], CASES[1], CASES[2], CASES[3], (1.0, 0.5, 96, 48, (0.4, -1.3))])
 def test_vcycles_match_reference(ctx, a, b, n, m, k):
     eps = _eps(n, m)
     geom = pbs.Geometry(eps, a, b)
@@ -127,19 +143,21 @@ def test_vcycles_match_reference(ctx, a, b, n, m, k):
     levels = mg.edge_hierarchy(mesh, eps, k, MU, 4)
     x = _block(2, mesh.D, 7)
     want = np.stack([mg.edge_vcycle(levels, x[c]) for c in range(2)])
+    bar64, bar32 = _bars(lambda v: mg.edge_vcycle(levels, v), x[0])
     got = _apply(ctx, geom, "VCYCLE_EDGE", x, mesh.D, k, precision=pbs.PBS_FP64)
-    assert _rel(got, want) <= 1e-12
+    assert _rel(got, want) <= bar64
     got32 = _apply(ctx, geom, "VCYCLE_EDGE", x, mesh.D, k, precision=pbs.PBS_MIXED)
-    assert _rel(got32, want) <= 1e-5
+    assert _rel(got32, want) <= bar32
     nlev = mg.nodal_hierarchy(mesh, eps, k, 4)
     xn = _block(2, mesh.N, 8)
     if fem.is_gamma(*fem.bloch_phases(k, a, b)):
         xn -= xn.mean(axis=1, keepdims=True)
     want = np.stack([mg.nodal_vcycle(nlev, xn[c]) for c in range(2)])
+    bar64, bar32 = _bars(lambda v: mg.nodal_vcycle(nlev, v), xn[0])
     got = _apply(ctx, geom, "VCYCLE_NODAL", xn, mesh.N, k, precision=pbs.PBS_FP64)
-    assert _rel(got, want) <= 1e-12
+    assert _rel(got, want) <= bar64
     got32 = _apply(ctx, geom, "VCYCLE_NODAL", xn, mesh.N, k, precision=pbs.PBS_MIXED)
-    assert _rel(got32, want) <= 1e-5
+    assert _rel(got32, want) <= bar32
 
 
 @pytest.mark.parametrize("a,b,n,m,k", [CASES[0], CASES[2], CASES[4]])
