@@ -112,23 +112,43 @@ __global__ void k_rayleigh_parts(Lvl<V> L, W w, const double* ph, int cpg, const
 // a perturbation of the stored vector of relative size eta moves the relative
 // residual by about eta lambda_max / lambda (1.6e7 at 256 x 256 next to Gamma),
 // which only FP64's 1.1e-16 keeps well under a tolerance of 1e-8.
-__global__ void k_residual(Lvl<double> L, Wts<double> w, const double* ph, int cpg, const double2* __restrict__ E,
-                           double2* __restrict__ R, long ld, const double* __restrict__ lam, double* __restrict__ part) {
-  const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y, c = blockIdx.z;
+// FP64 issues slowly on this GPU, so the kernel spends as few FP64 operations as
+// it can: each CTA forms H = w curl once per cell of its 32 x 8 tile and of a
+// one-cell halo below and to the left (shared memory), A_x = H(i,j-1) - H(i,j),
+// A_y = H(i,j) - H(i-1,j), and the mass stencil is (h2/h1)/6 (4 x0 + x+ + x-).
+__global__ void __launch_bounds__(kBX * kBY) k_residual(Lvl<double> L, Wts<double> w, const double* ph, int cpg,
+                                                         const double2* __restrict__ E, double2* __restrict__ R,
+                                                         long ld, const double* __restrict__ lam,
+                                                         double* __restrict__ part) {
+  __shared__ double2 Hs[kBY + 1][kBX + 1];  // cell (i0 - 1 + a, j0 - 1 + b) at Hs[b][a]
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int i0 = blockIdx.x * kBX, j0 = blockIdx.y * kBY;
+  const int i = i0 + tx, j = j0 + ty, c = blockIdx.z;
+  const bool in = i < L.n && j < L.m;
+  const ERd<double> r{E + c * ld, L.n, L.m, load_ph<double>(ph, c / cpg)};
+  if (in) Hs[ty + 1][tx + 1] = w(i, j) * curl_at<double>(r, i, j);
+  if (ty == 0 && i < L.n) Hs[0][tx + 1] = w(i, j0 - 1) * curl_at<double>(r, i, j0 - 1);
+  if (tx == 0 && j < L.m) Hs[ty + 1][0] = w(i0 - 1, j) * curl_at<double>(r, i0 - 1, j);
+  __syncthreads();
   double rr = 0, mm = 0;
-  if (i < L.n && j < L.m) {
-    const ERd<double> r{E + c * ld, L.n, L.m, load_ph<double>(ph, c / cpg)};
+  if (in) {
     const double l = lam[c];
-    const double2 mx = M_x<double>(r, L, i, j), my = M_y<double>(r, L, i, j);
-    const double2 rx = A_x<double>(r, w, i, j) - l * mx, ry = A_y<double>(r, w, i, j) - l * my;
+    const double sx = L.mx * (1.0 / 6.0), sy = L.my * (1.0 / 6.0);
+    const double2 x0 = r.x(i, j), x1 = r.x(i, j + 1), x2 = r.x(i, j - 1);
+    const double2 y0 = r.y(i, j), y1 = r.y(i + 1, j), y2 = r.y(i - 1, j);
+    const double2 mx = make_double2(sx * fma(4.0, x0.x, x1.x + x2.x), sx * fma(4.0, x0.y, x1.y + x2.y));
+    const double2 my = make_double2(sy * fma(4.0, y0.x, y1.x + y2.x), sy * fma(4.0, y0.y, y1.y + y2.y));
+    const double2 h = Hs[ty + 1][tx + 1], hb = Hs[ty][tx + 1], hl = Hs[ty + 1][tx];
+    const double2 rx = make_double2(fma(-l, mx.x, hb.x - h.x), fma(-l, mx.y, hb.y - h.y));
+    const double2 ry = make_double2(fma(-l, my.x, h.x - hl.x), fma(-l, my.y, h.y - hl.y));
     const long N = (long)L.n * L.m, e = (long)j * L.n + i;
     R[c * ld + e] = rx;
     R[c * ld + N + e] = ry;
-    rr = nrm2(rx) + nrm2(ry);
-    mm = nrm2(mx) + nrm2(my);
+    rr = fma(rx.x, rx.x, fma(rx.y, rx.y, fma(ry.x, ry.x, ry.y * ry.y)));
+    mm = fma(mx.x, mx.x, fma(mx.y, mx.y, fma(my.x, my.x, my.y * my.y)));
   }
   block_sum2(rr, mm);
-  if (threadIdx.x == 0 && threadIdx.y == 0) {
+  if (tx == 0 && ty == 0) {
     const int nblk = gridDim.x * gridDim.y, b = blockIdx.y * gridDim.x + blockIdx.x;
     part[((long)c * nblk + b) * 2] = rr;
     part[((long)c * nblk + b) * 2 + 1] = mm;
@@ -331,7 +351,7 @@ __global__ void __launch_bounds__(256) k_gram_fused(Lvl<double> L, Wts<double> w
 // which 256/P tiles this block holds) of GM and GA over rows phase, phase + P, ...
 // of each staged chunk, with Dot2 accumulators folded once per chunk.  The P
 // phases of a tile sit in one warp and are combined by shuffles in a fixed order.
-constexpr int kGdRows = 16;
+constexpr int kGdRows = 16;  // rows (nodes) per staged chunk
 
 __device__ __forceinline__ void mac_conj(acc2& re, acc2& im, const dcx& a, const dcx& b) {
   // += conj(a) b
@@ -343,14 +363,14 @@ __device__ __forceinline__ void mac_conj(acc2& re, acc2& im, const dcx& a, const
 
 template <int P>
 __global__ void __launch_bounds__(256) k_gram_df(Lvl<df> L, WtsDF w, const double* ph, Roles roles, int q, int qp,
-                                                 double2* __restrict__ part, int npart) {
+                                                 int rows, double2* __restrict__ part, int npart) {
   extern __shared__ float4 smf[];
-  dcx* sx = reinterpret_cast<dcx*>(smf);  // [kGdRows][qp] each
-  dcx* sy = sx + kGdRows * qp;
-  dcx* mx = sy + kGdRows * qp;
-  dcx* my = mx + kGdRows * qp;
-  dcx* cc = my + kGdRows * qp;
-  dcx* cw = cc + kGdRows * qp;
+  dcx* sx = reinterpret_cast<dcx*>(smf);  // [rows][qp] each
+  dcx* sy = sx + rows * qp;
+  dcx* mx = sy + rows * qp;
+  dcx* my = mx + rows * qp;
+  dcx* cc = my + rows * qp;
+  dcx* cw = cc + rows * qp;
   const int g = blockIdx.y;
   const int tid = threadIdx.x;
   const int T3 = qp / 3, ntile = T3 * (T3 + 1) / 2;
@@ -364,7 +384,7 @@ __global__ void __launch_bounds__(256) k_gram_df(Lvl<df> L, WtsDF w, const doubl
     I = slot - J * (J + 1) / 2;
   }
   const dcx z = dcx_make(df_zero(), df_zero());
-  for (int t = tid; t < kGdRows * (qp - q); t += blockDim.x) {
+  for (int t = tid; t < rows * (qp - q); t += blockDim.x) {
     const int e = (t / (qp - q)) * qp + q + t % (qp - q);
     sx[e] = z; sy[e] = z; mx[e] = z; my[e] = z; cc[e] = z; cw[e] = z;
   }
@@ -375,12 +395,12 @@ __global__ void __launch_bounds__(256) k_gram_df(Lvl<df> L, WtsDF w, const doubl
   }
   const Ph<df> p = load_ph<df>(ph, g);
   const long N = (long)L.n * L.m;
-  const long nchunks = (N + kGdRows - 1) / kGdRows;
+  const long nchunks = (N + rows - 1) / rows;
   for (long ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
-    const long r0 = ch * kGdRows;
+    const long r0 = ch * rows;
     __syncthreads();
-    for (int t = tid; t < q * kGdRows; t += blockDim.x) {
-      const int col = t / kGdRows, rr = t % kGdRows;
+    for (int t = tid; t < q * rows; t += blockDim.x) {
+      const int col = t / rows, rr = t % rows;
       const long node = r0 + rr;
       dcx vx = z, vy = z, vmx = z, vmy = z, vc = z, vcw = z;
       if (node < N) {
@@ -398,21 +418,23 @@ __global__ void __launch_bounds__(256) k_gram_df(Lvl<df> L, WtsDF w, const doubl
     }
     __syncthreads();
     if (active) {
-      for (int rr = phase; rr < kGdRows; rr += P) {
+      // the M sums take two row streams per node (x and y edges), the A sums one
+      // (curls); the streams of a matrix are consecutive rows of one loop
+      for (int rr = phase; rr < rows; rr += P) {
         const int ra = rr * qp + 3 * I, rb = rr * qp + 3 * J;
+#pragma unroll 1
+        for (int st = 0; st < 2; ++st) {
+          const dcx* A = st == 0 ? sx : sy;
+          const dcx* B = st == 0 ? mx : my;
+          dcx a[3], b[3];
+#pragma unroll
+          for (int k = 0; k < 3; ++k) { a[k] = A[ra + k]; b[k] = B[rb + k]; }
+#pragma unroll
+          for (int k = 0; k < 3; ++k)
+#pragma unroll
+            for (int l = 0; l < 3; ++l) mac_conj(mre[3 * k + l], mim[3 * k + l], a[k], b[l]);
+        }
         dcx a[3], b[3];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) { a[k] = sx[ra + k]; b[k] = mx[rb + k]; }
-#pragma unroll
-        for (int k = 0; k < 3; ++k)
-#pragma unroll
-          for (int l = 0; l < 3; ++l) mac_conj(mre[3 * k + l], mim[3 * k + l], a[k], b[l]);
-#pragma unroll
-        for (int k = 0; k < 3; ++k) { a[k] = sy[ra + k]; b[k] = my[rb + k]; }
-#pragma unroll
-        for (int k = 0; k < 3; ++k)
-#pragma unroll
-          for (int l = 0; l < 3; ++l) mac_conj(mre[3 * k + l], mim[3 * k + l], a[k], b[l]);
 #pragma unroll
         for (int k = 0; k < 3; ++k) { a[k] = cc[ra + k]; b[k] = cw[rb + k]; }
 #pragma unroll
@@ -617,18 +639,41 @@ __global__ void __launch_bounds__(kRRThreads) k_small_rr(const double2* __restri
   }
   const int r = q;
   t_phase[1] = clock64();
-  // 2a. T = R^{-1} by Gauss-Jordan: rows from the bottom; row k of T is
-  //     (e_k - sum_{c>k} R[k][c] T[c][:]) / R[k][k], all columns in parallel
-  for (int k = r - 1; k >= 0; --k) {
-    const df rkk = G[(long)k * q + k].re;
-    for (int c = tid; c < r; c += nt) {
-      if (c < k) continue;
-      cdf acc = cdf_make(df_make(c == k ? 1.0f : 0.0f, 0.0f), df_zero());
-      for (int m = k + 1; m <= c; ++m) acc = acc - G[(long)m * q + k] * T[(long)c * q + m];
-      T[(long)c * q + k] = cdf_make(acc.re / rkk, acc.im / rkk);
+  // 2a. T = R^{-1}, column c solving R t = e_c by back substitution, one warp per
+  //     column: lanes hold the right-hand side rows; at step k the owner of row k
+  //     divides by R[k][k], broadcasts t_k, and every lane removes R[m][k] t_k from
+  //     its rows m < k (R[m][k] = G[k q + m]).  Rows above c of T stay zero.
+  {
+    const int lane = tid & 31, warp = tid >> 5;
+    constexpr int kSlots = (kMaxTrial + 31) / 32;
+    for (int c = warp; c < r; c += kRRWarps) {
+      cdf bv[kSlots];
+#pragma unroll
+      for (int sl = 0; sl < kSlots; ++sl)
+        bv[sl] = cdf_make(df_make(lane + 32 * sl == c ? 1.0f : 0.0f, 0.0f), df_zero());
+      for (int k = c; k >= 0; --k) {
+        const int owner = k & 31, slot = k >> 5;
+        cdf xk = cdf_zero();
+#pragma unroll
+        for (int sl = 0; sl < kSlots; ++sl)
+          if (sl == slot && lane == owner) {
+            const df rkk = G[(long)k * q + k].re;
+            xk = cdf_make(bv[sl].re / rkk, bv[sl].im / rkk);
+            T[(long)c * q + k] = xk;
+          }
+        xk.re.hi = __shfl_sync(0xffffffffu, xk.re.hi, owner);
+        xk.re.lo = __shfl_sync(0xffffffffu, xk.re.lo, owner);
+        xk.im.hi = __shfl_sync(0xffffffffu, xk.im.hi, owner);
+        xk.im.lo = __shfl_sync(0xffffffffu, xk.im.lo, owner);
+#pragma unroll
+        for (int sl = 0; sl < kSlots; ++sl) {
+          const int m = lane + 32 * sl;
+          if (m < k) bv[sl] = bv[sl] - G[(long)k * q + m] * xk;
+        }
+      }
     }
-    __syncthreads();
   }
+  __syncthreads();
   // 2b. Y = A T into G (R is no longer needed), then H = T^* Y
   for (long t = tid; t < (long)r * r; t += nt) {
     const int i = int(t % r), c = int(t / r);
@@ -658,14 +703,19 @@ __global__ void __launch_bounds__(kRRThreads) k_small_rr(const double2* __restri
     }
   }
   __syncthreads();
+  // Gershgorin row sums of the kept rows (in te, which the reduction below fills
+  // before it is used again), then the bound by one thread
+  for (int i = tid; i < r; i += nt) {
+    df rs = df_zero();
+    if (s_keep[i])
+      for (int j = 0; j < r; ++j) rs = rs + df_sqrt(cdf_norm2(H[(long)j * q + i]));
+    te[i] = rs;
+  }
+  __syncthreads();
   if (tid == 0) {
     df bound = df_zero();
-    for (int i = 0; i < r; ++i) {
-      if (!s_keep[i]) continue;
-      df rs = df_zero();
-      for (int j = 0; j < r; ++j) rs = rs + df_sqrt(cdf_norm2(H[(long)j * q + i]));
-      if (df_lt(bound, rs)) bound = rs;
-    }
+    for (int i = 0; i < r; ++i)
+      if (df_lt(bound, te[i])) bound = te[i];
     for (int i = 0; i < r; ++i)
       if (!s_keep[i]) H[(long)i * q + i] = cdf_make(bound + bound + df_make(1.0f, 0.0f), df_zero());
   }
@@ -780,43 +830,46 @@ __global__ void __launch_bounds__(kRRThreads) k_small_rr(const double2* __restri
   __syncthreads();
   t_phase[4] = clock64();
   // 4b. inverse iteration on Tr - lam_j I (Gaussian elimination with partial
-  //     pivoting), one thread per eigenvalue; cluster members re-orthogonalised
+  //     pivoting, factored once), one thread per eigenvalue; cluster members
+  //     re-orthogonalised after every sweep
+  df u0[kMaxTrial], u1[kMaxTrial], u2[kMaxTrial], mult[kMaxTrial];
+  bool swp[kMaxTrial];
+  if (tid < p) {
+    const df shift = lam[tid];
+    df d0 = ta[0] - shift, s1 = r > 1 ? te[0] : df_zero();
+    for (int i = 0; i < r; ++i) {
+      const df below_sub = i + 1 < r ? te[i] : df_zero();
+      const df below_diag = i + 1 < r ? ta[i + 1] - shift : df_zero();
+      const df below_sup = i + 2 < r ? te[i + 1] : df_zero();
+      if (i + 1 < r && fabsf(below_sub.hi) > fabsf(d0.hi)) {
+        swp[i] = true;
+        u0[i] = below_sub;
+        u1[i] = below_diag;
+        u2[i] = below_sup;
+        const df mlt = d0 / below_sub;
+        mult[i] = mlt;
+        d0 = s1 - mlt * below_diag;
+        s1 = -(mlt * below_sup);
+      } else {
+        swp[i] = false;
+        df dd = d0;
+        if (fabsf(dd.hi) < pivmin_ii) dd = df_make(dd.hi < 0.0f ? -pivmin_ii : pivmin_ii, 0.0f);
+        u0[i] = dd;
+        u1[i] = s1;
+        u2[i] = df_zero();
+        const df mlt = i + 1 < r ? below_sub / dd : df_zero();
+        mult[i] = mlt;
+        d0 = below_diag - mlt * s1;
+        s1 = below_sup;
+      }
+    }
+  }
   for (int sweep = 0; sweep < 4; ++sweep) {
     if (tid < p) {
       const int j = tid;
       df* z = Z + j * q;
       if (sweep == 0)
         for (int i = 0; i < r; ++i) z[i] = df_make(1.0f + 0.37f * __sinf(1.7f * (i + 1) * (j + 1)), 0.0f);
-      const df shift = lam[j];
-      df u0[kMaxTrial], u1[kMaxTrial], u2[kMaxTrial], mult[kMaxTrial];
-      bool swp[kMaxTrial];
-      df d0 = ta[0] - shift, s1 = r > 1 ? te[0] : df_zero();
-      for (int i = 0; i < r; ++i) {
-        const df below_sub = i + 1 < r ? te[i] : df_zero();
-        const df below_diag = i + 1 < r ? ta[i + 1] - shift : df_zero();
-        const df below_sup = i + 2 < r ? te[i + 1] : df_zero();
-        if (i + 1 < r && fabsf(below_sub.hi) > fabsf(d0.hi)) {
-          swp[i] = true;
-          u0[i] = below_sub;
-          u1[i] = below_diag;
-          u2[i] = below_sup;
-          const df mlt = d0 / below_sub;
-          mult[i] = mlt;
-          d0 = s1 - mlt * below_diag;
-          s1 = -(mlt * below_sup);
-        } else {
-          swp[i] = false;
-          df dd = d0;
-          if (fabsf(dd.hi) < pivmin_ii) dd = df_make(dd.hi < 0.0f ? -pivmin_ii : pivmin_ii, 0.0f);
-          u0[i] = dd;
-          u1[i] = s1;
-          u2[i] = df_zero();
-          const df mlt = i + 1 < r ? below_sub / dd : df_zero();
-          mult[i] = mlt;
-          d0 = below_diag - mlt * s1;
-          s1 = below_sup;
-        }
-      }
       for (int i = 0; i + 1 < r; ++i) {
         if (swp[i]) {
           const df t0 = z[i];
@@ -1130,9 +1183,10 @@ template <int P> void launch_gram_df(const Level& L, const double* d_ph, Roles r
     attr = true;
   }
   const int T3 = qp / 3, ntile = T3 * (T3 + 1) / 2, per = 256 / P;
-  const size_t smem = 6ull * qp * kGdRows * sizeof(dcx);
+  const int rows = kGdRows;
+  const size_t smem = 6ull * qp * rows * sizeof(dcx);
   k_gram_df<P><<<dim3(npart, ngroups, (ntile + per - 1) / per), 256, smem, s>>>(L.lvl<df>(), L.wts_df(), d_ph, roles,
-                                                                                q, qp, d_partials, npart);
+                                                                                q, qp, rows, d_partials, npart);
 }
 
 void gram_groups(const Level& L, const double* d_ph, Roles roles, int q, int ngroups, double2* GM, double2* GA,

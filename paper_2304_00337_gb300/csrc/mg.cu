@@ -199,6 +199,127 @@ __global__ void k_node_smooth(Lvl<T> L, const double* ph, int cpg, cx<T>* X, con
   node_smooth_at<T>(L, r, X + c * ld, B + c * ld, i, j);
 }
 
+// ---- tiled fine-level nodal steps ------------------------------------------------
+// On levels too large for the fused tail, the pre-smoothing, residual and
+// restriction of the nodal cycle run as one kernel ("down") and the prolongation
+// and post-smoothing as another ("up").  A CTA owns a 32 x 32 tile of fine nodes of
+// one column and keeps a halo in shared memory wide enough that every colour step
+// can be carried out there: colour step s of S = 4 nu needs the previous state one
+// node further out, so the region shrinks by one ring per step.  Nodes outside the
+// level are read through the Bloch extension and keep their colour (the sides are
+// even), so the redundant halo work reproduces the neighbours' values exactly.
+// The node updates use the per-node formulas of the step-by-step kernels.
+constexpr int kFT = 32;          // fine tile side
+constexpr int kFineThreads = 256;
+
+// reader of a shared-memory region whose element (0,0) is global node (oa, ob)
+template <class T> struct NRdSm {
+  const cx<T>* s;
+  int W, oa, ob;
+  __device__ __forceinline__ cx<T> v(int i, int j) const { return s[(j - ob) * W + (i - oa)]; }
+};
+
+// colour q nodes (global parity (q & 1, q >> 1)) of the region rows/cols [r0, r1) in
+// region coordinates, the region's global origin being (oa, ob)
+template <class T, class F>
+__device__ __forceinline__ void for_colour(int q, int r0, int r1, int oa, int ob, F&& f) {
+  const int pa = ((q & 1) - oa) & 1, pb = ((q >> 1) - ob) & 1;
+  const int a0 = r0 + ((pa - r0) & 1), b0 = r0 + ((pb - r0) & 1);
+  const int na = (r1 - a0 + 1) / 2, nb = (r1 - b0 + 1) / 2;
+  for (int t = threadIdx.x; t < na * nb; t += blockDim.x) f(a0 + 2 * (t % na), b0 + 2 * (t / na));
+}
+
+template <class T>
+__global__ void __launch_bounds__(kFineThreads) k_node_down(Lvl<T> L, int nc, int mc, const double* ph, int cpg,
+                                                            const cx<T>* __restrict__ B, long ldb,
+                                                            cx<T>* __restrict__ Xs, long lds, cx<T>* __restrict__ Bc,
+                                                            long ldc, int nu) {
+  extern __shared__ float4 fine_sm[];
+  // rows/cols [lo-2, lo+T+1) hold x after the last colour step (the residual reads
+  // them); step s works on that range widened by 4 nu - 1 - s rings and reads one
+  // ring further, so the region adds 4 nu + 2 rings below and 4 nu + 1 above
+  const int lo = 4 * nu + 2, W = kFT + 8 * nu + 3;
+  cx<T>* sx = reinterpret_cast<cx<T>*>(fine_sm);
+  cx<T>* sb = sx + W * W;
+  const int c = blockIdx.z, tid = threadIdx.x, nt = blockDim.x;
+  const int i0 = blockIdx.x * kFT, j0 = blockIdx.y * kFT, oa = i0 - lo, ob = j0 - lo;
+  const Ph<T> p = load_ph<T>(ph, c / cpg);
+  const cx<T>* b = B + c * ldb;
+  for (int t = tid; t < W * W; t += nt) {
+    sb[t] = gread<T>(b, oa + t % W, ob + t / W, L.n, L.m, p);
+    sx[t] = czero<T>();
+  }
+  __syncthreads();
+  const NRdSm<T> rs{sx, W, oa, ob};
+  for (int it = 0; it < nu; ++it)
+    for (int q = 0; q < 4; ++q) {
+      const int e = 4 * nu - 1 - (4 * it + q);  // rings beyond what the residual needs
+      for_colour<T>(q, lo - 2 - e, lo + kFT + 1 + e, oa, ob, [&](int a, int bb) {
+        const int k = bb * W + a;
+        const cx<T> res = sb[k] - P_at<T>(rs, L, oa + a, ob + bb);
+        sx[k] = sx[k] + (T(1) / P_diag<T>(L)) * res;
+      });
+      __syncthreads();
+    }
+  // residual b - P x in place on the fine nodes the restriction reads
+  for (int t = tid; t < (kFT + 1) * (kFT + 1); t += nt) {
+    const int a = lo - 1 + t % (kFT + 1), bb = lo - 1 + t / (kFT + 1), k = bb * W + a;
+    cx<T> y = T(-1) * P_at<T>(rs, L, oa + a, ob + bb);
+    y = y + T(1) * sb[k];
+    sb[k] = y;
+  }
+  __syncthreads();
+  const NRdSm<T> rr{sb, W, oa, ob};
+  for (int t = tid; t < (kFT / 2) * (kFT / 2); t += nt) {
+    const int I = i0 / 2 + t % (kFT / 2), J = j0 / 2 + t / (kFT / 2);
+    if (I < nc && J < mc) Bc[c * ldc + (long)J * nc + I] = restrict_node_at<T>(rr, I, J);
+  }
+  for (int t = tid; t < kFT * kFT; t += nt) {
+    const int i = i0 + t % kFT, j = j0 + t / kFT;
+    if (i < L.n && j < L.m) Xs[c * lds + (long)j * L.n + i] = sx[(lo + t / kFT) * W + lo + t % kFT];
+  }
+}
+
+template <class T>
+__global__ void __launch_bounds__(kFineThreads) k_node_up(Lvl<T> L, int nc, int mc, const double* ph, int cpg,
+                                                          const cx<T>* __restrict__ B, long ldb,
+                                                          const cx<T>* __restrict__ Xs, long lds,
+                                                          const cx<T>* __restrict__ Xc, long ldc,
+                                                          cx<T>* __restrict__ X, long ldx, int nu) {
+  extern __shared__ float4 fine_sm[];
+  // step s works on the tile widened by 4 nu - 1 - s rings and reads one ring further
+  const int lo = 4 * nu, W = kFT + 8 * nu;
+  cx<T>* sx = reinterpret_cast<cx<T>*>(fine_sm);
+  cx<T>* sb = sx + W * W;
+  const int c = blockIdx.z, tid = threadIdx.x, nt = blockDim.x;
+  const int i0 = blockIdx.x * kFT, j0 = blockIdx.y * kFT, oa = i0 - lo, ob = j0 - lo;
+  const Ph<T> p = load_ph<T>(ph, c / cpg);
+  const cx<T>* b = B + c * ldb;
+  const cx<T>* xs = Xs + c * lds;
+  const NRd<T> rc{Xc + c * ldc, nc, mc, p};
+  for (int t = tid; t < W * W; t += nt) {
+    const int i = oa + t % W, j = ob + t / W;
+    sb[t] = gread<T>(b, i, j, L.n, L.m, p);
+    sx[t] = gread<T>(xs, i, j, L.n, L.m, p) + prolong_node_at<T>(rc, i, j);
+  }
+  __syncthreads();
+  const NRdSm<T> rs{sx, W, oa, ob};
+  for (int it = 0; it < nu; ++it)
+    for (int q = 3; q >= 0; --q) {
+      const int e = 4 * nu - 1 - (4 * it + 3 - q);
+      for_colour<T>(q, lo - e, lo + kFT + e, oa, ob, [&](int a, int bb) {
+        const int k = bb * W + a;
+        const cx<T> res = sb[k] - P_at<T>(rs, L, oa + a, ob + bb);
+        sx[k] = sx[k] + (T(1) / P_diag<T>(L)) * res;
+      });
+      __syncthreads();
+    }
+  for (int t = tid; t < kFT * kFT; t += nt) {
+    const int i = i0 + t % kFT, j = j0 + t / kFT;
+    if (i < L.n && j < L.m) X[c * ldx + (long)j * L.n + i] = sx[(lo + t / kFT) * W + lo + t % kFT];
+  }
+}
+
 // ---- fused coarse-level V-cycles ---------------------------------------------
 // The levels from `top` down to the coarsest run as one kernel: one CTA per
 // column walks the rest of the V-cycle (zero, pre-smoothing by colour, residual
@@ -594,6 +715,30 @@ template <class T> double tail_bytes(const Hierarchy& H, int l, int ncols, int n
   return b;
 }
 
+// The tiled fine-level nodal kernels need the halo to wrap at most once (sides of at
+// least one tile plus both halos) and at most three sweeps per side.
+constexpr int kFineMaxNu = 3;
+inline bool fine_tiled(const Level& L, int nu_pre, int nu_post) {
+  const int need = kFT + 8 * kFineMaxNu + 3;
+  return nu_pre >= 1 && nu_post >= 1 && nu_pre <= kFineMaxNu && nu_post <= kFineMaxNu && L.n >= need && L.m >= need;
+}
+template <class T> void set_fine_smem() {
+  static bool done = false;
+  if (done) return;
+  const int W = kFT + 8 * kFineMaxNu + 3;
+  const int bytes = 2 * W * W * (int)sizeof(cx<T>);
+  PBS_CUDA(cudaFuncSetAttribute(k_node_down<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  PBS_CUDA(cudaFuncSetAttribute(k_node_up<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  done = true;
+}
+// algorithmic bytes of a tiled step: each level vector read or written once
+// (down: b in, x and the coarse right-hand side out; up: b, x, the coarse
+// correction in, x out)
+template <class T> double fine_bytes(const Level& L, int ncols, int, bool down) {
+  const double v = (double)L.N() * ncols * sizeof(cx<T>);
+  return down ? 2.25 * v : 3.25 * v;
+}
+
 template <class T>
 TailArgs<T> tail_args(const Hierarchy& H, const KData& K, MgWork<T>& w, int l, const cx<T>* b, cx<T>* x, long ld,
                       int cpg, int nu_pre, int nu_post, bool nodal) {
@@ -684,6 +829,25 @@ void node_cycle(const Hierarchy& H, const KData& K, MgWork<T>& w, int l, const c
     timer_begin(KC_NODE_TAIL, s, tail_bytes<T>(H, l, ncols, nu_pre + nu_post, true));
     k_node_tail<T><<<ncols, kTailThreads, 0, s>>>(tail_args<T>(H, K, w, l, b, x, ld, cpg, nu_pre, nu_post, true));
     timer_end(KC_NODE_TAIL, s);
+    PBS_LAUNCHED();
+    return;
+  }
+  if (fine_tiled(L, nu_pre, nu_post)) {
+    const Level& C = H.lev[l + 1];
+    const dim3 grid((L.n + kFT - 1) / kFT, (L.m + kFT - 1) / kFT, ncols);
+    const int Wd = kFT + 8 * nu_pre + 3, Wu = kFT + 8 * nu_post;
+    const size_t smd = 2ull * Wd * Wd * sizeof(cx<T>), smu = 2ull * Wu * Wu * sizeof(cx<T>);
+    set_fine_smem<T>();
+    timer_begin(KC_NODE_SMOOTH, s, fine_bytes<T>(L, ncols, nu_pre, true));
+    k_node_down<T><<<grid, kFineThreads, smd, s>>>(L.lvl<T>(), C.n, C.m, K.d_ph, cpg, b, ld, w.r[l], L.N(), w.b[l + 1],
+                                                    C.N(), nu_pre);
+    timer_end(KC_NODE_SMOOTH, s);
+    PBS_LAUNCHED();
+    node_cycle<T>(H, K, w, l + 1, w.b[l + 1], w.x[l + 1], C.N(), ncols, cpg, nu_pre, nu_post, s);
+    timer_begin(KC_NODE_SMOOTH, s, fine_bytes<T>(L, ncols, nu_post, false));
+    k_node_up<T><<<grid, kFineThreads, smu, s>>>(L.lvl<T>(), C.n, C.m, K.d_ph, cpg, b, ld, w.r[l], L.N(), w.x[l + 1],
+                                                  C.N(), x, ld, nu_post);
+    timer_end(KC_NODE_SMOOTH, s);
     PBS_LAUNCHED();
     return;
   }

@@ -134,8 +134,10 @@ def test_transfers_and_coarse_level_operators(ctx, a, b, n, m, k):
 
 
 # levels with at most 4096 nodes run as one fused kernel; 96 x 48 (4608 nodes) runs
-# its top level step by step and the rest fused, the smaller cases fused throughout
-@pytest.mark.parametrize("a,b,n,m,k", [CASES[0], CASES[1], CASES[2], CASES[3], (1.0, 0.5, 96, 48, (0.4, -1.3))])
+# its top level step by step and the rest fused; 128 x 64 runs its top nodal level as
+# the tiled down/up kernels (both sides at least 59); the smaller cases fused throughout
+@pytest.mark.parametrize("a,b,n,m,k", [CASES[0], CASES[1], CASES[2], CASES[3], (1.0, 0.5, 96, 48, (0.4, -1.3)),
+                                       (1.0, 0.5, 128, 64, (-0.8, 2.2))])
 def test_vcycles_match_reference(ctx, a, b, n, m, k):
     eps = _eps(n, m)
     geom = pbs.Geometry(eps, a, b)
