@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 
 #include "df32.cuh"
 #include "internal.h"
@@ -346,12 +347,13 @@ __global__ void __launch_bounds__(256) k_gram_fused(Lvl<double> L, Wts<double> w
 }
 
 // The same partial sums in double-float on the FP32 pipe.  Trial columns are
-// padded to qp = 3 ceil(q/3) and taken in tiles of three; thread (slot, phase)
-// accumulates the 3 x 3 tile `slot` (tiles I <= J, J-major; blockIdx.z selects
+// padded to qp = TS ceil(q/TS) and taken in tiles of TS; thread (slot, phase)
+// accumulates the TS x TS tile `slot` (tiles I <= J, J-major; blockIdx.z selects
 // which 256/P tiles this block holds) of GM and GA over rows phase, phase + P, ...
 // of each staged chunk, with Dot2 accumulators folded once per chunk.  The P
 // phases of a tile sit in one warp and are combined by shuffles in a fixed order.
 constexpr int kGdRows = 16;  // rows (nodes) per staged chunk
+constexpr int kGdTile = 2;   // tile side: 2 x 2 entries of GM and GA per thread (80 registers, 3 CTAs per SM)
 
 __device__ __forceinline__ void mac_conj(acc2& re, acc2& im, const dcx& a, const dcx& b) {
   // += conj(a) b
@@ -361,8 +363,8 @@ __device__ __forceinline__ void mac_conj(acc2& re, acc2& im, const dcx& a, const
   dot2_neg(im, a.y, b.x);
 }
 
-template <int P>
-__global__ void __launch_bounds__(256) k_gram_df(Lvl<df> L, WtsDF w, const double* ph, Roles roles, int q, int qp,
+template <int P, int TS>
+__global__ void __launch_bounds__(256, 3) k_gram_df(Lvl<df> L, WtsDF w, const double* ph, Roles roles, int q, int qp,
                                                  int rows, double2* __restrict__ part, int npart) {
   extern __shared__ float4 smf[];
   dcx* sx = reinterpret_cast<dcx*>(smf);  // [rows][qp] each
@@ -373,7 +375,7 @@ __global__ void __launch_bounds__(256) k_gram_df(Lvl<df> L, WtsDF w, const doubl
   dcx* cw = cc + rows * qp;
   const int g = blockIdx.y;
   const int tid = threadIdx.x;
-  const int T3 = qp / 3, ntile = T3 * (T3 + 1) / 2;
+  const int T3 = qp / TS, ntile = T3 * (T3 + 1) / 2;
   const int slot = blockIdx.z * (256 / P) + tid / P, phase = tid % P;
   const bool active = slot < ntile;
   int I = 0, J = 0;
@@ -388,9 +390,9 @@ __global__ void __launch_bounds__(256) k_gram_df(Lvl<df> L, WtsDF w, const doubl
     const int e = (t / (qp - q)) * qp + q + t % (qp - q);
     sx[e] = z; sy[e] = z; mx[e] = z; my[e] = z; cc[e] = z; cw[e] = z;
   }
-  acc2 mre[9], mim[9], are[9], aim[9];
+  acc2 mre[TS * TS], mim[TS * TS], are[TS * TS], aim[TS * TS];
 #pragma unroll
-  for (int k = 0; k < 9; ++k) {
+  for (int k = 0; k < TS * TS; ++k) {
     mre[k] = acc2_zero(); mim[k] = acc2_zero(); are[k] = acc2_zero(); aim[k] = acc2_zero();
   }
   const Ph<df> p = load_ph<df>(ph, g);
@@ -421,29 +423,29 @@ __global__ void __launch_bounds__(256) k_gram_df(Lvl<df> L, WtsDF w, const doubl
       // the M sums take two row streams per node (x and y edges), the A sums one
       // (curls); the streams of a matrix are consecutive rows of one loop
       for (int rr = phase; rr < rows; rr += P) {
-        const int ra = rr * qp + 3 * I, rb = rr * qp + 3 * J;
+        const int ra = rr * qp + TS * I, rb = rr * qp + TS * J;
 #pragma unroll 1
         for (int st = 0; st < 2; ++st) {
           const dcx* A = st == 0 ? sx : sy;
           const dcx* B = st == 0 ? mx : my;
-          dcx a[3], b[3];
+          dcx a[TS], b[TS];
 #pragma unroll
-          for (int k = 0; k < 3; ++k) { a[k] = A[ra + k]; b[k] = B[rb + k]; }
+          for (int k = 0; k < TS; ++k) { a[k] = A[ra + k]; b[k] = B[rb + k]; }
 #pragma unroll
-          for (int k = 0; k < 3; ++k)
+          for (int k = 0; k < TS; ++k)
 #pragma unroll
-            for (int l = 0; l < 3; ++l) mac_conj(mre[3 * k + l], mim[3 * k + l], a[k], b[l]);
+            for (int l = 0; l < TS; ++l) mac_conj(mre[TS * k + l], mim[TS * k + l], a[k], b[l]);
         }
-        dcx a[3], b[3];
+        dcx a[TS], b[TS];
 #pragma unroll
-        for (int k = 0; k < 3; ++k) { a[k] = cc[ra + k]; b[k] = cw[rb + k]; }
+        for (int k = 0; k < TS; ++k) { a[k] = cc[ra + k]; b[k] = cw[rb + k]; }
 #pragma unroll
-        for (int k = 0; k < 3; ++k)
+        for (int k = 0; k < TS; ++k)
 #pragma unroll
-          for (int l = 0; l < 3; ++l) mac_conj(are[3 * k + l], aim[3 * k + l], a[k], b[l]);
+          for (int l = 0; l < TS; ++l) mac_conj(are[TS * k + l], aim[TS * k + l], a[k], b[l]);
       }
 #pragma unroll
-      for (int k = 0; k < 9; ++k) {
+      for (int k = 0; k < TS * TS; ++k) {
         dot2_fold(mre[k]); dot2_fold(mim[k]); dot2_fold(are[k]); dot2_fold(aim[k]);
       }
     }
@@ -451,13 +453,13 @@ __global__ void __launch_bounds__(256) k_gram_df(Lvl<df> L, WtsDF w, const doubl
   const int ne = q * (q + 1) / 2;
   double2* pm = part + ((long)g * npart + blockIdx.x) * 2 * ne;
 #pragma unroll
-  for (int k = 0; k < 9; ++k) {
+  for (int k = 0; k < TS * TS; ++k) {
     df v[4] = {acc2_df(mre[k]), acc2_df(mim[k]), acc2_df(are[k]), acc2_df(aim[k])};
 #pragma unroll
     for (int o = 1; o < P; o <<= 1)
 #pragma unroll
       for (int t = 0; t < 4; ++t) v[t] = v[t] + shfl_df(v[t], o);
-    const int a = 3 * I + k / 3, b = 3 * J + k % 3;
+    const int a = TS * I + k / TS, b = TS * J + k % TS;
     if (active && phase == 0 && a < q && b < q && a <= b) {
       const int e = b * (b + 1) / 2 + a;
       pm[e] = make_double2(df_to(v[0]), df_to(v[1]));
@@ -1174,19 +1176,27 @@ int gram_partials(long rows, int ngroups) {
   return (int)(chunks < per ? chunks : per);
 }
 
-template <int P> void launch_gram_df(const Level& L, const double* d_ph, Roles roles, int q, int qp, int ngroups,
-                                     int npart, double2* d_partials, cudaStream_t s) {
+template <int P, int TS> void launch_gram_df(const Level& L, const double* d_ph, Roles roles, int q, int ngroups,
+                                             int npart, double2* d_partials, cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
-    PBS_CUDA(cudaFuncSetAttribute(k_gram_df<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  6 * kMaxTrial * kGdRows * (int)sizeof(dcx)));
+    PBS_CUDA(cudaFuncSetAttribute(k_gram_df<P, TS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  6 * (kMaxTrial + TS) * kGdRows * (int)sizeof(dcx)));
     attr = true;
   }
-  const int T3 = qp / 3, ntile = T3 * (T3 + 1) / 2, per = 256 / P;
-  const int rows = kGdRows;
-  const size_t smem = 6ull * qp * rows * sizeof(dcx);
-  k_gram_df<P><<<dim3(npart, ngroups, (ntile + per - 1) / per), 256, smem, s>>>(L.lvl<df>(), L.wts_df(), d_ph, roles,
-                                                                                q, qp, rows, d_partials, npart);
+  const int qp = TS * ((q + TS - 1) / TS), T = qp / TS, ntile = T * (T + 1) / 2, per = 256 / P;
+  const size_t smem = 6ull * qp * kGdRows * sizeof(dcx);
+  k_gram_df<P, TS><<<dim3(npart, ngroups, (ntile + per - 1) / per), 256, smem, s>>>(
+      L.lvl<df>(), L.wts_df(), d_ph, roles, q, qp, kGdRows, d_partials, npart);
+}
+
+template <int TS> void gram_df_dispatch(const Level& L, const double* d_ph, Roles roles, int q, int ngroups, int npart,
+                                        double2* d_partials, cudaStream_t s) {
+  const int T = (q + TS - 1) / TS, ntile = T * (T + 1) / 2;
+  if (ntile <= 16) launch_gram_df<16, TS>(L, d_ph, roles, q, ngroups, npart, d_partials, s);
+  else if (ntile <= 32) launch_gram_df<8, TS>(L, d_ph, roles, q, ngroups, npart, d_partials, s);
+  else if (ntile <= 64) launch_gram_df<4, TS>(L, d_ph, roles, q, ngroups, npart, d_partials, s);
+  else launch_gram_df<2, TS>(L, d_ph, roles, q, ngroups, npart, d_partials, s);
 }
 
 void gram_groups(const Level& L, const double* d_ph, Roles roles, int q, int ngroups, double2* GM, double2* GA,
@@ -1198,10 +1208,7 @@ void gram_groups(const Level& L, const double* d_ph, Roles roles, int q, int ngr
   if ((long)ngroups * npart * 2 * ne > partial_capacity) fail(PBS_EINVAL, "gram partials buffer too small");
   timer_begin(KC_GRAM, s, 8.0 * ne * 3.0 * L.N() * ngroups);  // flops: three complex MACs per entry and node
   if (dfa) {
-    const int qp = 3 * ((q + 2) / 3), T3 = qp / 3, ntile = T3 * (T3 + 1) / 2;
-    if (ntile <= 16) launch_gram_df<16>(L, d_ph, roles, q, qp, ngroups, npart, d_partials, s);
-    else if (ntile <= 32) launch_gram_df<8>(L, d_ph, roles, q, qp, ngroups, npart, d_partials, s);
-    else launch_gram_df<4>(L, d_ph, roles, q, qp, ngroups, npart, d_partials, s);
+    gram_df_dispatch<kGdTile>(L, d_ph, roles, q, ngroups, npart, d_partials, s);
   } else {
     static bool attr = false;
     if (!attr) {

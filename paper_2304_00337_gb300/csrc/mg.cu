@@ -28,6 +28,7 @@
 // colour is one parallel launch and equals the sequential block Gauss-Seidel
 // sweep; the resulting V-cycle is Hermitian.
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 
 #include "internal.h"
