@@ -124,7 +124,10 @@ typedef struct {
 } pbs_opts;
 
 /* Create a context on CUDA device `device`. `hbm_budget_bytes` caps the
- * library's device allocations (0 = no cap beyond free memory). */
+ * library's device allocations (0 = no cap beyond free memory); the multigrid
+ * work of the solver is then sized for chunks of at most an eighth of it (of
+ * 8 GiB without a cap), so more Bloch vectors in flight fit at a small cost in
+ * launches. */
 PBS_API int pbs_create(pbs_ctx **ctx, int device, size_t hbm_budget_bytes);
 
 /* Free every device allocation of the context and the context itself. NULL is a no-op. */

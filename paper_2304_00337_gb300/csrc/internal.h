@@ -70,6 +70,7 @@ struct KData {
   float2* node32 = nullptr;
   std::vector<double> k1, k2;  // host mirror
   std::vector<char> gamma;
+  int goff = 0;                // chunk views: column c uses coarsest factors of group (c / cpg + goff) % ngroups
   bool owner = true;
   bool any_gamma() const {
     for (char g : gamma)
@@ -84,6 +85,7 @@ class DevMem {
   void* alloc(size_t bytes);
   void free(void* p);
   size_t used() const { return used_; }
+  size_t budget() const { return budget_; }  // 0 = no cap
 
  private:
   size_t budget_, used_ = 0;
@@ -135,6 +137,9 @@ void free_hierarchy(DevMem& mem, Hierarchy& H);
 void alloc_kdata(DevMem& mem, const Hierarchy& H, KData& K, int ngroups);
 void set_group_k(DevMem& mem, const Hierarchy& H, KData& K, int g, double k1, double k2, cudaStream_t s);
 KData kdata_view(const KData& K, int g);  // non-owning single-group view of group g
+// non-owning view for a chunk of a role-major block starting at column group v0
+// (phase and flag tables shifted by v0, factors selected with the matching offset)
+KData kdata_chunk(const KData& K, int v0);
 void free_kdata(DevMem& mem, KData& K);
 
 // ---- operators (ops.cu); X, Y device blocks of ncols columns with stride ld ----

@@ -169,10 +169,10 @@ __global__ void k_cholesky(double2* A, int n, float2* A32, int* info) {
 // Solve L L^* x = b for each column (one warp per column).
 template <class T>
 __global__ void k_chol_solve(const cx<T>* __restrict__ Lbase, int n, const cx<T>* __restrict__ B, long ldb,
-                             cx<T>* __restrict__ X, long ldx, int ncols, int cpg, int ngroups) {
+                             cx<T>* __restrict__ X, long ldx, int ncols, int cpg, int ngroups, int goff) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (warp >= ncols) return;
-  const cx<T>* Lf = Lbase + (long)((warp / cpg) % ngroups) * n * n;
+  const cx<T>* Lf = Lbase + (long)((warp / cpg + goff) % ngroups) * n * n;
   chol_solve_warp<T>(Lf, n, B + warp * ldb, X + warp * ldx, lane);
 }
 
@@ -346,7 +346,7 @@ template <class T> struct TailArgs {
   const double* ph;
   int cpg;
   const cx<T>* factor;  // per-group coarsest Cholesky factors (nfac x nfac)
-  int nfac, ngroups;
+  int nfac, ngroups, goff;
   T mu;
   int nu_pre, nu_post;
 };
@@ -397,7 +397,7 @@ __global__ void __launch_bounds__(kTailThreads) k_node_tail(TailArgs<T> a) {
   }
   if (tid < 32) {
     const int l = a.nl - 1;
-    chol_solve_warp<T>(a.factor + (long)((c / a.cpg) % a.ngroups) * a.nfac * a.nfac, a.nfac, tail_b(a, l, c),
+    chol_solve_warp<T>(a.factor + (long)((c / a.cpg + a.goff) % a.ngroups) * a.nfac * a.nfac, a.nfac, tail_b(a, l, c),
                        tail_x(a, l, c), tid);
   }
   __syncthreads();
@@ -459,7 +459,7 @@ __global__ void __launch_bounds__(kTailThreads) k_edge_tail(TailArgs<T> a) {
   }
   if (tid < 32) {
     const int l = a.nl - 1;
-    chol_solve_warp<T>(a.factor + (long)((c / a.cpg) % a.ngroups) * a.nfac * a.nfac, a.nfac, tail_b(a, l, c),
+    chol_solve_warp<T>(a.factor + (long)((c / a.cpg + a.goff) % a.ngroups) * a.nfac * a.nfac, a.nfac, tail_b(a, l, c),
                        tail_x(a, l, c), tid);
   }
   __syncthreads();
@@ -655,6 +655,25 @@ KData kdata_view(const KData& K, int g) {
   return v;
 }
 
+KData kdata_chunk(const KData& K, int v0) {
+  KData v;
+  v.ngroups = K.ngroups;
+  v.Dc = K.Dc;
+  v.Nc = K.Nc;
+  v.d_ph = K.d_ph + 4L * v0;
+  v.d_gamma = K.d_gamma + v0;
+  v.edge64 = K.edge64;
+  v.edge32 = K.edge32;
+  v.node64 = K.node64;
+  v.node32 = K.node32;
+  v.k1 = K.k1;
+  v.k2 = K.k2;
+  v.gamma = K.gamma;
+  v.goff = (K.goff + v0) % K.ngroups;
+  v.owner = false;
+  return v;
+}
+
 void free_kdata(DevMem& mem, KData& K) {
   if (K.owner)
     for (void* p : {(void*)K.d_ph, (void*)K.d_gamma, (void*)K.edge64, (void*)K.edge32, (void*)K.node64,
@@ -765,6 +784,7 @@ TailArgs<T> tail_args(const Hierarchy& H, const KData& K, MgWork<T>& w, int l, c
   a.factor = nodal ? node_factor<T>(K) : edge_factor<T>(K);
   a.nfac = (int)(nodal ? Cst.N() : Cst.D());
   a.ngroups = K.ngroups;
+  a.goff = K.goff;
   a.mu = T(H.mu);
   a.nu_pre = nu_pre;
   a.nu_post = nu_post;
@@ -777,7 +797,7 @@ void edge_cycle(const Hierarchy& H, const KData& K, MgWork<T>& w, int l, const c
   const Level& L = H.lev[l];
   if (l == H.nlev - 1) {
     k_chol_solve<T><<<(ncols * 32 + 127) / 128, 128, 0, s>>>(edge_factor<T>(K), (int)L.D(), b, ld, x, ld, ncols, cpg,
-                                                             K.ngroups);
+                                                             K.ngroups, K.goff);
     PBS_LAUNCHED();
     return;
   }
@@ -822,7 +842,7 @@ void node_cycle(const Hierarchy& H, const KData& K, MgWork<T>& w, int l, const c
   const Level& L = H.lev[l];
   if (l == H.nlev - 1) {
     k_chol_solve<T><<<(ncols * 32 + 127) / 128, 128, 0, s>>>(node_factor<T>(K), (int)L.N(), b, ld, x, ld, ncols, cpg,
-                                                             K.ngroups);
+                                                             K.ngroups, K.goff);
     PBS_LAUNCHED();
     return;
   }

@@ -163,25 +163,33 @@ inline unsigned nblocks(long n) { return (unsigned)std::min<long>(std::max<long>
 }  // namespace
 
 // Batched solver workspace: G groups (Bloch vectors in flight) of p columns.
-// The block lives role-major, S = [E_all | P_all | W_all], group g's columns of
-// each role at g*p; S2 receives the next block.
+// The iteration's four blocks of G p columns live in one allocation of four
+// quarters: [E P | W R] or [W R | E P] (`half` says which).  E and P stay adjacent
+// (they are projected together), and the update writes P_new over R and E_new over
+// W, after which the halves swap roles: no second copy of the block is kept.
+// Group g's columns of a role start at g p.  Multigrid work (edge V-cycles, nodal
+// projection) covers at most `chunk` columns at a time and exists only in the
+// arithmetic of the precision policy in use.
 struct Work {
-  int G = 0, p = 0;
-  long D = 0, N = 0;
-  double2 *S = nullptr, *S2 = nullptr, *R = nullptr, *init = nullptr, *hist = nullptr;
+  int G = 0, p = 0, prec = -1, chunk = 0;
+  long D = 0, N = 0, hist_cols = 0;
+  double2* blk = nullptr;
+  int half = 0;
+  double2 *init = nullptr, *hist = nullptr;
   double2 *GM = nullptr, *GA = nullptr, *C = nullptr, *rr_scr = nullptr, *gpart = nullptr;
   long gpart_cap = 0;
   double *theta = nullptr, *lam = nullptr, *parts = nullptr, *norms = nullptr, *rq = nullptr;
   int* info = nullptr;
   float2 *r32 = nullptr, *w32 = nullptr;
-  float2 *nb32 = nullptr, *nx32 = nullptr, *nr32 = nullptr, *nd32 = nullptr;
-  double2 *nb64 = nullptr, *nx64 = nullptr, *nr64 = nullptr, *nd64 = nullptr;
+  void *nb = nullptr, *nx = nullptr, *nr = nullptr, *nd = nullptr;  // nodal vectors, chunk columns
   MgWork<float> e32, n32;
   MgWork<double> e64, n64;
   std::vector<void*> allocs;
-  double2* E() const { return S; }
-  double2* P() const { return S + (long)G * p * D; }
-  double2* W() const { return S + 2L * G * p * D; }
+  long block() const { return (long)G * p * D; }
+  double2* E() const { return blk + 2L * half * block(); }
+  double2* P() const { return E() + block(); }
+  double2* W() const { return blk + 2L * (1 - half) * block(); }
+  double2* R() const { return W() + block(); }
 };
 
 }  // namespace pbs
@@ -321,15 +329,40 @@ uint64_t device_eps_hash(pbs_ctx* ctx, const double* d_eps, long N) {
 }
 
 
-void ensure_work(pbs_ctx* ctx, int p, int G) {
+// Multigrid work of one chunk is kept near chunk_bytes: 8 GiB, or an eighth of the
+// context's device budget when that is smaller.  With D edges and N nodes a column
+// needs about 2 D FP32 values for the preconditioner's FP32 copies (mixed), 4 D
+// values of V-cycle work and 8 N values of nodal work, in the policy's precision.
+double chunk_bytes(size_t budget) {
+  const double cap = 8.0 * (1ull << 30);
+  return budget > 0 ? std::min(cap, (double)budget / 8.0) : cap;
+}
+
+int chunk_columns(double D, double N, int p, int q, long want, int prec, double bytes) {
+  const double c = prec == PBS_MIXED ? 8.0 : 16.0;
+  const double per = (prec == PBS_MIXED ? 2.0 * D * 8.0 : 0.0) + 4.0 * D * c + 8.0 * N * c;
+  long k = (long)(bytes / per);
+  k -= k % p;
+  k = std::max<long>(k, q);
+  return (int)std::min<long>(k, std::max<long>(want, q));
+}
+
+// Work for G groups of p columns under precision policy `prec`, with `hist_cols`
+// columns of extrapolation history.
+void ensure_work(pbs_ctx* ctx, int p, int G, int prec, long hist_cols) {
   Work& W = ctx->W;
-  if (ctx->have_w && W.p == p && W.G == G) return;
-  free_work(ctx);
   const Hierarchy& H = ctx->H;
+  if (ctx->have_w && W.p == p && W.G == G && W.prec == prec && W.hist_cols >= hist_cols &&
+      W.D == H.lev[0].D() && W.N == H.lev[0].N())
+    return;
+  free_work(ctx);
   W.G = G;
   W.p = p;
+  W.prec = prec;
   W.D = H.lev[0].D();
   W.N = H.lev[0].N();
+  W.hist_cols = hist_cols;
+  W.half = 0;
   const int q = 3 * p;
   auto A = [&](size_t bytes) {
     void* ptr = ctx->mem.alloc(bytes);
@@ -337,11 +370,12 @@ void ensure_work(pbs_ctx* ctx, int p, int G) {
     return ptr;
   };
   const long D = W.D, N = W.N, Gp = (long)G * p;
-  W.S = (double2*)A(sizeof(double2) * D * 3 * Gp);
-  W.S2 = (double2*)A(sizeof(double2) * D * 3 * Gp);
-  W.R = (double2*)A(sizeof(double2) * D * Gp);
+  const int ck = chunk_columns((double)D, (double)N, p, q, std::max<long>(2 * Gp, q), prec,
+                               chunk_bytes(ctx->mem.budget()));
+  W.chunk = ck;
+  W.blk = (double2*)A(sizeof(double2) * D * 4 * Gp);
   W.init = (double2*)A(sizeof(double2) * D * q);
-  W.hist = (double2*)A(sizeof(double2) * D * 3 * Gp);
+  if (hist_cols > 0) W.hist = (double2*)A(sizeof(double2) * D * hist_cols);
   W.GM = (double2*)A(sizeof(double2) * q * q * G);
   W.GA = (double2*)A(sizeof(double2) * q * q * G);
   W.C = (double2*)A(sizeof(double2) * q * p * G);
@@ -356,22 +390,21 @@ void ensure_work(pbs_ctx* ctx, int p, int G) {
   W.norms = (double*)A(sizeof(double) * 2 * ncol);
   W.rq = (double*)A(sizeof(double) * 2 * ncol);
   W.info = (int*)A(sizeof(int) * 8 * G);
-  W.r32 = (float2*)A(sizeof(float2) * D * Gp);
-  W.w32 = (float2*)A(sizeof(float2) * D * Gp);
-  W.nb32 = (float2*)A(sizeof(float2) * N * ncol);
-  W.nx32 = (float2*)A(sizeof(float2) * N * ncol);
-  W.nr32 = (float2*)A(sizeof(float2) * N * ncol);
-  W.nd32 = (float2*)A(sizeof(float2) * N * ncol);
-  W.nb64 = (double2*)A(sizeof(double2) * N * ncol);
-  W.nx64 = (double2*)A(sizeof(double2) * N * ncol);
-  W.nr64 = (double2*)A(sizeof(double2) * N * ncol);
-  W.nd64 = (double2*)A(sizeof(double2) * N * ncol);
-  alloc_mg_work<float>(ctx->mem, H, (int)std::max<long>(Gp, p), false, W.e32);
-  alloc_mg_work<float>(ctx->mem, H, (int)ncol, true, W.n32);
-  alloc_mg_work<double>(ctx->mem, H, (int)std::max<long>(Gp, p), false, W.e64);
-  alloc_mg_work<double>(ctx->mem, H, (int)ncol, true, W.n64);
-  PBS_CUDA(cudaMemsetAsync(W.S, 0, sizeof(double2) * D * 3 * Gp, ctx->stream));
-  PBS_CUDA(cudaMemsetAsync(W.S2, 0, sizeof(double2) * D * 3 * Gp, ctx->stream));
+  const size_t cxb = prec == PBS_MIXED ? sizeof(float2) : sizeof(double2);
+  W.nb = A(cxb * N * ck);
+  W.nx = A(cxb * N * ck);
+  W.nr = A(cxb * N * ck);
+  W.nd = A(cxb * N * ck);
+  if (prec == PBS_MIXED) {
+    W.r32 = (float2*)A(sizeof(float2) * D * ck);
+    W.w32 = (float2*)A(sizeof(float2) * D * ck);
+    alloc_mg_work<float>(ctx->mem, H, ck, false, W.e32);
+    alloc_mg_work<float>(ctx->mem, H, ck, true, W.n32);
+  } else {
+    alloc_mg_work<double>(ctx->mem, H, ck, false, W.e64);
+    alloc_mg_work<double>(ctx->mem, H, ck, true, W.n64);
+  }
+  PBS_CUDA(cudaMemsetAsync(W.blk, 0, sizeof(double2) * D * 4 * Gp, ctx->stream));
   ctx->have_w = true;
 }
 
@@ -379,18 +412,18 @@ void ensure_work(pbs_ctx* ctx, int p, int G) {
 
 template <class T> struct Bufs;
 template <> struct Bufs<float> {
-  static float2* nb(Work& W) { return W.nb32; }
-  static float2* nx(Work& W) { return W.nx32; }
-  static float2* nr(Work& W) { return W.nr32; }
-  static float2* nd(Work& W) { return W.nd32; }
+  static float2* nb(Work& W) { return (float2*)W.nb; }
+  static float2* nx(Work& W) { return (float2*)W.nx; }
+  static float2* nr(Work& W) { return (float2*)W.nr; }
+  static float2* nd(Work& W) { return (float2*)W.nd; }
   static MgWork<float>& emg(Work& W) { return W.e32; }
   static MgWork<float>& nmg(Work& W) { return W.n32; }
 };
 template <> struct Bufs<double> {
-  static double2* nb(Work& W) { return W.nb64; }
-  static double2* nx(Work& W) { return W.nx64; }
-  static double2* nr(Work& W) { return W.nr64; }
-  static double2* nd(Work& W) { return W.nd64; }
+  static double2* nb(Work& W) { return (double2*)W.nb; }
+  static double2* nx(Work& W) { return (double2*)W.nx; }
+  static double2* nr(Work& W) { return (double2*)W.nr; }
+  static double2* nd(Work& W) { return (double2*)W.nd; }
   static MgWork<double>& emg(Work& W) { return W.e64; }
   static MgWork<double>& nmg(Work& W) { return W.n64; }
 };
@@ -423,24 +456,42 @@ void project(pbs_ctx* ctx, const pbs_opts& o, const KData& K, double2* X, int nc
   if (K.any_gamma()) deflate_constants(L0, X, D, ncols, K.d_gamma, cpg, W.parts, s);
 }
 
+// Columns [0, ncols) in pieces of whole groups of cpg columns, at most the
+// workspace's chunk per piece: f(first column, columns, view of K for the piece).
+template <class F> void for_chunks(pbs_ctx* ctx, const KData& K, int ncols, int cpg, F&& f) {
+  const int per = std::max(cpg, ctx->W.chunk - ctx->W.chunk % cpg);
+  for (int c0 = 0; c0 < ncols; c0 += per) {
+    const int nc = std::min(per, ncols - c0);
+    if (c0 == 0 && nc == ncols) f(0, nc, K);
+    else f(c0, nc, kdata_chunk(K, c0 / cpg));
+  }
+}
+
 void project_dispatch(pbs_ctx* ctx, const pbs_opts& o, const KData& K, double2* X, int ncols, int cpg, int cycles,
                       cudaStream_t s) {
   if (cycles <= 0) cycles = o.nodal_cycles;
-  if (o.precision == PBS_MIXED) project<float>(ctx, o, K, X, ncols, cpg, cycles, s);
-  else project<double>(ctx, o, K, X, ncols, cpg, cycles, s);
+  const long D = ctx->W.D;
+  for_chunks(ctx, K, ncols, cpg, [&](int c0, int nc, const KData& Kc) {
+    if (o.precision == PBS_MIXED) project<float>(ctx, o, Kc, X + (long)c0 * D, nc, cpg, cycles, s);
+    else project<double>(ctx, o, Kc, X + (long)c0 * D, nc, cpg, cycles, s);
+  });
 }
 
 // W = B R (one edge V-cycle per column)
 void precondition_dispatch(pbs_ctx* ctx, const pbs_opts& o, const KData& K, const double2* R, double2* Wout, int ncols,
                            int cpg, cudaStream_t s) {
   Work& W = ctx->W;
-  if (o.precision == PBS_MIXED) {
-    convert_d2f(R, W.r32, W.D * ncols, s);
-    edge_vcycle<float>(ctx->H, K, W.e32, 0, W.r32, W.w32, W.D, ncols, cpg, o.nu_pre, o.nu_post, s);
-    convert_f2d(W.w32, Wout, W.D * ncols, s);
-  } else {
-    edge_vcycle<double>(ctx->H, K, W.e64, 0, R, Wout, W.D, ncols, cpg, o.nu_pre, o.nu_post, s);
-  }
+  for_chunks(ctx, K, ncols, cpg, [&](int c0, int nc, const KData& Kc) {
+    const double2* Rc = R + (long)c0 * W.D;
+    double2* Wc = Wout + (long)c0 * W.D;
+    if (o.precision == PBS_MIXED) {
+      convert_d2f(Rc, W.r32, W.D * nc, s);
+      edge_vcycle<float>(ctx->H, Kc, W.e32, 0, W.r32, W.w32, W.D, nc, cpg, o.nu_pre, o.nu_post, s);
+      convert_f2d(W.w32, Wc, W.D * nc, s);
+    } else {
+      edge_vcycle<double>(ctx->H, Kc, W.e64, 0, Rc, Wc, W.D, nc, cpg, o.nu_pre, o.nu_post, s);
+    }
+  });
 }
 
 // Nodal cycles for the iteration's projections.  The preconditioner maps a
@@ -501,8 +552,8 @@ void init_group(pbs_ctx* ctx, const pbs_opts& o, Group& gr, int g, const pbs_c64
   if (depth > 0) {
     // S = [E_{k-1}, E_{k-2}, ...] as stored coefficient vectors (Section 6)
     const int q = depth * p;
-    PBS_CUDA(cudaMemcpyAsync(W.init, W.hist + (long)g * 3 * p * D, sizeof(double2) * D * q, cudaMemcpyDeviceToDevice,
-                             s));
+    PBS_CUDA(cudaMemcpyAsync(W.init, W.hist + (long)g * o.extrap_depth * p * D, sizeof(double2) * D * q,
+                             cudaMemcpyDeviceToDevice, s));
     project_dispatch(ctx, o, Kv, W.init, q, q, projection_cycles(o, gr.theta_max, ctx->H.mu), s);
     tm = rr_single(ctx, Kv, W.init, q, p, Eg, o.precision == PBS_MIXED, s);
   } else {
@@ -516,7 +567,7 @@ void init_group(pbs_ctx* ctx, const pbs_opts& o, Group& gr, int g, const pbs_c64
     const int cyc = projection_cycles(o, 1e300, ctx->H.mu);
     project_dispatch(ctx, o, Kv, X0, p, p, cyc, s);
     rr_single(ctx, Kv, X0, p, p, X1, o.precision == PBS_MIXED, s);
-    double2* Rg = W.R + (long)g * p * D;
+    double2* Rg = W.R() + (long)g * p * D;
     for (int step = 0; step < 2; ++step) {
       apply_edge<double>(ctx->H.lev[0], Kv.d_ph, p, X1, Rg, nullptr, D, p, 0.0, 1.0, 0.0, nullptr, 0.0, s);
       precondition_dispatch(ctx, o, Kv, Rg, X0, p, p, s);
@@ -547,7 +598,9 @@ PathResult solve_chains(pbs_ctx* ctx, const pbs_opts& o, int nk, const double* k
   const bool dfa = o.precision == PBS_MIXED;
   const int p = o.block, G = std::max(1, std::min(nchains, nk));
   alloc_kdata(ctx->mem, ctx->H, ctx->K, G);
-  ensure_work(ctx, p, G);
+  // history slots per chain: the extrapolation depth, when some chain has a second k
+  const bool chained = o.extrap_depth > 0 && nk > G;
+  ensure_work(ctx, p, G, o.precision, chained ? (long)o.extrap_depth * G * p : 0);
   Work& W = ctx->W;
   const Level& L0 = ctx->H.lev[0];
   const long D = W.D, Gp = (long)G * p;
@@ -582,7 +635,7 @@ PathResult solve_chains(pbs_ctx* ctx, const pbs_opts& o, int nk, const double* k
     rayleigh_parts(L0, ctx->K.d_ph, p, W.E(), D, (int)Gp, W.parts, W.rq, dfa, s);
     k_rq<<<nblocks(Gp), 256, 0, s>>>(W.rq, W.lam, (int)Gp);
     PBS_LAUNCHED();
-    residual(L0, ctx->K.d_ph, p, W.E(), W.R, D, (int)Gp, W.lam, W.parts, W.norms, s);
+    residual(L0, ctx->K.d_ph, p, W.E(), W.R(), D, (int)Gp, W.lam, W.parts, W.norms, s);
     PBS_CUDA(cudaMemcpyAsync(h_norms.data(), W.norms, 2 * Gp * sizeof(double), cudaMemcpyDeviceToHost, s));
     PBS_CUDA(cudaMemcpyAsync(h_lam.data(), W.lam, Gp * sizeof(double), cudaMemcpyDeviceToHost, s));
     PBS_CUDA(cudaStreamSynchronize(s));
@@ -620,14 +673,15 @@ PathResult solve_chains(pbs_ctx* ctx, const pbs_opts& o, int nk, const double* k
         out.iters[x.pos] = x.it;
         if (!conv) out.all_converged = false;
         // history ring of the chain (newest first; oldest slot first, so no copy overlaps)
-        if (o.extrap_depth > 0 && x.pos < x.last) {
-          double2* hg = W.hist + (long)g * 3 * p * D;
-          const int keep = std::min(x.nhist, 2);
+        if (W.hist && x.pos < x.last) {
+          const int depth = o.extrap_depth;
+          double2* hg = W.hist + (long)g * depth * p * D;
+          const int keep = std::min(x.nhist, depth - 1);
           for (int slot = keep; slot >= 1; --slot)
             PBS_CUDA(cudaMemcpyAsync(hg + D * p * slot, hg + D * p * (slot - 1), sizeof(double2) * D * p,
                                      cudaMemcpyDeviceToDevice, s));
           PBS_CUDA(cudaMemcpyAsync(hg, W.E() + (long)g * p * D, sizeof(double2) * D * p, cudaMemcpyDeviceToDevice, s));
-          x.nhist = std::min(x.nhist + 1, 3);
+          x.nhist = std::min(x.nhist + 1, depth);
         }
         if (x.pos < x.last) {
           x.pos += 1;
@@ -644,7 +698,7 @@ PathResult solve_chains(pbs_ctx* ctx, const pbs_opts& o, int nk, const double* k
     if (any_cont) {
       // W = B R, projected; Gram matrices of [E, P, W] per group; Rayleigh-Ritz; update
       double2* Wd = W.W();
-      precondition_dispatch(ctx, o, ctx->K, W.R, Wd, (int)Gp, p, s);
+      precondition_dispatch(ctx, o, ctx->K, W.R(), Wd, (int)Gp, p, s);
       if (o.span == 1) {  // PINVIT (Algorithm 1): the trial block is E_hat = E - B R alone
         k_sub_from<<<nblocks(D * Gp), 256, 0, s>>>(W.E(), Wd, D * Gp);
         PBS_LAUNCHED();
@@ -676,21 +730,22 @@ PathResult solve_chains(pbs_ctx* ctx, const pbs_opts& o, int nk, const double* k
         PBS_CUDA(cudaStreamSynchronize(s));
         if (inf2[0] != 0) fail(PBS_ENUMERIC, "trial space lost rank");
       }
-      double2* E2 = W.S2;
-      double2* P2 = W.S2 + Gp * D;
       if (o.span == 1) {
-        // E_new = E_hat C
-        block_update(trial, p, W.C, p, (long)p * p, E2, D, p, nullptr, 0, D, G, false, s);
-        PBS_CUDA(cudaMemsetAsync(P2, 0, sizeof(double2) * D * Gp, s));
+        // E_new = E_hat C over the old E (E_hat lives in W); P stays zero
+        block_update(trial, p, W.C, p, (long)p * p, W.E(), D, p, nullptr, 0, D, G, false, s);
+        PBS_CUDA(cudaMemsetAsync(W.P(), 0, sizeof(double2) * D * Gp, s));
       } else {
-        // P_new = [P, W] C[p:q], E_new = E C[0:p] + P_new   (into S2, then swap)
+        // P_new = [P, W] C[p:q] over R, E_new = E C[0:p] + P_new over W, then the
+        // halves swap roles (new E, P = old W, R blocks)
+        double2* P2 = W.R();
+        double2* E2 = W.W();
         const Roles pw{{W.P(), W.W(), W.W()}, p, D};
         block_update(pw, 2 * p, W.C + p, q, (long)q * p, P2, D, p, nullptr, 0, D, G, dfa, s);
         const Roles ee{{W.E(), W.E(), W.E()}, p, D};
         block_update(ee, p, W.C, q, (long)q * p, E2, D, p, P2, D, D, G, false, s);
-        if (o.span == 2) PBS_CUDA(cudaMemsetAsync(P2, 0, sizeof(double2) * D * Gp, s));  // gradient method: no P
+        W.half = 1 - W.half;
+        if (o.span == 2) PBS_CUDA(cudaMemsetAsync(W.P(), 0, sizeof(double2) * D * Gp, s));  // gradient method: no P
       }
-      std::swap(W.S, W.S2);
       for (int g = 0; g < G; ++g)
         if (cont[g]) {
           gr[g].have_p = true;
@@ -967,7 +1022,7 @@ int pbs_apply(pbs_ctx* ctx, const pbs_geom* geom, const pbs_opts* opts, int op, 
         if (op == PBS_OP_PROJECT) {
           const int pw = std::max(1, (ncols + 2) / 3);
           if (pw > kMaxBlock) fail(PBS_EINVAL, "too many columns");
-          ensure_work(ctx, pw, 1);
+          ensure_work(ctx, pw, 1, o.precision, 0);
           PBS_CUDA(cudaMemcpyAsync(Y, X, sizeof(double2) * D * ncols, cudaMemcpyDeviceToDevice, s));
           project_dispatch(ctx, o, K, Y, ncols, ncols, o.nodal_cycles, s);
           PBS_CUDA(cudaStreamSynchronize(s));
@@ -1064,7 +1119,7 @@ int pbs_rayleigh_ritz(pbs_ctx* ctx, const pbs_geom* geom, const pbs_opts* opts, 
     ensure_hierarchy_host(ctx, geom, effective_mu(o, geom->a, geom->b), o.coarsest);
     const int pw = std::max(p, (q + 2) / 3);
     if (pw > kMaxBlock) fail(PBS_EINVAL, "q too large");
-    ensure_work(ctx, pw, 1);
+    ensure_work(ctx, pw, 1, o.precision, 0);
     set_single_k(ctx, k[0], k[1]);
     cudaStream_t s = ctx->stream;
     cudaEvent_t ev;
