@@ -109,7 +109,11 @@ typedef struct {
                        3 = LOBPCG, span(E, W, P) (Algorithm 2; default 3); W is the
                        preconditioned residual, P the previous search direction    */
   double tol;       /* convergence: ||A e - lambda M e||_2 / (lambda ||M e||_2) <= tol on
-                       the nev wanted bands (default 1e-8)                         */
+                       the nev wanted bands (default 1e-8).  A band whose FP64
+                       rounding floor is higher converges at
+                       max(tol, 0.5 * 2^-53 * lambda_max / lambda), lambda_max =
+                       max(1/eps) * 12 (1/h1^2 + 1/h2^2) (small lambda on fine
+                       meshes, e.g. band 1 next to Gamma at 1024^2)             */
   double mu;        /* regularisation A + mu M of the preconditioner (Section 5); <= 0 selects 1/(a b) */
   int nu_pre;       /* pre-smoothing sweeps (default 1)                            */
   int nu_post;      /* post-smoothing sweeps (default 1)                           */

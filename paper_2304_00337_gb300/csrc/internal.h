@@ -48,6 +48,7 @@ template <> inline Wts<float> Level::wts<float>() const { return Wts<float>{winv
 // Multigrid hierarchy of one geometry and regularisation mu.
 struct Hierarchy {
   double a = 0, b = 0, mu = 0;
+  double winv_max = 0;  // largest 1/eps on the finest level
   int n = 0, m = 0, nlev = 0;
   uint64_t key = 0;
   Level lev[kMaxLevels];

@@ -50,7 +50,7 @@ __global__ void k_weights_df(const double* __restrict__ winv, double scale, floa
 }
 
 __global__ void k_inv_eps(const double* __restrict__ eps, double* __restrict__ w64, float* __restrict__ w32, long N,
-                          int* __restrict__ bad) {
+                          int* __restrict__ bad, unsigned long long* __restrict__ wmax) {
   const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (t >= N) return;
   const double e = eps[t];
@@ -62,6 +62,8 @@ __global__ void k_inv_eps(const double* __restrict__ eps, double* __restrict__ w
   }
   w64[t] = 1.0 / e;
   w32[t] = float(1.0 / e);
+  // positive doubles order like their bit patterns
+  atomicMax(wmax, (unsigned long long)__double_as_longlong(1.0 / e));
 }
 
 __global__ void k_coarsen_w(const double* __restrict__ wf, int nf, double* __restrict__ wc, float* __restrict__ wc32,
@@ -525,9 +527,10 @@ int num_levels(int n, int m, int coarsest) {
 void build_hierarchy(DevMem& mem, Hierarchy& H, const double* d_eps, int coarsest, cudaStream_t s) {
   H.nlev = num_levels(H.n, H.m, coarsest);
   if (H.nlev < 1) fail(-1, "invalid mesh for the hierarchy");
-  int* d_bad = (int*)mem.alloc(sizeof(int));
+  int* d_bad = (int*)mem.alloc(2 * sizeof(unsigned long long));
+  unsigned long long* d_wmax = (unsigned long long*)d_bad + 1;
   H.allocs.push_back(d_bad);
-  PBS_CUDA(cudaMemsetAsync(d_bad, 0, sizeof(int), s));
+  PBS_CUDA(cudaMemsetAsync(d_bad, 0, 2 * sizeof(unsigned long long), s));
   int n = H.n, m = H.m;
   for (int l = 0; l < H.nlev; ++l) {
     Level& L = H.lev[l];
@@ -542,7 +545,7 @@ void build_hierarchy(DevMem& mem, Hierarchy& H, const double* d_eps, int coarses
     L.k3_32 = (float*)mem.alloc(6 * N * sizeof(float));
     H.allocs.insert(H.allocs.end(), {L.winv64, L.winv32, L.k3_64, L.k3_32});
     if (l == 0) {
-      k_inv_eps<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(d_eps, L.winv64, L.winv32, N, d_bad);
+      k_inv_eps<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(d_eps, L.winv64, L.winv32, N, d_bad, d_wmax);
     } else {
       const Level& F = H.lev[l - 1];
       k_coarsen_w<<<dim3((n + kBX - 1) / kBX, (m + kBY - 1) / kBY), dim3(kBX, kBY), 0, s>>>(F.winv64, F.n, L.winv64,
@@ -563,9 +566,12 @@ void build_hierarchy(DevMem& mem, Hierarchy& H, const double* d_eps, int coarses
     m /= 2;
   }
   int bad = 0;
+  unsigned long long wmax = 0;
   PBS_CUDA(cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+  PBS_CUDA(cudaMemcpyAsync(&wmax, d_wmax, sizeof(wmax), cudaMemcpyDeviceToHost, s));
   PBS_CUDA(cudaStreamSynchronize(s));
   if (bad) fail(-1, "eps must be finite and positive");
+  std::memcpy(&H.winv_max, &wmax, sizeof(double));
   const Level& C = H.lev[H.nlev - 1];
   if (C.D() > kMaxCoarseEdges) fail(-1, "coarsest level too large for the dense solve (raise coarsest or use sides with more factors of 2)");
 }

@@ -528,6 +528,20 @@ double rr_single(pbs_ctx* ctx, const KData& Kv, const double2* S, int q, int p, 
   return tm;
 }
 
+// The FP64 residual of a band with eigenvalue lambda cannot go below about
+// 0.1 u lambda_max / lambda (u = 2^-53; the curl-curl stencil's terms are up to
+// lambda_max / lambda times larger than the result; measured 0.08 - 0.16 on rod
+// crystals from 256^2 to 1024^2).  A band converges at max(tol, 0.5 u
+// lambda_max / lambda); lambda_max is bounded by max(1/eps) 12 (1/h1^2 + 1/h2^2),
+// the largest symbol value of the stencils.
+double lambda_max_bound(const Hierarchy& H) {
+  const Level& L = H.lev[0];
+  return H.winv_max * 12.0 * (1.0 / (L.h1 * L.h1) + 1.0 / (L.h2 * L.h2));
+}
+double band_tol(double tol, double lam_max, double lam) {
+  return std::max(tol, 0.5 * std::ldexp(1.0, -53) * lam_max / std::fabs(lam));
+}
+
 // Host-side state of one group (one Bloch vector in flight, one chain of the path).
 struct Group {
   int first = 0, last = -1;  // indices of its chain in the k list
@@ -619,6 +633,7 @@ PathResult solve_chains(pbs_ctx* ctx, const pbs_opts& o, int nk, const double* k
     init_group(ctx, o, gr[g], g, g == 0 ? init : nullptr, s);
   }
   std::vector<double> h_norms(2 * Gp), h_lam(Gp);
+  const double lam_max = lambda_max_bound(ctx->H);
   std::vector<int> h_info(8 * G);
   const int q = 3 * p;
   for (int round = 0;; ++round) {
@@ -653,7 +668,7 @@ PathResult solve_chains(pbs_ctx* ctx, const pbs_opts& o, int nk, const double* k
         const double r = std::sqrt(h_norms[2 * c]) / (std::fabs(h_lam[c]) * std::sqrt(h_norms[2 * c + 1]));
         if (!std::isfinite(r) || !std::isfinite(h_lam[c])) fail(PBS_ENUMERIC, "non-finite residual");
         res[j] = r;
-        conv = conv && r <= o.tol;
+        conv = conv && r <= band_tol(o.tol, lam_max, h_lam[c]);
       }
       x.theta_max = tm;
       if (verbose()) {
