@@ -230,6 +230,35 @@ PBS_API int pbs_profile_read(pbs_ctx *ctx, const char *kernel_class, double *tot
 PBS_API unsigned long long pbs_launch_count(void);
 
 /*
+ * Serving: paths of Bloch vectors (Section 6) submitted as independent requests
+ * and solved one after another by a host thread of the context, in submission
+ * order, with the same computation as pbs_solve_path.  No counterpart in the
+ * paper; it exists so that many small jobs can share one device.
+ *
+ * pbs_job_bytes: device bytes a path job of nk Bloch vectors on an n x m mesh with
+ *   these options needs on a context without a budget that holds nothing else
+ *   (hierarchy, coarsest factors, solver workspace; the admission estimate).
+ * pbs_submit: copies geom (including eps), opts and ks (host, nk*2) and queues the
+ *   job; returns at once with *job_id.  PBS_EINVAL for invalid input (checked at
+ *   submission, eps included), PBS_ENOMEM when the job's estimate exceeds the
+ *   context's budget (or 95% of the device memory when the budget is 0).
+ * pbs_poll: *done = 1 once the job has finished (successfully or not), else 0.
+ * pbs_fetch: waits until the job has finished, copies its results (host,
+ *   nk*nev eigvals and resid, nk iters; any may be NULL) and the latency from
+ *   submission to completion in seconds (may be NULL), forgets the job and
+ *   returns its status (the pbs_solve_path status; pbs_last_error in the calling
+ *   thread then describes a failure).  Unknown ids give PBS_EINVAL.
+ * Synchronous calls on the same context wait for the job in progress.
+ * pbs_destroy lets the job in progress finish and drops queued ones.
+ */
+PBS_API int pbs_job_bytes(int n, int m, const pbs_opts *opts, int nk, size_t *bytes);
+PBS_API int pbs_submit(pbs_ctx *ctx, const pbs_geom *geom, const pbs_opts *opts, int nk, const double *ks,
+                       uint64_t *job_id);
+PBS_API int pbs_poll(pbs_ctx *ctx, uint64_t job_id, int *done);
+PBS_API int pbs_fetch(pbs_ctx *ctx, uint64_t job_id, double *eigvals, double *resid, int *iters,
+                      double *latency_s);
+
+/*
  * Allocation-free Rayleigh-Ritz step.  No counterpart in the paper: it exists
  * for callers that cannot call cudaMalloc, because all of their device memory
  * is owned by another allocator (a framework's caching allocator or a fixed

@@ -98,6 +98,11 @@ def lib() -> ct.CDLL:
                                         ct.POINTER(ct.c_double)]),
         "pbs_launch_count": (ct.c_ulonglong, []),
         "pbs_small_rr_noalloc": (ct.c_int, [P, P, ct.c_int, ct.c_int, P, P, P, P]),
+        "pbs_job_bytes": (ct.c_int, [ct.c_int, ct.c_int, ct.POINTER(pbs_opts), ct.c_int, ct.POINTER(ct.c_size_t)]),
+        "pbs_submit": (ct.c_int, [P, ct.POINTER(pbs_geom), ct.POINTER(pbs_opts), ct.c_int, dp,
+                                  ct.POINTER(ct.c_uint64)]),
+        "pbs_poll": (ct.c_int, [P, ct.c_uint64, ip]),
+        "pbs_fetch": (ct.c_int, [P, ct.c_uint64, dp, dp, ip, dp]),
         "pbs_strerror": (ct.c_char_p, [ct.c_int]),
         "pbs_last_error": (ct.c_char_p, []),
     }
@@ -120,6 +125,14 @@ def small_rr_noalloc(gm_ptr: int, ga_ptr: int, q: int, p: int, c_ptr: int, theta
     without any device allocation (for callers that cannot call cudaMalloc)."""
     _check(lib().pbs_small_rr_noalloc(gm_ptr, ga_ptr, q, p, c_ptr, theta_ptr, info_ptr, _stream_ptr(stream)),
            "pbs_small_rr_noalloc")
+
+
+def job_bytes(n: int, m: int, opts, nk: int) -> int:
+    """Device bytes a path job needs (``pbs_job_bytes``, the admission estimate)."""
+    o = _opts(opts)
+    b = ct.c_size_t(0)
+    _check(lib().pbs_job_bytes(n, m, ct.byref(o), nk, ct.byref(b)), "pbs_job_bytes")
+    return int(b.value)
 
 
 def strerror(status: int) -> str:
@@ -197,6 +210,7 @@ class Context:
 
     def __init__(self, device: int = 0, hbm_budget_bytes: int = 0):
         self._ptr = ct.c_void_p()
+        self._jobs = {}  # job id -> (nk, nev) for sizing pbs_fetch's outputs
         _check(lib().pbs_create(ct.byref(self._ptr), device, hbm_budget_bytes), "pbs_create")
 
     def close(self):
@@ -252,6 +266,34 @@ class Context:
                                   it.ctypes.data_as(ct.POINTER(ct.c_int)))
         _check(st, "pbs_solve_path", (PBS_OK, PBS_ENOCONV) if allow_noconv else (PBS_OK,))
         return ev, rs, it
+
+    def submit(self, geom: Geometry, opts, ks) -> int:
+        """``pbs_submit``: queue a path job; returns its id at once."""
+        o = _opts(opts)
+        kk = np.ascontiguousarray(np.asarray(ks, dtype=np.float64).reshape(-1, 2))
+        jid = ct.c_uint64(0)
+        _check(lib().pbs_submit(self._ptr, geom.ref(), ct.byref(o), kk.shape[0], _dp(kk), ct.byref(jid)),
+               "pbs_submit")
+        self._jobs[int(jid.value)] = (kk.shape[0], o.nev)
+        return int(jid.value)
+
+    def poll(self, job: int) -> bool:
+        """``pbs_poll``: True once the job has finished."""
+        d = ct.c_int(0)
+        _check(lib().pbs_poll(self._ptr, job, ct.byref(d)), "pbs_poll")
+        return bool(d.value)
+
+    def fetch(self, job: int, allow_noconv: bool = False):
+        """``pbs_fetch``: wait for the job; returns ``(eigvals, resid, iters, latency_s)``."""
+        nk, nev = self._jobs.pop(job, (0, 0))
+        ev = np.zeros((nk, nev))
+        rs = np.zeros((nk, nev))
+        it = np.zeros(nk, dtype=np.int32)
+        lat = ct.c_double(0.0)
+        st = lib().pbs_fetch(self._ptr, job, _dp(ev), _dp(rs), it.ctypes.data_as(ct.POINTER(ct.c_int)),
+                             ct.byref(lat))
+        _check(st, "pbs_fetch", (PBS_OK, PBS_ENOCONV) if allow_noconv else (PBS_OK,))
+        return ev, rs, it, lat.value
 
     def solve_path_device(self, a, b, n, m, d_eps: int, opts, nk: int, d_ks: int, d_eigvals: int, d_resid: int,
                           d_iters: int, stream=None, allow_noconv: bool = False):

@@ -14,13 +14,19 @@
 // direction P keeps the trial basis well conditioned.
 #include <algorithm>
 #include <atomic>
-#include <cstdlib>
+#include <chrono>
 #include <cmath>
-#include <functional>
+#include <condition_variable>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <deque>
+#include <functional>
+#include <map>
 #include <memory>
+#include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "internal.h"
@@ -196,7 +202,39 @@ struct Work {
 
 using namespace pbs;
 
+namespace pbs {
+
+// One submitted path (pbs_submit): its inputs, copied at submission, and results.
+struct Job {
+  uint64_t id = 0;
+  double a = 0, b = 0;
+  int n = 0, m = 0, nk = 0;
+  std::vector<double> eps, ks;
+  pbs_opts o{};
+  std::chrono::steady_clock::time_point t_submit, t_done;
+  std::vector<double> lam, res;
+  std::vector<int> iters;
+  int status = PBS_OK;
+  std::string err;
+  bool done = false;
+};
+
+// First-in first-out job queue of a context and the host thread that runs it.
+struct Server {
+  std::mutex m;
+  std::condition_variable cv_work, cv_done;
+  std::deque<std::shared_ptr<Job>> queue;
+  std::map<uint64_t, std::shared_ptr<Job>> jobs;
+  uint64_t next_id = 1;
+  std::thread worker;
+  bool stop = false;
+};
+
+}  // namespace pbs
+
 struct pbs_ctx {
+  std::mutex gpu_mu;  // every call that uses the context's device state holds it
+  pbs::Server srv;
   int device = 0;
   cudaStream_t stream = nullptr;
   DevMem mem;
@@ -786,6 +824,71 @@ void set_single_k(pbs_ctx* ctx, double k1, double k2) {
 }  // namespace
 
 namespace {
+int run_guarded_impl(const std::function<void()>& f);
+
+// Device bytes a path job needs on a context that holds nothing else: the
+// geometry's hierarchy, the per-Bloch-vector coarsest factors and the solver
+// workspace, as ensure_work and build_hierarchy allocate them (the nodal and edge
+// multigrid work counted as 4/3 of three fine-level vectors per column).
+double job_bytes(int n, int m, const pbs_opts& o, int nk, size_t budget) {
+  const int nl = num_levels(n, m, o.coarsest);
+  double hb = 0.0;
+  for (int l = 0; l < nl; ++l) hb += (double)(n >> l) * (m >> l) * (8 + 4 + 48 + 24);
+  const double N = (double)n * m, D = 2.0 * N;
+  hb += 8.0 * N + 8.0 * N;  // level-0 double-float weights, device copy of eps
+  const double Nc = (double)(n >> (nl - 1)) * (m >> (nl - 1)), Dc = 2.0 * Nc;
+  const int G = std::max(1, std::min(o.kbatch, nk)), p = o.block, q = 3 * p;
+  const double Gp = (double)G * p;
+  const double kd = G * (Dc * Dc + Nc * Nc) * (16.0 + 8.0);
+  const int ck = chunk_columns(D, N, p, q, (long)std::max<double>(2 * Gp, q), o.precision, chunk_bytes(budget));
+  const double cxb = o.precision == PBS_MIXED ? 8.0 : 16.0;
+  const bool chained = o.extrap_depth > 0 && nk > G;
+  double wb = 16.0 * D * (4.0 * Gp + q) + (chained ? 16.0 * D * o.extrap_depth * Gp : 0.0);
+  wb += 4.0 * N * ck * cxb + 4.0 * D * ck * cxb + 4.0 * N * ck * cxb;
+  if (o.precision == PBS_MIXED) wb += 2.0 * D * ck * 8.0;
+  wb += 16.0 * (3.0 * q * q * G) + 16.0 * q * (q + 1) * 2 * 152 + 64.0 * D / 8.0 * std::max<double>(3 * Gp, q);
+  return hb + kd + wb;
+}
+
+// Host thread of a context's job queue: runs each job as pbs_solve_path would,
+// under the context lock, and records its results and completion time.
+void serve(pbs_ctx* ctx) {
+  cudaSetDevice(ctx->device);
+  Server& sv = ctx->srv;
+  for (;;) {
+    std::shared_ptr<Job> j;
+    {
+      std::unique_lock<std::mutex> lk(sv.m);
+      sv.cv_work.wait(lk, [&] { return sv.stop || !sv.queue.empty(); });
+      if (sv.stop) return;
+      j = sv.queue.front();
+      sv.queue.pop_front();
+    }
+    int status = PBS_OK;
+    const int rc = run_guarded_impl([&] {
+      std::lock_guard<std::mutex> ctx_lock(ctx->gpu_mu);
+      TimerScope ts(ctx);
+      const pbs_geom geom{j->a, j->b, j->n, j->m, j->eps.data()};
+      ensure_hierarchy_host(ctx, &geom, effective_mu(j->o, j->a, j->b), j->o.coarsest);
+      const PathResult r = solve_chains(ctx, j->o, j->nk, j->ks.data(), j->o.kbatch, nullptr);
+      j->lam = r.lam;
+      j->res = r.res;
+      j->iters = r.iters;
+      if (!r.all_converged) status = PBS_ENOCONV;
+    });
+    {
+      std::lock_guard<std::mutex> lk(sv.m);
+      j->status = rc != PBS_OK ? rc : status;
+      if (rc != PBS_OK) j->err = g_last_error;
+      j->t_done = std::chrono::steady_clock::now();
+      j->done = true;
+    }
+    sv.cv_done.notify_all();
+  }
+}
+}  // namespace
+
+namespace {
 int run_guarded_impl(const std::function<void()>& f) {
   try {
     g_last_error.clear();
@@ -861,6 +964,13 @@ int pbs_create(pbs_ctx** ctx, int device, size_t hbm_budget_bytes) {
 
 int pbs_destroy(pbs_ctx* ctx) {
   if (!ctx) return PBS_OK;
+  {
+    // the job in progress finishes; queued jobs are dropped
+    std::lock_guard<std::mutex> lk(ctx->srv.m);
+    ctx->srv.stop = true;
+  }
+  ctx->srv.cv_work.notify_all();
+  if (ctx->srv.worker.joinable()) ctx->srv.worker.join();
   return run_guarded_impl([&] {
     DeviceGuard g(ctx->device);
     cudaStreamSynchronize(ctx->stream);
@@ -883,6 +993,7 @@ int pbs_solve_k(pbs_ctx* ctx, const pbs_geom* geom, const pbs_opts* opts, const 
   if (!ctx || !geom || !opts || !k || !eigvals || !resid || !iters) return PBS_EINVAL;
   int status = PBS_OK;
   const int rc = run_guarded_impl([&] {
+    std::lock_guard<std::mutex> ctx_lock(ctx->gpu_mu);
     DeviceGuard g(ctx->device);
     TimerScope ts(ctx);
     pbs_opts o = *opts;
@@ -918,6 +1029,7 @@ int pbs_solve_path(pbs_ctx* ctx, const pbs_geom* geom, const pbs_opts* opts, int
   if (!ctx || !geom || !opts || nk < 0 || (nk > 0 && (!ks || !eigvals || !resid || !iters))) return PBS_EINVAL;
   int status = PBS_OK;
   const int rc = run_guarded_impl([&] {
+    std::lock_guard<std::mutex> ctx_lock(ctx->gpu_mu);
     DeviceGuard g(ctx->device);
     TimerScope ts(ctx);
     validate_opts(*opts);
@@ -939,6 +1051,7 @@ int pbs_solve_path_device(pbs_ctx* ctx, double a, double b, int n, int m, const 
     return PBS_EINVAL;
   int status = PBS_OK;
   const int rc = run_guarded_impl([&] {
+    std::lock_guard<std::mutex> ctx_lock(ctx->gpu_mu);
     DeviceGuard g(ctx->device);
     TimerScope ts(ctx);
     validate_opts(*opts);
@@ -971,6 +1084,7 @@ int pbs_apply(pbs_ctx* ctx, const pbs_geom* geom, const pbs_opts* opts, int op, 
   if (!ctx || !geom || !opts || !k || ncols < 0) return PBS_EINVAL;
   if (ncols > 0 && (!x || !y)) return PBS_EINVAL;
   return run_guarded_impl([&] {
+    std::lock_guard<std::mutex> ctx_lock(ctx->gpu_mu);
     DeviceGuard g(ctx->device);
     TimerScope ts(ctx);
     const pbs_opts& o = *opts;
@@ -1094,6 +1208,7 @@ int pbs_gram(pbs_ctx* ctx, const pbs_geom* geom, const double k[2], int q, const
   if (precision != PBS_FP64 && precision != PBS_MIXED) return PBS_EINVAL;
   if (q > 0 && (!S || !GM || !GA)) return PBS_EINVAL;
   return run_guarded_impl([&] {
+    std::lock_guard<std::mutex> ctx_lock(ctx->gpu_mu);
     DeviceGuard g(ctx->device);
     TimerScope ts(ctx);
     if (q == 0) return;
@@ -1127,6 +1242,7 @@ int pbs_rayleigh_ritz(pbs_ctx* ctx, const pbs_geom* geom, const pbs_opts* opts, 
   if (!ctx || !geom || !opts || !k || q < 1 || p < 1 || p > q || p > kMaxBlock || !S || !theta || !X)
     return PBS_EINVAL;
   return run_guarded_impl([&] {
+    std::lock_guard<std::mutex> ctx_lock(ctx->gpu_mu);
     DeviceGuard g(ctx->device);
     TimerScope ts(ctx);
     const pbs_opts& o = *opts;
@@ -1164,6 +1280,7 @@ static int class_of(const char* name) {
 
 int pbs_profile_enable(pbs_ctx* ctx, const char* classes) {
   if (!ctx) return PBS_EINVAL;
+  std::lock_guard<std::mutex> ctx_lock(ctx->gpu_mu);
   unsigned mask = 0;
   int every = 1;
   std::string spec = classes ? classes : "";
@@ -1211,6 +1328,7 @@ int pbs_profile_enable(pbs_ctx* ctx, const char* classes) {
 
 int pbs_profile_read(pbs_ctx* ctx, const char* kernel_class, double* total_ms, long* launches, double* work) {
   if (!ctx || !kernel_class || !total_ms || !launches || !work) return PBS_EINVAL;
+  std::lock_guard<std::mutex> ctx_lock(ctx->gpu_mu);
   const int c = class_of(kernel_class);
   if (c < 0) return PBS_EINVAL;
   *total_ms = ctx->timer.total_ms[c];
@@ -1220,5 +1338,95 @@ int pbs_profile_read(pbs_ctx* ctx, const char* kernel_class, double* total_ms, l
 }
 
 unsigned long long pbs_launch_count(void) { return g_launches.load(); }
+
+int pbs_job_bytes(int n, int m, const pbs_opts* opts, int nk, size_t* bytes) {
+  if (!opts || !bytes || nk < 1) return PBS_EINVAL;
+  return run_guarded_impl([&] {
+    validate_opts(*opts);
+    validate_mesh(1.0, 1.0, n, m);
+    if (num_levels(n, m, opts->coarsest) < 1) fail(PBS_EINVAL, "invalid mesh for the hierarchy");
+    *bytes = (size_t)job_bytes(n, m, *opts, nk, 0);
+  });
+}
+
+int pbs_submit(pbs_ctx* ctx, const pbs_geom* geom, const pbs_opts* opts, int nk, const double* ks,
+               uint64_t* job_id) {
+  if (!ctx || !geom || !opts || nk < 1 || !ks || !job_id || !geom->eps) return PBS_EINVAL;
+  return run_guarded_impl([&] {
+    validate_opts(*opts);
+    validate_mesh(geom->a, geom->b, geom->n, geom->m);
+    if (num_levels(geom->n, geom->m, opts->coarsest) < 1) fail(PBS_EINVAL, "invalid mesh for the hierarchy");
+    const long N = (long)geom->n * geom->m;
+    for (long t = 0; t < N; ++t)
+      if (!(geom->eps[t] > 0.0) || !std::isfinite(geom->eps[t])) fail(PBS_EINVAL, "eps must be finite and positive");
+    for (long t = 0; t < 2L * nk; ++t)
+      if (!std::isfinite(ks[t])) fail(PBS_EINVAL, "k must be finite");
+    // admission: the job must fit the context's budget, or the device
+    const double need = job_bytes(geom->n, geom->m, *opts, nk, ctx->mem.budget());
+    size_t cap = ctx->mem.budget();
+    if (cap == 0) {
+      DeviceGuard g(ctx->device);
+      size_t fr = 0, tot = 0;
+      PBS_CUDA(cudaMemGetInfo(&fr, &tot));
+      cap = (size_t)(0.95 * (double)tot);
+    }
+    if (need > (double)cap) fail(PBS_ENOMEM, "job needs more device memory than the context may use");
+    auto j = std::make_shared<Job>();
+    j->a = geom->a;
+    j->b = geom->b;
+    j->n = geom->n;
+    j->m = geom->m;
+    j->nk = nk;
+    j->eps.assign(geom->eps, geom->eps + N);
+    j->ks.assign(ks, ks + 2L * nk);
+    j->o = *opts;
+    Server& sv = ctx->srv;
+    {
+      std::lock_guard<std::mutex> lk(sv.m);
+      if (sv.stop) fail(PBS_EINVAL, "context is shutting down");
+      j->id = sv.next_id++;
+      j->t_submit = std::chrono::steady_clock::now();
+      sv.jobs[j->id] = j;
+      sv.queue.push_back(j);
+      if (!sv.worker.joinable()) sv.worker = std::thread(serve, ctx);
+    }
+    sv.cv_work.notify_one();
+    *job_id = j->id;
+  });
+}
+
+int pbs_poll(pbs_ctx* ctx, uint64_t job_id, int* done) {
+  if (!ctx || !done) return PBS_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->srv.m);
+  auto it = ctx->srv.jobs.find(job_id);
+  if (it == ctx->srv.jobs.end()) {
+    g_last_error = "unknown job";
+    return PBS_EINVAL;
+  }
+  *done = it->second->done ? 1 : 0;
+  return PBS_OK;
+}
+
+int pbs_fetch(pbs_ctx* ctx, uint64_t job_id, double* eigvals, double* resid, int* iters, double* latency_s) {
+  if (!ctx) return PBS_EINVAL;
+  std::shared_ptr<Job> j;
+  {
+    std::unique_lock<std::mutex> lk(ctx->srv.m);
+    auto it = ctx->srv.jobs.find(job_id);
+    if (it == ctx->srv.jobs.end()) {
+      g_last_error = "unknown job";
+      return PBS_EINVAL;
+    }
+    j = it->second;
+    ctx->srv.cv_done.wait(lk, [&] { return j->done; });
+    ctx->srv.jobs.erase(it);
+  }
+  if (eigvals) std::copy(j->lam.begin(), j->lam.end(), eigvals);
+  if (resid) std::copy(j->res.begin(), j->res.end(), resid);
+  if (iters) std::copy(j->iters.begin(), j->iters.end(), iters);
+  if (latency_s) *latency_s = std::chrono::duration<double>(j->t_done - j->t_submit).count();
+  g_last_error = j->err;
+  return j->status;
+}
 
 }  // extern "C"

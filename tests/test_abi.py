@@ -53,3 +53,22 @@ def test_struct_layout_matches_header(built):
     # pbs_opts: 5 ints, 2 doubles, 5 ints, 1 uint64, 1 int with natural alignment
     assert ct.sizeof(pbs.pbs_opts) == 80
     assert ct.sizeof(pbs.pbs_geom) == 32
+
+
+def test_job_bytes_admission_estimate(built):
+    # pbs_job_bytes is host arithmetic: the device bytes a path job needs
+    o = dict(nev=8, block=10, kbatch=4)
+    b256 = pbs.job_bytes(256, 256, o, 31)
+    assert 1e8 < b256 < 2e10
+    assert pbs.job_bytes(256, 256, dict(o, kbatch=8), 31) > b256  # more Bloch vectors in flight
+    assert pbs.job_bytes(512, 512, o, 31) > 3 * b256  # four times the unknowns
+    # a chain needs extrapolation history; all Bloch vectors in flight need none
+    assert pbs.job_bytes(256, 256, dict(o, kbatch=31), 31) < pbs.job_bytes(256, 256, dict(o, kbatch=31), 62)
+    # 1024 x 1024, 64 Bloch vectors in flight, block 10, fits one 288 GB device
+    # (multigrid work is chunked to a fixed byte size, so both policies need about the same)
+    c3 = pbs.job_bytes(1024, 1024, dict(nev=8, block=10, kbatch=64), 64)
+    assert 64 * 40 * 32 * 2 ** 20 < c3 < 250e9  # at least the four role blocks of 640 FP64 columns
+    assert pbs.job_bytes(1024, 1024, dict(nev=8, block=10, kbatch=64, precision=pbs.PBS_FP64), 64) < 250e9
+    with pytest.raises(pbs.PbsError) as e:
+        pbs.job_bytes(255, 256, o, 4)
+    assert e.value.status == pbs.PBS_EINVAL
