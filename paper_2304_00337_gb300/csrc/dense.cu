@@ -1169,10 +1169,19 @@ void residual(const Level& L, const double* d_ph, int cpg, const double2* E, dou
   PBS_LAUNCHED();
 }
 
+// Partial blocks per group: enough to fill the GPU, and enough that no block sums
+// more than kGramChunksPerBlock chunks of rows.  The double-float kernel keeps its
+// sums as float pairs whose trailing parts collect rounding errors; a bounded row
+// count per block keeps that error at a few units of 2^-48 whatever the mesh size
+// and the number of Bloch vectors in flight (unbounded, 64 groups on a 512^2 mesh
+// left about 1e-10 and the iteration stalled).
+constexpr long kGramChunksPerBlock = 64;
+
 int gram_partials(long rows, int ngroups) {
   const long chunks = (rows + kGramRows - 1) / kGramRows;
   long per = (2 * 152 + ngroups - 1) / ngroups;
   if (per < 8) per = 8;
+  per = std::max(per, (chunks + kGramChunksPerBlock - 1) / kGramChunksPerBlock);
   return (int)(chunks < per ? chunks : per);
 }
 

@@ -846,7 +846,9 @@ double job_bytes(int n, int m, const pbs_opts& o, int nk, size_t budget) {
   double wb = 16.0 * D * (4.0 * Gp + q) + (chained ? 16.0 * D * o.extrap_depth * Gp : 0.0);
   wb += 4.0 * N * ck * cxb + 4.0 * D * ck * cxb + 4.0 * N * ck * cxb;
   if (o.precision == PBS_MIXED) wb += 2.0 * D * ck * 8.0;
-  wb += 16.0 * (3.0 * q * q * G) + 16.0 * q * (q + 1) * 2 * 152 + 64.0 * D / 8.0 * std::max<double>(3 * Gp, q);
+  wb += 16.0 * (3.0 * q * q * G) + 16.0 * (double)std::max(gram_partials_size((long)N, q, G),
+                                                           gram_partials_size((long)N, q, 1)) +
+        64.0 * D / 8.0 * std::max<double>(3 * Gp, q);
   return hb + kd + wb;
 }
 
