@@ -332,7 +332,8 @@ def profile_run(nk: int, precision: str):
     ks = gi.gxmg_path(NK)[:nk]
     prec = pbs.PBS_MIXED if precision == "mixed" else pbs.PBS_FP64
     with pbs.Context(0) as ctx:
-        lam, res, it = ctx.solve_path(geom, pbs.default_opts(nev=NEV, block=BLOCK, tol=TOL, precision=prec), ks)
+        lam, res, it = ctx.solve_path(geom, pbs.default_opts(nev=NEV, block=BLOCK, tol=TOL, precision=prec,
+                                                             kbatch=min(KBATCH, nk)), ks)
     print(f"profile-run ok: {nk} k-points, iterations {it.tolist()}, max resid {res.max():.2e}", flush=True)
 
 
