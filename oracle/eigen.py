@@ -45,8 +45,10 @@ def closed_form_eps_const(a: float, b: float, n: int, m: int, eps: float, k, cou
     q = np.arange(m)
     t1 = (k[0] + 2 * np.pi * p / a) * h1
     t2 = (k[1] + 2 * np.pi * q / b) * h2
-    f1 = 6 * (1 - np.cos(t1)) / (h1 ** 2 * (2 + np.cos(t1)))
-    f2 = 6 * (1 - np.cos(t2)) / (h2 ** 2 * (2 + np.cos(t2)))
+    # 1 - cos t written as 2 sin^2(t/2): the same value without the cancellation
+    # that costs u / (t^2 / 2) relative accuracy for small angles (fine meshes near k = 0)
+    f1 = 12 * np.sin(t1 / 2) ** 2 / (h1 ** 2 * (2 + np.cos(t1)))
+    f2 = 12 * np.sin(t2 / 2) ** 2 / (h2 ** 2 * (2 + np.cos(t2)))
     lam = (f1[None, :] + f2[:, None]).ravel() / eps
     lam = np.sort(lam)
     # drop exact zeros (the constant wave at k = 0)
