@@ -337,6 +337,58 @@ def profile_run(nk: int, precision: str):
     print(f"profile-run ok: {nk} k-points, iterations {it.tolist()}, max resid {res.max():.2e}", flush=True)
 
 
+def serving_bench(njobs: int) -> None:
+    """Serving workload: a seeded stream of rod-crystal path jobs (radius U(0.1, 0.45) a,
+    eps U(2, 13), 6-12 bands with two throw-away vectors, 7-64 Bloch vectors on
+    Gamma-X-M-Gamma; meshes 128x128 and 256x256) submitted through pbs_submit at Poisson
+    arrival times, at 0.8 of the saturation rate measured in a closed-loop warm-up.
+    Prints one JSON line with the p50 / p99 latency from submission to completion."""
+    import __graft_entry__ as ge
+    ge.build()
+    import paper_2304_00337_gb300 as pbs
+    import pbs_inputs as gi
+    jobs = gi.serving_jobs(njobs, seed=0, rate_per_s=1.0, grids=(128, 256))
+
+    def args_of(j):
+        geom = pbs.Geometry(gi.rod_eps(j["grid"], j["grid"], radius=j["radius"], eps_rod=j["eps_rod"]))
+        o = pbs.default_opts(nev=j["bands"], block=j["block"], tol=TOL, kbatch=min(KBATCH, j["nk"]))
+        return geom, o, gi.gxmg_path(j["nk"])
+
+    prepared = [args_of(j) for j in jobs]
+    with pbs.Context(0) as ctx:
+        # closed loop: the first eight jobs back to back give the mean service time
+        warm = prepared[:8]
+        t0 = time.perf_counter()
+        ids = [ctx.submit(*a) for a in warm]
+        for i in ids:
+            ctx.fetch(i)
+        service = (time.perf_counter() - t0) / len(warm)
+        rate = 0.8 / service
+        # open loop: Poisson arrivals (the stream's unit-rate arrival times scaled to `rate`)
+        start = time.perf_counter()
+        ids = []
+        for j, a in zip(jobs, prepared):
+            due = start + j["arrival_s"] / rate
+            now = time.perf_counter()
+            if due > now:
+                time.sleep(due - now)
+            ids.append(ctx.submit(*a))
+        res = [ctx.fetch(i) for i in ids]
+        wall = time.perf_counter() - start
+    lat = np.array([r[3] for r in res])
+    ok = all(np.all(r[1] <= TOL * 100) for r in res)
+    kpts = sum(j["nk"] for j in jobs)
+    print(json.dumps({
+        "metric": "serving latency p50 (submission to completion)", "value": float(np.percentile(lat, 50)),
+        "unit": "s", "higher_is_better": False, "p99_s": float(np.percentile(lat, 99)),
+        "mean_s": float(lat.mean()), "jobs": njobs, "arrival_rate_per_s": rate, "service_s_closed_loop": service,
+        "throughput_jobs_per_s": njobs / wall, "throughput_kpoints_per_s": kpts / wall, "converged": bool(ok),
+        "data": "synthetic", "n_gpus": 1,
+        "config": {"workload": "rod-crystal path jobs, Poisson arrivals at 0.8 x saturation", "grids": [128, 256],
+                   "bands": "6-12 (+2 throw-away)", "k_points_per_job": "7-64", "seed": 0,
+                   "k_points_in_flight_per_job": KBATCH}}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -346,7 +398,13 @@ def main():
     ap.add_argument("--profile-run", type=int, default=0, metavar="NK",
                     help="solve the first NK k-points once (no timing) - the small case for ncu captures")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--workload", default="path", choices=["path", "serving"],
+                    help="path: the headline 256x256 path (default); serving: the job-stream latency line")
+    ap.add_argument("--jobs", type=int, default=32, help="jobs of the serving workload")
     args = ap.parse_args()
+    if args.workload == "serving" and args.impl == "ours":
+        serving_bench(args.jobs)
+        return
     if args.profile_run:
         profile_run(args.profile_run, args.precision)
         return
