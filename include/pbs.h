@@ -125,7 +125,17 @@ typedef struct {
                        into kbatch contiguous chains solved in lock-step, one block of
                        `block` columns each, every launch covering all of them; each chain
                        extrapolates along its own segment (Section 6)                 */
+  int start;        /* first Bloch vector of each chain when no init block is given:
+                       PBS_START_RANDOM (default): seeded random block smoothed by two
+                       preconditioned inverse-iteration steps; PBS_START_NESTED: the
+                       nested iteration of Section 6 (solve on the coarsest hierarchy
+                       mesh with at least 16 x 16 cells, prolongate the block level by
+                       level, iterate each finer mesh to relative residual 1e-3)     */
 } pbs_opts;
+
+/* ---- starts (pbs_opts.start) ------------------------------------------ */
+#define PBS_START_RANDOM 0
+#define PBS_START_NESTED 1
 
 /* Create a context on CUDA device `device`. `hbm_budget_bytes` caps the
  * library's device allocations (0 = no cap beyond free memory); the multigrid

@@ -31,6 +31,8 @@ PBS_ECUDA = -6
 # precision
 PBS_FP64 = 0
 PBS_MIXED = 1
+PBS_START_RANDOM = 0
+PBS_START_NESTED = 1
 # operators
 OPS = dict(A=0, M=1, A_MU_M=2, C=3, CH=4, L=5, LH=6, P_NODAL=7, PROLONG=8, RESTRICT=9, PROLONG_NODAL=10,
            RESTRICT_NODAL=11, VCYCLE_EDGE=12, VCYCLE_NODAL=13, PROJECT=14)
@@ -62,7 +64,8 @@ class pbs_opts(ct.Structure):
     _fields_ = [("nev", ct.c_int), ("block", ct.c_int), ("max_iter", ct.c_int), ("precision", ct.c_int),
                 ("span", ct.c_int), ("tol", ct.c_double), ("mu", ct.c_double), ("nu_pre", ct.c_int),
                 ("nu_post", ct.c_int), ("coarsest", ct.c_int), ("nodal_cycles", ct.c_int),
-                ("extrap_depth", ct.c_int), ("seed", ct.c_uint64), ("kbatch", ct.c_int)]
+                ("extrap_depth", ct.c_int), ("seed", ct.c_uint64), ("kbatch", ct.c_int),
+                ("start", ct.c_int)]
 
 
 _lib = None

@@ -297,6 +297,7 @@ void validate_opts(const pbs_opts& o) {
   if (o.nodal_cycles < 1) fail(PBS_EINVAL, "nodal_cycles must be >= 1");
   if (o.extrap_depth < 0 || o.extrap_depth > 3) fail(PBS_EINVAL, "extrap_depth must be 0..3");
   if (o.kbatch < 1 || o.kbatch > 256) fail(PBS_EINVAL, "kbatch must be 1..256");
+  if (o.start != PBS_START_RANDOM && o.start != PBS_START_NESTED) fail(PBS_EINVAL, "unknown start");
 }
 
 void validate_mesh(double a, double b, int n, int m) {
@@ -592,7 +593,8 @@ struct Group {
 
 // Start block of group g into E_g (P_g zeroed): extrapolation from the group's history,
 // else `init` (host, D x p) or a seeded random block smoothed by two steps E <- B M E.
-void init_group(pbs_ctx* ctx, const pbs_opts& o, Group& gr, int g, const pbs_c64* init, cudaStream_t s) {
+void init_group(pbs_ctx* ctx, const pbs_opts& o, Group& gr, int g, const pbs_c64* init, cudaStream_t s,
+                const double2* dev_init = nullptr) {
   Work& W = ctx->W;
   const int p = o.block;
   const long D = W.D;
@@ -608,6 +610,11 @@ void init_group(pbs_ctx* ctx, const pbs_opts& o, Group& gr, int g, const pbs_c64
                              cudaMemcpyDeviceToDevice, s));
     project_dispatch(ctx, o, Kv, W.init, q, q, projection_cycles(o, gr.theta_max, ctx->H.mu), s);
     tm = rr_single(ctx, Kv, W.init, q, p, Eg, o.precision == PBS_MIXED, s);
+  } else if (dev_init) {
+    // a block prolongated from a coarser mesh (nested iteration): project, Rayleigh-Ritz
+    PBS_CUDA(cudaMemcpyAsync(W.init, dev_init, sizeof(double2) * D * p, cudaMemcpyDeviceToDevice, s));
+    project_dispatch(ctx, o, Kv, W.init, p, p, projection_cycles(o, 1e300, ctx->H.mu), s);
+    tm = rr_single(ctx, Kv, W.init, p, p, Eg, o.precision == PBS_MIXED, s);
   } else {
     double2* X0 = W.init;           // p columns
     double2* X1 = W.init + D * p;   // p columns
@@ -645,7 +652,10 @@ struct PathResult {
 // chain after its first starts from the extrapolation of that chain's previous
 // bases (Section 6).  A group whose k converged records it and restarts on the next
 // k of its chain while the other groups keep iterating.
-PathResult solve_chains(pbs_ctx* ctx, const pbs_opts& o, int nk, const double* ks, int nchains, const pbs_c64* init) {
+const double2* nested_blocks(pbs_ctx* ctx, const pbs_opts& o, int G, const std::vector<double>& kfirst);
+
+PathResult solve_chains(pbs_ctx* ctx, const pbs_opts& o, int nk, const double* ks, int nchains, const pbs_c64* init,
+                        const double2* dev_init = nullptr) {
   cudaStream_t s = ctx->stream;
   const bool dfa = o.precision == PBS_MIXED;
   const int p = o.block, G = std::max(1, std::min(nchains, nk));
@@ -662,14 +672,21 @@ PathResult solve_chains(pbs_ctx* ctx, const pbs_opts& o, int nk, const double* k
   out.res.assign((long)nk * o.nev, 0.0);
   out.iters.assign(nk, 0);
   std::vector<Group> gr(G);
+  std::vector<double> kfirst(2 * G);
   for (int g = 0; g < G; ++g) {
     gr[g].first = (int)((long)nk * g / G);
     gr[g].last = (int)((long)nk * (g + 1) / G) - 1;
     gr[g].pos = gr[g].first;
     gr[g].active = true;
-    set_group_k(ctx->mem, ctx->H, ctx->K, g, ks[2 * gr[g].pos], ks[2 * gr[g].pos + 1], s);
-    init_group(ctx, o, gr[g], g, g == 0 ? init : nullptr, s);
+    kfirst[2 * g] = ks[2 * gr[g].pos];
+    kfirst[2 * g + 1] = ks[2 * gr[g].pos + 1];
+    set_group_k(ctx->mem, ctx->H, ctx->K, g, kfirst[2 * g], kfirst[2 * g + 1], s);
   }
+  // first Bloch vector of every chain: a given block, the nested iteration, or a smoothed random start
+  const double2* first = dev_init;
+  if (!first && !init && o.start == PBS_START_NESTED) first = nested_blocks(ctx, o, G, kfirst);
+  for (int g = 0; g < G; ++g)
+    init_group(ctx, o, gr[g], g, g == 0 ? init : nullptr, s, first ? first + (long)g * p * D : nullptr);
   std::vector<double> h_norms(2 * Gp), h_lam(Gp);
   const double lam_max = lambda_max_bound(ctx->H);
   std::vector<int> h_info(8 * G);
@@ -829,6 +846,60 @@ PathResult solve_chains(pbs_ctx* ctx, const pbs_opts& o, int nk, const double* k
 }
 
 // single-group tables for the operator entry points
+// Nested iteration for the first Bloch vector of each chain (Section 6): the block
+// iteration on the coarsest hierarchy level with at least 16 x 16 cells (the
+// "direct" solve: run there to the requested tolerance), then level by level the
+// converged blocks are prolongated by the natural embedding (Section 5) and iterated
+// on the next finer mesh to a relative residual of 1e-3 (the mesh change itself
+// moves eigenvectors by about that much), all chains together.  The coarse meshes
+// carry the hierarchy's averaged 1/eps.  Returns the prolongated level-1 blocks on
+// level 0 (G groups of p columns in the R block), or null when the mesh has no
+// coarse level of that size (then random starts are used).
+struct ChildCtxs {
+  std::vector<pbs_ctx*> c;
+  ~ChildCtxs() {
+    for (pbs_ctx* x : c)
+      if (x) pbs_destroy(x);
+  }
+};
+
+const double2* nested_blocks(pbs_ctx* ctx, const pbs_opts& o, int G, const std::vector<double>& kfirst) {
+  const Hierarchy& H = ctx->H;
+  int lc = 0;
+  for (int l = 1; l < H.nlev; ++l)
+    if (H.lev[l].n >= 16 && H.lev[l].m >= 16) lc = l;
+  if (lc == 0) return nullptr;
+  cudaStream_t s = ctx->stream;
+  Work& W = ctx->W;
+  const int p = o.block;
+  ChildCtxs kids;
+  kids.c.assign(lc + 1, nullptr);
+  const double2* prev = nullptr;  // prolongated blocks on level l (device), none on the coarsest
+  for (int l = lc; l >= 1; --l) {
+    const Level& L = H.lev[l];
+    std::vector<double> winv(L.N()), eps(L.N());
+    PBS_CUDA(cudaMemcpyAsync(winv.data(), L.winv64, sizeof(double) * L.N(), cudaMemcpyDeviceToHost, s));
+    PBS_CUDA(cudaStreamSynchronize(s));
+    for (long t = 0; t < L.N(); ++t) eps[t] = 1.0 / winv[t];
+    if (pbs_create(&kids.c[l], ctx->device, 0) != PBS_OK) fail(PBS_ECUDA, "nested iteration: context");
+    pbs_ctx* c = kids.c[l];
+    const pbs_geom geom{H.a, H.b, L.n, L.m, eps.data()};
+    pbs_opts ol = o;
+    ol.start = PBS_START_RANDOM;
+    ol.kbatch = G;
+    ol.tol = l == lc ? o.tol : std::max(o.tol, 1e-3);
+    ensure_hierarchy_host(c, &geom, H.mu, o.coarsest);
+    solve_chains(c, ol, G, kfirst.data(), G, nullptr, prev);
+    // natural embedding of the converged blocks into level l - 1, phases of each group
+    PBS_CUDA(cudaStreamSynchronize(c->stream));
+    prolong_edge<double>(H.lev[l - 1], L, ctx->K.d_ph, p, c->W.E(), L.D(), W.R(), H.lev[l - 1].D(), G * p, false,
+                         s);
+    PBS_CUDA(cudaStreamSynchronize(s));
+    prev = W.R();
+  }
+  return W.R();
+}
+
 void set_single_k(pbs_ctx* ctx, double k1, double k2) {
   alloc_kdata(ctx->mem, ctx->H, ctx->K, 1);
   set_group_k(ctx->mem, ctx->H, ctx->K, 0, k1, k2, ctx->stream);
@@ -955,6 +1026,7 @@ void pbs_default_opts(pbs_opts* o) {
   o->extrap_depth = 3;
   o->seed = 0;
   o->kbatch = 1;
+  o->start = PBS_START_RANDOM;
 }
 
 int pbs_num_levels(int n, int m, int coarsest) {

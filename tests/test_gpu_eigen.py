@@ -162,3 +162,30 @@ def test_batched_path_is_deterministic(ctx):
     a = ctx.solve_path(geom, o, ks)[0]
     b = ctx.solve_path(geom, o, ks)[0]
     assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_nested_start_on_rod64_path(ctx, precision):
+    # nested iteration (Section 6) for the first Bloch vector of each of 3 chains:
+    # 64x64 -> coarse solve on 16x16, prolongated through 32x32; the converged path
+    # must match the oracle like the random start does
+    data = np.loadtxt(os.path.join(GOLDEN, "rod64_path31.txt"))
+    ks, want = data[:, :2], data[:, 2:]
+    geom = pbs.Geometry(gi.rod_eps(64, 64))
+    lam, res, iters = ctx.solve_path(geom, dict(nev=8, block=10, precision=precision, kbatch=3,
+                                                start=pbs.PBS_START_NESTED), ks)
+    assert np.max(np.abs(lam - want) / want) <= 1e-10
+    assert np.all(res <= 1e-8)
+
+
+def test_nested_start_saves_fine_iterations(ctx):
+    # the first Bloch vector at 256x256: starting from the prolongated coarse solutions
+    # needs fewer iterations on the finest mesh than the smoothed random start, and
+    # converges to the same eigenvalues
+    geom = pbs.Geometry(gi.rod_eps(256, 256))
+    k = (0.9, 0.3)
+    lam_r, res_r, it_r, _ = ctx.solve_k(geom, dict(nev=8, block=10), k)
+    lam_n, res_n, it_n, _ = ctx.solve_k(geom, dict(nev=8, block=10, start=pbs.PBS_START_NESTED), k)
+    assert np.all(res_n <= 1e-8) and np.all(res_r <= 1e-8)
+    assert np.allclose(lam_n, lam_r, rtol=1e-10)
+    assert it_n < it_r
