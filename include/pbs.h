@@ -180,6 +180,21 @@ PBS_API int pbs_solve_path(pbs_ctx *ctx, const pbs_geom *geom, const pbs_opts *o
                    double *eigvals, double *resid, int *iters);
 
 /*
+ * The kappa x kappa Brillouin-zone sample of Section 6,
+ *   k_ij = (pi/a (2 i/(kappa-1) - 1), pi/b (2 j/(kappa-1) - 1)),  i, j in [0, kappa),
+ * with the paper's extrapolation schedule: k_00 from the start block (opts->start),
+ * row 0 horizontally (k_i0 from up to three predecessors in the row), columns 0, 1, 2
+ * vertically from row 0, and every other k_ij horizontally from k_{i-3..i-1, j} (the
+ * paper leaves rows 1 and 2 beyond column 2 unstated; read as horizontal).  The rows
+ * beyond column 2 are independent chains and run opts->kbatch at a time.
+ * Outputs (host, index j*kappa + i): ks (kappa^2 * 2, may be NULL), eigvals and resid
+ * (kappa^2 * nev), iters (kappa^2).  kappa >= 2.  Returns PBS_ENOCONV (outputs
+ * filled) when some Bloch vector reached max_iter.
+ */
+PBS_API int pbs_solve_grid(pbs_ctx *ctx, const pbs_geom *geom, const pbs_opts *opts, int kappa, double *ks,
+                           double *eigvals, double *resid, int *iters);
+
+/*
  * Same as pbs_solve_path with every array on the device: d_eps (n*m doubles),
  * d_ks (nk*2), d_eigvals (nk*nev), d_resid (nk*nev), d_iters (nk ints); the
  * work is issued on `cuda_stream` (a cudaStream_t, NULL = legacy default) and

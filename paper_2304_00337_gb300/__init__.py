@@ -101,6 +101,7 @@ def lib() -> ct.CDLL:
                                         ct.POINTER(ct.c_double)]),
         "pbs_launch_count": (ct.c_ulonglong, []),
         "pbs_small_rr_noalloc": (ct.c_int, [P, P, ct.c_int, ct.c_int, P, P, P, P]),
+        "pbs_solve_grid": (ct.c_int, [P, ct.POINTER(pbs_geom), ct.POINTER(pbs_opts), ct.c_int, dp, dp, dp, ip]),
         "pbs_job_bytes": (ct.c_int, [ct.c_int, ct.c_int, ct.POINTER(pbs_opts), ct.c_int, ct.POINTER(ct.c_size_t)]),
         "pbs_submit": (ct.c_int, [P, ct.POINTER(pbs_geom), ct.POINTER(pbs_opts), ct.c_int, dp,
                                   ct.POINTER(ct.c_uint64)]),
@@ -269,6 +270,20 @@ class Context:
                                   it.ctypes.data_as(ct.POINTER(ct.c_int)))
         _check(st, "pbs_solve_path", (PBS_OK, PBS_ENOCONV) if allow_noconv else (PBS_OK,))
         return ev, rs, it
+
+    def solve_grid(self, geom: Geometry, opts, kappa: int, allow_noconv: bool = False):
+        """``pbs_solve_grid``: the kappa x kappa sample with the paper's extrapolation schedule;
+        returns ``(ks, eigvals, resid, iters)`` indexed ``j * kappa + i``."""
+        o = _opts(opts)
+        nk = kappa * kappa
+        ks = np.zeros((nk, 2))
+        ev = np.zeros((nk, o.nev))
+        rs = np.zeros((nk, o.nev))
+        it = np.zeros(nk, dtype=np.int32)
+        st = lib().pbs_solve_grid(self._ptr, geom.ref(), ct.byref(o), kappa, _dp(ks), _dp(ev), _dp(rs),
+                                  it.ctypes.data_as(ct.POINTER(ct.c_int)))
+        _check(st, "pbs_solve_grid", (PBS_OK, PBS_ENOCONV) if allow_noconv else (PBS_OK,))
+        return ks, ev, rs, it
 
     def submit(self, geom: Geometry, opts, ks) -> int:
         """``pbs_submit``: queue a path job; returns its id at once."""

@@ -583,8 +583,9 @@ double band_tol(double tol, double lam_max, double lam) {
 
 // Host-side state of one group (one Bloch vector in flight, one chain of the path).
 struct Group {
-  int first = 0, last = -1;  // indices of its chain in the k list
-  int pos = 0;               // index being solved
+  int chain = -1;  // chain being solved (index into the chain list)
+  int t = 0;       // position in the chain
+  int pos = 0;     // index of the Bloch vector being solved in the k list
   int it = 0;
   bool have_p = false, active = false, need_init = false;
   int nhist = 0;
@@ -654,14 +655,42 @@ struct PathResult {
 // k of its chain while the other groups keep iterating.
 const double2* nested_blocks(pbs_ctx* ctx, const pbs_opts& o, int G, const std::vector<double>& kfirst);
 
+// A chain of Bloch vectors solved in order by one group (Section 6): `idx` indexes
+// the k list; `seeds` (device blocks of p columns, newest first, at most
+// extrap_depth) are the bases its first Bloch vector is extrapolated from (none:
+// a start block); save[t] >= 0 copies the converged block of its t-th Bloch vector
+// into slot save[t] of the caller's store (p columns per slot).
+struct Chain {
+  std::vector<int> idx;
+  std::vector<const double2*> seeds;
+  std::vector<int> save;
+};
+
+// Solve every chain of the list with G groups in lock-step; a group whose chain is
+// done takes the next chain of the list.
+PathResult solve_chain_list(pbs_ctx* ctx, const pbs_opts& o, int nk, const double* ks, const std::vector<Chain>& chains,
+                            int Gwant, const pbs_c64* init, const double2* dev_init, double2* store);
+
 PathResult solve_chains(pbs_ctx* ctx, const pbs_opts& o, int nk, const double* ks, int nchains, const pbs_c64* init,
                         const double2* dev_init = nullptr) {
+  const int G = std::max(1, std::min(nchains, nk));
+  std::vector<Chain> chains(G);
+  for (int g = 0; g < G; ++g)
+    for (int i = (int)((long)nk * g / G); i <= (int)((long)nk * (g + 1) / G) - 1; ++i) chains[g].idx.push_back(i);
+  return solve_chain_list(ctx, o, nk, ks, chains, G, init, dev_init, nullptr);
+}
+
+PathResult solve_chain_list(pbs_ctx* ctx, const pbs_opts& o, int nk, const double* ks, const std::vector<Chain>& chains,
+                            int Gwant, const pbs_c64* init, const double2* dev_init, double2* store) {
   cudaStream_t s = ctx->stream;
   const bool dfa = o.precision == PBS_MIXED;
-  const int p = o.block, G = std::max(1, std::min(nchains, nk));
+  const int p = o.block, G = std::max(1, std::min<int>(Gwant, (int)chains.size()));
   alloc_kdata(ctx->mem, ctx->H, ctx->K, G);
-  // history slots per chain: the extrapolation depth, when some chain has a second k
-  const bool chained = o.extrap_depth > 0 && nk > G;
+  // history slots per group: the extrapolation depth, when some chain has a second
+  // Bloch vector or seeds
+  bool chained = false;
+  for (const Chain& c : chains) chained = chained || c.idx.size() > 1 || !c.seeds.empty();
+  chained = chained && o.extrap_depth > 0;
   ensure_work(ctx, p, G, o.precision, chained ? (long)o.extrap_depth * G * p : 0);
   Work& W = ctx->W;
   const Level& L0 = ctx->H.lev[0];
@@ -673,16 +702,31 @@ PathResult solve_chains(pbs_ctx* ctx, const pbs_opts& o, int nk, const double* k
   out.iters.assign(nk, 0);
   std::vector<Group> gr(G);
   std::vector<double> kfirst(2 * G);
+  int next_chain = G;
+  // the seeds of group g's chain become its history (newest first)
+  auto seed_history = [&](int g) {
+    Group& x = gr[g];
+    x.nhist = 0;
+    if (!W.hist) return;
+    const Chain& c = chains[x.chain];
+    const int ns = std::min<int>((int)c.seeds.size(), o.extrap_depth);
+    double2* hg = W.hist + (long)g * o.extrap_depth * p * D;
+    for (int t = 0; t < ns; ++t)
+      PBS_CUDA(cudaMemcpyAsync(hg + D * p * t, c.seeds[t], sizeof(double2) * D * p, cudaMemcpyDeviceToDevice, s));
+    x.nhist = ns;
+  };
   for (int g = 0; g < G; ++g) {
-    gr[g].first = (int)((long)nk * g / G);
-    gr[g].last = (int)((long)nk * (g + 1) / G) - 1;
-    gr[g].pos = gr[g].first;
+    gr[g].chain = g;
+    gr[g].t = 0;
+    gr[g].pos = chains[g].idx[0];
     gr[g].active = true;
     kfirst[2 * g] = ks[2 * gr[g].pos];
     kfirst[2 * g + 1] = ks[2 * gr[g].pos + 1];
     set_group_k(ctx->mem, ctx->H, ctx->K, g, kfirst[2 * g], kfirst[2 * g + 1], s);
+    seed_history(g);
   }
-  // first Bloch vector of every chain: a given block, the nested iteration, or a smoothed random start
+  // first Bloch vector of every chain: seeds, a given block, the nested iteration, or a
+  // smoothed random start
   const double2* first = dev_init;
   if (!first && !init && o.start == PBS_START_NESTED) first = nested_blocks(ctx, o, G, kfirst);
   for (int g = 0; g < G; ++g)
@@ -755,8 +799,13 @@ PathResult solve_chains(pbs_ctx* ctx, const pbs_opts& o, int nk, const double* k
         }
         out.iters[x.pos] = x.it;
         if (!conv) out.all_converged = false;
+        const Chain& ch = chains[x.chain];
+        if (store && x.t < (int)ch.save.size() && ch.save[x.t] >= 0)
+          PBS_CUDA(cudaMemcpyAsync(store + (long)ch.save[x.t] * p * D, W.E() + (long)g * p * D,
+                                   sizeof(double2) * D * p, cudaMemcpyDeviceToDevice, s));
+        const bool more = x.t + 1 < (int)ch.idx.size();
         // history ring of the chain (newest first; oldest slot first, so no copy overlaps)
-        if (W.hist && x.pos < x.last) {
+        if (W.hist && more) {
           const int depth = o.extrap_depth;
           double2* hg = W.hist + (long)g * depth * p * D;
           const int keep = std::min(x.nhist, depth - 1);
@@ -766,8 +815,16 @@ PathResult solve_chains(pbs_ctx* ctx, const pbs_opts& o, int nk, const double* k
           PBS_CUDA(cudaMemcpyAsync(hg, W.E() + (long)g * p * D, sizeof(double2) * D * p, cudaMemcpyDeviceToDevice, s));
           x.nhist = std::min(x.nhist + 1, depth);
         }
-        if (x.pos < x.last) {
-          x.pos += 1;
+        if (more) {
+          x.t += 1;
+          x.pos = ch.idx[x.t];
+          x.need_init = true;
+        } else if (next_chain < (int)chains.size()) {
+          // the next chain of the list, started from its own seeds
+          x.chain = next_chain++;
+          x.t = 0;
+          x.pos = chains[x.chain].idx[0];
+          seed_history(g);
           x.need_init = true;
         } else {
           x.active = false;
@@ -1425,6 +1482,81 @@ int pbs_profile_read(pbs_ctx* ctx, const char* kernel_class, double* total_ms, l
 }
 
 unsigned long long pbs_launch_count(void) { return g_launches.load(); }
+
+int pbs_solve_grid(pbs_ctx* ctx, const pbs_geom* geom, const pbs_opts* opts, int kappa, double* ks_out,
+                   double* eigvals, double* resid, int* iters) {
+  if (!ctx || !geom || !opts || kappa < 2 || !eigvals || !resid || !iters) return PBS_EINVAL;
+  int status = PBS_OK;
+  const int rc = run_guarded_impl([&] {
+    std::lock_guard<std::mutex> ctx_lock(ctx->gpu_mu);
+    DeviceGuard g(ctx->device);
+    TimerScope ts(ctx);
+    const pbs_opts o = *opts;
+    validate_opts(o);
+    ensure_hierarchy_host(ctx, geom, effective_mu(o, geom->a, geom->b), o.coarsest);
+    // k_ij = (pi/a (2 i/(kappa-1) - 1), pi/b (2 j/(kappa-1) - 1)), index j kappa + i (Section 6)
+    const int K = kappa, nk = K * K, p = o.block;
+    std::vector<double> ks(2L * nk);
+    for (int j = 0; j < K; ++j)
+      for (int i = 0; i < K; ++i) {
+        ks[2L * (j * K + i)] = M_PI / geom->a * (2.0 * i / (K - 1) - 1.0);
+        ks[2L * (j * K + i) + 1] = M_PI / geom->b * (2.0 * j / (K - 1) - 1.0);
+      }
+    if (ks_out) std::copy(ks.begin(), ks.end(), ks_out);
+    // bases of the first three columns, kept for the vertical and the row extrapolations
+    const int nc = std::min(3, K);
+    const long D = ctx->H.lev[0].D();
+    auto slot = [&](int i, int j) { return j * nc + i; };
+    double2* store = (double2*)ctx->mem.alloc(sizeof(double2) * D * p * nc * K);
+    auto at = [&](int i, int j) -> const double2* { return store + (long)slot(i, j) * p * D; };
+    bool all_conv = true;
+    auto merge = [&](const std::vector<Chain>& chains, const PathResult& r) {
+      for (const Chain& c : chains)
+        for (int k : c.idx) {
+          for (int b = 0; b < o.nev; ++b) {
+            eigvals[(long)k * o.nev + b] = r.lam[(long)k * o.nev + b];
+            resid[(long)k * o.nev + b] = r.res[(long)k * o.nev + b];
+          }
+          iters[k] = r.iters[k];
+        }
+      all_conv = all_conv && r.all_converged;
+    };
+    try {
+      // row 0, horizontally: k_00 from the start, k_i0 from up to three predecessors
+      std::vector<Chain> row0(1);
+      for (int i = 0; i < K; ++i) {
+        row0[0].idx.push_back(i);
+        row0[0].save.push_back(i < nc ? slot(i, 0) : -1);
+      }
+      merge(row0, solve_chain_list(ctx, o, nk, ks.data(), row0, 1, nullptr, nullptr, store));
+      // columns 0..2, vertically from row 0
+      std::vector<Chain> cols(nc);
+      for (int i = 0; i < nc; ++i) {
+        cols[i].seeds = {at(i, 0)};
+        for (int j = 1; j < K; ++j) {
+          cols[i].idx.push_back(j * K + i);
+          cols[i].save.push_back(slot(i, j));
+        }
+      }
+      if (K > 1) merge(cols, solve_chain_list(ctx, o, nk, ks.data(), cols, o.kbatch, nullptr, nullptr, store));
+      // rows 1.., horizontally from k_2j, k_1j, k_0j (the survey's reading for j = 1, 2 as well)
+      std::vector<Chain> rows;
+      for (int j = 1; j < K && K > 3; ++j) {
+        Chain c;
+        c.seeds = {at(2, j), at(1, j), at(0, j)};
+        for (int i = 3; i < K; ++i) c.idx.push_back(j * K + i);
+        rows.push_back(c);
+      }
+      if (!rows.empty()) merge(rows, solve_chain_list(ctx, o, nk, ks.data(), rows, o.kbatch, nullptr, nullptr, store));
+    } catch (...) {
+      ctx->mem.free(store);
+      throw;
+    }
+    ctx->mem.free(store);
+    if (!all_conv) status = PBS_ENOCONV;
+  });
+  return rc != PBS_OK ? rc : status;
+}
 
 int pbs_job_bytes(int n, int m, const pbs_opts* opts, int nk, size_t* bytes) {
   if (!opts || !bytes || nk < 1) return PBS_EINVAL;

@@ -189,3 +189,26 @@ def test_nested_start_saves_fine_iterations(ctx):
     assert np.all(res_n <= 1e-8) and np.all(res_r <= 1e-8)
     assert np.allclose(lam_n, lam_r, rtol=1e-10)
     assert it_n < it_r
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+@pytest.mark.parametrize("kappa", [5, 6])
+def test_brillouin_zone_grid_schedule(ctx, precision, kappa):
+    # kappa x kappa sample of Section 6 with its horizontal / vertical extrapolation
+    # schedule, 16x16 rod crystal (kappa = 5 includes Gamma at the centre): every
+    # eigenvalue against the oracle's dense solve, lambda(k) = lambda(-k) across the
+    # mirrored grid points, and extrapolated points need fewer iterations than k_00
+    n, nev = 16, 4
+    eps = gi.rod_eps(n, n)
+    geom = pbs.Geometry(eps)
+    ks, lam, res, iters = ctx.solve_grid(geom, dict(nev=nev, block=6, precision=precision, kbatch=3), kappa)
+    assert np.all(res <= 1e-8)
+    i, j = np.meshgrid(np.arange(kappa), np.arange(kappa))
+    want_k = np.stack([np.pi * (2 * i / (kappa - 1) - 1), np.pi * (2 * j / (kappa - 1) - 1)], -1).reshape(-1, 2)
+    assert np.allclose(ks, want_k, atol=1e-15)
+    for t, k in enumerate(ks):
+        want = eigen.solve_k(1, 1, n, n, eps, k, nev, "dense")[0]
+        assert np.max(np.abs(lam[t] - want) / want) <= 1e-10, (t, k)
+    mirror = (kappa - 1 - j) * kappa + (kappa - 1 - i)
+    assert np.allclose(lam, lam[mirror.ravel()], rtol=1e-9)
+    assert np.mean(iters[1:]) < iters[0]
