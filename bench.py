@@ -420,6 +420,38 @@ def grid_bench(kappa: int, n: int) -> None:
                                  "k_points_in_flight": KBATCH, "precision": "mixed"}}), flush=True)
 
 
+def throwaway_bench(n: int) -> None:
+    """Section 7 experiment: eps = 100 in the disk |x - (1/2, 1/2)| <= 1/3, 1 elsewhere;
+    16 wanted bands plus 1..16 throw-away vectors, at k = (pi/2, pi/4) on an n x n mesh
+    (the paper names neither), for the paper's preconditioned block inverse iteration
+    (span 1) and LOBPCG (span 3), tolerance 1e-8 on the wanted bands only.  One JSON
+    line: iterations, time and the observed convergence factor per iteration,
+    (1e-8)^(1/iterations), for each count of throw-away vectors."""
+    import __graft_entry__ as ge
+    ge.build()
+    import paper_2304_00337_gb300 as pbs
+    import pbs_inputs as gi
+    geom = pbs.Geometry(gi.rod_eps(n, n, radius=1.0 / 3.0, eps_rod=100.0))
+    k = (np.pi / 2, np.pi / 4)
+    rows = []
+    with pbs.Context(0) as ctx:
+        ctx.solve_k(geom, dict(nev=16, block=17, tol=1e-4), k, allow_noconv=True)  # warm-up
+        for span in (1, 3):
+            for extra in (1, 2, 4, 8, 16):
+                o = dict(nev=16, block=16 + extra, span=span, max_iter=2000, seed=0)
+                t0 = time.perf_counter()
+                lam, res, it, _ = ctx.solve_k(geom, o, k, allow_noconv=True)
+                dt = time.perf_counter() - t0
+                rows.append({"span": span, "throw_away": extra, "iterations": int(it), "seconds": dt,
+                             "rate_per_iteration": float(1e-8 ** (1.0 / max(int(it), 1))),
+                             "max_resid": float(res.max())})
+    best = min((r for r in rows if r["span"] == 3), key=lambda r: r["seconds"])
+    print(json.dumps({"metric": "throw-away study: fastest LOBPCG solve (16 bands)", "value": best["seconds"],
+                      "unit": "s", "higher_is_better": False, "n_gpus": 1, "data": "synthetic", "results": rows,
+                      "config": {"workload": f"eps=100 disk r=1/3, {n}x{n}, k=(pi/2,pi/4), 16 bands",
+                                 "precision": "mixed", "tol": 1e-8}}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -429,7 +461,7 @@ def main():
     ap.add_argument("--profile-run", type=int, default=0, metavar="NK",
                     help="solve the first NK k-points once (no timing) - the small case for ncu captures")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--workload", default="path", choices=["path", "serving", "grid"],
+    ap.add_argument("--workload", default="path", choices=["path", "serving", "grid", "throwaway"],
                     help="path: the headline 256x256 path (default); serving: the job-stream latency line; "
                          "grid: the paper's kappa x kappa Brillouin-zone workload")
     ap.add_argument("--kappa", type=int, default=30, help="grid workload: k-points per direction")
@@ -441,6 +473,9 @@ def main():
         return
     if args.workload == "grid" and args.impl == "ours":
         grid_bench(args.kappa, args.grid_n)
+        return
+    if args.workload == "throwaway" and args.impl == "ours":
+        throwaway_bench(128)
         return
     if args.profile_run:
         profile_run(args.profile_run, args.precision)
