@@ -508,7 +508,7 @@ __global__ void k_gram_finalize(const double2* __restrict__ part, int npart, int
 // recomputed in FP64 from the updated block), and a serial chain of FP64
 // instructions is what limited this one-block kernel on GB300.
 constexpr double kDropTol = 1e-12;  // relative pivot below which a trial direction is dropped
-constexpr int kRRThreads = 256;
+constexpr int kRRThreads = 512;
 constexpr int kRRWarps = kRRThreads / 32;
 
 __device__ __forceinline__ df warp_sum_df(df v) {
