@@ -290,16 +290,22 @@ __global__ void __launch_bounds__(kFineThreads) k_node_up(Lvl<T> L, int nc, int 
                                                           const cx<T>* __restrict__ Xc, long ldc,
                                                           cx<T>* __restrict__ X, long ldx, int nu) {
   extern __shared__ float4 fine_sm[];
-  // step s works on the tile widened by 4 nu - 1 - s rings and reads one ring further
-  const int lo = 4 * nu, W = kFT + 8 * nu;
+  // step s works on the tile widened by 4 nu - 1 - s rings and reads one ring further;
+  // the coarse nodes the region's prolongation reads (origin (oa/2, ob/2), W/2 + 1
+  // per side, oa and ob even) are staged first
+  const int lo = 4 * nu, W = kFT + 8 * nu, Wc = W / 2 + 1;
   cx<T>* sx = reinterpret_cast<cx<T>*>(fine_sm);
   cx<T>* sb = sx + W * W;
+  cx<T>* sc = sb + W * W;
   const int c = blockIdx.z, tid = threadIdx.x, nt = blockDim.x;
   const int i0 = blockIdx.x * kFT, j0 = blockIdx.y * kFT, oa = i0 - lo, ob = j0 - lo;
   const Ph<T> p = load_ph<T>(ph, c / cpg);
   const cx<T>* b = B + c * ldb;
   const cx<T>* xs = Xs + c * lds;
-  const NRd<T> rc{Xc + c * ldc, nc, mc, p};
+  const cx<T>* xc = Xc + c * ldc;
+  for (int t = tid; t < Wc * Wc; t += nt) sc[t] = gread<T>(xc, (oa >> 1) + t % Wc, (ob >> 1) + t / Wc, nc, mc, p);
+  __syncthreads();
+  const NRdSm<T> rc{sc, Wc, oa >> 1, ob >> 1};
   for (int t = tid; t < W * W; t += nt) {
     const int i = oa + t % W, j = ob + t / W;
     sb[t] = gread<T>(b, i, j, L.n, L.m, p);
@@ -330,21 +336,22 @@ __global__ void __launch_bounds__(kFineThreads) k_node_up(Lvl<T> L, int nc, int 
 // and post-smoothing on the way up) with block-wide barriers between the steps.
 // Every point update is the function the one-launch-per-step kernels call, in
 // the same colour order, so the result is the one of the unfused V-cycle.
+// The level vectors live in shared memory for the whole cycle: x on every tail
+// level, b below the top one (the top right-hand side is read in place) and one
+// residual buffer of the top level's size; the top x is written out at the end.
 template <class T> struct TailLevel {
   Lvl<T> L;
   Wts<T> w;     // edge cycles only
   const T* k3;  // edge cycles only
-  cx<T>* x;     // level work vectors (columns of `len` at stride `len`); x, b unused at the top
-  cx<T>* b;
-  cx<T>* r;
-  long len;
+  int sx, sb;   // shared-memory offsets (elements) of x and b; sb unused at the top
 };
 template <class T> struct TailArgs {
   int nl;  // levels in the tail, the last one the coarsest
   TailLevel<T> lev[kMaxLevels];
+  int sr;           // shared-memory offset of the residual buffer
   const cx<T>* b0;  // top level right-hand sides and solutions, columns at stride ld0
   cx<T>* x0;
-  long ld0;
+  long ld0, len0;   // len0: values per top-level column
   const double* ph;
   int cpg;
   const cx<T>* factor;  // per-group coarsest Cholesky factors (nfac x nfac)
@@ -353,13 +360,11 @@ template <class T> struct TailArgs {
   int nu_pre, nu_post;
 };
 constexpr int kTailThreads = 512;
-constexpr long kTailMaxNodes = 4096;  // a level joins the tail when it has at most this many nodes
+constexpr long kTailMaxNodes = 4096;        // a level joins the tail when it has at most this many nodes
+constexpr int kTailSmemBytes = 200 * 1024;  // and the tail's shared-memory vectors fit in this
 
-template <class T> __device__ __forceinline__ cx<T>* tail_x(const TailArgs<T>& a, int l, int c) {
-  return l == 0 ? a.x0 + c * a.ld0 : a.lev[l].x + c * a.lev[l].len;
-}
-template <class T> __device__ __forceinline__ const cx<T>* tail_b(const TailArgs<T>& a, int l, int c) {
-  return l == 0 ? a.b0 + c * a.ld0 : a.lev[l].b + c * a.lev[l].len;
+template <class T> __device__ __forceinline__ const cx<T>* tail_b(const TailArgs<T>& a, cx<T>* sm, int l, int c) {
+  return l == 0 ? a.b0 + c * a.ld0 : sm + a.lev[l].sb;
 }
 
 // colour q of the 2 x 2 node colouring on an n x m grid: node t of the colour
@@ -369,6 +374,8 @@ __device__ __forceinline__ int colour_count(int n, int m, int ci, int cj) {
 
 template <class T>
 __global__ void __launch_bounds__(kTailThreads) k_node_tail(TailArgs<T> a) {
+  extern __shared__ float4 fine_sm[];
+  cx<T>* sm = reinterpret_cast<cx<T>*>(fine_sm);
   const int c = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
   const Ph<T> p = load_ph<T>(a.ph, c / a.cpg);
   auto sweep = [&](const Lvl<T>& L, cx<T>* x, const cx<T>* b, int q) {
@@ -378,45 +385,49 @@ __global__ void __launch_bounds__(kTailThreads) k_node_tail(TailArgs<T> a) {
       node_smooth_at<T>(L, rx, x, b, ci + 2 * (t % nh), cj + 2 * (t / nh));
     __syncthreads();
   };
+  cx<T>* r = sm + a.sr;
   for (int l = 0; l < a.nl - 1; ++l) {
     const Lvl<T> L = a.lev[l].L;
     const int N = L.n * L.m;
-    cx<T>* x = tail_x(a, l, c);
-    const cx<T>* b = tail_b(a, l, c);
+    cx<T>* x = sm + a.lev[l].sx;
+    const cx<T>* b = tail_b(a, sm, l, c);
     for (int t = tid; t < N; t += nt) x[t] = czero<T>();
     __syncthreads();
     for (int it = 0; it < a.nu_pre; ++it)
       for (int q = 0; q < 4; ++q) sweep(L, x, b, q);
-    cx<T>* r = a.lev[l].r + c * a.lev[l].len;
     const NRdPlain<T> rx{x, L.n, L.m, p};
     for (int t = tid; t < N; t += nt) r[t] = apply_nodal_at<T>(L, rx, b, T(-1), T(1), t % L.n, t / L.n);
     __syncthreads();
     const Lvl<T> C = a.lev[l + 1].L;
-    cx<T>* bc = a.lev[l + 1].b + c * a.lev[l + 1].len;
+    cx<T>* bc = sm + a.lev[l + 1].sb;
     const NRdPlain<T> rr{r, L.n, L.m, p};
     for (int t = tid; t < C.n * C.m; t += nt) bc[t] = restrict_node_at<T>(rr, t % C.n, t / C.n);
     __syncthreads();
   }
   if (tid < 32) {
     const int l = a.nl - 1;
-    chol_solve_warp<T>(a.factor + (long)((c / a.cpg + a.goff) % a.ngroups) * a.nfac * a.nfac, a.nfac, tail_b(a, l, c),
-                       tail_x(a, l, c), tid);
+    chol_solve_warp<T>(a.factor + (long)((c / a.cpg + a.goff) % a.ngroups) * a.nfac * a.nfac, a.nfac,
+                       tail_b(a, sm, l, c), sm + a.lev[l].sx, tid);
   }
   __syncthreads();
   for (int l = a.nl - 2; l >= 0; --l) {
     const Lvl<T> L = a.lev[l].L, C = a.lev[l + 1].L;
-    cx<T>* x = tail_x(a, l, c);
-    const cx<T>* b = tail_b(a, l, c);
-    const NRdPlain<T> rc{tail_x(a, l + 1, c), C.n, C.m, p};
+    cx<T>* x = sm + a.lev[l].sx;
+    const cx<T>* b = tail_b(a, sm, l, c);
+    const NRdPlain<T> rc{sm + a.lev[l + 1].sx, C.n, C.m, p};
     for (int t = tid; t < L.n * L.m; t += nt) x[t] = x[t] + prolong_node_at<T>(rc, t % L.n, t / L.n);
     __syncthreads();
     for (int it = 0; it < a.nu_post; ++it)
       for (int q = 3; q >= 0; --q) sweep(L, x, b, q);
   }
+  const cx<T>* x = sm + a.lev[0].sx;
+  for (long t = tid; t < a.len0; t += nt) a.x0[c * a.ld0 + t] = x[t];
 }
 
 template <class T>
 __global__ void __launch_bounds__(kTailThreads) k_edge_tail(TailArgs<T> a) {
+  extern __shared__ float4 fine_sm[];
+  cx<T>* sm = reinterpret_cast<cx<T>*>(fine_sm);
   const int c = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
   const Ph<T> p = load_ph<T>(a.ph, c / a.cpg);
   auto sweep = [&](const TailLevel<T>& TL, cx<T>* x, const cx<T>* b, int q) {
@@ -428,17 +439,17 @@ __global__ void __launch_bounds__(kTailThreads) k_edge_tail(TailArgs<T> a) {
       edge_smooth_at<T>(L, TL.w, TL.k3, a.mu, p, rx, rb, x, ci + 2 * (t % nh), cj + 2 * (t / nh));
     __syncthreads();
   };
+  cx<T>* r = sm + a.sr;
   for (int l = 0; l < a.nl - 1; ++l) {
     const TailLevel<T> TL = a.lev[l];
     const Lvl<T> L = TL.L;
     const int N = L.n * L.m;
-    cx<T>* x = tail_x(a, l, c);
-    const cx<T>* b = tail_b(a, l, c);
+    cx<T>* x = sm + TL.sx;
+    const cx<T>* b = tail_b(a, sm, l, c);
     for (int t = tid; t < 2 * N; t += nt) x[t] = czero<T>();
     __syncthreads();
     for (int it = 0; it < a.nu_pre; ++it)
       for (int q = 0; q < 4; ++q) sweep(TL, x, b, q);
-    cx<T>* r = TL.r + c * TL.len;
     const ERdPlain<T> rx{x, L.n, L.m, p};
     for (int t = tid; t < N; t += nt) {
       cx<T> yx, yy;
@@ -449,7 +460,7 @@ __global__ void __launch_bounds__(kTailThreads) k_edge_tail(TailArgs<T> a) {
     __syncthreads();
     const Lvl<T> C = a.lev[l + 1].L;
     const int Nc = C.n * C.m;
-    cx<T>* bc = a.lev[l + 1].b + c * a.lev[l + 1].len;
+    cx<T>* bc = sm + a.lev[l + 1].sb;
     const ERdPlain<T> rr{r, L.n, L.m, p};
     for (int t = tid; t < Nc; t += nt) {
       cx<T> vx, vy;
@@ -461,17 +472,17 @@ __global__ void __launch_bounds__(kTailThreads) k_edge_tail(TailArgs<T> a) {
   }
   if (tid < 32) {
     const int l = a.nl - 1;
-    chol_solve_warp<T>(a.factor + (long)((c / a.cpg + a.goff) % a.ngroups) * a.nfac * a.nfac, a.nfac, tail_b(a, l, c),
-                       tail_x(a, l, c), tid);
+    chol_solve_warp<T>(a.factor + (long)((c / a.cpg + a.goff) % a.ngroups) * a.nfac * a.nfac, a.nfac,
+                       tail_b(a, sm, l, c), sm + a.lev[l].sx, tid);
   }
   __syncthreads();
   for (int l = a.nl - 2; l >= 0; --l) {
     const TailLevel<T> TL = a.lev[l];
     const Lvl<T> L = TL.L, C = a.lev[l + 1].L;
     const int N = L.n * L.m;
-    cx<T>* x = tail_x(a, l, c);
-    const cx<T>* b = tail_b(a, l, c);
-    const ERdPlain<T> rc{tail_x(a, l + 1, c), C.n, C.m, p};
+    cx<T>* x = sm + TL.sx;
+    const cx<T>* b = tail_b(a, sm, l, c);
+    const ERdPlain<T> rc{sm + a.lev[l + 1].sx, C.n, C.m, p};
     for (int t = tid; t < N; t += nt) {
       cx<T> vx, vy;
       prolong_edge_at<T>(rc, t % L.n, t / L.n, vx, vy);
@@ -482,6 +493,8 @@ __global__ void __launch_bounds__(kTailThreads) k_edge_tail(TailArgs<T> a) {
     for (int it = 0; it < a.nu_post; ++it)
       for (int q = 3; q >= 0; --q) sweep(TL, x, b, q);
   }
+  const cx<T>* x = sm + a.lev[0].sx;
+  for (long t = tid; t < a.len0; t += nt) a.x0[c * a.ld0 + t] = x[t];
 }
 
 template <class T> const cx<T>* edge_factor(const KData& K);
@@ -723,21 +736,39 @@ template <class T> void zero_columns(cx<T>* x, long ld, long len, int ncols, cud
   }
 }
 
-// The fused tail covers level l and everything below when l is not the coarsest
-// and has at most kTailMaxNodes nodes.
-inline bool tail_from(const Hierarchy& H, int l) { return l < H.nlev - 1 && H.lev[l].N() <= kTailMaxNodes; }
+// Shared-memory elements of a fused tail from level l: x on every level, b below
+// the top one and a residual buffer of the top level's size.
+inline long tail_smem_elems(const Hierarchy& H, int l, bool nodal) {
+  auto len = [&](int k) { return nodal ? H.lev[k].N() : H.lev[k].D(); };
+  long e = 2 * len(l);
+  for (int k = l + 1; k < H.nlev; ++k) e += 2 * len(k);
+  return e;
+}
 
-// Algorithmic bytes of a fused tail: its smoothing sweeps as counted for the
-// per-step kernels, plus one read and one write of a level vector for each of the
-// residual, restriction and prolongation.
-template <class T> double tail_bytes(const Hierarchy& H, int l, int ncols, int nu, bool nodal) {
-  double b = 0.0;
-  for (int k = l; k < H.nlev - 1; ++k) {
-    const Level& L = H.lev[k];
-    const double len = nodal ? (double)L.N() : (double)L.D();
-    b += 4.0 * nu * (nodal ? node_smooth_bytes<T>(L, ncols) : smooth_bytes<T>(L, ncols));
-    b += 6.0 * len * ncols * sizeof(cx<T>);
-  }
+// The fused tail covers level l and everything below when l is not the coarsest,
+// has at most kTailMaxNodes nodes and its vectors fit in shared memory.
+template <class T> bool tail_from(const Hierarchy& H, int l, bool nodal) {
+  return l < H.nlev - 1 && H.lev[l].N() <= kTailMaxNodes &&
+         tail_smem_elems(H, l, nodal) * (long)sizeof(cx<T>) <= kTailSmemBytes;
+}
+template <class T> void set_tail_smem() {
+  static bool done = false;
+  if (done) return;
+  PBS_CUDA(cudaFuncSetAttribute(k_node_tail<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTailSmemBytes));
+  PBS_CUDA(cudaFuncSetAttribute(k_edge_tail<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTailSmemBytes));
+  done = true;
+}
+
+// Algorithmic bytes of a fused tail: the top right-hand sides in and solutions
+// out, the patch factors of its edge levels and the coarsest factors of the
+// groups its columns belong to (the level vectors stay on chip).
+template <class T> double tail_bytes(const Hierarchy& H, int l, int ncols, int cpg, bool nodal) {
+  const Level& L = H.lev[l];
+  const Level& C = H.lev[H.nlev - 1];
+  const double len = nodal ? (double)L.N() : (double)L.D(), nfac = nodal ? (double)C.N() : (double)C.D();
+  double b = 2.0 * len * ncols * sizeof(cx<T>) + nfac * nfac * sizeof(cx<T>) * ((ncols + cpg - 1) / cpg);
+  if (!nodal)
+    for (int k = l; k < H.nlev - 1; ++k) b += 6.0 * sizeof(T) * H.lev[k].N();
   return b;
 }
 
@@ -748,13 +779,22 @@ inline bool fine_tiled(const Level& L, int nu_pre, int nu_post) {
   const int need = kFT + 8 * kFineMaxNu + 3;
   return nu_pre >= 1 && nu_post >= 1 && nu_pre <= kFineMaxNu && nu_post <= kFineMaxNu && L.n >= need && L.m >= need;
 }
+// shared memory of the tiled kernels for nu sweeps
+template <class T> size_t fine_down_smem(int nu) {
+  const size_t W = kFT + 8 * nu + 3;
+  return 2 * W * W * sizeof(cx<T>);
+}
+template <class T> size_t fine_up_smem(int nu) {
+  const size_t W = kFT + 8 * nu, Wc = W / 2 + 1;
+  return (2 * W * W + Wc * Wc) * sizeof(cx<T>);
+}
 template <class T> void set_fine_smem() {
   static bool done = false;
   if (done) return;
-  const int W = kFT + 8 * kFineMaxNu + 3;
-  const int bytes = 2 * W * W * (int)sizeof(cx<T>);
-  PBS_CUDA(cudaFuncSetAttribute(k_node_down<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-  PBS_CUDA(cudaFuncSetAttribute(k_node_up<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  PBS_CUDA(cudaFuncSetAttribute(k_node_down<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)fine_down_smem<T>(kFineMaxNu)));
+  PBS_CUDA(cudaFuncSetAttribute(k_node_up<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)fine_up_smem<T>(kFineMaxNu)));
   done = true;
 }
 // algorithmic bytes of a tiled step: each level vector read or written once
@@ -766,21 +806,29 @@ template <class T> double fine_bytes(const Level& L, int ncols, int, bool down) 
 }
 
 template <class T>
-TailArgs<T> tail_args(const Hierarchy& H, const KData& K, MgWork<T>& w, int l, const cx<T>* b, cx<T>* x, long ld,
-                      int cpg, int nu_pre, int nu_post, bool nodal) {
+TailArgs<T> tail_args(const Hierarchy& H, const KData& K, int l, const cx<T>* b, cx<T>* x, long ld, int cpg,
+                      int nu_pre, int nu_post, bool nodal, size_t* smem) {
   TailArgs<T> a{};
   a.nl = H.nlev - l;
+  int off = 0;
   for (int k = 0; k < a.nl; ++k) {
     const Level& L = H.lev[l + k];
+    const int len = (int)(nodal ? L.N() : L.D());
     TailLevel<T>& t = a.lev[k];
     t.L = L.lvl<T>();
     t.w = L.wts<T>();
     t.k3 = k3_of<T>(L);
-    t.x = w.x[l + k];
-    t.b = w.b[l + k];
-    t.r = w.r[l + k];
-    t.len = nodal ? L.N() : L.D();
+    t.sx = off;
+    off += len;
+    if (k > 0) {
+      t.sb = off;
+      off += len;
+    }
   }
+  a.len0 = nodal ? H.lev[l].N() : H.lev[l].D();
+  a.sr = off;
+  off += (int)a.len0;
+  *smem = (size_t)off * sizeof(cx<T>);
   a.b0 = b;
   a.x0 = x;
   a.ld0 = ld;
@@ -807,9 +855,12 @@ void edge_cycle(const Hierarchy& H, const KData& K, MgWork<T>& w, int l, const c
     PBS_LAUNCHED();
     return;
   }
-  if (tail_from(H, l)) {
-    timer_begin(KC_EDGE_TAIL, s, tail_bytes<T>(H, l, ncols, nu_pre + nu_post, false));
-    k_edge_tail<T><<<ncols, kTailThreads, 0, s>>>(tail_args<T>(H, K, w, l, b, x, ld, cpg, nu_pre, nu_post, false));
+  if (tail_from<T>(H, l, false)) {
+    size_t smem = 0;
+    const TailArgs<T> ta = tail_args<T>(H, K, l, b, x, ld, cpg, nu_pre, nu_post, false, &smem);
+    set_tail_smem<T>();
+    timer_begin(KC_EDGE_TAIL, s, tail_bytes<T>(H, l, ncols, cpg, false));
+    k_edge_tail<T><<<ncols, kTailThreads, smem, s>>>(ta);
     timer_end(KC_EDGE_TAIL, s);
     PBS_LAUNCHED();
     return;
@@ -852,9 +903,12 @@ void node_cycle(const Hierarchy& H, const KData& K, MgWork<T>& w, int l, const c
     PBS_LAUNCHED();
     return;
   }
-  if (tail_from(H, l)) {
-    timer_begin(KC_NODE_TAIL, s, tail_bytes<T>(H, l, ncols, nu_pre + nu_post, true));
-    k_node_tail<T><<<ncols, kTailThreads, 0, s>>>(tail_args<T>(H, K, w, l, b, x, ld, cpg, nu_pre, nu_post, true));
+  if (tail_from<T>(H, l, true)) {
+    size_t smem = 0;
+    const TailArgs<T> ta = tail_args<T>(H, K, l, b, x, ld, cpg, nu_pre, nu_post, true, &smem);
+    set_tail_smem<T>();
+    timer_begin(KC_NODE_TAIL, s, tail_bytes<T>(H, l, ncols, cpg, true));
+    k_node_tail<T><<<ncols, kTailThreads, smem, s>>>(ta);
     timer_end(KC_NODE_TAIL, s);
     PBS_LAUNCHED();
     return;
@@ -862,8 +916,7 @@ void node_cycle(const Hierarchy& H, const KData& K, MgWork<T>& w, int l, const c
   if (fine_tiled(L, nu_pre, nu_post)) {
     const Level& C = H.lev[l + 1];
     const dim3 grid((L.n + kFT - 1) / kFT, (L.m + kFT - 1) / kFT, ncols);
-    const int Wd = kFT + 8 * nu_pre + 3, Wu = kFT + 8 * nu_post;
-    const size_t smd = 2ull * Wd * Wd * sizeof(cx<T>), smu = 2ull * Wu * Wu * sizeof(cx<T>);
+    const size_t smd = fine_down_smem<T>(nu_pre), smu = fine_up_smem<T>(nu_post);
     set_fine_smem<T>();
     timer_begin(KC_NODE_SMOOTH, s, fine_bytes<T>(L, ncols, nu_pre, true));
     k_node_down<T><<<grid, kFineThreads, smd, s>>>(L.lvl<T>(), C.n, C.m, K.d_ph, cpg, b, ld, w.r[l], L.N(), w.b[l + 1],
