@@ -188,7 +188,11 @@ __global__ void k_edge_smooth(Lvl<T> L, Wts<T> w, const T* __restrict__ k3, T mu
   const Ph<T> p = load_ph<T>(ph, c / cpg);
   const ERd<T> r{X + c * ld, L.n, L.m, p};
   const ERd<T> rb{B + c * ld, L.n, L.m, p};
-  edge_smooth_at<T>(L, w, k3, mu, p, r, rb, X + c * ld, i, j);
+  if (inside(i, j, L.n, L.m, 1, 1))
+    edge_smooth_at<T>(L, inner<T>(w), k3, mu, p, inner_e<T>(X + c * ld, L.n, L.m), inner_e<T>(B + c * ld, L.n, L.m),
+                      X + c * ld, i, j);
+  else
+    edge_smooth_at<T>(L, w, k3, mu, p, r, rb, X + c * ld, i, j);
 }
 
 // One colour of point Gauss-Seidel for P = L^* M L.
@@ -199,7 +203,10 @@ __global__ void k_node_smooth(Lvl<T> L, const double* ph, int cpg, cx<T>* X, con
   const int c = blockIdx.z;
   if (i >= L.n || j >= L.m) return;
   const NRd<T> r{X + c * ld, L.n, L.m, load_ph<T>(ph, c / cpg)};
-  node_smooth_at<T>(L, r, X + c * ld, B + c * ld, i, j);
+  if (inside(i, j, L.n, L.m, 1, 1))
+    node_smooth_at<T>(L, inner_n<T>(X + c * ld, L.n), X + c * ld, B + c * ld, i, j);
+  else
+    node_smooth_at<T>(L, r, X + c * ld, B + c * ld, i, j);
 }
 
 // ---- tiled fine-level nodal steps ------------------------------------------------
@@ -349,6 +356,7 @@ template <class T> struct TailArgs {
   int nl;  // levels in the tail, the last one the coarsest
   TailLevel<T> lev[kMaxLevels];
   int sr;           // shared-memory offset of the residual buffer
+  int sf;           // shared-memory offset of the column's coarsest factor (leading dimension nfac + 1), or -1
   const cx<T>* b0;  // top level right-hand sides and solutions, columns at stride ld0
   cx<T>* x0;
   long ld0, len0;   // len0: values per top-level column
@@ -367,9 +375,49 @@ template <class T> __device__ __forceinline__ const cx<T>* tail_b(const TailArgs
   return l == 0 ? a.b0 + c * a.ld0 : sm + a.lev[l].sb;
 }
 
-// colour q of the 2 x 2 node colouring on an n x m grid: node t of the colour
-__device__ __forceinline__ int colour_count(int n, int m, int ci, int cj) {
-  return ((n - ci + 1) / 2) * ((m - cj + 1) / 2);
+// Copy of the column's coarsest factor into shared memory (the block's first barrier
+// orders it before the solve).
+template <class T> __device__ __forceinline__ void stage_factor(const TailArgs<T>& a, const cx<T>* F, cx<T>* sm) {
+  if (a.sf < 0) return;
+  const int n = a.nfac;
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) sm[a.sf + (t / n) * (n + 1) + t % n] = F[t];
+}
+
+// Range [lo, hi) of lattice steps a (point i0 + s a, 0 <= a < na) whose point lies in [ilo, ihi].
+__device__ __forceinline__ void lattice_range(int i0, int s, int na, int ilo, int ihi, int& lo, int& hi) {
+  lo = ilo <= i0 ? 0 : min(na, (ilo - i0 + s - 1) / s);
+  hi = ihi < i0 ? 0 : min(na, (ihi - i0) / s + 1);
+  hi = max(hi, lo);
+}
+
+// Calls f(i, j, inner) for every point (i0 + s a, j0 + s b), 0 <= a < na, 0 <= b < nb,
+// spread over the block's threads: first the points with i in [ilo, ihi] and j in
+// [jlo, jhi] (inner = true), then the frame around them, so that only the warp at
+// the seam mixes the two kinds.
+template <class F>
+__device__ __forceinline__ void for_lattice(int i0, int j0, int s, int na, int nb, int ilo, int ihi, int jlo, int jhi,
+                                            F&& f) {
+  int alo, ahi, blo, bhi;
+  lattice_range(i0, s, na, ilo, ihi, alo, ahi);
+  lattice_range(j0, s, nb, jlo, jhi, blo, bhi);
+  const int nai = ahi - alo, nbi = bhi - blo, nin = nai * nbi;
+  const int nrows = (nb - nbi) * na, total = na * nb;
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    int a, b;
+    if (t < nin) {
+      a = alo + t % nai;
+      b = blo + t / nai;
+    } else if (t - nin < nrows) {  // whole rows below and above the inner block
+      const int u = t - nin, r = u / na;
+      a = u % na;
+      b = r < blo ? r : bhi + (r - blo);
+    } else {  // the side pieces of the inner rows
+      const int u = t - nin - nrows, w = na - nai, k = u % w;
+      b = blo + u / w;
+      a = k < alo ? k : ahi + (k - alo);
+    }
+    f(i0 + s * a, j0 + s * b, t < nin);
+  }
 }
 
 template <class T>
@@ -378,11 +426,18 @@ __global__ void __launch_bounds__(kTailThreads) k_node_tail(TailArgs<T> a) {
   cx<T>* sm = reinterpret_cast<cx<T>*>(fine_sm);
   const int c = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
   const Ph<T> p = load_ph<T>(a.ph, c / a.cpg);
+  const cx<T>* F = a.factor + (long)((c / a.cpg + a.goff) % a.ngroups) * a.nfac * a.nfac;
+  stage_factor<T>(a, F, sm);
+  // colour q of (0,0), (1,0), (0,1), (1,1); inner nodes have all neighbours on the level
   auto sweep = [&](const Lvl<T>& L, cx<T>* x, const cx<T>* b, int q) {
-    const int ci = q & 1, cj = q >> 1, nh = (L.n - ci + 1) / 2;  // colour q of (0,0), (1,0), (0,1), (1,1)
+    const int ci = q & 1, cj = q >> 1;
     const NRdPlain<T> rx{x, L.n, L.m, p};
-    for (int t = tid; t < colour_count(L.n, L.m, ci, cj); t += nt)
-      node_smooth_at<T>(L, rx, x, b, ci + 2 * (t % nh), cj + 2 * (t / nh));
+    for_lattice(ci, cj, 2, (L.n - ci + 1) / 2, (L.m - cj + 1) / 2, 1, L.n - 2, 1, L.m - 2, [&](int i, int j, bool in) {
+      if (in)
+        node_smooth_at<T>(L, inner_n<T>(x, L.n), x, b, i, j);
+      else
+        node_smooth_at<T>(L, rx, x, b, i, j);
+    });
     __syncthreads();
   };
   cx<T>* r = sm + a.sr;
@@ -396,26 +451,39 @@ __global__ void __launch_bounds__(kTailThreads) k_node_tail(TailArgs<T> a) {
     for (int it = 0; it < a.nu_pre; ++it)
       for (int q = 0; q < 4; ++q) sweep(L, x, b, q);
     const NRdPlain<T> rx{x, L.n, L.m, p};
-    for (int t = tid; t < N; t += nt) r[t] = apply_nodal_at<T>(L, rx, b, T(-1), T(1), t % L.n, t / L.n);
+    for_lattice(0, 0, 1, L.n, L.m, 1, L.n - 2, 1, L.m - 2, [&](int i, int j, bool in) {
+      r[j * L.n + i] = in ? apply_nodal_at<T>(L, inner_n<T>(x, L.n), b, T(-1), T(1), i, j)
+                          : apply_nodal_at<T>(L, rx, b, T(-1), T(1), i, j);
+    });
     __syncthreads();
+    // restriction at (I, J) reads fine nodes 2I-1 .. 2I+1
     const Lvl<T> C = a.lev[l + 1].L;
     cx<T>* bc = sm + a.lev[l + 1].sb;
     const NRdPlain<T> rr{r, L.n, L.m, p};
-    for (int t = tid; t < C.n * C.m; t += nt) bc[t] = restrict_node_at<T>(rr, t % C.n, t / C.n);
+    for_lattice(0, 0, 1, C.n, C.m, 1, (L.n - 2) / 2, 1, (L.m - 2) / 2, [&](int I, int J, bool in) {
+      bc[J * C.n + I] = in ? restrict_node_at<T>(inner_n<T>(r, L.n), I, J) : restrict_node_at<T>(rr, I, J);
+    });
     __syncthreads();
   }
   if (tid < 32) {
     const int l = a.nl - 1;
-    chol_solve_warp<T>(a.factor + (long)((c / a.cpg + a.goff) % a.ngroups) * a.nfac * a.nfac, a.nfac,
-                       tail_b(a, sm, l, c), sm + a.lev[l].sx, tid);
+    if (a.sf >= 0)
+      chol_solve_warp_cols<T>(sm + a.sf, a.nfac + 1, a.nfac, tail_b(a, sm, l, c), sm + a.lev[l].sx, tid);
+    else
+      chol_solve_warp<T>(F, a.nfac, tail_b(a, sm, l, c), sm + a.lev[l].sx, tid);
   }
   __syncthreads();
   for (int l = a.nl - 2; l >= 0; --l) {
     const Lvl<T> L = a.lev[l].L, C = a.lev[l + 1].L;
     cx<T>* x = sm + a.lev[l].sx;
     const cx<T>* b = tail_b(a, sm, l, c);
-    const NRdPlain<T> rc{sm + a.lev[l + 1].sx, C.n, C.m, p};
-    for (int t = tid; t < L.n * L.m; t += nt) x[t] = x[t] + prolong_node_at<T>(rc, t % L.n, t / L.n);
+    const cx<T>* xc = sm + a.lev[l + 1].sx;
+    const NRdPlain<T> rc{xc, C.n, C.m, p};
+    // prolongation at fine (i, j) reads coarse nodes i/2 .. i/2 + 1
+    for_lattice(0, 0, 1, L.n, L.m, 0, 2 * C.n - 3, 0, 2 * C.m - 3, [&](int i, int j, bool in) {
+      const int e = j * L.n + i;
+      x[e] = x[e] + (in ? prolong_node_at<T>(inner_n<T>(xc, C.n), i, j) : prolong_node_at<T>(rc, i, j));
+    });
     __syncthreads();
     for (int it = 0; it < a.nu_post; ++it)
       for (int q = 3; q >= 0; --q) sweep(L, x, b, q);
@@ -430,13 +498,21 @@ __global__ void __launch_bounds__(kTailThreads) k_edge_tail(TailArgs<T> a) {
   cx<T>* sm = reinterpret_cast<cx<T>*>(fine_sm);
   const int c = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
   const Ph<T> p = load_ph<T>(a.ph, c / a.cpg);
+  const cx<T>* F = a.factor + (long)((c / a.cpg + a.goff) % a.ngroups) * a.nfac * a.nfac;
+  stage_factor<T>(a, F, sm);
+  // colour q of (0,0), (1,0), (0,1), (1,1); inner patches have all their edges and cells on the level
   auto sweep = [&](const TailLevel<T>& TL, cx<T>* x, const cx<T>* b, int q) {
     const Lvl<T>& L = TL.L;
-    const int ci = q & 1, cj = q >> 1, nh = (L.n - ci + 1) / 2;  // colour q of (0,0), (1,0), (0,1), (1,1)
+    const int ci = q & 1, cj = q >> 1;
     const ERdPlain<T> rx{x, L.n, L.m, p};
     const ERdPlain<T> rb{b, L.n, L.m, p};
-    for (int t = tid; t < colour_count(L.n, L.m, ci, cj); t += nt)
-      edge_smooth_at<T>(L, TL.w, TL.k3, a.mu, p, rx, rb, x, ci + 2 * (t % nh), cj + 2 * (t / nh));
+    for_lattice(ci, cj, 2, (L.n - ci + 1) / 2, (L.m - cj + 1) / 2, 1, L.n - 2, 1, L.m - 2, [&](int i, int j, bool in) {
+      if (in)
+        edge_smooth_at<T>(L, inner<T>(TL.w), TL.k3, a.mu, p, inner_e<T>(x, L.n, L.m), inner_e<T>(b, L.n, L.m), x, i,
+                          j);
+      else
+        edge_smooth_at<T>(L, TL.w, TL.k3, a.mu, p, rx, rb, x, i, j);
+    });
     __syncthreads();
   };
   cx<T>* r = sm + a.sr;
@@ -451,29 +527,38 @@ __global__ void __launch_bounds__(kTailThreads) k_edge_tail(TailArgs<T> a) {
     for (int it = 0; it < a.nu_pre; ++it)
       for (int q = 0; q < 4; ++q) sweep(TL, x, b, q);
     const ERdPlain<T> rx{x, L.n, L.m, p};
-    for (int t = tid; t < N; t += nt) {
+    for_lattice(0, 0, 1, L.n, L.m, 1, L.n - 2, 1, L.m - 2, [&](int i, int j, bool in) {
       cx<T> yx, yy;
-      apply_edge_at<T>(L, TL.w, rx, b, T(-1), -a.mu, T(1), t % L.n, t / L.n, yx, yy);
-      r[t] = yx;
-      r[N + t] = yy;
-    }
+      if (in)
+        apply_edge_at<T>(L, inner<T>(TL.w), inner_e<T>(x, L.n, L.m), b, T(-1), -a.mu, T(1), i, j, yx, yy);
+      else
+        apply_edge_at<T>(L, TL.w, rx, b, T(-1), -a.mu, T(1), i, j, yx, yy);
+      r[j * L.n + i] = yx;
+      r[N + j * L.n + i] = yy;
+    });
     __syncthreads();
+    // restriction at (I, J) reads fine edges with indices 2I-1 .. 2I+1
     const Lvl<T> C = a.lev[l + 1].L;
     const int Nc = C.n * C.m;
     cx<T>* bc = sm + a.lev[l + 1].sb;
     const ERdPlain<T> rr{r, L.n, L.m, p};
-    for (int t = tid; t < Nc; t += nt) {
+    for_lattice(0, 0, 1, C.n, C.m, 1, (L.n - 2) / 2, 1, (L.m - 2) / 2, [&](int I, int J, bool in) {
       cx<T> vx, vy;
-      restrict_edge_at<T>(rr, t % C.n, t / C.n, vx, vy);
-      bc[t] = vx;
-      bc[Nc + t] = vy;
-    }
+      if (in)
+        restrict_edge_at<T>(inner_e<T>(r, L.n, L.m), I, J, vx, vy);
+      else
+        restrict_edge_at<T>(rr, I, J, vx, vy);
+      bc[J * C.n + I] = vx;
+      bc[Nc + J * C.n + I] = vy;
+    });
     __syncthreads();
   }
   if (tid < 32) {
     const int l = a.nl - 1;
-    chol_solve_warp<T>(a.factor + (long)((c / a.cpg + a.goff) % a.ngroups) * a.nfac * a.nfac, a.nfac,
-                       tail_b(a, sm, l, c), sm + a.lev[l].sx, tid);
+    if (a.sf >= 0)
+      chol_solve_warp_cols<T>(sm + a.sf, a.nfac + 1, a.nfac, tail_b(a, sm, l, c), sm + a.lev[l].sx, tid);
+    else
+      chol_solve_warp<T>(F, a.nfac, tail_b(a, sm, l, c), sm + a.lev[l].sx, tid);
   }
   __syncthreads();
   for (int l = a.nl - 2; l >= 0; --l) {
@@ -482,13 +567,19 @@ __global__ void __launch_bounds__(kTailThreads) k_edge_tail(TailArgs<T> a) {
     const int N = L.n * L.m;
     cx<T>* x = sm + TL.sx;
     const cx<T>* b = tail_b(a, sm, l, c);
-    const ERdPlain<T> rc{sm + a.lev[l + 1].sx, C.n, C.m, p};
-    for (int t = tid; t < N; t += nt) {
+    const cx<T>* xc = sm + a.lev[l + 1].sx;
+    const ERdPlain<T> rc{xc, C.n, C.m, p};
+    // prolongation at fine (i, j) reads coarse edges with indices i/2 .. i/2 + 1
+    for_lattice(0, 0, 1, L.n, L.m, 0, 2 * C.n - 3, 0, 2 * C.m - 3, [&](int i, int j, bool in) {
       cx<T> vx, vy;
-      prolong_edge_at<T>(rc, t % L.n, t / L.n, vx, vy);
-      x[t] = x[t] + vx;
-      x[N + t] = x[N + t] + vy;
-    }
+      if (in)
+        prolong_edge_at<T>(inner_e<T>(xc, C.n, C.m), i, j, vx, vy);
+      else
+        prolong_edge_at<T>(rc, i, j, vx, vy);
+      const int e = j * L.n + i;
+      x[e] = x[e] + vx;
+      x[N + e] = x[N + e] + vy;
+    });
     __syncthreads();
     for (int it = 0; it < a.nu_post; ++it)
       for (int q = 3; q >= 0; --q) sweep(TL, x, b, q);
@@ -828,6 +919,13 @@ TailArgs<T> tail_args(const Hierarchy& H, const KData& K, int l, const cx<T>* b,
   a.len0 = nodal ? H.lev[l].N() : H.lev[l].D();
   a.sr = off;
   off += (int)a.len0;
+  const Level& Cst0 = H.lev[H.nlev - 1];
+  const long nf = nodal ? Cst0.N() : Cst0.D();
+  a.sf = -1;
+  if ((off + nf * (nf + 1)) * (long)sizeof(cx<T>) <= kTailSmemBytes) {
+    a.sf = off;
+    off += (int)(nf * (nf + 1));
+  }
   *smem = (size_t)off * sizeof(cx<T>);
   a.b0 = b;
   a.x0 = x;

@@ -53,6 +53,37 @@ template <class T> struct ERdPlain {
   __device__ __forceinline__ cx<T> y(int i, int j) const { return gread_plain<T>(X + (long)n * m, i, j, n, m, p); }
 };
 
+// Readers without the Bloch extension, for stencils that stay inside the level:
+// there the extended readers return the stored value unchanged, so a point
+// computed through these gives the same result without the wrap tests.
+template <class T> struct NRdIn {
+  const cx<T>* X;
+  int n;
+  __device__ __forceinline__ cx<T> v(int i, int j) const { return X[(long)j * n + i]; }
+};
+template <class T> struct ERdIn {
+  const cx<T>* X;
+  int n;
+  long N;
+  __device__ __forceinline__ cx<T> x(int i, int j) const { return X[(long)j * n + i]; }
+  __device__ __forceinline__ cx<T> y(int i, int j) const { return X[N + (long)j * n + i]; }
+};
+template <class T> struct WtsIn {
+  const T* winv;
+  int n;
+  T scale;
+  __device__ __forceinline__ T operator()(int i, int j) const { return scale * winv[(long)j * n + i]; }
+};
+template <class T> __device__ __forceinline__ WtsIn<T> inner(const Wts<T>& w) { return WtsIn<T>{w.winv, w.n, w.scale}; }
+template <class T> __device__ __forceinline__ NRdIn<T> inner_n(const cx<T>* X, int n) { return NRdIn<T>{X, n}; }
+template <class T> __device__ __forceinline__ ERdIn<T> inner_e(const cx<T>* X, int n, int m) {
+  return ERdIn<T>{X, n, (long)n * m};
+}
+// the neighbourhood [i - lo, i + hi] x [j - lo, j + hi] lies inside an n x m level
+__device__ __forceinline__ bool inside(int i, int j, int n, int m, int lo, int hi) {
+  return i >= lo && j >= lo && i + hi < n && j + hi < m;
+}
+
 // ---- nodal (P = L^* M L) ----------------------------------------------------
 
 // point Gauss-Seidel update of node (i,j); r reads x
@@ -98,8 +129,8 @@ template <class T, class R> __device__ __forceinline__ cx<T> restrict_node_at(co
 // ---- edges (A + mu M) -------------------------------------------------------
 
 // (sA A + s M) x + sB b at x-edge and y-edge (i,j)
-template <class T, class R>
-__device__ __forceinline__ void apply_edge_at(const Lvl<T>& L, const Wts<T>& w, const R& r, const cx<T>* B, T sA, T s,
+template <class T, class R, class W>
+__device__ __forceinline__ void apply_edge_at(const Lvl<T>& L, const W& w, const R& r, const cx<T>* B, T sA, T s,
                                               T sB, int i, int j, cx<T>& yx, cx<T>& yy) {
   const long N = (long)L.n * L.m, e = (long)j * L.n + i;
   yx = czero<T>();
@@ -120,9 +151,9 @@ __device__ __forceinline__ void apply_edge_at(const Lvl<T>& L, const Wts<T>& w, 
 
 // Block Gauss-Seidel update of the patch of node (i,j) (its edges L, R, B, T);
 // r reads x, rb reads b; K3^{-1} of the node in k3 (SoA [6][N]).
-template <class T, class R>
-__device__ __forceinline__ void edge_smooth_at(const Lvl<T>& L, const Wts<T>& w, const T* k3, T mu, const Ph<T>& p,
-                                               const R& r, const R& rb, cx<T>* X, int i, int j) {
+template <class T, class R, class RB, class W>
+__device__ __forceinline__ void edge_smooth_at(const Lvl<T>& L, const W& w, const T* k3, T mu, const Ph<T>& p,
+                                               const R& r, const RB& rb, cx<T>* X, int i, int j) {
   // residual b - (A + mu M) x on the patch, in ghost coordinates
   const cx<T> rL = rb.x(i - 1, j) - (A_x<T>(r, w, i - 1, j) + mu * M_x<T>(r, L, i - 1, j));
   const cx<T> rR = rb.x(i, j) - (A_x<T>(r, w, i, j) + mu * M_x<T>(r, L, i, j));
@@ -211,6 +242,38 @@ __device__ __forceinline__ void chol_solve_warp(const cx<T>* Lf, int n, const cx
       const cx<T> v = x[i] - acc;
       x[i] = mk<T>(v.x / d, v.y / d);
     }
+    __syncwarp();
+  }
+}
+
+// The same solve with the factor in shared memory at leading dimension ld (n + 1
+// keeps both a column and a row of it free of bank conflicts), both triangular
+// sweeps in column order: once x_k is known, its multiple of column k of L (row
+// k of L^*) leaves the remaining right-hand side, so a step is one division and
+// one strided update with no reduction.
+template <class T>
+__device__ __forceinline__ void chol_solve_warp_cols(const cx<T>* Lf, int ld, int n, const cx<T>* b, cx<T>* x,
+                                                     int lane) {
+  for (int j = lane; j < n; j += 32) x[j] = b[j];
+  __syncwarp();
+  // forward: L y = b  (y stored in x)
+  for (int k = 0; k < n; ++k) {
+    const T d = Lf[k * ld + k].x;
+    const cx<T> v = x[k];
+    const cx<T> y = mk<T>(v.x / d, v.y / d);
+    for (int j = k + 1 + lane; j < n; j += 32) x[j] = x[j] - cmul(Lf[k * ld + j], y);
+    __syncwarp();
+    if (lane == 0) x[k] = y;
+    __syncwarp();
+  }
+  // backward: L^* x = y, (L^*)(i,k) = conj(L(k,i)) = conj(Lf[i ld + k])
+  for (int k = n - 1; k >= 0; --k) {
+    const T d = Lf[k * ld + k].x;
+    const cx<T> v = x[k];
+    const cx<T> xk = mk<T>(v.x / d, v.y / d);
+    for (int i = lane; i < k; i += 32) x[i] = x[i] - cmulc(Lf[i * ld + k], xk);
+    __syncwarp();
+    if (lane == 0) x[k] = xk;
     __syncwarp();
   }
 }

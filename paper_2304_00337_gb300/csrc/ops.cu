@@ -23,7 +23,11 @@ __global__ void k_apply_edge(Lvl<T> L, Wts<T> w, const double* ph, int cpg, cons
   const long N = (long)L.n * L.m, e = (long)j * L.n + i;
   const T s = sM + (lam ? sL * lam[c] : T(0));
   cx<T> yx, yy;
-  apply_edge_at<T>(L, w, r, B ? B + c * ld : nullptr, sA, s, sB, i, j, yx, yy);
+  if (inside(i, j, L.n, L.m, 1, 1))
+    apply_edge_at<T>(L, inner<T>(w), inner_e<T>(X + c * ld, L.n, L.m), B ? B + c * ld : nullptr, sA, s, sB, i, j, yx,
+                     yy);
+  else
+    apply_edge_at<T>(L, w, r, B ? B + c * ld : nullptr, sA, s, sB, i, j, yx, yy);
   Y[c * ld + e] = yx;
   Y[c * ld + N + e] = yy;
 }
@@ -81,7 +85,10 @@ __global__ void k_apply_nodal(Lvl<T> L, const double* ph, int cpg, const cx<T>* 
   const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y, c = blockIdx.z;
   if (i >= L.n || j >= L.m) return;
   const NRd<T> r{X + c * ld, L.n, L.m, load_ph<T>(ph, c / cpg)};
-  Y[c * ld + (long)j * L.n + i] = apply_nodal_at<T>(L, r, B ? B + c * ld : nullptr, sP, sB, i, j);
+  Y[c * ld + (long)j * L.n + i] = inside(i, j, L.n, L.m, 1, 1)
+                                      ? apply_nodal_at<T>(L, inner_n<T>(X + c * ld, L.n), B ? B + c * ld : nullptr,
+                                                          sP, sB, i, j)
+                                      : apply_nodal_at<T>(L, r, B ? B + c * ld : nullptr, sP, sB, i, j);
 }
 
 // Natural embedding of coarse edges (Section 5): a fine edge lying on a coarse
@@ -96,7 +103,10 @@ __global__ void k_prolong_edge(int nf, int mf, int nc, int mc, const double* ph,
   const ERd<T> rc{Xc + c * ldc, nc, mc, load_ph<T>(ph, c / cpg)};
   const long Nf = (long)nf * mf, e = (long)j * nf + i;
   cx<T> vx, vy;
-  prolong_edge_at<T>(rc, i, j, vx, vy);
+  if (inside(i >> 1, j >> 1, nc, mc, 0, 1))
+    prolong_edge_at<T>(inner_e<T>(Xc + c * ldc, nc, mc), i, j, vx, vy);
+  else
+    prolong_edge_at<T>(rc, i, j, vx, vy);
   cx<T>* yf = Yf + c * ldf;
   if (accumulate) {
     yf[e] = yf[e] + vx;
@@ -115,7 +125,10 @@ __global__ void k_restrict_edge(int nf, int mf, int nc, int mc, const double* ph
   if (I >= nc || J >= mc) return;
   const ERd<T> r{Xf + c * ldf, nf, mf, load_ph<T>(ph, c / cpg)};
   cx<T> vx, vy;
-  restrict_edge_at<T>(r, I, J, vx, vy);
+  if (inside(2 * I, 2 * J, nf, mf, 1, 1))
+    restrict_edge_at<T>(inner_e<T>(Xf + c * ldf, nf, mf), I, J, vx, vy);
+  else
+    restrict_edge_at<T>(r, I, J, vx, vy);
   const long Nc = (long)nc * mc, e = (long)J * nc + I;
   Yc[c * ldc + e] = vx;
   Yc[c * ldc + Nc + e] = vy;
