@@ -452,6 +452,64 @@ def throwaway_bench(n: int) -> None:
                                  "precision": "mixed", "tol": 1e-8}}), flush=True)
 
 
+def householder_bench(n: int, q: int, reps: int) -> None:
+    """The generalised Householder orthonormalisation of Section 4 (``pbs_m_householder``) on
+    the bench geometry: a seeded D x q block (q = 30, the trial width of the path's iteration)
+    of the 256x256 rod crystal at X.  One JSON line: factorisations/s (CUDA events around
+    ``reps`` calls on the caller's stream, inputs resident), the streaming kernels' achieved
+    bandwidth, and the oracle's time for one factorisation on the host cores."""
+    import __graft_entry__ as ge
+    ge.build()
+    import torch
+    import paper_2304_00337_gb300 as pbs
+    import pbs_inputs as gi
+    from oracle import fem
+    from oracle.householder import m_householder, pivots
+    eps = gi.rod_eps(n, n, radius=0.2, eps_rod=8.9)
+    geom = pbs.Geometry(eps)
+    k = (np.pi, 0.0)
+    S = gi.random_block(geom.D, q, seed=23)
+    Sd = torch.from_numpy(S).cuda()
+    Ed = torch.zeros_like(Sd)
+    Rd = torch.zeros((q, q), dtype=torch.complex128, device="cuda")
+    st = torch.cuda.current_stream()
+    with pbs.Context(0) as ctx:
+        for _ in range(3):
+            ctx.m_householder(geom, k, q, Sd.data_ptr(), Ed.data_ptr(), Rd.data_ptr(), st)
+        ctx.profile_enable("householder")
+        launches0 = pbs.launch_count()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        t0.record(st)
+        for _ in range(reps):
+            ctx.m_householder(geom, k, q, Sd.data_ptr(), Ed.data_ptr(), Rd.data_ptr(), st)
+        t1.record(st)
+        torch.cuda.synchronize()
+        ms = t0.elapsed_time(t1) / reps
+        launches = (pbs.launch_count() - launches0) // reps
+        kms, klaunch, kbytes = ctx.profile_read("householder")
+    peaks, peak_kind = _peaks()
+    achieved = kbytes / (kms * 1e-3) / 1e9 if kms > 0 else 0.0
+    c0 = time.perf_counter()
+    M = fem.assemble(fem.Mesh(1.0, 1.0, n, n), eps, k)["M"]
+    m_householder(M, S.T, pivots(n, n, q))
+    cpu_s = time.perf_counter() - c0
+    print(json.dumps({
+        "metric": "M-Householder block orthonormalisations/s", "value": 1e3 / ms, "unit": "factorisations/s",
+        "higher_is_better": True, "n_gpus": 1, "ms_per_factorisation": ms, "gpu_launches_per_call": int(launches),
+        "dtype": "c128 (FP64)", "data": "synthetic",
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                     "kernel": "k_hh_mdots + k_hh_update (reflection of the later columns)",
+                     "peak_kind": f"{peak_kind} hbm_gbs",
+                     "note": "working set (S copy and E, 2 x 63 MB) is about the L2 size: partly L2-resident",
+                     "launches_timed": int(klaunch)},
+        "cpu_baseline": {"value": 1.0 / cpu_s, "unit": "factorisations/s", "cores": os.cpu_count(),
+                         "kind": "oracle", "sample": "one factorisation of the same block, incl. mass assembly"},
+        "config": {"workload": f"rod eps=8.9 r=0.2a, {n}x{n} (D = {geom.D}), {q} columns, k = X",
+                   "precision": "fp64"}}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -461,7 +519,7 @@ def main():
     ap.add_argument("--profile-run", type=int, default=0, metavar="NK",
                     help="solve the first NK k-points once (no timing) - the small case for ncu captures")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--workload", default="path", choices=["path", "serving", "grid", "throwaway"],
+    ap.add_argument("--workload", default="path", choices=["path", "serving", "grid", "throwaway", "householder"],
                     help="path: the headline 256x256 path (default); serving: the job-stream latency line; "
                          "grid: the paper's kappa x kappa Brillouin-zone workload")
     ap.add_argument("--kappa", type=int, default=30, help="grid workload: k-points per direction")
@@ -476,6 +534,9 @@ def main():
         return
     if args.workload == "throwaway" and args.impl == "ours":
         throwaway_bench(128)
+        return
+    if args.workload == "householder" and args.impl == "ours":
+        householder_bench(256, 30, 10)
         return
     if args.profile_run:
         profile_run(args.profile_run, args.precision)

@@ -226,6 +226,22 @@ PBS_API int pbs_gram(pbs_ctx *ctx, const pbs_geom *geom, const double k[2], int 
              pbs_c64 *GA, int precision, void *cuda_stream);
 
 /*
+ * Generalised Householder orthonormalisation (Section 4): reflections
+ * Q_i = I - 2 v_i v_i^* M / (v_i^* M v_i) with Q_q ... Q_1 S = P R, where P is
+ * the prescribed M-orthonormal basis of scaled unit vectors of the x-edges
+ * (k mod n, 2 (k div n)), k = 0 .. q-1 (they share no mass-matrix entry), and
+ * R is upper triangular; E = Q_1 ... Q_q P is M-orthonormal and S = E R.  When
+ * S loses rank the matching diagonal entries of R vanish (exactly zero columns
+ * leave Q_i = I) and E still is M-orthonormal with span(S) inside span(E).
+ * S, E: device D x q column-major (leading dimension D = 2 n m); R: device
+ * q x q column-major; FP64; S is not modified and must not overlap E or R.
+ * q <= 96 and q <= n * floor(m / 2), else PBS_EINVAL.  Work space (about D q
+ * complex doubles) comes from the context's budget for the duration of the call.
+ */
+PBS_API int pbs_m_householder(pbs_ctx *ctx, const pbs_geom *geom, const double k[2], int q, const pbs_c64 *S,
+                              pbs_c64 *E, pbs_c64 *R, void *cuda_stream);
+
+/*
  * Rayleigh-Ritz of the pencil on span(S) (Section 4, eq. ritz_eigenvalue):
  * the p smallest Ritz values (host `theta`) and M-orthonormal Ritz vectors
  * (device X, D x p).  With project != 0 the columns of S are first projected
@@ -240,7 +256,8 @@ PBS_API int pbs_rayleigh_ritz(pbs_ctx *ctx, const pbs_geom *geom, const pbs_opts
  * CUDA events on the stream it is launched on (the library's stream).
  * `classes` is "all" or a comma-separated list of "edge_smooth",
  * "node_smooth", "gram", "small_rr", "residual", "block_update",
- * "lift_adj_mass", optionally followed by "/N" to time only every N-th launch
+ * "lift_adj_mass", "edge_apply", "edge_tail", "node_tail", "householder",
+ * optionally followed by "/N" to time only every N-th launch
  * of each listed class; NULL or "" switches timing off.  Enabling resets the
  * counters.  pbs_profile_read returns, for one class, the summed device time
  * (ms), the number of timed launches and their summed algorithmic work (bytes

@@ -94,6 +94,7 @@ def lib() -> ct.CDLL:
         "pbs_apply": (ct.c_int, [P, ct.POINTER(pbs_geom), ct.POINTER(pbs_opts), ct.c_int, ct.c_int, dp, ct.c_int,
                                  P, P, P]),
         "pbs_gram": (ct.c_int, [P, ct.POINTER(pbs_geom), dp, ct.c_int, P, P, P, ct.c_int, P]),
+        "pbs_m_householder": (ct.c_int, [P, ct.POINTER(pbs_geom), dp, ct.c_int, P, P, P, P]),
         "pbs_rayleigh_ritz": (ct.c_int, [P, ct.POINTER(pbs_geom), ct.POINTER(pbs_opts), dp, ct.c_int, P, ct.c_int,
                                          ct.c_int, dp, P, P]),
         "pbs_profile_enable": (ct.c_int, [P, ct.c_char_p]),
@@ -336,6 +337,15 @@ class Context:
         kk = np.asarray(k, dtype=np.float64)
         _check(lib().pbs_gram(self._ptr, geom.ref(), _dp(kk), q, s_ptr, gm_ptr, ga_ptr, precision,
                               _stream_ptr(stream)), "pbs_gram")
+
+    def m_householder(self, geom: Geometry, k, q: int, s_ptr: int, e_ptr: int, r_ptr: int, stream=None):
+        """Generalised Householder factorisation ``S = E R`` with ``E^* M E = I`` (``pbs_m_householder``).
+
+        ``s_ptr``, ``e_ptr``: device ``D x q`` column-major complex128; ``r_ptr``: device ``q x q``.
+        """
+        kk = np.asarray(k, dtype=np.float64)
+        _check(lib().pbs_m_householder(self._ptr, geom.ref(), _dp(kk), q, s_ptr, e_ptr, r_ptr, _stream_ptr(stream)),
+               "pbs_m_householder")
 
     def profile_enable(self, classes: str | None):
         """Time kernel classes with CUDA events on the library's stream (``pbs_profile_enable``)."""

@@ -101,7 +101,7 @@ int num_levels(int n, int m, int coarsest);
 // flops for arithmetic-bound ones) so the achieved rate can be derived.
 enum KernelClass {
   KC_NONE = 0, KC_EDGE_SMOOTH, KC_NODE_SMOOTH, KC_GRAM, KC_SMALL_RR, KC_RESIDUAL, KC_BLOCK_UPDATE,
-  KC_LIFT_ADJ_MASK, KC_EDGE_APPLY, KC_EDGE_TAIL, KC_NODE_TAIL, KC_COUNT
+  KC_LIFT_ADJ_MASK, KC_EDGE_APPLY, KC_EDGE_TAIL, KC_NODE_TAIL, KC_HOUSEHOLDER, KC_COUNT
 };
 struct TimedLaunch {
   int cls;
@@ -246,6 +246,14 @@ size_t small_rr_scratch(int q);
 void block_update(Roles X, int q, const double2* C, int ldc, long cgs, double2* Y, long ldy, int p,
                   const double2* Z, long ldz, long rows, int ngroups, bool dfa, cudaStream_t s);
 void random_block(double2* X, long ld, long rows, int ncols, uint64_t seed, cudaStream_t s);
+
+// ---- generalised Householder orthonormalisation (householder.cu) ----------
+// Q_q .. Q_1 S = P R, E = Q_1 .. Q_q P (Section 4); S, E: D x q (ld D), R: q x q
+// column-major, all on the device; `work` holds householder_work_bytes(D, q).
+int householder_max_columns(int n, int m);
+size_t householder_work_bytes(long D, int q);
+void m_householder(const Level& L0, const double* d_ph, const double2* S, double2* E, double2* R, int q, void* work,
+                   cudaStream_t s);
 void scale_columns(double2* X, long ld, long rows, int ncols, const double* d_scale, cudaStream_t s);
 
 }  // namespace pbs

@@ -1381,6 +1381,39 @@ int pbs_gram(pbs_ctx* ctx, const pbs_geom* geom, const double k[2], int q, const
   });
 }
 
+int pbs_m_householder(pbs_ctx* ctx, const pbs_geom* geom, const double k[2], int q, const pbs_c64* S, pbs_c64* E,
+                      pbs_c64* R, void* cuda_stream) {
+  if (!ctx || !geom || !k || q < 0 || q > kMaxTrial) return PBS_EINVAL;
+  if (q > 0 && (!S || !E || !R)) return PBS_EINVAL;
+  if (q > householder_max_columns(geom->n, geom->m)) return PBS_EINVAL;
+  return run_guarded_impl([&] {
+    std::lock_guard<std::mutex> ctx_lock(ctx->gpu_mu);
+    DeviceGuard g(ctx->device);
+    TimerScope ts(ctx);
+    if (q == 0) return;
+    pbs_opts o;
+    pbs_default_opts(&o);
+    ensure_hierarchy_host(ctx, geom, effective_mu(o, geom->a, geom->b), o.coarsest);
+    set_single_k(ctx, k[0], k[1]);
+    const Level& L0 = ctx->H.lev[0];
+    cudaStream_t s = ctx->stream;
+    cudaEvent_t ev;
+    PBS_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    PBS_CUDA(cudaEventRecord(ev, (cudaStream_t)cuda_stream));
+    PBS_CUDA(cudaStreamWaitEvent(s, ev, 0));
+    cudaEventDestroy(ev);
+    void* work = ctx->mem.alloc(householder_work_bytes(L0.D(), q));
+    try {
+      m_householder(L0, ctx->K.d_ph, (const double2*)S, (double2*)E, (double2*)R, q, work, s);
+      PBS_CUDA(cudaStreamSynchronize(s));
+    } catch (...) {
+      ctx->mem.free(work);
+      throw;
+    }
+    ctx->mem.free(work);
+  });
+}
+
 int pbs_rayleigh_ritz(pbs_ctx* ctx, const pbs_geom* geom, const pbs_opts* opts, const double k[2], int q,
                       const pbs_c64* S, int p, int project, double* theta, pbs_c64* X, void* cuda_stream) {
   if (!ctx || !geom || !opts || !k || q < 1 || p < 1 || p > q || p > kMaxBlock || !S || !theta || !X)
@@ -1414,7 +1447,7 @@ int pbs_rayleigh_ritz(pbs_ctx* ctx, const pbs_geom* geom, const pbs_opts* opts, 
 
 static const char* kClassNames[KC_COUNT] = {"", "edge_smooth", "node_smooth", "gram", "small_rr", "residual",
                                              "block_update", "lift_adj_mass", "edge_apply", "edge_tail",
-                                             "node_tail"};
+                                             "node_tail", "householder"};
 
 static int class_of(const char* name) {
   for (int c = 1; c < KC_COUNT; ++c)

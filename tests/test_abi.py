@@ -47,6 +47,7 @@ def test_null_arguments_are_rejected(built):
     assert L.pbs_destroy(None) == pbs.PBS_OK
     assert L.pbs_solve_k(None, None, None, None, None, None, None, None, None) == pbs.PBS_EINVAL
     assert L.pbs_apply(None, None, None, 0, 0, None, 1, None, None, None) == pbs.PBS_EINVAL
+    assert L.pbs_m_householder(None, None, None, 4, None, None, None, None) == pbs.PBS_EINVAL
 
 
 def test_struct_layout_matches_header(built):
