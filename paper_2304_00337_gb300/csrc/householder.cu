@@ -11,11 +11,13 @@
 //                R[i, i] = sigma, v_i = y - sigma P_i (in place of column i),
 //                v_i^* M v_i = 2 ||y||_M^2 + 2 ||y||_M |gamma|;
 //   k_hh_mdots   partial sums of v_i^* M y_j for the later columns j;
-//   k_hh_coef    their fixed-order totals, c_j = 2 v_i^* M y_j / v_i^* M v_i;
-//   k_hh_update  y_j -= c_j v_i.
-// E starts as P and takes the reflections q .. 1 (the last three kernels on
+//   k_hh_update  their fixed-order totals, c_j = 2 v_i^* M y_j / v_i^* M v_i,
+//                and y_j -= c_j v_i.
+// E starts as P and takes the reflections q .. 1 (the last two kernels on
 // columns i .. q-1: Q_i keeps P_k for k < i).  A step whose y is exactly zero
 // (rank loss) keeps Q_i = I and R[i, i] = 0.
+#include <algorithm>
+
 #include "internal.h"
 #include "mgpoint.cuh"
 
@@ -46,6 +48,14 @@ __device__ __forceinline__ double2 mass_at(const ERd<double>& r, const Lvl<doubl
 
 __device__ __forceinline__ double2 cconj_mul(double2 a, double2 b) {  // conj(a) b
   return make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+// acc + conj(a) b as four fused multiply-adds (the FP64 pipe is the bound)
+__device__ __forceinline__ double2 cconj_fma(double2 a, double2 b, double2 acc) {
+  return make_double2(fma(a.x, b.x, fma(a.y, b.y, acc.x)), fma(a.x, b.y, fma(-a.y, b.x, acc.y)));
+}
+// x - c v as four fused multiply-adds
+__device__ __forceinline__ double2 cfms(double2 x, double2 c, double2 v) {
+  return make_double2(fma(-c.x, v.x, fma(c.y, v.y, x.x)), fma(-c.x, v.y, fma(-c.y, v.x, x.y)));
 }
 
 // Fixed-order block sum of a complex value; result valid in thread 0.
@@ -130,6 +140,7 @@ __global__ void __launch_bounds__(kHT) k_hh_mdots(Lvl<double> L, const double* p
                                                   const double2* X, long ld, int j0, int j1, const double* vmv,
                                                   int i, double2* part) {
   if (vmv[i] == 0.0) return;
+  __shared__ double2 red[kHT / 32][kHCols];
   const Ph<double> p = load_ph<double>(ph, 0);
   const ERd<double> r{V, L.n, L.m, p};
   const long N = (long)L.n * L.m, D = 2 * N;
@@ -141,36 +152,53 @@ __global__ void __launch_bounds__(kHT) k_hh_mdots(Lvl<double> L, const double* p
     const double2 mv = mass_at(r, L, e, N);
 #pragma unroll
     for (int t = 0; t < kHCols; ++t)
-      if (t < nj) acc[t] = acc[t] + cconj_mul(mv, X[(long)(jb + t) * ld + e]);
+      if (t < nj) acc[t] = cconj_fma(mv, X[(long)(jb + t) * ld + e], acc[t]);
   }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
   for (int t = 0; t < kHCols; ++t) {
-    const double2 sum = block_sum_c(acc[t]);  // every thread takes part (barriers inside)
-    if (threadIdx.x == 0 && t < nj) part[(long)(jb - j0 + t) * gridDim.x + blockIdx.x] = sum;
+    for (int o = 16; o > 0; o >>= 1) {
+      acc[t].x += __shfl_xor_sync(0xffffffffu, acc[t].x, o);
+      acc[t].y += __shfl_xor_sync(0xffffffffu, acc[t].y, o);
+    }
+    if (lane == 0) red[w][t] = acc[t];
+  }
+  __syncthreads();
+  if (threadIdx.x < nj) {
+    double2 sum = make_double2(0, 0);
+    for (int k = 0; k < kHT / 32; ++k) sum = sum + red[k][threadIdx.x];
+    part[(long)(jb - j0 + threadIdx.x) * gridDim.x + blockIdx.x] = sum;
   }
 }
 
-// c_j = 2 (v^* M x_j) / (v^* M v), fixed-order sums of the partials
-__global__ void k_hh_coef(const double2* part, int nparts, int ncols, const double* vmv, int i, double2* coef) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= ncols || vmv[i] == 0.0) return;
-  double2 s = make_double2(0, 0);
-  for (int b = 0; b < nparts; ++b) s = s + part[(long)t * nparts + b];
-  const double f = 2.0 / vmv[i];
-  coef[t] = make_double2(f * s.x, f * s.y);
-}
-
-// x_j -= c_j v for columns j0 .. j1-1
-__global__ void __launch_bounds__(kHT) k_hh_update(const double2* V, double2* X, long ld, long D, int j0, int j1,
-                                                   const double2* coef, const double* vmv, int i) {
+// x_j -= c_j v for column j = j0 + blockIdx.y, c_j = 2 (v^* M x_j) / (v^* M v) from the
+// nparts partial sums (fixed order, the same in every block of the column)
+__global__ void __launch_bounds__(kHT) k_hh_update(const double2* V, double2* X, long ld, long D, int j0,
+                                                   const double2* part, int nparts, const double* vmv, int i) {
   if (vmv[i] == 0.0) return;
+  __shared__ double2 red[kHT / 32];
+  __shared__ double2 coef;
   const int j = j0 + blockIdx.y;
-  if (j >= j1) return;
-  const double2 c = coef[j - j0];
+  double2 s = make_double2(0, 0);
+  for (int b = threadIdx.x; b < nparts; b += kHT) s = s + part[(long)blockIdx.y * nparts + b];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int o = 16; o > 0; o >>= 1) {
+    s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
+    s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
+  }
+  if (lane == 0) red[w] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double2 t = make_double2(0, 0);
+    for (int k = 0; k < kHT / 32; ++k) t = t + red[k];
+    const double f = 2.0 / vmv[i];
+    coef = make_double2(f * t.x, f * t.y);
+  }
+  __syncthreads();
+  const double2 c = coef;
   double2* x = X + (long)j * ld;
   for (long e = blockIdx.x * (long)kHT + threadIdx.x; e < D; e += (long)gridDim.x * kHT) {
-    const double2 v = V[e];
-    x[e] = x[e] - make_double2(c.x * v.x - c.y * v.y, c.x * v.y + c.y * v.x);
+    x[e] = cfms(x[e], c, V[e]);
   }
 }
 
@@ -180,21 +208,20 @@ __global__ void k_hh_basis(Lvl<double> L, double2* E, long ld, int q) {
   if (k < q) E[(long)k * ld + pivot_edge(k, L.n)] = make_double2(1.0 / sqrt(2.0 / 3.0 * L.mx), 0.0);
 }
 
-// apply Q_i (vector in column i of V) to columns j0 .. j1-1 of X
+// apply Q_i (vector in column i of V) to columns j0 .. j1-1 of X; about two blocks
+// per SM in each launch
 void reflect_columns(const Level& L0, const double* d_ph, const double2* V, double2* X, long ld, int j0, int j1,
-                     const double* vmv, int i, double2* part, double2* coef, cudaStream_t s) {
+                     const double* vmv, int i, double2* part, cudaStream_t s) {
   if (j1 <= j0) return;
-  const int nc = j1 - j0;
+  const int nc = j1 - j0, nchunk = (nc + kHCols - 1) / kHCols;
+  const int nparts = std::max(1, kHBlocks / nchunk), ub = std::max(1, 2 * kHBlocks / nc);
   const Lvl<double> lv = L0.lvl<double>();
-  const double bytes = 16.0 * L0.D() * (nc + 1);
-  timer_begin(KC_HOUSEHOLDER, s, bytes);
-  k_hh_mdots<<<dim3(kHBlocks, (nc + kHCols - 1) / kHCols), kHT, 0, s>>>(lv, d_ph, V, X, ld, j0, j1, vmv, i, part);
+  timer_begin(KC_HOUSEHOLDER, s, 16.0 * L0.D() * (nc + 1));
+  k_hh_mdots<<<dim3(nparts, nchunk), kHT, 0, s>>>(lv, d_ph, V, X, ld, j0, j1, vmv, i, part);
   timer_end(KC_HOUSEHOLDER, s);
   PBS_LAUNCHED();
-  k_hh_coef<<<(nc + 127) / 128, 128, 0, s>>>(part, kHBlocks, nc, vmv, i, coef);
-  PBS_LAUNCHED();
   timer_begin(KC_HOUSEHOLDER, s, 16.0 * L0.D() * (2 * nc + 1));
-  k_hh_update<<<dim3(kHBlocks, nc), kHT, 0, s>>>(V, X, ld, L0.D(), j0, j1, coef, vmv, i);
+  k_hh_update<<<dim3(ub, nc), kHT, 0, s>>>(V, X, ld, L0.D(), j0, part, nparts, vmv, i);
   timer_end(KC_HOUSEHOLDER, s);
   PBS_LAUNCHED();
 }
@@ -204,7 +231,7 @@ void reflect_columns(const Level& L0, const double* d_ph, const double2* V, doub
 int householder_max_columns(int n, int m) { return n * (m / 2); }
 
 size_t householder_work_bytes(long D, int q) {
-  return sizeof(double2) * ((size_t)D * q + (size_t)kHBlocks * (q + 1) + (size_t)q) + sizeof(double) * q;
+  return sizeof(double2) * ((size_t)D * q + (size_t)kHBlocks * (q + 1)) + sizeof(double) * q;
 }
 
 void m_householder(const Level& L0, const double* d_ph, const double2* S, double2* E, double2* R, int q, void* work,
@@ -214,8 +241,7 @@ void m_householder(const Level& L0, const double* d_ph, const double2* S, double
   const long D = L0.D();
   double2* Y = (double2*)work;
   double2* part = Y + D * q;
-  double2* coef = part + (long)kHBlocks * (q + 1);
-  double* vmv = (double*)(coef + q);
+  double* vmv = (double*)(part + (long)kHBlocks * (q + 1));
   const Lvl<double> lv = L0.lvl<double>();
   PBS_CUDA(cudaMemcpyAsync(Y, S, sizeof(double2) * D * q, cudaMemcpyDeviceToDevice, s));
   PBS_CUDA(cudaMemsetAsync(R, 0, sizeof(double2) * q * q, s));
@@ -228,12 +254,12 @@ void m_householder(const Level& L0, const double* d_ph, const double2* S, double
     PBS_LAUNCHED();
     k_hh_sigma<<<1, 32, 0, s>>>(lv, d_ph, Y, D, i, part, kHBlocks, R, q, vmv);
     PBS_LAUNCHED();
-    reflect_columns(L0, d_ph, Y + (long)i * D, Y, D, i + 1, q, vmv, i, part, coef, s);
+    reflect_columns(L0, d_ph, Y + (long)i * D, Y, D, i + 1, q, vmv, i, part, s);
   }
   PBS_CUDA(cudaMemsetAsync(E, 0, sizeof(double2) * D * q, s));
   k_hh_basis<<<(q + 127) / 128, 128, 0, s>>>(lv, E, D, q);
   PBS_LAUNCHED();
-  for (int i = q - 1; i >= 0; --i) reflect_columns(L0, d_ph, Y + (long)i * D, E, D, i, q, vmv, i, part, coef, s);
+  for (int i = q - 1; i >= 0; --i) reflect_columns(L0, d_ph, Y + (long)i * D, E, D, i, q, vmv, i, part, s);
 }
 
 }  // namespace pbs
