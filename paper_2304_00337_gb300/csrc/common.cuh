@@ -113,7 +113,7 @@ template <> __device__ __forceinline__ double2 ld_as<double>(const double2* p) {
 template <> __device__ __forceinline__ dcx ld_as<df>(const double2* p) { return dcx_split(*p); }
 template <> __device__ __forceinline__ float2 ld_as<float>(const double2* p) {
   const double2 v = *p;
-  return make_float2(float(v.x), float(v.y));
+  return make_float2(d2f_rn(v.x), d2f_rn(v.y));
 }
 template <class T> __device__ __forceinline__ T ld_scalar(double d);
 template <> __device__ __forceinline__ double ld_scalar<double>(double d) { return d; }
@@ -123,12 +123,15 @@ __device__ __forceinline__ double2 to_d2(dcx v) { return dcx_to(v); }
 __device__ __forceinline__ double to_double(double v) { return v; }
 __device__ __forceinline__ double to_double(df v) { return df_to(v); }
 template <class T> __device__ __forceinline__ T narrow(double v) { return T(v); }
+template <> __device__ __forceinline__ float narrow<float>(double v) { return d2f_rn(v); }
 template <class T> __device__ __forceinline__ T narrow(df v);
 template <> __device__ __forceinline__ float narrow<float>(df v) { return df_to_float(v); }
 template <> __device__ __forceinline__ double narrow<double>(df v) { return df_to(v); }
 // exact widening of a stored value to the arithmetic type
 template <class T> __device__ __forceinline__ cx<T> widen(float2 v);
-template <> __device__ __forceinline__ double2 widen<double>(float2 v) { return make_double2(v.x, v.y); }
+template <> __device__ __forceinline__ double2 widen<double>(float2 v) {
+  return make_double2(f2d_exact(v.x), f2d_exact(v.y));
+}
 template <> __device__ __forceinline__ dcx widen<df>(float2 v) {
   return dcx_make(df_make(v.x, 0.0f), df_make(v.y, 0.0f));
 }
@@ -140,7 +143,7 @@ template <> __device__ __forceinline__ dcx widen<df>(double2 v) { return dcx_spl
 template <class T> __device__ __forceinline__ cx<T> ph_as(double re, double im);
 template <> __device__ __forceinline__ double2 ph_as<double>(double re, double im) { return make_double2(re, im); }
 template <> __device__ __forceinline__ float2 ph_as<float>(double re, double im) {
-  return make_float2(float(re), float(im));
+  return make_float2(d2f_rn(re), d2f_rn(im));
 }
 template <> __device__ __forceinline__ dcx ph_as<df>(double re, double im) {
   return dcx_make(df_split(re), df_split(im));

@@ -9,6 +9,7 @@
 
 #include "df32.cuh"
 #include "internal.h"
+#include "mgpoint.cuh"
 
 namespace pbs {
 
@@ -117,23 +118,21 @@ __global__ void k_rayleigh_parts(Lvl<V> L, W w, const double* ph, int cpg, const
 // it can: each CTA forms H = w curl once per cell of its 32 x 8 tile and of a
 // one-cell halo below and to the left (shared memory), A_x = H(i,j-1) - H(i,j),
 // A_y = H(i,j) - H(i-1,j), and the mass stencil is (h2/h1)/6 (4 x0 + x+ + x-).
-__global__ void __launch_bounds__(kBX * kBY) k_residual(Lvl<double> L, Wts<double> w, const double* ph, int cpg,
-                                                         const double2* __restrict__ E, double2* __restrict__ R,
-                                                         long ld, const double* __restrict__ lam,
-                                                         double* __restrict__ part) {
+// The tile's work with a reader r and weights w (the Bloch-extended ones, or the
+// direct ones on tiles whose reads all stay inside the level).
+template <class Rd, class Wt>
+__device__ __forceinline__ void residual_tile(const Lvl<double>& L, const Wt& w, const Rd& r, double l,
+                                              double2* __restrict__ Rc, double& rr, double& mm) {
   __shared__ double2 Hs[kBY + 1][kBX + 1];  // cell (i0 - 1 + a, j0 - 1 + b) at Hs[b][a]
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int i0 = blockIdx.x * kBX, j0 = blockIdx.y * kBY;
-  const int i = i0 + tx, j = j0 + ty, c = blockIdx.z;
+  const int i = i0 + tx, j = j0 + ty;
   const bool in = i < L.n && j < L.m;
-  const ERd<double> r{E + c * ld, L.n, L.m, load_ph<double>(ph, c / cpg)};
   if (in) Hs[ty + 1][tx + 1] = w(i, j) * curl_at<double>(r, i, j);
   if (ty == 0 && i < L.n) Hs[0][tx + 1] = w(i, j0 - 1) * curl_at<double>(r, i, j0 - 1);
   if (tx == 0 && j < L.m) Hs[ty + 1][0] = w(i0 - 1, j) * curl_at<double>(r, i0 - 1, j);
   __syncthreads();
-  double rr = 0, mm = 0;
   if (in) {
-    const double l = lam[c];
     const double sx = L.mx * (1.0 / 6.0), sy = L.my * (1.0 / 6.0);
     const double2 x0 = r.x(i, j), x1 = r.x(i, j + 1), x2 = r.x(i, j - 1);
     const double2 y0 = r.y(i, j), y1 = r.y(i + 1, j), y2 = r.y(i - 1, j);
@@ -143,13 +142,28 @@ __global__ void __launch_bounds__(kBX * kBY) k_residual(Lvl<double> L, Wts<doubl
     const double2 rx = make_double2(fma(-l, mx.x, hb.x - h.x), fma(-l, mx.y, hb.y - h.y));
     const double2 ry = make_double2(fma(-l, my.x, h.x - hl.x), fma(-l, my.y, h.y - hl.y));
     const long N = (long)L.n * L.m, e = (long)j * L.n + i;
-    R[c * ld + e] = rx;
-    R[c * ld + N + e] = ry;
+    Rc[e] = rx;
+    Rc[N + e] = ry;
     rr = fma(rx.x, rx.x, fma(rx.y, rx.y, fma(ry.x, ry.x, ry.y * ry.y)));
     mm = fma(mx.x, mx.x, fma(mx.y, mx.y, fma(my.x, my.x, my.y * my.y)));
   }
+}
+
+__global__ void __launch_bounds__(kBX * kBY) k_residual(Lvl<double> L, Wts<double> w, const double* ph, int cpg,
+                                                         const double2* __restrict__ E, double2* __restrict__ R,
+                                                         long ld, const double* __restrict__ lam,
+                                                         double* __restrict__ part) {
+  const int i0 = blockIdx.x * kBX, j0 = blockIdx.y * kBY, c = blockIdx.z;
+  double rr = 0, mm = 0;
+  // every read of the tile (indices i0 - 1 .. i0 + kBX, j0 - 1 .. j0 + kBY) inside the level
+  if (i0 >= 1 && j0 >= 1 && i0 + kBX < L.n && j0 + kBY < L.m)
+    residual_tile(L, WtsIn<double>{w.winv, w.n, w.scale}, ERdIn<double>{E + c * ld, L.n, (long)L.n * L.m},
+                  lam[c], R + c * ld, rr, mm);
+  else
+    residual_tile(L, w, ERd<double>{E + c * ld, L.n, L.m, load_ph<double>(ph, c / cpg)}, lam[c], R + c * ld, rr,
+                  mm);
   block_sum2(rr, mm);
-  if (tx == 0 && ty == 0) {
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
     const int nblk = gridDim.x * gridDim.y, b = blockIdx.y * gridDim.x + blockIdx.x;
     part[((long)c * nblk + b) * 2] = rr;
     part[((long)c * nblk + b) * 2 + 1] = mm;
@@ -175,21 +189,27 @@ __global__ void k_sub_lift(int n, int m, const double* ph, int cpg, const cx<T>*
                            double2* __restrict__ X, long ldx) {
   const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y, c = blockIdx.z;
   if (i >= n || j >= m) return;
-  const Ph<double> p = load_ph<double>(ph, c / cpg);
   const cx<T>* f = Phi + c * ldp;
   const long N = (long)n * m, e = (long)j * n + i;
+  double2* x = X + c * ldx;
+  // phi in FP64 (widened exactly by integer operations)
+  auto at = [&](int ii, int jj) -> double2 { return widen<double>(f[(long)jj * n + ii]); };
+  const double2 f0 = at(i, j);
+  if (i + 1 < n && j + 1 < m) {  // no wrap: the common case, without phase products
+    x[e] = x[e] - (at(i + 1, j) - f0);
+    x[N + e] = x[N + e] - (at(i, j + 1) - f0);
+    return;
+  }
   // read phi in FP64 through the Bloch extension
+  const Ph<double> p = load_ph<double>(ph, c / cpg);
   auto rd = [&](int ii, int jj) -> double2 {
     double2 ph1 = make_double2(1, 0);
     bool wr = false;
     if (ii >= n) { ii -= n; ph1 = p.al; wr = true; }
     if (jj >= m) { jj -= m; ph1 = cmul(ph1, p.be); wr = true; }
-    const cx<T> v = f[(long)jj * n + ii];
-    const double2 d = make_double2(double(v.x), double(v.y));
+    const double2 d = at(ii, jj);
     return wr ? cmul(d, ph1) : d;
   };
-  const double2 f0 = rd(i, j);
-  double2* x = X + c * ldx;
   x[e] = x[e] - (rd(i + 1, j) - f0);
   x[N + e] = x[N + e] - (rd(i, j + 1) - f0);
 }
@@ -234,11 +254,11 @@ __global__ void k_edge_sub_means(long N, double2* __restrict__ X, long ld, const
 
 __global__ void k_d2f(const double2* __restrict__ X, float2* __restrict__ Y, long n) {
   for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x)
-    Y[t] = make_float2(float(X[t].x), float(X[t].y));
+    Y[t] = make_float2(d2f_rn(X[t].x), d2f_rn(X[t].y));
 }
 __global__ void k_f2d(const float2* __restrict__ X, double2* __restrict__ Y, long n) {
   for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x)
-    Y[t] = make_double2(double(X[t].x), double(X[t].y));
+    Y[t] = make_double2(f2d_exact(X[t].x), f2d_exact(X[t].y));
 }
 
 // ---- block Gram matrices of a trial block, fused with the stencils ---------

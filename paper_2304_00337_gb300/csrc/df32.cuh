@@ -7,6 +7,7 @@
 // operations.  Built from the standard error-free transformations: Knuth's
 // two-sum (exact a + b = s + e) and the FMA two-product (exact a * b = p + e).
 #pragma once
+#include "fpconv.cuh"
 #include <cuda_runtime.h>
 
 namespace pbs {
@@ -28,7 +29,9 @@ __device__ __forceinline__ df df_from(double d) {
   const float h = (float)d;
   return df_make(h, (float)(d - (double)h));
 }
-__device__ __forceinline__ double df_to(df a) { return (double)a.hi + (double)a.lo; }
+// hi + lo in FP64; the widening of the two floats is exact and done by integer
+// operations (fpconv.cuh), so only the sum uses the FP64 pipe
+__device__ __forceinline__ double df_to(df a) { return f2d_exact(a.hi) + f2d_exact(a.lo); }
 
 // exact s + e = a + b (no ordering requirement)
 __device__ __forceinline__ df two_sum(float a, float b) {
@@ -95,13 +98,14 @@ __device__ __forceinline__ df df_zero() { return df_make(0.0f, 0.0f); }
 // FP64 -> df with integer operations only (no FP64 instruction): hi keeps the
 // leading 24 significand bits of d (truncated), lo the next 24 rounded to nearest,
 // so |d - (hi + lo)| <= 2^-47 |d|.  Magnitudes below 2^-100 give 0; magnitudes of
-// 2^127 and above (and inf / NaN) take the FP64 conversion, which keeps them.
+// 2^127 and above (and inf / NaN) give the rounded float alone (d2f_rn, which keeps
+// them without an FP64 instruction).
 __device__ __forceinline__ df df_split(double d) {
   const unsigned long long u = (unsigned long long)__double_as_longlong(d);
   const unsigned hw = (unsigned)(u >> 32), lw = (unsigned)u;
   const int e = (int)((hw >> 20) & 0x7FFu) - 1023;
   if (e < -100) return df_make(0.0f, 0.0f);
-  if (e > 126) return df_make((float)d, 0.0f);
+  if (e > 126) return df_make(d2f_rn(d), 0.0f);
   const unsigned sgn = hw & 0x80000000u;
   const float hi = __uint_as_float(sgn | ((unsigned)(e + 127) << 23) | ((hw & 0xFFFFFu) << 3) | (lw >> 29));
   // the remaining 29 bits r scaled by 2^(e-52): round to 23 bits and place them under
