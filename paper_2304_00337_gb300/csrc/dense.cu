@@ -171,15 +171,64 @@ __global__ void __launch_bounds__(kBX * kBY) k_residual(Lvl<double> L, Wts<doubl
 }
 
 // rhs(i,j) = (L^* M x)(i,j) = (Mx)_x(i-1,j) - (Mx)_x(i,j) + (Mx)_y(i,j-1) - (Mx)_y(i,j),
-// computed in V and stored in T
+// computed in V and stored in T.  A CTA stages the edge values its 32 x 8 nodes
+// read (converted to V once), forms each mass-stencil value once in shared
+// memory, then combines them; the stencil functions and the order of the sums
+// are those of the per-node formula.
+template <class V> struct TileERd {  // edge values of a tile region, x-edge (i, j) at sx[(j - oj) wx + i - oi]
+  const cx<V>* sx;
+  const cx<V>* sy;
+  int oi, oj, wx, wy;
+  __device__ __forceinline__ cx<V> x(int i, int j) const { return sx[(j - oj) * wx + (i - oi)]; }
+  __device__ __forceinline__ cx<V> y(int i, int j) const { return sy[(j - oj) * wy + (i - oi)]; }
+};
+
 template <class V, class T>
-__global__ void k_lift_adj_mass(Lvl<V> L, const double* ph, int cpg, const double2* __restrict__ X, long ldx,
-                                cx<T>* __restrict__ Y, long ldy) {
-  const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y, c = blockIdx.z;
-  if (i >= L.n || j >= L.m) return;
-  const ERdD<V> r{X + c * ldx, L.n, L.m, load_ph<V>(ph, c / cpg)};
-  const cx<V> v = M_x<V>(r, L, i - 1, j) - M_x<V>(r, L, i, j) + M_y<V>(r, L, i, j - 1) - M_y<V>(r, L, i, j);
-  Y[c * ldy + (long)j * L.n + i] = mk<T>(narrow<T>(v.x), narrow<T>(v.y));
+__global__ void __launch_bounds__(kBX * kBY) k_lift_adj_mass(Lvl<V> L, const double* ph, int cpg,
+                                                             const double2* __restrict__ X, long ldx,
+                                                             cx<T>* __restrict__ Y, long ldy) {
+  constexpr int WX = kBX + 1, WY = kBX + 2;
+  __shared__ cx<V> sx[(kBY + 2) * WX];  // x-edges (i0 - 1 + a, j0 - 1 + b)
+  __shared__ cx<V> sy[(kBY + 1) * WY];  // y-edges (i0 - 1 + a, j0 - 1 + b)
+  __shared__ cx<V> mxs[kBY * WX];       // (Mx)_x(i0 - 1 + a, j0 + b)
+  __shared__ cx<V> mys[(kBY + 1) * kBX];  // (Mx)_y(i0 + a, j0 - 1 + b)
+  const int i0 = blockIdx.x * kBX, j0 = blockIdx.y * kBY, c = blockIdx.z;
+  const int tid = threadIdx.y * kBX + threadIdx.x, nt = kBX * kBY;
+  const int nx = min(kBX, L.n - i0), ny = min(kBY, L.m - j0);  // nodes of the tile inside the level
+  const double2* xc = X + c * ldx;
+  const long N = (long)L.n * L.m;
+  // the values the tile's nodes read: x-edges a <= nx, b <= ny + 1; y-edges a <= nx + 1, b <= ny
+  if (i0 >= 1 && j0 >= 1 && i0 + kBX < L.n && j0 + kBY < L.m) {
+    for (int t = tid; t < (kBY + 2) * WX; t += nt)
+      sx[t] = ld_as<V>(xc + (long)(j0 - 1 + t / WX) * L.n + (i0 - 1 + t % WX));
+    for (int t = tid; t < (kBY + 1) * WY; t += nt)
+      sy[t] = ld_as<V>(xc + N + (long)(j0 - 1 + t / WY) * L.n + (i0 - 1 + t % WY));
+  } else {
+    const ERdD<V> r{xc, L.n, L.m, load_ph<V>(ph, c / cpg)};
+    for (int t = tid; t < (kBY + 2) * WX; t += nt) {
+      const int a = t % WX, b = t / WX;
+      if (a <= nx && b <= ny + 1) sx[t] = r.x(i0 - 1 + a, j0 - 1 + b);
+    }
+    for (int t = tid; t < (kBY + 1) * WY; t += nt) {
+      const int a = t % WY, b = t / WY;
+      if (a <= nx + 1 && b <= ny) sy[t] = r.y(i0 - 1 + a, j0 - 1 + b);
+    }
+  }
+  __syncthreads();
+  const TileERd<V> tr{sx, sy, i0 - 1, j0 - 1, WX, WY};
+  for (int t = tid; t < kBY * WX; t += nt) {
+    const int a = t % WX, b = t / WX;
+    if (a <= nx && b < ny) mxs[t] = M_x<V>(tr, L, i0 - 1 + a, j0 + b);
+  }
+  for (int t = tid; t < (kBY + 1) * kBX; t += nt) {
+    const int a = t % kBX, b = t / kBX;
+    if (a < nx && b <= ny) mys[t] = M_y<V>(tr, L, i0 + a, j0 - 1 + b);
+  }
+  __syncthreads();
+  const int a = threadIdx.x, b = threadIdx.y;
+  if (a >= nx || b >= ny) return;
+  const cx<V> v = mxs[b * WX + a] - mxs[b * WX + a + 1] + mys[b * kBX + a] - mys[(b + 1) * kBX + a];
+  Y[c * ldy + (long)(j0 + b) * L.n + i0 + a] = mk<T>(narrow<T>(v.x), narrow<T>(v.y));
 }
 
 // x <- x - L phi, in FP64 in every precision policy (it writes the iterate; see

@@ -97,16 +97,22 @@ __device__ __forceinline__ df df_zero() { return df_make(0.0f, 0.0f); }
 
 // FP64 -> df with integer operations only (no FP64 instruction): hi keeps the
 // leading 24 significand bits of d (truncated), lo the next 24 rounded to nearest,
-// so |d - (hi + lo)| <= 2^-47 |d|.  Magnitudes below 2^-100 give 0; magnitudes of
-// 2^127 and above (and inf / NaN) give the rounded float alone (d2f_rn, which keeps
-// them without an FP64 instruction).
+// so |d - (hi + lo)| <= 2^-47 |d|.  Magnitudes below 2^-100 give 0; magnitudes in
+// [2^127, 2^128) give their leading 24 bits alone, larger ones infinity (NaN stays
+// NaN) - all without an FP64 instruction.
 __device__ __forceinline__ df df_split(double d) {
   const unsigned long long u = (unsigned long long)__double_as_longlong(d);
   const unsigned hw = (unsigned)(u >> 32), lw = (unsigned)u;
   const int e = (int)((hw >> 20) & 0x7FFu) - 1023;
   if (e < -100) return df_make(0.0f, 0.0f);
-  if (e > 126) return df_make(d2f_rn(d), 0.0f);
   const unsigned sgn = hw & 0x80000000u;
+  if (__builtin_expect(e > 126, 0)) {
+    // |d| >= 2^127: the leading 24 bits alone; beyond the binary32 range infinity
+    // (NaN stays NaN).  A few integer operations, cheap where the compiler predicates them.
+    const unsigned over = sgn | 0x7F800000u | ((e == 1024 && ((hw & 0xFFFFFu) | lw)) ? 0x400000u : 0u);
+    const unsigned top = sgn | (254u << 23) | ((hw & 0xFFFFFu) << 3) | (lw >> 29);
+    return df_make(__uint_as_float(e > 127 ? over : top), 0.0f);
+  }
   const float hi = __uint_as_float(sgn | ((unsigned)(e + 127) << 23) | ((hw & 0xFFFFFu) << 3) | (lw >> 29));
   // the remaining 29 bits r scaled by 2^(e-52): round to 23 bits and place them under
   // the implicit bit of 2^(e-23); a carry out of the 23 bits moves into the exponent,
