@@ -118,6 +118,57 @@ __global__ void k_rayleigh_parts(Lvl<V> L, W w, const double* ph, int cpg, const
 // it can: each CTA forms H = w curl once per cell of its 32 x 8 tile and of a
 // one-cell halo below and to the left (shared memory), A_x = H(i,j-1) - H(i,j),
 // A_y = H(i,j) - H(i-1,j), and the mass stencil is (h2/h1)/6 (4 x0 + x+ + x-).
+// Reader of a tile region staged in shared memory (origin (oi, oj), row widths wx, wy).
+template <class V> struct TileERd {  // edge values of a tile region, x-edge (i, j) at sx[(j - oj) wx + i - oi]
+  const cx<V>* sx;
+  const cx<V>* sy;
+  int oi, oj, wx, wy;
+  __device__ __forceinline__ cx<V> x(int i, int j) const { return sx[(j - oj) * wx + (i - oi)]; }
+  __device__ __forceinline__ cx<V> y(int i, int j) const { return sy[(j - oj) * wy + (i - oi)]; }
+};
+
+// Bloch phase of an index one step outside the level, formed as the extended
+// readers form it (so the staged values equal theirs bit for bit).
+__device__ __forceinline__ double2 bloch_phase(int i, int j, int n, int m, const Ph<double>& p) {
+  double2 ph = make_double2(1.0, 0.0);
+  if (i < 0) ph = conj(p.al);
+  else if (i >= n) ph = p.al;
+  if (j < 0) ph = cmul(ph, conj(p.be));
+  else if (j >= m) ph = cmul(ph, p.be);
+  return ph;
+}
+
+// Stage the edges of one field around a tile: region element (a, b), a < w, b < h,
+// is edge (i0 - 1 + a, j0 - 1 + b) of the field at F (n x m); only a <= amax and
+// b <= bmax are read.  Edges inside the level are copied; those one step outside
+// (only on the region's ring) are read through the Bloch extension by one thread
+// each, so the phase products are not spread over every element.
+__device__ __forceinline__ void stage_field(const double2* __restrict__ F, int n, int m, const Ph<double>& p,
+                                            int i0, int j0, int w, int h, int amax, int bmax, double2* S) {
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y;
+  for (int t = tid; t < w * h; t += nt) {
+    const int a = t % w, b = t / w, i = i0 - 1 + a, j = j0 - 1 + b;
+    if (a <= amax && b <= bmax && i >= 0 && i < n && j >= 0 && j < m) S[t] = F[(long)j * n + i];
+  }
+  // ring: rows b = 0 and b = bmax (a = 0 .. amax), columns a = 0 and a = amax (b = 1 .. bmax - 1)
+  const int ring = 2 * (amax + 1) + 2 * max(bmax - 1, 0);
+  for (int t = tid; t < ring; t += nt) {
+    int a, b;
+    if (t < 2 * (amax + 1)) {
+      a = t % (amax + 1);
+      b = t < amax + 1 ? 0 : bmax;
+    } else {
+      const int u = t - 2 * (amax + 1);
+      a = u % 2 == 0 ? 0 : amax;
+      b = 1 + u / 2;
+    }
+    const int i = i0 - 1 + a, j = j0 - 1 + b;
+    if (i >= 0 && i < n && j >= 0 && j < m) continue;
+    const int ii = i < 0 ? i + n : (i >= n ? i - n : i), jj = j < 0 ? j + m : (j >= m ? j - m : j);
+    S[b * w + a] = cmul(F[(long)jj * n + ii], bloch_phase(i, j, n, m, p));
+  }
+}
+
 // The tile's work with a reader r and weights w (the Bloch-extended ones, or the
 // direct ones on tiles whose reads all stay inside the level).
 template <class Rd, class Wt>
@@ -156,12 +207,22 @@ __global__ void __launch_bounds__(kBX * kBY) k_residual(Lvl<double> L, Wts<doubl
   const int i0 = blockIdx.x * kBX, j0 = blockIdx.y * kBY, c = blockIdx.z;
   double rr = 0, mm = 0;
   // every read of the tile (indices i0 - 1 .. i0 + kBX, j0 - 1 .. j0 + kBY) inside the level
-  if (i0 >= 1 && j0 >= 1 && i0 + kBX < L.n && j0 + kBY < L.m)
+  if (i0 >= 1 && j0 >= 1 && i0 + kBX < L.n && j0 + kBY < L.m) {
     residual_tile(L, WtsIn<double>{w.winv, w.n, w.scale}, ERdIn<double>{E + c * ld, L.n, (long)L.n * L.m},
                   lam[c], R + c * ld, rr, mm);
-  else
-    residual_tile(L, w, ERd<double>{E + c * ld, L.n, L.m, load_ph<double>(ph, c / cpg)}, lam[c], R + c * ld, rr,
-                  mm);
+  } else {
+    // tiles at the level's edges: x-edges (i0 - 1 .. i0 + nx - 1, j0 - 1 .. j0 + ny) and y-edges
+    // (i0 - 1 .. i0 + nx, j0 - 1 .. j0 + ny - 1) staged with their Bloch phases
+    constexpr int WX = kBX + 1, WY = kBX + 2;
+    __shared__ double2 sx[(kBY + 2) * WX], sy[(kBY + 1) * WY];
+    const int nx = min(kBX, L.n - i0), ny = min(kBY, L.m - j0);
+    const Ph<double> p = load_ph<double>(ph, c / cpg);
+    const double2* Ec = E + c * ld;
+    stage_field(Ec, L.n, L.m, p, i0, j0, WX, kBY + 2, nx, ny + 1, sx);
+    stage_field(Ec + (long)L.n * L.m, L.n, L.m, p, i0, j0, WY, kBY + 1, nx + 1, ny, sy);
+    __syncthreads();
+    residual_tile(L, w, TileERd<double>{sx, sy, i0 - 1, j0 - 1, WX, WY}, lam[c], R + c * ld, rr, mm);
+  }
   block_sum2(rr, mm);
   if (threadIdx.x == 0 && threadIdx.y == 0) {
     const int nblk = gridDim.x * gridDim.y, b = blockIdx.y * gridDim.x + blockIdx.x;
@@ -175,14 +236,6 @@ __global__ void __launch_bounds__(kBX * kBY) k_residual(Lvl<double> L, Wts<doubl
 // read (converted to V once), forms each mass-stencil value once in shared
 // memory, then combines them; the stencil functions and the order of the sums
 // are those of the per-node formula.
-template <class V> struct TileERd {  // edge values of a tile region, x-edge (i, j) at sx[(j - oj) wx + i - oi]
-  const cx<V>* sx;
-  const cx<V>* sy;
-  int oi, oj, wx, wy;
-  __device__ __forceinline__ cx<V> x(int i, int j) const { return sx[(j - oj) * wx + (i - oi)]; }
-  __device__ __forceinline__ cx<V> y(int i, int j) const { return sy[(j - oj) * wy + (i - oi)]; }
-};
-
 template <class V, class T>
 __global__ void __launch_bounds__(kBX * kBY) k_lift_adj_mass(Lvl<V> L, const double* ph, int cpg,
                                                              const double2* __restrict__ X, long ldx,
