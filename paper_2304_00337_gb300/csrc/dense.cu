@@ -127,8 +127,8 @@ template <class V> struct TileERd {  // edge values of a tile region, x-edge (i,
   __device__ __forceinline__ cx<V> y(int i, int j) const { return sy[(j - oj) * wy + (i - oi)]; }
 };
 
-// Bloch phase of an index one step outside the level, formed as the extended
-// readers form it (so the staged values equal theirs bit for bit).
+// Bloch phase of an index one step outside the level, formed in the order the
+// extended readers use.
 __device__ __forceinline__ double2 bloch_phase(int i, int j, int n, int m, const Ph<double>& p) {
   double2 ph = make_double2(1.0, 0.0);
   if (i < 0) ph = conj(p.al);
