@@ -367,9 +367,7 @@ template <class T> struct TailArgs {
   T mu;
   int nu_pre, nu_post;
 };
-// threads of a fused tail: the steps are latency chains on one SM, so more warps
-// shorten the large levels' steps; FP64 tails need more registers and keep 512
-template <class T> constexpr int tail_threads() { return sizeof(T) == 4 ? 1024 : 512; }
+constexpr int kTailThreads = 512;
 constexpr long kTailMaxNodes = 4096;        // a level joins the tail when it has at most this many nodes
 constexpr int kTailSmemBytes = 200 * 1024;  // and the tail's shared-memory vectors fit in this
 
@@ -423,7 +421,7 @@ __device__ __forceinline__ void for_lattice(int i0, int j0, int s, int na, int n
 }
 
 template <class T>
-__global__ void __launch_bounds__(tail_threads<T>()) k_node_tail(TailArgs<T> a) {
+__global__ void __launch_bounds__(kTailThreads) k_node_tail(TailArgs<T> a) {
   extern __shared__ float4 fine_sm[];
   cx<T>* sm = reinterpret_cast<cx<T>*>(fine_sm);
   const int c = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
@@ -495,7 +493,7 @@ __global__ void __launch_bounds__(tail_threads<T>()) k_node_tail(TailArgs<T> a) 
 }
 
 template <class T>
-__global__ void __launch_bounds__(tail_threads<T>()) k_edge_tail(TailArgs<T> a) {
+__global__ void __launch_bounds__(kTailThreads) k_edge_tail(TailArgs<T> a) {
   extern __shared__ float4 fine_sm[];
   cx<T>* sm = reinterpret_cast<cx<T>*>(fine_sm);
   const int c = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
@@ -960,7 +958,7 @@ void edge_cycle(const Hierarchy& H, const KData& K, MgWork<T>& w, int l, const c
     const TailArgs<T> ta = tail_args<T>(H, K, l, b, x, ld, cpg, nu_pre, nu_post, false, &smem);
     set_tail_smem<T>();
     timer_begin(KC_EDGE_TAIL, s, tail_bytes<T>(H, l, ncols, cpg, false));
-    k_edge_tail<T><<<ncols, tail_threads<T>(), smem, s>>>(ta);
+    k_edge_tail<T><<<ncols, kTailThreads, smem, s>>>(ta);
     timer_end(KC_EDGE_TAIL, s);
     PBS_LAUNCHED();
     return;
@@ -1008,7 +1006,7 @@ void node_cycle(const Hierarchy& H, const KData& K, MgWork<T>& w, int l, const c
     const TailArgs<T> ta = tail_args<T>(H, K, l, b, x, ld, cpg, nu_pre, nu_post, true, &smem);
     set_tail_smem<T>();
     timer_begin(KC_NODE_TAIL, s, tail_bytes<T>(H, l, ncols, cpg, true));
-    k_node_tail<T><<<ncols, tail_threads<T>(), smem, s>>>(ta);
+    k_node_tail<T><<<ncols, kTailThreads, smem, s>>>(ta);
     timer_end(KC_NODE_TAIL, s);
     PBS_LAUNCHED();
     return;
