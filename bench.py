@@ -323,6 +323,7 @@ def run_ours(args):
         "gpu_launches_note": f"library kernel launches in the {args.steps} timed steps (pbs_launch_count)",
         "roofline": roof,
         "kernel_time_ms_per_class_warmup": {c: round(v[0], 3) for c, v in shares.items()},
+        "achieved_per_class_warmup": per_class_rates(shares, peaks["hbm_gbs"]),
         "cpu_baseline": cb,
     }
     print(json.dumps(line), flush=True)
@@ -456,6 +457,22 @@ def throwaway_bench(n: int) -> None:
                       "unit": "s", "higher_is_better": False, "n_gpus": 1, "data": "synthetic", "results": rows,
                       "config": {"workload": f"eps=100 disk r=1/3, {n}x{n}, k=(pi/2,pi/4), 16 bands",
                                  "precision": "mixed", "tol": 1e-8}}), flush=True)
+
+
+def per_class_rates(shares: dict, hbm_gbs: float) -> dict:
+    """Achieved rate of every timed kernel class in the first warm-up step: algorithmic
+    bytes per second (and the fraction of the measured HBM copy bandwidth) for the
+    streaming classes, algorithmic flops per second for the arithmetic-bound ones."""
+    out = {}
+    for c, (ms, n, work) in shares.items():
+        if ms <= 0 or n <= 0:
+            continue
+        if c in ("gram", "small_rr", "block_update"):
+            out[c] = {"tflops": work / (ms * 1e-3) / 1e12, "ms": round(ms, 3), "launches": int(n)}
+        else:
+            gbs = work / (ms * 1e-3) / 1e9
+            out[c] = {"gbs": gbs, "frac_hbm": gbs / hbm_gbs, "ms": round(ms, 3), "launches": int(n)}
+    return out
 
 
 def householder_bench(n: int, q: int, reps: int) -> None:
