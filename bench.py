@@ -25,6 +25,7 @@ import os
 import resource
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -75,7 +76,9 @@ class ClockSampler:
     def __init__(self, device_index: int):
         self.dev = device_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        # the raw samples go to PBS_CLOCKS_DIR (default: the system's temporary directory)
+        base = os.environ.get("PBS_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(base, f"clocks_{os.getpid()}.csv")
 
     def start(self):
         try:

@@ -1572,7 +1572,8 @@ int pbs_solve_grid(pbs_ctx* ctx, const pbs_geom* geom, const pbs_opts* opts, int
         }
       }
       if (K > 1) merge(cols, solve_chain_list(ctx, o, nk, ks.data(), cols, o.kbatch, nullptr, nullptr, store));
-      // rows 1.., horizontally from k_2j, k_1j, k_0j (the survey's reading for j = 1, 2 as well)
+      // rows 1.., horizontally from k_2j, k_1j, k_0j (read the same way for j = 1, 2, where the
+      // printed schedule leaves the order open)
       std::vector<Chain> rows;
       for (int j = 1; j < K && K > 3; ++j) {
         Chain c;
