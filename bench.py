@@ -59,6 +59,35 @@ def _dist():
     return rank, ws
 
 
+class Ranks:
+    """The replica ranks of a run: one process per GPU, each solving the whole workload
+    (weak scaling, no data-path collective); torch.distributed only for the barrier
+    around the timed region and the maximum of the per-rank times."""
+
+    def __init__(self, ws: int, device):
+        self.ws = ws
+        self.device = device
+
+    def barrier(self):
+        if self.ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def max(self, x: float) -> float:
+        if self.ws == 1:
+            return x
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([x], dtype=torch.float64, device=self.device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+
+def job_throughput(ws: int, units_per_rank: int, ms_max: float) -> float:
+    """Whole-job units per second: every rank's units over the slowest rank's time."""
+    return ws * units_per_rank / (ms_max / 1e3)
+
+
 def _peaks():
     try:
         return json.load(open(PEAKS_PATH)), "measured"
@@ -178,18 +207,8 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    def barrier():
-        if ws > 1:
-            import torch.distributed as dist
-            dist.barrier()
-
-    def max_over_ranks(x: float) -> float:
-        if ws == 1:
-            return x
-        import torch.distributed as dist
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    ranks = Ranks(ws, dev)
+    barrier, max_over_ranks = ranks.barrier, ranks.max
 
     eps = gi.rod_eps(N_SIDE, N_SIDE)
     ks = gi.gxmg_path(NK)
@@ -275,7 +294,7 @@ def run_ours(args):
     ms_step = max_over_ranks(float(np.sum(t_mixed)) / args.steps)
     ms_fp64 = max_over_ranks(float(np.sum(t_fp64)) / len(t_fp64))
     ms_e2e = max_over_ranks(float(np.sum(e2e_t)) / len(e2e_t))
-    value = ws * NK / (ms_step / 1e3)
+    value = job_throughput(ws, NK, ms_step)
     if rank != 0:
         return
     peaks, peak_kind = _peaks()
@@ -317,9 +336,9 @@ def run_ours(args):
                    "precision": "mixed", "l2": "flushed (512 MiB write) before every timed step",
                    "replicas": ws},
         "converged": ok, "max_resid": float(rs.max()), "iters_per_k": its.tolist(),
-        "plain_fp64": {"value": ws * NK / (ms_fp64 / 1e3), "unit": UNIT, "ms_per_step": ms_fp64},
+        "plain_fp64": {"value": job_throughput(ws, NK, ms_fp64), "unit": UNIT, "ms_per_step": ms_fp64},
         "clocks": clk,
-        "e2e": {"value": ws * NK / (ms_e2e / 1e3), "unit": UNIT,
+        "e2e": {"value": job_throughput(ws, NK, ms_e2e), "unit": UNIT,
                 "h2d_bytes_per_step": int(eps.nbytes + ks.nbytes),
                 "d2h_bytes_per_step": int(lam_h.nbytes + res_h.nbytes + it_h.nbytes)},
         "gpu_launches": int(launches),
