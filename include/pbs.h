@@ -141,7 +141,8 @@ typedef struct {
  * library's device allocations (0 = no cap beyond free memory); the multigrid
  * work of the solver is then sized for chunks of at most an eighth of it (of
  * 8 GiB without a cap), so more Bloch vectors in flight fit at a small cost in
- * launches. */
+ * launches.  A process drives one device: contexts on a second device fail with
+ * PBS_EINVAL (run one process per GPU). */
 PBS_API int pbs_create(pbs_ctx **ctx, int device, size_t hbm_budget_bytes);
 
 /* Free every device allocation of the context and the context itself. NULL is a no-op. */

@@ -1091,6 +1091,10 @@ int pbs_num_levels(int n, int m, int coarsest) {
   return num_levels(n, m, coarsest);
 }
 
+// The device this process drives (-1: none yet).  Kernel attributes such as the
+// dynamic shared-memory limits are raised once per process, on this device.
+static std::atomic<int> g_process_device{-1};
+
 int pbs_create(pbs_ctx** ctx, int device, size_t hbm_budget_bytes) {
   if (!ctx) return PBS_EINVAL;
   *ctx = nullptr;
@@ -1098,6 +1102,10 @@ int pbs_create(pbs_ctx** ctx, int device, size_t hbm_budget_bytes) {
     int count = 0;
     PBS_CUDA(cudaGetDeviceCount(&count));
     if (device < 0 || device >= count) fail(PBS_EINVAL, "no such CUDA device");
+    int bound = -1;
+    if (!g_process_device.compare_exchange_strong(bound, device) && bound != device)
+      fail(PBS_EINVAL, "this process already drives CUDA device " + std::to_string(bound) +
+                           "; use one process per device");
     DeviceGuard g(device);
     std::unique_ptr<pbs_ctx> c(new pbs_ctx(hbm_budget_bytes));
     c->device = device;
