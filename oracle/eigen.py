@@ -16,6 +16,10 @@ This module computes that definition directly:
 * ``rayleigh``: factored Rayleigh quotients ``(Ce)^* W (Ce) / e^* M e``.
 * ``closed_form_eps_const``: the exact discrete spectrum for constant ``eps``
   (symbol of the stencils on discrete plane waves).
+* ``certify_pairs``: a posteriori checks of given approximate eigenpairs on the
+  assembled pencil (residuals, the constraint ``L^* M e = 0``, M-orthonormality
+  and the residual-over-gap bound on each eigenvalue), for meshes too large for
+  a direct solve.
 """
 from __future__ import annotations
 
@@ -27,7 +31,7 @@ import scipy.sparse.linalg as spla
 from .fem import Mesh, assemble, is_gamma
 
 __all__ = ["closed_form_eps_const", "eigs_dense", "eigs_reduced", "eigs_sparse",
-           "rayleigh", "solve_k", "null_dimension"]
+           "rayleigh", "solve_k", "null_dimension", "certify_pairs"]
 
 
 def closed_form_eps_const(a: float, b: float, n: int, m: int, eps: float, k, count: int) -> np.ndarray:
@@ -176,3 +180,54 @@ def solve_k(a: float, b: float, n: int, m: int, eps, k, count: int, method: str 
     else:
         lam, V = eigs_sparse(ops, count)
     return lam, V, ops
+
+
+def certify_pairs(ops, lam, V, cluster_rtol: float = 1e-6):
+    """A posteriori certificate of approximate eigenpairs ``(lam[j], V[:, j])`` of the pencil.
+
+    For a Hermitian pencil with ``M`` positive definite and an M-normalised vector
+    ``e`` with Rayleigh quotient ``rho`` and residual ``r = A e - rho M e``, some
+    eigenvalue lies within ``eta = ||r||_{M^-1}`` of ``rho``; if the interval
+    ``(rho - delta, rho + delta)`` holds no other eigenvalue, the distance shrinks
+    to ``eta^2 / delta`` (Kato-Temple).  Values closer than ``cluster_rtol``
+    (relative) form a cluster (degenerate bands) and share the gap ``delta`` from
+    the cluster to the nearest other value of ``lam``, with ``eta^2`` summed over
+    the cluster.  The gap is taken between the given values: the bound says each
+    value is that close to an eigenvalue of the pencil, not which one.
+
+    Returns a dict of arrays over the columns: ``rq`` (factored Rayleigh quotients),
+    ``res`` (``||A e - lam M e||_2 / (lam ||M e||_2)``), ``constraint``
+    (``||L^* M e||_2 / (||L||_1 ||M e||_2)``, zero on ``(ker A)^{perp M}``),
+    ``bound`` (the residual-over-gap bound, relative to ``lam``) and the scalar
+    ``orth`` (``max |V^* M V - I|``).
+    """
+    A, M, L = ops["A"], ops["M"], ops["L"]
+    V = np.asarray(V, complex)
+    lam = np.asarray(lam, float)
+    MV = M @ V
+    G = V.conj().T @ MV
+    orth = float(np.abs(G - np.eye(V.shape[1])).max())
+    rq = rayleigh(ops, V)
+    R = A @ V - MV * lam[None, :]
+    res = np.linalg.norm(R, axis=0) / (np.abs(lam) * np.linalg.norm(MV, axis=0))
+    lnorm = float(np.abs(L).sum(axis=0).max())  # ||L||_1: the largest column sum
+    constraint = np.linalg.norm(L.conj().T @ MV, axis=0) / (lnorm * np.linalg.norm(MV, axis=0))
+    # ||r||_{M^-1}^2 = r^* M^-1 r with the vector normalised in the M-norm
+    lu = spla.splu(M.tocsc())
+    eta2 = np.array([np.real(np.vdot(R[:, j], lu.solve(R[:, j]))) for j in range(V.shape[1])])
+    eta2 /= np.real(np.einsum("dq,dq->q", V.conj(), MV))
+    order = np.argsort(lam)
+    bound = np.zeros_like(lam)
+    j = 0
+    while j < len(order):
+        c = [order[j]]
+        while j + len(c) < len(order) and lam[order[j + len(c)]] - lam[c[-1]] <= cluster_rtol * abs(lam[c[-1]]):
+            c.append(order[j + len(c)])
+        others = [lam[t] for t in order if t not in c]
+        lo, hi = min(lam[c]), max(lam[c])
+        delta = min([abs(x - lo) if x < lo else abs(x - hi) for x in others], default=np.inf)
+        e2 = eta2[c].sum()
+        for t in c:
+            bound[t] = min(np.sqrt(e2), e2 / delta) / abs(lam[t])
+        j += len(c)
+    return dict(rq=rq, res=res, constraint=constraint, bound=bound, orth=orth)
