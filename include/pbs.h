@@ -59,12 +59,19 @@ extern "C" {
 #define PBS_ECUDA (-6)    /* a CUDA runtime call failed                     */
 
 /* ---- precision policies (Section 4/5 preconditioner precision) -------- */
-#define PBS_FP64 0  /* every kernel in FP64 ("plain")                         */
-#define PBS_MIXED 1 /* FP32 multigrid V-cycles and nodal cycles; residual,
-                       Rayleigh quotients, Gram matrices, projection right-hand
-                       side and update in double-float arithmetic on the FP32
-                       pipe (FP64 storage, about 2^-47 relative rounding); the
-                       small Rayleigh-Ritz eigensolve in double-float too      */
+#define PBS_FP64 0  /* every kernel in FP64 ("plain"), the small Rayleigh-Ritz
+                       eigensolve included; no double-float kernel runs
+                       (pbs_launch_count_df does not move)                    */
+#define PBS_MIXED 1 /* FP32 multigrid V-cycles and nodal cycles; the Gram
+                       matrices, the Rayleigh quotients of the iteration, the
+                       projection right-hand side L^* M x, the search direction
+                       P and the small Rayleigh-Ritz eigensolve in double-float
+                       arithmetic on the FP32 pipe (FP64 storage, about 2^-47
+                       relative rounding); FP64 for everything that writes the
+                       iterate or differences it through the curl-curl stencil
+                       (residual A E - M E Lambda, E update, x - L phi) and for
+                       the reported eigenvalues (FP64 Rayleigh quotients of the
+                       converged block)                                       */
 
 /* ---- operators for pbs_apply ----------------------------------------- */
 #define PBS_OP_A 0             /* edge -> edge: y = A x  (Section 3)            */
@@ -84,6 +91,12 @@ extern "C" {
 #define PBS_OP_PROJECT 14      /* edge -> edge: y = x - L phi, phi from nodal_cycles V-cycles on
                                   L^* M L phi = L^* M x (Section 4); at k = 0 the two constant
                                   edge fields are also M-projected out          */
+#define PBS_OP_RESIDUAL 15     /* edge -> edge: y = A x - mu M x by the FP64 residual kernel of the
+                                  iteration (R = A E - M E Lambda, Algorithm 2, with every
+                                  Lambda entry equal to opts->mu)               */
+#define PBS_OP_LH_M 16         /* edge -> node: y = L^* M x, the right-hand side of the projection
+                                  (Section 4), in the arithmetic of opts->precision (FP64, or
+                                  double-float under PBS_MIXED)                 */
 
 typedef struct pbs_ctx pbs_ctx; /* opaque; owns every device allocation of the library */
 
@@ -101,7 +114,9 @@ typedef struct {
 /* Solver options; pbs_default_opts fills documented defaults. */
 typedef struct {
   int nev;          /* wanted bands (smallest non-zero eigenvalues), >= 1          */
-  int block;        /* block width p (wanted + throw-away vectors, Section 7), nev <= block <= 32 */
+  int block;        /* block width p (wanted + throw-away vectors, Section 7), nev <= block <= 32
+                       (the trial block [E, W, P] then has at most 96 columns, the size
+                       the one-CTA small dense eigensolve holds on chip)              */
   int max_iter;     /* iteration limit per Bloch vector (default 400)              */
   int precision;    /* PBS_FP64 or PBS_MIXED (default PBS_MIXED)                   */
   int span;         /* trial space of the Rayleigh-Ritz step (Section 4): 1 = PINVIT,
@@ -141,8 +156,8 @@ typedef struct {
  * library's device allocations (0 = no cap beyond free memory); the multigrid
  * work of the solver is then sized for chunks of at most an eighth of it (of
  * 8 GiB without a cap), so more Bloch vectors in flight fit at a small cost in
- * launches.  A process drives one device: contexts on a second device fail with
- * PBS_EINVAL (run one process per GPU). */
+ * launches.  Contexts on different devices may live in one process; each
+ * device gets its kernel attributes raised on its first launch there. */
 PBS_API int pbs_create(pbs_ctx **ctx, int device, size_t hbm_budget_bytes);
 
 /* Free every device allocation of the context and the context itself. NULL is a no-op. */
@@ -179,6 +194,18 @@ PBS_API int pbs_solve_k(pbs_ctx *ctx, const pbs_geom *geom, const pbs_opts *opts
  */
 PBS_API int pbs_solve_path(pbs_ctx *ctx, const pbs_geom *geom, const pbs_opts *opts, int nk, const double *ks,
                    double *eigvals, double *resid, int *iters);
+
+/*
+ * pbs_solve_path with the eigenvectors of selected Bloch vectors: sel (host, nsel
+ * distinct indices into ks) picks them; evecs (host, nsel * nev * D complex) gets,
+ * for selection t, the nev wanted eigenvectors of Bloch vector sel[t] at
+ * evecs + t nev D (column-major, M-normalised: e^* M e = 1), copied when that
+ * Bloch vector converges.  The computation is the one of pbs_solve_path: eigvals,
+ * resid and iters are identical.  nsel = 0 is pbs_solve_path.
+ */
+PBS_API int pbs_solve_path_vectors(pbs_ctx *ctx, const pbs_geom *geom, const pbs_opts *opts, int nk, const double *ks,
+                                   double *eigvals, double *resid, int *iters, int nsel, const int *sel,
+                                   pbs_c64 *evecs);
 
 /*
  * The kappa x kappa Brillouin-zone sample of Section 6,
@@ -272,6 +299,12 @@ PBS_API int pbs_profile_read(pbs_ctx *ctx, const char *kernel_class, double *tot
 /* Number of CUDA kernels the library has launched in this process. */
 PBS_API unsigned long long pbs_launch_count(void);
 
+/* Number of those launches whose kernel computes in double-float arithmetic on
+ * the FP32 pipe (Gram, Rayleigh quotients, L^* M x, search direction and small
+ * Rayleigh-Ritz of the mixed policy, and pbs_small_rr_noalloc).  A PBS_FP64
+ * solve leaves it unchanged. */
+PBS_API unsigned long long pbs_launch_count_df(void);
+
 /*
  * Serving: paths of Bloch vectors (Section 6) submitted as independent requests
  * and solved one after another by a host thread of the context, in submission
@@ -317,8 +350,11 @@ PBS_API int pbs_fetch(pbs_ctx *ctx, uint64_t job_id, double *eigvals, double *re
  *           input is not finite, -3 if the eigensolve broke down; info[1] =
  *           numerical rank of the span.
  * Limits: 1 <= q <= 96, 1 <= p <= min(q, 32); larger sizes return PBS_EINVAL.
- * The kernel runs on `cuda_stream` on the current device; the call returns
- * after the launch, without waiting for it.  It allocates nothing: its work
+ * The kernel runs on `cuda_stream` on whichever device is current; the call
+ * needs no context and is not tied to the device of any pbs_create.  It returns
+ * after the launch, without waiting for it.  Failures set pbs_last_error; an
+ * error already pending on the calling thread (from earlier CUDA work) is
+ * reported as PBS_ECUDA without launching and is left in place.  It allocates nothing: its work
  * space is a fixed device array of about 480 KB compiled into the library and
  * held by every GPU that loads it until the process exits.  The first call on a
  * device looks up that array's device address, so make the first call on each

@@ -35,7 +35,7 @@ PBS_START_RANDOM = 0
 PBS_START_NESTED = 1
 # operators
 OPS = dict(A=0, M=1, A_MU_M=2, C=3, CH=4, L=5, LH=6, P_NODAL=7, PROLONG=8, RESTRICT=9, PROLONG_NODAL=10,
-           RESTRICT_NODAL=11, VCYCLE_EDGE=12, VCYCLE_NODAL=13, PROJECT=14)
+           RESTRICT_NODAL=11, VCYCLE_EDGE=12, VCYCLE_NODAL=13, PROJECT=14, RESIDUAL=15, LH_M=16)
 for _k, _v in OPS.items():
     globals()["PBS_OP_" + _k] = _v
 
@@ -89,6 +89,8 @@ def lib() -> ct.CDLL:
         "pbs_num_levels": (ct.c_int, [ct.c_int, ct.c_int, ct.c_int]),
         "pbs_solve_k": (ct.c_int, [P, ct.POINTER(pbs_geom), ct.POINTER(pbs_opts), dp, P, dp, dp, ip, P]),
         "pbs_solve_path": (ct.c_int, [P, ct.POINTER(pbs_geom), ct.POINTER(pbs_opts), ct.c_int, dp, dp, dp, ip]),
+        "pbs_solve_path_vectors": (ct.c_int, [P, ct.POINTER(pbs_geom), ct.POINTER(pbs_opts), ct.c_int, dp, dp, dp, ip,
+                                              ct.c_int, ip, P]),
         "pbs_solve_path_device": (ct.c_int, [P, ct.c_double, ct.c_double, ct.c_int, ct.c_int, P,
                                              ct.POINTER(pbs_opts), ct.c_int, P, P, P, P, P]),
         "pbs_apply": (ct.c_int, [P, ct.POINTER(pbs_geom), ct.POINTER(pbs_opts), ct.c_int, ct.c_int, dp, ct.c_int,
@@ -101,6 +103,7 @@ def lib() -> ct.CDLL:
         "pbs_profile_read": (ct.c_int, [P, ct.c_char_p, ct.POINTER(ct.c_double), ct.POINTER(ct.c_long),
                                         ct.POINTER(ct.c_double)]),
         "pbs_launch_count": (ct.c_ulonglong, []),
+        "pbs_launch_count_df": (ct.c_ulonglong, []),
         "pbs_small_rr_noalloc": (ct.c_int, [P, P, ct.c_int, ct.c_int, P, P, P, P]),
         "pbs_solve_grid": (ct.c_int, [P, ct.POINTER(pbs_geom), ct.POINTER(pbs_opts), ct.c_int, dp, dp, dp, ip]),
         "pbs_job_bytes": (ct.c_int, [ct.c_int, ct.c_int, ct.POINTER(pbs_opts), ct.c_int, ct.POINTER(ct.c_size_t)]),
@@ -122,6 +125,11 @@ def lib() -> ct.CDLL:
 def launch_count() -> int:
     """Kernels launched by the library in this process (``pbs_launch_count``)."""
     return int(lib().pbs_launch_count())
+
+
+def launch_count_df() -> int:
+    """Launches of double-float kernels in this process (``pbs_launch_count_df``)."""
+    return int(lib().pbs_launch_count_df())
 
 
 def small_rr_noalloc(gm_ptr: int, ga_ptr: int, q: int, p: int, c_ptr: int, theta_ptr: int, info_ptr: int,
@@ -271,6 +279,24 @@ class Context:
                                   it.ctypes.data_as(ct.POINTER(ct.c_int)))
         _check(st, "pbs_solve_path", (PBS_OK, PBS_ENOCONV) if allow_noconv else (PBS_OK,))
         return ev, rs, it
+
+    def solve_path_vectors(self, geom: Geometry, opts, ks, sel, allow_noconv: bool = False):
+        """``pbs_solve_path_vectors``: ``solve_path`` plus the M-normalised eigenvectors of the
+        Bloch vectors ``sel``; returns ``(eigvals, resid, iters, vecs)`` with ``vecs`` of shape
+        ``(len(sel), nev, D)`` (row ``j`` = eigenvector of band ``j``)."""
+        o = _opts(opts)
+        kk = np.ascontiguousarray(np.asarray(ks, dtype=np.float64).reshape(-1, 2))
+        nk = kk.shape[0]
+        sl = np.ascontiguousarray(np.asarray(sel, dtype=np.int32).reshape(-1))
+        ev = np.zeros((nk, o.nev))
+        rs = np.zeros((nk, o.nev))
+        it = np.zeros(nk, dtype=np.int32)
+        vecs = np.zeros((sl.size, o.nev, geom.D), dtype=np.complex128)
+        st = lib().pbs_solve_path_vectors(self._ptr, geom.ref(), ct.byref(o), nk, _dp(kk), _dp(ev), _dp(rs),
+                                          it.ctypes.data_as(ct.POINTER(ct.c_int)), int(sl.size),
+                                          sl.ctypes.data_as(ct.POINTER(ct.c_int)), vecs.ctypes.data)
+        _check(st, "pbs_solve_path_vectors", (PBS_OK, PBS_ENOCONV) if allow_noconv else (PBS_OK,))
+        return ev, rs, it, vecs
 
     def solve_grid(self, geom: Geometry, opts, kappa: int, allow_noconv: bool = False):
         """``pbs_solve_grid``: the kappa x kappa sample with the paper's extrapolation schedule;

@@ -625,53 +625,120 @@ __global__ void k_gram_finalize(const double2* __restrict__ part, int npart, int
 //  4. the p smallest eigenvalues of Tr by multisection on Sturm counts, their
 //     eigenvectors by inverse iteration (re-orthogonalised inside clusters);
 //  5. back-transformation and C = D T Q U.
-// Steps 2-5 use double-float arithmetic (about 48 bits) on the FP32 pipe: the
-// coefficients only need ~1e-14 accuracy (Ritz values and residuals are
-// recomputed in FP64 from the updated block), and a serial chain of FP64
-// instructions is what limited this one-block kernel on GB300.
+// Steps 2-5 run in the arithmetic R: FP64 under the plain policy, double-float
+// (about 48 bits, FP32 pipe) under the mixed one, where the coefficients only need
+// ~1e-14 accuracy (Ritz values and residuals are recomputed in FP64 from the
+// updated block) and a serial chain of FP64 instructions is what limited this
+// one-block kernel on GB300.
 constexpr double kDropTol = 1e-12;  // relative pivot below which a trial direction is dropped
 constexpr int kRRThreads = 512;
 constexpr int kRRWarps = kRRThreads / 32;
 
-__device__ __forceinline__ df warp_sum_df(df v) {
-  for (int o = 16; o > 0; o >>= 1) v = v + shfl_df(v, o);
+// Arithmetic of the small dense solve: R = df (double-float on the FP32 pipe,
+// the mixed policy) or double (plain FP64).  Ar<R> names the operations the
+// kernel needs on reals and on complex values C of that precision.
+// (operators as hidden friends, found by argument-dependent lookup only, so they
+// do not hide the namespace's operators on double2 and the double-float types)
+struct cd {
+  double re, im;
+  friend __device__ __forceinline__ cd operator+(cd a, cd b) { return cd{a.re + b.re, a.im + b.im}; }
+  friend __device__ __forceinline__ cd operator-(cd a, cd b) { return cd{a.re - b.re, a.im - b.im}; }
+  friend __device__ __forceinline__ cd operator-(cd a) { return cd{-a.re, -a.im}; }
+  friend __device__ __forceinline__ cd operator*(cd a, cd b) {
+    return cd{a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+  }
+};
+
+template <class R> struct Ar;
+template <> struct Ar<df> {
+  using C = cdf;
+  using lead_t = float;  // leading part: comparisons, magnitudes and pivot limits
+  static __device__ __forceinline__ df mk(float v) { return df_make(v, 0.0f); }
+  static __device__ __forceinline__ df zero() { return df_zero(); }
+  static __device__ __forceinline__ float lead(df a) { return a.hi; }
+  static __device__ __forceinline__ double to(df a) { return df_to(a); }
+  static __device__ __forceinline__ df sqrt(df a) { return df_sqrt(a); }
+  static __device__ __forceinline__ bool lt(df a, df b) { return df_lt(a, b); }
+  static __device__ __forceinline__ df mulf(df a, float b) { return df_mul_f(a, b); }
+  static __device__ __forceinline__ df xshfl(df v, int o) { return shfl_df(v, o); }
+  static __device__ __forceinline__ df ishfl(df v, int src) {
+    return df_make(__shfl_sync(0xffffffffu, v.hi, src), __shfl_sync(0xffffffffu, v.lo, src));
+  }
+  static __device__ __forceinline__ C cmk(df r, df i) { return cdf_make(r, i); }
+  static __device__ __forceinline__ C czero() { return cdf_zero(); }
+  static __device__ __forceinline__ C cfrom(double2 v) { return cdf_from(v); }
+  static __device__ __forceinline__ double2 cto(C z) { return cdf_to(z); }
+  static __device__ __forceinline__ C conj(C a) { return cdf_conj(a); }
+  static __device__ __forceinline__ C mulc(C a, C b) { return cdf_mulc(a, b); }
+  static __device__ __forceinline__ C scale(C a, df s) { return cdf_scale(a, s); }
+  static __device__ __forceinline__ df norm2(C a) { return cdf_norm2(a); }
+};
+template <> struct Ar<double> {
+  using C = cd;
+  using lead_t = double;
+  static __device__ __forceinline__ double mk(double v) { return v; }
+  static __device__ __forceinline__ double zero() { return 0.0; }
+  static __device__ __forceinline__ double lead(double a) { return a; }
+  static __device__ __forceinline__ double to(double a) { return a; }
+  static __device__ __forceinline__ double sqrt(double a) { return a > 0.0 ? ::sqrt(a) : 0.0; }
+  static __device__ __forceinline__ bool lt(double a, double b) { return a < b; }
+  static __device__ __forceinline__ double mulf(double a, float b) { return a * (double)b; }
+  static __device__ __forceinline__ double xshfl(double v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+  static __device__ __forceinline__ double ishfl(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+  static __device__ __forceinline__ C cmk(double r, double i) { return cd{r, i}; }
+  static __device__ __forceinline__ C czero() { return cd{0.0, 0.0}; }
+  static __device__ __forceinline__ C cfrom(double2 v) { return cd{v.x, v.y}; }
+  static __device__ __forceinline__ double2 cto(C z) { return make_double2(z.re, z.im); }
+  static __device__ __forceinline__ C conj(C a) { return cd{a.re, -a.im}; }
+  static __device__ __forceinline__ C mulc(C a, C b) { return cd{a.re * b.re + a.im * b.im, a.re * b.im - a.im * b.re}; }
+  static __device__ __forceinline__ C scale(C a, double s) { return cd{a.re * s, a.im * s}; }
+  static __device__ __forceinline__ double norm2(C a) { return a.re * a.re + a.im * a.im; }
+};
+
+template <class R> __device__ __forceinline__ R warp_sum_r(R v) {
+  for (int o = 16; o > 0; o >>= 1) v = v + Ar<R>::xshfl(v, o);
   return v;
 }
-__device__ __forceinline__ cdf warp_sum_cdf(cdf v) {
-  for (int o = 16; o > 0; o >>= 1) v = v + cdf_make(shfl_df(v.re, o), shfl_df(v.im, o));
+template <class R> __device__ __forceinline__ typename Ar<R>::C warp_sum_c(typename Ar<R>::C v) {
+  for (int o = 16; o > 0; o >>= 1) v = v + Ar<R>::cmk(Ar<R>::xshfl(v.re, o), Ar<R>::xshfl(v.im, o));
   return v;
 }
-// block-wide sum of a df value (all threads participate; result in every thread)
-__device__ __forceinline__ df block_sum_df(df v, df* red) {
+// block-wide sum (all threads participate; result in every thread)
+template <class R> __device__ __forceinline__ R block_sum_r(R v, R* red) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  v = warp_sum_df(v);
+  v = warp_sum_r<R>(v);
   __syncthreads();
   if (lane == 0) red[warp] = v;
   __syncthreads();
-  df t = df_zero();
+  R t = Ar<R>::zero();
   for (int w = 0; w < kRRWarps; ++w) t = t + red[w];
   return t;
 }
 
 // number of eigenvalues of the real symmetric tridiagonal (a, e^2) below x
-__device__ int sturm_count_df(const df* a, const df* e2, int n, df x, float pivmin) {
+template <class R, class P> __device__ int sturm_count_r(const R* a, const R* e2, int n, R x, P pivmin) {
+  using A = Ar<R>;
   int cnt = 0;
-  df d = a[0] - x;
-  if (fabsf(d.hi) < pivmin) d = df_make(-pivmin, 0.0f);
-  if (d.hi < 0.0f) ++cnt;
+  R d = a[0] - x;
+  if (fabs(A::lead(d)) < pivmin) d = A::mk(-pivmin);
+  if (A::lead(d) < 0) ++cnt;
   for (int i = 1; i < n; ++i) {
     d = (a[i] - x) - e2[i - 1] / d;
-    if (fabsf(d.hi) < pivmin) d = df_make(-pivmin, 0.0f);
-    if (d.hi < 0.0f) ++cnt;
+    if (fabs(A::lead(d)) < pivmin) d = A::mk(-pivmin);
+    if (A::lead(d) < 0) ++cnt;
   }
   return cnt;
 }
 
+template <class R>
 __global__ void __launch_bounds__(kRRThreads) k_small_rr(const double2* __restrict__ GM, const double2* __restrict__ GA,
                                                          int q, int p, double2* __restrict__ Cout,
                                                          double* __restrict__ theta_out, double2* __restrict__ scr,
                                                          int* __restrict__ info, int in_smem, int* __restrict__ phase_out,
                                                          long scr_stride) {
+  using A = Ar<R>;
+  using C = typename A::C;
+  using LT = typename A::lead_t;
   extern __shared__ double2 dsm[];
   {  // group blockIdx.x: its own Gram matrices, outputs and scratch
     const long g = blockIdx.x;
@@ -685,18 +752,18 @@ __global__ void __launch_bounds__(kRRThreads) k_small_rr(const double2* __restri
   }
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = kRRWarps;
   const long qq = (long)q * q;
-  cdf* G = (cdf*)(in_smem ? dsm : scr);  // M-Gram -> R -> Y
-  cdf* H = G + qq;                        // A-Gram -> H -> reflectors
-  cdf* T = H + qq;                        // R^{-1}
-  cdf* U = T + qq;                        // q x p eigenvectors
+  C* G = (C*)(in_smem ? dsm : scr);  // M-Gram -> R -> Y
+  C* H = G + qq;                        // A-Gram -> H -> reflectors
+  C* T = H + qq;                        // R^{-1}
+  C* U = T + qq;                        // q x p eigenvectors
   __shared__ double d[kMaxTrial];         // column scales (FP64)
   __shared__ int s_keep[kMaxTrial];
-  __shared__ df ta[kMaxTrial], te[kMaxTrial], te2[kMaxTrial], tbeta[kMaxTrial];
-  __shared__ cdf talpha[kMaxTrial], tphase[kMaxTrial], tvec[kMaxTrial], tp[kMaxTrial];
-  __shared__ df lam[kMaxBlock], lo_s[kMaxBlock], hi_s[kMaxBlock];
-  __shared__ df Z[kMaxTrial * kMaxBlock];  // real eigenvectors of the tridiagonal, column j at j*q
+  __shared__ R ta[kMaxTrial], te[kMaxTrial], te2[kMaxTrial], tbeta[kMaxTrial];
+  __shared__ C talpha[kMaxTrial], tphase[kMaxTrial], tvec[kMaxTrial], tp[kMaxTrial];
+  __shared__ R lam[kMaxBlock], lo_s[kMaxBlock], hi_s[kMaxBlock];
+  __shared__ R Z[kMaxTrial * kMaxBlock];  // real eigenvectors of the tridiagonal, column j at j*q
   __shared__ int s_r, s_bad, s_cnt[kRRThreads];
-  __shared__ df s_piv, s_red[kRRWarps];
+  __shared__ R s_piv, s_red[kRRWarps];
   long long t_phase[8];
   t_phase[0] = clock64();
 
@@ -712,9 +779,9 @@ __global__ void __launch_bounds__(kRRThreads) k_small_rr(const double2* __restri
     const double sc = d[i] * d[j];
     const double2 gm = GM[t], ga = GA[t];
     if (!isfinite(gm.x) || !isfinite(gm.y) || !isfinite(ga.x) || !isfinite(ga.y)) s_bad = 1;
-    G[t] = cdf_from(sc * gm);
-    H[t] = cdf_from(sc * ga);
-    T[t] = cdf_zero();
+    G[t] = A::cfrom(sc * gm);
+    H[t] = A::cfrom(sc * ga);
+    T[t] = A::czero();
   }
   __syncthreads();
   // Cholesky with dropping: R row k stored in G[j*q + k] (j >= k).  A dropped
@@ -722,28 +789,28 @@ __global__ void __launch_bounds__(kRRThreads) k_small_rr(const double2* __restri
   // value above every kept one.
   for (int k = 0; k < q; ++k) {
     if (tid == 0) {
-      const df pv = G[(long)k * q + k].re;
-      const bool keep = d[k] > 0.0 && df_to(pv) > kDropTol && isfinite(pv.hi);
+      const R pv = G[(long)k * q + k].re;
+      const bool keep = d[k] > 0.0 && A::to(pv) > kDropTol && isfinite(A::lead(pv));
       s_keep[k] = keep;
-      s_piv = keep ? df_make(1.0f, 0.0f) / df_sqrt(pv) : df_zero();  // 1 / R_kk
+      s_piv = keep ? A::mk(1.0f) / A::sqrt(pv) : A::zero();  // 1 / R_kk
     }
     __syncthreads();
-    const df inv = s_piv;
-    if (inv.hi > 0.0f) {
-      for (int j = k + tid; j < q; j += nt) G[(long)j * q + k] = cdf_scale(G[(long)j * q + k], inv);
+    const R inv = s_piv;
+    if (A::lead(inv) > 0.0f) {
+      for (int j = k + tid; j < q; j += nt) G[(long)j * q + k] = A::scale(G[(long)j * q + k], inv);
       __syncthreads();
       const int rem = q - k - 1;
       for (long t = tid; t < (long)rem * rem; t += nt) {
         const int ii = k + 1 + int(t % rem), jj = k + 1 + int(t / rem);
         if (ii > jj) continue;
-        G[(long)jj * q + ii] = G[(long)jj * q + ii] - cdf_mulc(G[(long)ii * q + k], G[(long)jj * q + k]);
+        G[(long)jj * q + ii] = G[(long)jj * q + ii] - A::mulc(G[(long)ii * q + k], G[(long)jj * q + k]);
       }
     } else {
       for (int j = tid; j < q; j += nt) {
-        G[(long)j * q + k] = cdf_make(df_make(j == k ? 1.0f : 0.0f, 0.0f), df_zero());
-        if (j < k) G[(long)k * q + j] = cdf_zero();
-        H[(long)j * q + k] = cdf_zero();
-        H[(long)k * q + j] = cdf_zero();
+        G[(long)j * q + k] = A::cmk(A::mk(j == k ? 1.0f : 0.0f), A::zero());
+        if (j < k) G[(long)k * q + j] = A::czero();
+        H[(long)j * q + k] = A::czero();
+        H[(long)k * q + j] = A::czero();
       }
     }
     __syncthreads();
@@ -771,24 +838,21 @@ __global__ void __launch_bounds__(kRRThreads) k_small_rr(const double2* __restri
     const int lane = tid & 31, warp = tid >> 5;
     constexpr int kSlots = (kMaxTrial + 31) / 32;
     for (int c = warp; c < r; c += kRRWarps) {
-      cdf bv[kSlots];
+      C bv[kSlots];
 #pragma unroll
       for (int sl = 0; sl < kSlots; ++sl)
-        bv[sl] = cdf_make(df_make(lane + 32 * sl == c ? 1.0f : 0.0f, 0.0f), df_zero());
+        bv[sl] = A::cmk(A::mk(lane + 32 * sl == c ? 1.0f : 0.0f), A::zero());
       for (int k = c; k >= 0; --k) {
         const int owner = k & 31, slot = k >> 5;
-        cdf xk = cdf_zero();
+        C xk = A::czero();
 #pragma unroll
         for (int sl = 0; sl < kSlots; ++sl)
           if (sl == slot && lane == owner) {
-            const df rkk = G[(long)k * q + k].re;
-            xk = cdf_make(bv[sl].re / rkk, bv[sl].im / rkk);
+            const R rkk = G[(long)k * q + k].re;
+            xk = A::cmk(bv[sl].re / rkk, bv[sl].im / rkk);
             T[(long)c * q + k] = xk;
           }
-        xk.re.hi = __shfl_sync(0xffffffffu, xk.re.hi, owner);
-        xk.re.lo = __shfl_sync(0xffffffffu, xk.re.lo, owner);
-        xk.im.hi = __shfl_sync(0xffffffffu, xk.im.hi, owner);
-        xk.im.lo = __shfl_sync(0xffffffffu, xk.im.lo, owner);
+        xk = A::cmk(A::ishfl(xk.re, owner), A::ishfl(xk.im, owner));
 #pragma unroll
         for (int sl = 0; sl < kSlots; ++sl) {
           const int m = lane + 32 * sl;
@@ -801,15 +865,15 @@ __global__ void __launch_bounds__(kRRThreads) k_small_rr(const double2* __restri
   // 2b. Y = A T into G (R is no longer needed), then H = T^* Y
   for (long t = tid; t < (long)r * r; t += nt) {
     const int i = int(t % r), c = int(t / r);
-    cdf acc = cdf_zero();
+    C acc = A::czero();
     for (int m = 0; m <= c; ++m) acc = acc + H[(long)m * q + i] * T[(long)c * q + m];
     G[(long)c * q + i] = acc;
   }
   __syncthreads();
   for (long t = tid; t < (long)r * r; t += nt) {
     const int i = int(t % r), c = int(t / r);
-    cdf acc = cdf_zero();
-    for (int m = 0; m <= i; ++m) acc = acc + cdf_mulc(T[(long)i * q + m], G[(long)c * q + m]);
+    C acc = A::czero();
+    for (int m = 0; m <= i; ++m) acc = acc + A::mulc(T[(long)i * q + m], G[(long)c * q + m]);
     H[(long)c * q + i] = acc;
   }
   __syncthreads();
@@ -817,31 +881,31 @@ __global__ void __launch_bounds__(kRRThreads) k_small_rr(const double2* __restri
   for (long t = tid; t < (long)r * r; t += nt) {
     const int i = int(t % r), c = int(t / r);
     if (i < c) {
-      const cdf up = H[(long)c * q + i], lo = H[(long)i * q + c];
-      const df half = df_make(0.5f, 0.0f);
-      const cdf m = cdf_make((up.re + lo.re) * half, (up.im - lo.im) * half);
+      const C up = H[(long)c * q + i], lo = H[(long)i * q + c];
+      const R half = A::mk(0.5f);
+      const C m = A::cmk((up.re + lo.re) * half, (up.im - lo.im) * half);
       H[(long)c * q + i] = m;
-      H[(long)i * q + c] = cdf_conj(m);
+      H[(long)i * q + c] = A::conj(m);
     } else if (i == c) {
-      H[(long)c * q + i].im = df_zero();
+      H[(long)c * q + i].im = A::zero();
     }
   }
   __syncthreads();
   // Gershgorin row sums of the kept rows (in te, which the reduction below fills
   // before it is used again), then the bound by one thread
   for (int i = tid; i < r; i += nt) {
-    df rs = df_zero();
+    R rs = A::zero();
     if (s_keep[i])
-      for (int j = 0; j < r; ++j) rs = rs + df_sqrt(cdf_norm2(H[(long)j * q + i]));
+      for (int j = 0; j < r; ++j) rs = rs + A::sqrt(A::norm2(H[(long)j * q + i]));
     te[i] = rs;
   }
   __syncthreads();
   if (tid == 0) {
-    df bound = df_zero();
+    R bound = A::zero();
     for (int i = 0; i < r; ++i)
-      if (df_lt(bound, te[i])) bound = te[i];
+      if (A::lt(bound, te[i])) bound = te[i];
     for (int i = 0; i < r; ++i)
-      if (!s_keep[i]) H[(long)i * q + i] = cdf_make(bound + bound + df_make(1.0f, 0.0f), df_zero());
+      if (!s_keep[i]) H[(long)i * q + i] = A::cmk(bound + bound + A::mk(1.0f), A::zero());
   }
   __syncthreads();
   t_phase[2] = clock64();
@@ -849,48 +913,48 @@ __global__ void __launch_bounds__(kRRThreads) k_small_rr(const double2* __restri
   //    stored in column k below the diagonal (v, with v_0 = x_0 - alpha) and tbeta[k]
   for (int k = 0; k + 2 < r; ++k) {
     const int m = r - k - 1;
-    df s2 = df_zero();
-    for (int i = tid; i < m; i += nt) s2 = s2 + cdf_norm2(H[(long)k * q + k + 1 + i]);
-    s2 = block_sum_df(s2, s_red);
+    R s2 = A::zero();
+    for (int i = tid; i < m; i += nt) s2 = s2 + A::norm2(H[(long)k * q + k + 1 + i]);
+    s2 = block_sum_r<R>(s2, s_red);
     if (tid == 0) {
-      const df sigma = df_sqrt(s2);
-      const cdf x0 = H[(long)k * q + k + 1];
-      const df ax0 = df_sqrt(cdf_norm2(x0));
-      cdf ph = ax0.hi > 0.0f ? cdf_make(x0.re / ax0, x0.im / ax0) : cdf_make(df_make(1.0f, 0.0f), df_zero());
-      if (sigma.hi > 0.0f) {
-        const cdf alpha = -cdf_scale(ph, sigma);
+      const R sigma = A::sqrt(s2);
+      const C x0 = H[(long)k * q + k + 1];
+      const R ax0 = A::sqrt(A::norm2(x0));
+      C ph = A::lead(ax0) > 0.0f ? A::cmk(x0.re / ax0, x0.im / ax0) : A::cmk(A::mk(1.0f), A::zero());
+      if (A::lead(sigma) > 0.0f) {
+        const C alpha = -A::scale(ph, sigma);
         talpha[k] = alpha;
-        tbeta[k] = df_make(1.0f, 0.0f) / (sigma * (sigma + ax0));
+        tbeta[k] = A::mk(1.0f) / (sigma * (sigma + ax0));
         H[(long)k * q + k + 1] = x0 - alpha;
       } else {
         talpha[k] = x0;
-        tbeta[k] = df_zero();
+        tbeta[k] = A::zero();
       }
     }
     __syncthreads();
-    const df beta = tbeta[k];
-    if (beta.hi != 0.0f) {
+    const R beta = tbeta[k];
+    if (A::lead(beta) != 0.0f) {
       // p = beta * Hsub v (rows by warps, columns by lanes)
       for (int i = warp; i < m; i += nw) {
-        cdf acc = cdf_zero();
+        C acc = A::czero();
         for (int j = lane; j < m; j += 32) acc = acc + H[(long)(k + 1 + j) * q + k + 1 + i] * H[(long)k * q + k + 1 + j];
-        acc = warp_sum_cdf(acc);
-        if (lane == 0) tp[i] = cdf_scale(acc, beta);
+        acc = warp_sum_c<R>(acc);
+        if (lane == 0) tp[i] = A::scale(acc, beta);
       }
       __syncthreads();
       // K = beta/2 v^* p (real for Hermitian H); w = p - K v
-      df kk = df_zero();
-      for (int i = tid; i < m; i += nt) kk = kk + cdf_mulc(H[(long)k * q + k + 1 + i], tp[i]).re;
-      kk = block_sum_df(kk, s_red);
-      const df K = kk * beta * df_make(0.5f, 0.0f);
-      for (int i = tid; i < m; i += nt) tvec[i] = tp[i] - cdf_scale(H[(long)k * q + k + 1 + i], K);
+      R kk = A::zero();
+      for (int i = tid; i < m; i += nt) kk = kk + A::mulc(H[(long)k * q + k + 1 + i], tp[i]).re;
+      kk = block_sum_r<R>(kk, s_red);
+      const R K = kk * beta * A::mk(0.5f);
+      for (int i = tid; i < m; i += nt) tvec[i] = tp[i] - A::scale(H[(long)k * q + k + 1 + i], K);
       __syncthreads();
       // Hsub -= v w^* + w v^*
       for (long t = tid; t < (long)m * m; t += nt) {
         const int i = int(t % m), j = int(t / m);
-        const cdf vi = H[(long)k * q + k + 1 + i], vj = H[(long)k * q + k + 1 + j];
-        cdf h = H[(long)(k + 1 + j) * q + k + 1 + i];
-        h = h - vi * cdf_conj(tvec[j]) - tvec[i] * cdf_conj(vj);
+        const C vi = H[(long)k * q + k + 1 + i], vj = H[(long)k * q + k + 1 + j];
+        C h = H[(long)(k + 1 + j) * q + k + 1 + i];
+        h = h - vi * A::conj(tvec[j]) - tvec[i] * A::conj(vj);
         H[(long)(k + 1 + j) * q + k + 1 + i] = h;
       }
     }
@@ -898,16 +962,16 @@ __global__ void __launch_bounds__(kRRThreads) k_small_rr(const double2* __restri
   }
   // real tridiagonal: diagonal ta, off-diagonal te = |alpha|, phases tphase
   if (tid == 0) {
-    cdf ph = cdf_make(df_make(1.0f, 0.0f), df_zero());
+    C ph = A::cmk(A::mk(1.0f), A::zero());
     for (int k = 0; k < r; ++k) {
       ta[k] = H[(long)k * q + k].re;
       tphase[k] = ph;
       if (k + 1 < r) {
-        const cdf al = (k + 2 < r) ? talpha[k] : H[(long)k * q + k + 1];
-        const df aa = df_sqrt(cdf_norm2(al));
+        const C al = (k + 2 < r) ? talpha[k] : H[(long)k * q + k + 1];
+        const R aa = A::sqrt(A::norm2(al));
         te[k] = aa;
         te2[k] = aa * aa;
-        if (aa.hi > 0.0f) ph = ph * cdf_make(al.re / aa, al.im / aa);
+        if (A::lead(aa) > 0.0f) ph = ph * A::cmk(al.re / aa, al.im / aa);
       }
     }
   }
@@ -915,38 +979,36 @@ __global__ void __launch_bounds__(kRRThreads) k_small_rr(const double2* __restri
   t_phase[3] = clock64();
   // 4a. multisection: each warp refines one wanted eigenvalue at a time, its 32
   //     lanes evaluating the Sturm count at 32 interior points of the bracket
-  df lo = df_zero(), hi = df_zero();
+  R lo = A::zero(), hi = A::zero();
   for (int k = 0; k < r; ++k) {
-    const df rad = (k > 0 ? te[k - 1] : df_zero()) + (k + 1 < r ? te[k] : df_zero());
-    const df l = ta[k] - rad, h = ta[k] + rad;
-    if (k == 0 || df_lt(l, lo)) lo = l;
-    if (k == 0 || df_lt(hi, h)) hi = h;
+    const R rad = (k > 0 ? te[k - 1] : A::zero()) + (k + 1 < r ? te[k] : A::zero());
+    const R l = ta[k] - rad, h = ta[k] + rad;
+    if (k == 0 || A::lt(l, lo)) lo = l;
+    if (k == 0 || A::lt(hi, h)) hi = h;
   }
-  const float tnorm = fmaxf(fabsf(lo.hi), fabsf(hi.hi)) + 1e-30f;
+  const LT tnorm = fmax(fabs(A::lead(lo)), fabs(A::lead(hi))) + LT(1e-30);
   // Sturm pivots below pivmin are replaced by -pivmin: e^2 / pivmin stays far below the float range
-  const float pivmin = fmaxf(1e-30f * tnorm * tnorm, 1e-36f);
+  const LT pivmin = fmax(LT(1e-30) * tnorm * tnorm, LT(1e-36));
   // inverse iteration: pivots are kept above the accuracy of the shift, so a solve
   // grows the vector by at most ~1e14 and never leaves the float range
-  const float pivmin_ii = 1e-14f * tnorm;
+  const LT pivmin_ii = LT(1e-14) * tnorm;
   for (int j = warp; j < p; j += nw) {
-    df a0 = lo - df_make(1e-6f * tnorm, 0.0f), b0 = hi + df_make(1e-6f * tnorm, 0.0f);
+    R a0 = lo - A::mk(1e-6f * tnorm), b0 = hi + A::mk(1e-6f * tnorm);
     for (int it = 0; it < 24; ++it) {
-      const df w = b0 - a0;
-      if (df_to(w) <= 4e-15 * (double)tnorm) break;
-      const df x = a0 + df_mul_f(w, float(lane + 1) / 33.0f);
-      const int cnt = sturm_count_df(ta, te2, r, x, pivmin);
+      const R w = b0 - a0;
+      if (A::to(w) <= 4e-15 * (double)tnorm) break;
+      const R x = a0 + A::mulf(w, float(lane + 1) / 33.0f);
+      const int cnt = sturm_count_r<R>(ta, te2, r, x, pivmin);
       // new bracket: largest point with count <= j, smallest with count > j
       const unsigned below = __ballot_sync(0xffffffffu, cnt <= j);
       const int nb = __popc(below);  // points 0..nb-1 have count <= j (counts increase with x)
-      const df xa = df_make(__shfl_sync(0xffffffffu, x.hi, nb > 0 ? nb - 1 : 0),
-                            __shfl_sync(0xffffffffu, x.lo, nb > 0 ? nb - 1 : 0));
-      const df xb = df_make(__shfl_sync(0xffffffffu, x.hi, nb < 32 ? nb : 31),
-                            __shfl_sync(0xffffffffu, x.lo, nb < 32 ? nb : 31));
+      const R xa = A::ishfl(x, nb > 0 ? nb - 1 : 0);
+      const R xb = A::ishfl(x, nb < 32 ? nb : 31);
       if (nb > 0) a0 = xa;
       if (nb < 32) b0 = xb;
     }
     if (lane == 0) {
-      lam[j] = (a0 + b0) * df_make(0.5f, 0.0f);
+      lam[j] = (a0 + b0) * A::mk(0.5f);
       lo_s[j] = a0;
       hi_s[j] = b0;
     }
@@ -956,32 +1018,32 @@ __global__ void __launch_bounds__(kRRThreads) k_small_rr(const double2* __restri
   // 4b. inverse iteration on Tr - lam_j I (Gaussian elimination with partial
   //     pivoting, factored once), one thread per eigenvalue; cluster members
   //     re-orthogonalised after every sweep
-  df u0[kMaxTrial], u1[kMaxTrial], u2[kMaxTrial], mult[kMaxTrial];
+  R u0[kMaxTrial], u1[kMaxTrial], u2[kMaxTrial], mult[kMaxTrial];
   bool swp[kMaxTrial];
   if (tid < p) {
-    const df shift = lam[tid];
-    df d0 = ta[0] - shift, s1 = r > 1 ? te[0] : df_zero();
+    const R shift = lam[tid];
+    R d0 = ta[0] - shift, s1 = r > 1 ? te[0] : A::zero();
     for (int i = 0; i < r; ++i) {
-      const df below_sub = i + 1 < r ? te[i] : df_zero();
-      const df below_diag = i + 1 < r ? ta[i + 1] - shift : df_zero();
-      const df below_sup = i + 2 < r ? te[i + 1] : df_zero();
-      if (i + 1 < r && fabsf(below_sub.hi) > fabsf(d0.hi)) {
+      const R below_sub = i + 1 < r ? te[i] : A::zero();
+      const R below_diag = i + 1 < r ? ta[i + 1] - shift : A::zero();
+      const R below_sup = i + 2 < r ? te[i + 1] : A::zero();
+      if (i + 1 < r && fabs(A::lead(below_sub)) > fabs(A::lead(d0))) {
         swp[i] = true;
         u0[i] = below_sub;
         u1[i] = below_diag;
         u2[i] = below_sup;
-        const df mlt = d0 / below_sub;
+        const R mlt = d0 / below_sub;
         mult[i] = mlt;
         d0 = s1 - mlt * below_diag;
         s1 = -(mlt * below_sup);
       } else {
         swp[i] = false;
-        df dd = d0;
-        if (fabsf(dd.hi) < pivmin_ii) dd = df_make(dd.hi < 0.0f ? -pivmin_ii : pivmin_ii, 0.0f);
+        R dd = d0;
+        if (fabs(A::lead(dd)) < pivmin_ii) dd = A::mk(A::lead(dd) < 0.0f ? -pivmin_ii : pivmin_ii);
         u0[i] = dd;
         u1[i] = s1;
-        u2[i] = df_zero();
-        const df mlt = i + 1 < r ? below_sub / dd : df_zero();
+        u2[i] = A::zero();
+        const R mlt = i + 1 < r ? below_sub / dd : A::zero();
         mult[i] = mlt;
         d0 = below_diag - mlt * s1;
         s1 = below_sup;
@@ -991,12 +1053,12 @@ __global__ void __launch_bounds__(kRRThreads) k_small_rr(const double2* __restri
   for (int sweep = 0; sweep < 4; ++sweep) {
     if (tid < p) {
       const int j = tid;
-      df* z = Z + j * q;
+      R* z = Z + j * q;
       if (sweep == 0)
-        for (int i = 0; i < r; ++i) z[i] = df_make(1.0f + 0.37f * __sinf(1.7f * (i + 1) * (j + 1)), 0.0f);
+        for (int i = 0; i < r; ++i) z[i] = A::mk(1.0f + 0.37f * __sinf(1.7f * (i + 1) * (j + 1)));
       for (int i = 0; i + 1 < r; ++i) {
         if (swp[i]) {
-          const df t0 = z[i];
+          const R t0 = z[i];
           z[i] = z[i + 1];
           z[i + 1] = t0 - mult[i] * z[i];
         } else {
@@ -1004,22 +1066,22 @@ __global__ void __launch_bounds__(kRRThreads) k_small_rr(const double2* __restri
         }
       }
       for (int i = r - 1; i >= 0; --i) {
-        df v = z[i];
+        R v = z[i];
         if (i + 1 < r) v = v - u1[i] * z[i + 1];
         if (i + 2 < r) v = v - u2[i] * z[i + 2];
-        df dd = u0[i];
-        if (fabsf(dd.hi) < pivmin_ii) dd = df_make(dd.hi < 0.0f ? -pivmin_ii : pivmin_ii, 0.0f);
+        R dd = u0[i];
+        if (fabs(A::lead(dd)) < pivmin_ii) dd = A::mk(A::lead(dd) < 0.0f ? -pivmin_ii : pivmin_ii);
         z[i] = v / dd;
       }
-      float zmax = 0.0f;
-      for (int i = 0; i < r; ++i) zmax = fmaxf(zmax, fabsf(z[i].hi));
-      const float sc = zmax > 0.0f ? 1.0f / zmax : 1.0f;
-      df nrm = df_zero();
+      LT zmax = 0;
+      for (int i = 0; i < r; ++i) zmax = fmax(zmax, fabs(A::lead(z[i])));
+      const float sc = zmax > 0 ? float(1.0 / zmax) : 1.0f;
+      R nrm = A::zero();
       for (int i = 0; i < r; ++i) {
-        z[i] = df_mul_f(z[i], sc);
+        z[i] = A::mulf(z[i], sc);
         nrm = nrm + z[i] * z[i];
       }
-      const df inv = df_make(1.0f, 0.0f) / df_sqrt(nrm);
+      const R inv = A::mk(1.0f) / A::sqrt(nrm);
       for (int i = 0; i < r; ++i) z[i] = z[i] * inv;
     }
     __syncthreads();
@@ -1028,23 +1090,23 @@ __global__ void __launch_bounds__(kRRThreads) k_small_rr(const double2* __restri
     // warp 0, lanes over the components
     if (warp == 0) {
       for (int j = 1; j < p; ++j) {
-        df* zj = Z + j * q;
+        R* zj = Z + j * q;
         bool touched = false;
         for (int c = 0; c < j; ++c) {
-          if (df_to(lam[j] - lam[c]) > 1e-3 * (double)tnorm) continue;
-          const df* zc = Z + c * q;
-          df dot = df_zero();
+          if (A::to(lam[j] - lam[c]) > 1e-3 * (double)tnorm) continue;
+          const R* zc = Z + c * q;
+          R dot = A::zero();
           for (int i = lane; i < r; i += 32) dot = dot + zc[i] * zj[i];
-          dot = warp_sum_df(dot);
+          dot = warp_sum_r<R>(dot);
           for (int i = lane; i < r; i += 32) zj[i] = zj[i] - dot * zc[i];
           __syncwarp();
           touched = true;
         }
         if (touched) {
-          df nrm = df_zero();
+          R nrm = A::zero();
           for (int i = lane; i < r; i += 32) nrm = nrm + zj[i] * zj[i];
-          nrm = warp_sum_df(nrm);
-          const df inv = df_make(1.0f, 0.0f) / df_sqrt(nrm);
+          nrm = warp_sum_r<R>(nrm);
+          const R inv = A::mk(1.0f) / A::sqrt(nrm);
           for (int i = lane; i < r; i += 32) zj[i] = zj[i] * inv;
           __syncwarp();
         }
@@ -1055,27 +1117,27 @@ __global__ void __launch_bounds__(kRRThreads) k_small_rr(const double2* __restri
   t_phase[5] = clock64();
   // 5. back-transformation u_j = Q (phase * z_j), then C = D T u (one warp per vector)
   for (int j = warp; j < p; j += nw) {
-    cdf* u = U + (long)j * q;
-    for (int i = lane; i < r; i += 32) u[i] = cdf_scale(tphase[i], Z[j * q + i]);
+    C* u = U + (long)j * q;
+    for (int i = lane; i < r; i += 32) u[i] = A::scale(tphase[i], Z[j * q + i]);
     __syncwarp();
     for (int k = r - 3; k >= 0; --k) {
-      const df beta = tbeta[k];
-      if (beta.hi == 0.0f) continue;
+      const R beta = tbeta[k];
+      if (A::lead(beta) == 0.0f) continue;
       const int m = r - k - 1;
-      cdf acc = cdf_zero();
-      for (int i = lane; i < m; i += 32) acc = acc + cdf_mulc(H[(long)k * q + k + 1 + i], u[k + 1 + i]);
-      acc = warp_sum_cdf(acc);
-      const cdf f = cdf_scale(acc, beta);
+      C acc = A::czero();
+      for (int i = lane; i < m; i += 32) acc = acc + A::mulc(H[(long)k * q + k + 1 + i], u[k + 1 + i]);
+      acc = warp_sum_c<R>(acc);
+      const C f = A::scale(acc, beta);
       for (int i = lane; i < m; i += 32) u[k + 1 + i] = u[k + 1 + i] - H[(long)k * q + k + 1 + i] * f;
       __syncwarp();
     }
     for (int i = lane; i < q; i += 32) {
-      cdf acc = cdf_zero();
+      C acc = A::czero();
       for (int m = i; m < r; ++m) acc = acc + T[(long)m * q + i] * u[m];
-      Cout[(long)j * q + i] = s_keep[i] ? d[i] * cdf_to(acc) : make_double2(0, 0);
+      Cout[(long)j * q + i] = s_keep[i] ? d[i] * A::cto(acc) : make_double2(0, 0);
     }
   }
-  for (int j = tid; j < p; j += nt) theta_out[j] = df_to(lam[j]);
+  for (int j = tid; j < p; j += nt) theta_out[j] = A::to(lam[j]);
   __syncthreads();
   // a non-finite coefficient means a breakdown: report it instead of passing it on
   int bad = 0;
@@ -1249,8 +1311,11 @@ void lift_adj_mass(const Level& L, const double* d_ph, int cpg, const double2* X
   if (ncols <= 0) return;
   timer_begin(KC_LIFT_ADJ_MASK, s, (16.0 * L.D() + 2.0 * sizeof(T) * L.N()) * ncols);
   const dim3 g = grid2(L.n, L.m, ncols);
-  if (dfa) k_lift_adj_mass<df, T><<<g, dim3(kBX, kBY), 0, s>>>(L.lvl<df>(), d_ph, cpg, X, ldx, Rhs, ldr);
-  else k_lift_adj_mass<double, T><<<g, dim3(kBX, kBY), 0, s>>>(L.lvl<double>(), d_ph, cpg, X, ldx, Rhs, ldr);
+  if (dfa) {
+    k_lift_adj_mass<df, T><<<g, dim3(kBX, kBY), 0, s>>>(L.lvl<df>(), d_ph, cpg, X, ldx, Rhs, ldr);
+    count_df_launch();
+  } else
+    k_lift_adj_mass<double, T><<<g, dim3(kBX, kBY), 0, s>>>(L.lvl<double>(), d_ph, cpg, X, ldx, Rhs, ldr);
   timer_end(KC_LIFT_ADJ_MASK, s);
   PBS_LAUNCHED();
 }
@@ -1269,9 +1334,10 @@ void rayleigh_parts(const Level& L, const double* d_ph, int cpg, const double2* 
                     double* d_partials, double* d_out, bool dfa, cudaStream_t s) {
   if (ncols <= 0) return;
   const dim3 g = grid2(L.n, L.m, ncols);
-  if (dfa)
+  if (dfa) {
     k_rayleigh_parts<df><<<g, dim3(kBX, kBY), 0, s>>>(L.lvl<df>(), L.wts_df(), d_ph, cpg, X, ld, d_partials);
-  else
+    count_df_launch();
+  } else
     k_rayleigh_parts<double><<<g, dim3(kBX, kBY), 0, s>>>(L.lvl<double>(), L.wts<double>(), d_ph, cpg, X, ld,
                                                          d_partials);
   PBS_LAUNCHED();
@@ -1309,12 +1375,11 @@ int gram_partials(long rows, int ngroups) {
 
 template <int P, int TS> void launch_gram_df(const Level& L, const double* d_ph, Roles roles, int q, int ngroups,
                                              int npart, double2* d_partials, cudaStream_t s) {
-  static bool attr = false;
-  if (!attr) {
+  static PerDeviceOnce once;
+  once([] {
     PBS_CUDA(cudaFuncSetAttribute(k_gram_df<P, TS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   6 * (kMaxTrial + TS) * kGdRows * (int)sizeof(dcx)));
-    attr = true;
-  }
+  });
   const int qp = TS * ((q + TS - 1) / TS), T = qp / TS, ntile = T * (T + 1) / 2, per = 256 / P;
   const size_t smem = 6ull * qp * kGdRows * sizeof(dcx);
   k_gram_df<P, TS><<<dim3(npart, ngroups, (ntile + per - 1) / per), 256, smem, s>>>(
@@ -1340,13 +1405,13 @@ void gram_groups(const Level& L, const double* d_ph, Roles roles, int q, int ngr
   timer_begin(KC_GRAM, s, 8.0 * ne * 3.0 * L.N() * ngroups);  // flops: three complex MACs per entry and node
   if (dfa) {
     gram_df_dispatch<kGdTile>(L, d_ph, roles, q, ngroups, npart, d_partials, s);
+    count_df_launch();
   } else {
-    static bool attr = false;
-    if (!attr) {
+    static PerDeviceOnce once;
+    once([] {
       PBS_CUDA(cudaFuncSetAttribute(k_gram_fused, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     6 * kMaxTrial * kGramRows * (int)sizeof(double2)));
-      attr = true;
-    }
+    });
     const size_t smem = 6ull * q * kGramRows * sizeof(double2);
     k_gram_fused<<<dim3(npart, ngroups), 256, smem, s>>>(L.lvl<double>(), L.wts<double>(), d_ph, roles, q, d_partials,
                                                           npart);
@@ -1364,19 +1429,26 @@ long gram_partials_size(long rows, int q, int ngroups) {
 size_t small_rr_scratch(int q) { return (3ull * q * q + (size_t)q * kMaxBlock) * sizeof(double2) + 64; }
 
 void small_rr(const double2* GM, const double2* GA, int q, int p, double2* C, double* theta, double2* scratch,
-              int* d_info, int ngroups, cudaStream_t s) {
+              int* d_info, int ngroups, bool dfa, cudaStream_t s) {
   if (q > kMaxTrial || p > q || p < 1 || p > kMaxBlock || ngroups < 1) fail(PBS_EINVAL, "small_rr: bad sizes");
   const size_t dyn = (3ull * q * q + (size_t)q * p) * sizeof(double2);
   const int in_smem = dyn <= 150 * 1024 ? 1 : 0;
-  static bool attr = false;
-  if (!attr) {
-    PBS_CUDA(cudaFuncSetAttribute(k_small_rr, cudaFuncAttributeMaxDynamicSharedMemorySize, 150 * 1024));
-    attr = true;
-  }
+  static PerDeviceOnce once;
+  once([] {
+    PBS_CUDA(cudaFuncSetAttribute(k_small_rr<df>, cudaFuncAttributeMaxDynamicSharedMemorySize, 150 * 1024));
+    PBS_CUDA(cudaFuncSetAttribute(k_small_rr<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 150 * 1024));
+  });
   const long stride = (long)(small_rr_scratch(q) / sizeof(double2));
   timer_begin(KC_SMALL_RR, s, 8.0 * 3.0 * q * q * q * ngroups);  // flops, order of magnitude
-  k_small_rr<<<ngroups, kRRThreads, in_smem ? dyn : 0, s>>>(GM, GA, q, p, C, theta, scratch, d_info, in_smem,
-                                                            verbose_enabled() ? d_info + 2 : nullptr, stride);
+  int* phases = verbose_enabled() ? d_info + 2 : nullptr;
+  if (dfa) {
+    k_small_rr<df><<<ngroups, kRRThreads, in_smem ? dyn : 0, s>>>(GM, GA, q, p, C, theta, scratch, d_info, in_smem,
+                                                                  phases, stride);
+    count_df_launch();
+  } else {
+    k_small_rr<double><<<ngroups, kRRThreads, in_smem ? dyn : 0, s>>>(GM, GA, q, p, C, theta, scratch, d_info,
+                                                                      in_smem, phases, stride);
+  }
   timer_end(KC_SMALL_RR, s);
   PBS_LAUNCHED();
   if (verbose_enabled()) {
@@ -1390,12 +1462,11 @@ void small_rr(const double2* GM, const double2* GA, int q, int p, double2* C, do
 
 template <int PB> void launch_update_df(Roles X, int q, const double2* C, int ldc, long cgs, double2* Y, long ldy,
                                         int p, const double2* Z, long ldz, long rows, dim3 grid, cudaStream_t s) {
-  static bool attr = false;
-  if (!attr) {
+  static PerDeviceOnce once;
+  once([] {
     PBS_CUDA(cudaFuncSetAttribute(k_block_update_df<PB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   kMaxBlock * kMaxTrial * (int)sizeof(dcx)));
-    attr = true;
-  }
+  });
   k_block_update_df<PB><<<grid, 256, (size_t)p * q * sizeof(dcx), s>>>(X, q, C, ldc, cgs, Y, ldy, p, Z, ldz, rows);
 }
 
@@ -1411,13 +1482,13 @@ void block_update(Roles X, int q, const double2* C, int ldc, long cgs, double2* 
     if (p <= 8) launch_update_df<8>(X, q, C, ldc, cgs, Y, ldy, p, Z, ldz, rows, grid, s);
     else if (p <= 16) launch_update_df<16>(X, q, C, ldc, cgs, Y, ldy, p, Z, ldz, rows, grid, s);
     else launch_update_df<32>(X, q, C, ldc, cgs, Y, ldy, p, Z, ldz, rows, grid, s);
+    count_df_launch();
   } else {
-    static bool attr = false;
-    if (!attr) {
+    static PerDeviceOnce once;
+    once([] {
       PBS_CUDA(cudaFuncSetAttribute(k_block_update, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     kMaxBlock * kMaxTrial * (int)sizeof(double2)));
-      attr = true;
-    }
+    });
     const size_t smem = (size_t)p * q * sizeof(double2);
     k_block_update<<<grid, 256, smem, s>>>(X, q, C, ldc, cgs, Y, ldy, p, Z, ldz, rows);
   }
@@ -1454,35 +1525,51 @@ void scale_columns(double2* X, long ld, long rows, int ncols, const double* d_sc
 namespace {
 constexpr int kNoAllocQ = pbs::kMaxTrial, kNoAllocP = pbs::kMaxBlock;
 static __device__ __align__(256) double2 g_small_rr_scratch[3 * kNoAllocQ * kNoAllocQ + kNoAllocQ * kNoAllocP + 8];
-constexpr int kMaxDevices = 64;
 std::mutex g_scratch_mutex;
-void* g_scratch_addr[kMaxDevices] = {};
+void* g_scratch_addr[pbs::kMaxDevices] = {};
+
+int noalloc_fail(int status, const std::string& what) {
+  pbs::set_last_error(what);
+  return status;
+}
 }  // namespace
 
 extern "C" int pbs_small_rr_noalloc(const pbs_c64* GM, const pbs_c64* GA, int q, int p, pbs_c64* C, double* theta,
                                     int* info, void* cuda_stream) {
   using namespace pbs;
-  if (!GM || !GA || !C || !theta || !info) return PBS_EINVAL;
-  if (q < 1 || q > kNoAllocQ || p < 1 || p > q || p > kNoAllocP) return PBS_EINVAL;
+  set_last_error("");
+  if (!GM || !GA || !C || !theta || !info) return noalloc_fail(PBS_EINVAL, "a device pointer is NULL");
+  if (q < 1 || q > kNoAllocQ || p < 1 || p > q || p > kNoAllocP)
+    return noalloc_fail(PBS_EINVAL, "need 1 <= q <= 96 and 1 <= p <= min(q, 32)");
   int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return PBS_ECUDA;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return noalloc_fail(PBS_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+  if (dev < 0 || dev >= kMaxDevices) return noalloc_fail(PBS_ECUDA, "device index beyond the library's table");
+  // an error left by earlier work on this thread is reported as such and not cleared
+  e = cudaPeekAtLastError();
+  if (e != cudaSuccess)
+    return noalloc_fail(PBS_ECUDA, std::string("an earlier CUDA error is pending: ") + cudaGetErrorString(e));
   void* scratch = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_scratch_mutex);
     if (!g_scratch_addr[dev]) {
       // set-up on the first call on this device (with the device current)
-      if (cudaGetSymbolAddress(&g_scratch_addr[dev], g_small_rr_scratch) != cudaSuccess) {
+      e = cudaGetSymbolAddress(&g_scratch_addr[dev], g_small_rr_scratch);
+      if (e != cudaSuccess) {
         g_scratch_addr[dev] = nullptr;
-        return PBS_ECUDA;
+        return noalloc_fail(PBS_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
       }
     }
     scratch = g_scratch_addr[dev];
   }
-  k_small_rr<<<1, kRRThreads, 0, (cudaStream_t)cuda_stream>>>((const double2*)GM, (const double2*)GA, q, p,
+  k_small_rr<df><<<1, kRRThreads, 0, (cudaStream_t)cuda_stream>>>((const double2*)GM, (const double2*)GA, q, p,
                                                                 (double2*)C, theta, (double2*)scratch, info, 0,
                                                                 nullptr, 0);
   count_launch();
-  return cudaGetLastError() == cudaSuccess ? PBS_OK : PBS_ECUDA;
+  count_df_launch();
+  e = cudaGetLastError();  // nothing was pending before the launch: this is the launch's own status
+  if (e != cudaSuccess) return noalloc_fail(PBS_ECUDA, std::string("k_small_rr launch: ") + cudaGetErrorString(e));
+  return PBS_OK;
 }
 
 namespace pbs {

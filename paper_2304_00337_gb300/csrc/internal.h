@@ -4,7 +4,9 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <mutex>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "common.cuh"
@@ -25,6 +27,23 @@ struct Error {
 [[noreturn]] void fail(int status, const std::string& what);
 void check_cuda(cudaError_t e, const char* what);
 #define PBS_CUDA(call) ::pbs::check_cuda((call), #call)
+// Detail of a failure for pbs_last_error on the calling thread.
+void set_last_error(const std::string& what);
+
+// Runs a set-up step once per CUDA device and process, from any thread, with
+// that device current: kernel attributes such as the dynamic shared-memory limit
+// belong to a device, so each device a process drives gets its own call.  A step
+// that throws leaves the device's flag unset (the next launch tries again).
+constexpr int kMaxDevices = 64;
+struct PerDeviceOnce {
+  std::once_flag flag[kMaxDevices];
+  template <class F> void operator()(F&& f) {
+    int dev = 0;
+    check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
+    if (dev < 0 || dev >= kMaxDevices) fail(PBS_ECUDA, "device index beyond the library's table of devices");
+    std::call_once(flag[dev], std::forward<F>(f));
+  }
+};
 
 // One level of the bisection hierarchy (Section 5).  Geometry only: the
 // Bloch phases enter the kernels separately, so a level serves every k.
@@ -123,8 +142,10 @@ extern thread_local KernelTimer* g_timer;
 void timer_begin(int cls, cudaStream_t s, double work);
 void timer_end(int cls, cudaStream_t s);
 void timer_collect();  // after a stream synchronisation
-// every kernel launch of the library is counted (process-wide)
+// every kernel launch of the library is counted (process-wide); launches of kernels
+// that compute in double-float arithmetic are counted a second time on their own
 void count_launch();
+void count_df_launch();
 bool verbose_enabled();  // PBS_VERBOSE set in the environment (diagnostic traces)
 #define PBS_LAUNCHED()                 \
   do {                                 \
@@ -237,9 +258,10 @@ void gram_groups(const Level& L, const double* d_ph, Roles roles, int q, int ngr
                  double2* d_partials, long partial_capacity, bool dfa, cudaStream_t s);
 long gram_partials_size(long rows, int q, int ngroups);  // double2 elements
 // Rayleigh-Ritz in coefficient space for ngroups groups: C (q x p per group), theta (p per
-// group), status in d_info[8 g], scratch small_rr_scratch(q) bytes per group
+// group), status in d_info[8 g], scratch small_rr_scratch(q) bytes per group; dfa selects
+// double-float (mixed policy) instead of FP64 arithmetic
 void small_rr(const double2* GM, const double2* GA, int q, int p, double2* C, double* theta, double2* scratch,
-              int* d_info, int ngroups, cudaStream_t s);
+              int* d_info, int ngroups, bool dfa, cudaStream_t s);
 size_t small_rr_scratch(int q);
 // Y_g[:, j] = sum_i X_g[:, i] C_g[i, j] (+ Z_g[:, j]) for each group
 // (dfa: double-float, for the search direction only; the iterate's update is FP64)

@@ -843,11 +843,11 @@ template <class T> bool tail_from(const Hierarchy& H, int l, bool nodal) {
          tail_smem_elems(H, l, nodal) * (long)sizeof(cx<T>) <= kTailSmemBytes;
 }
 template <class T> void set_tail_smem() {
-  static bool done = false;
-  if (done) return;
-  PBS_CUDA(cudaFuncSetAttribute(k_node_tail<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTailSmemBytes));
-  PBS_CUDA(cudaFuncSetAttribute(k_edge_tail<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTailSmemBytes));
-  done = true;
+  static PerDeviceOnce once;
+  once([] {
+    PBS_CUDA(cudaFuncSetAttribute(k_node_tail<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTailSmemBytes));
+    PBS_CUDA(cudaFuncSetAttribute(k_edge_tail<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTailSmemBytes));
+  });
 }
 
 // Algorithmic bytes of a fused tail: the top right-hand sides in and solutions
@@ -880,13 +880,13 @@ template <class T> size_t fine_up_smem(int nu) {
   return (2 * W * W + Wc * Wc) * sizeof(cx<T>);
 }
 template <class T> void set_fine_smem() {
-  static bool done = false;
-  if (done) return;
-  PBS_CUDA(cudaFuncSetAttribute(k_node_down<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)fine_down_smem<T>(kFineMaxNu)));
-  PBS_CUDA(cudaFuncSetAttribute(k_node_up<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)fine_up_smem<T>(kFineMaxNu)));
-  done = true;
+  static PerDeviceOnce once;
+  once([] {
+    PBS_CUDA(cudaFuncSetAttribute(k_node_down<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)fine_down_smem<T>(kFineMaxNu)));
+    PBS_CUDA(cudaFuncSetAttribute(k_node_up<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)fine_up_smem<T>(kFineMaxNu)));
+  });
 }
 // algorithmic bytes of a tiled step: each level vector read or written once
 // (down: b in, x and the coarse right-hand side out; up: b, x, the coarse

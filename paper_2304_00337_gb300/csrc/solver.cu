@@ -36,9 +36,10 @@ namespace pbs {
 
 static thread_local std::string g_last_error;
 thread_local KernelTimer* g_timer = nullptr;
-static std::atomic<unsigned long long> g_launches{0};
+static std::atomic<unsigned long long> g_launches{0}, g_df_launches{0};
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void count_df_launch() { g_df_launches.fetch_add(1, std::memory_order_relaxed); }
 
 bool verbose_enabled() {
   static const bool v = std::getenv("PBS_VERBOSE") != nullptr;
@@ -85,6 +86,8 @@ void timer_collect() {
 }
 
 void fail(int status, const std::string& what) { throw Error{status, what}; }
+
+void set_last_error(const std::string& what) { g_last_error = what; }
 
 void check_cuda(cudaError_t e, const char* what) {
   if (e != cudaSuccess) {
@@ -552,7 +555,7 @@ double rr_single(pbs_ctx* ctx, const KData& Kv, const double2* S, int q, int p, 
   const Level& L0 = ctx->H.lev[0];
   const Roles R{{S, S, S}, q, W.D};
   gram_groups(L0, Kv.d_ph, R, q, 1, W.GM, W.GA, W.gpart, W.gpart_cap, dfa, s);
-  small_rr(W.GM, W.GA, q, p, W.C, W.theta, W.rr_scr, W.info, 1, s);
+  small_rr(W.GM, W.GA, q, p, W.C, W.theta, W.rr_scr, W.info, 1, dfa, s);
   int info[2] = {0, 0};
   std::vector<double> th(p);
   PBS_CUDA(cudaMemcpyAsync(info, W.info, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -666,22 +669,31 @@ struct Chain {
   std::vector<int> save;
 };
 
+// Eigenvectors of selected Bloch vectors copied out as they converge: slot[k] >= 0
+// sends the nev wanted columns of Bloch vector k, M-normalised, to host + slot[k] nev D.
+struct VecOut {
+  std::vector<int> slot;
+  pbs_c64* host = nullptr;
+};
+
 // Solve every chain of the list with G groups in lock-step; a group whose chain is
 // done takes the next chain of the list.
 PathResult solve_chain_list(pbs_ctx* ctx, const pbs_opts& o, int nk, const double* ks, const std::vector<Chain>& chains,
-                            int Gwant, const pbs_c64* init, const double2* dev_init, double2* store);
+                            int Gwant, const pbs_c64* init, const double2* dev_init, double2* store,
+                            const VecOut* vout = nullptr);
 
 PathResult solve_chains(pbs_ctx* ctx, const pbs_opts& o, int nk, const double* ks, int nchains, const pbs_c64* init,
-                        const double2* dev_init = nullptr) {
+                        const double2* dev_init = nullptr, const VecOut* vout = nullptr) {
   const int G = std::max(1, std::min(nchains, nk));
   std::vector<Chain> chains(G);
   for (int g = 0; g < G; ++g)
     for (int i = (int)((long)nk * g / G); i <= (int)((long)nk * (g + 1) / G) - 1; ++i) chains[g].idx.push_back(i);
-  return solve_chain_list(ctx, o, nk, ks, chains, G, init, dev_init, nullptr);
+  return solve_chain_list(ctx, o, nk, ks, chains, G, init, dev_init, nullptr, vout);
 }
 
 PathResult solve_chain_list(pbs_ctx* ctx, const pbs_opts& o, int nk, const double* ks, const std::vector<Chain>& chains,
-                            int Gwant, const pbs_c64* init, const double2* dev_init, double2* store) {
+                            int Gwant, const pbs_c64* init, const double2* dev_init, double2* store,
+                            const VecOut* vout) {
   cudaStream_t s = ctx->stream;
   const bool dfa = o.precision == PBS_MIXED;
   const int p = o.block, G = std::max(1, std::min<int>(Gwant, (int)chains.size()));
@@ -797,6 +809,22 @@ PathResult solve_chain_list(pbs_ctx* ctx, const pbs_opts& o, int nk, const doubl
           out.lam[(long)x.pos * o.nev + j] = lam_out[j];
           out.res[(long)x.pos * o.nev + j] = res[j];
         }
+        if (vout && vout->slot[x.pos] >= 0) {
+          // M-normalised copy of the wanted columns (the iterate itself stays as it is)
+          const KData Kv = kdata_view(ctx->K, g);
+          double2* V = W.init;
+          PBS_CUDA(cudaMemcpyAsync(V, W.E() + (long)g * p * D, sizeof(double2) * D * o.nev, cudaMemcpyDeviceToDevice, s));
+          rayleigh_parts(L0, Kv.d_ph, o.nev, V, D, o.nev, W.parts, W.rq, false, s);
+          std::vector<double> rq(2 * o.nev), sc(o.nev);
+          PBS_CUDA(cudaMemcpyAsync(rq.data(), W.rq, rq.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+          PBS_CUDA(cudaStreamSynchronize(s));
+          for (int j = 0; j < o.nev; ++j) sc[j] = 1.0 / std::sqrt(rq[2 * j]);
+          PBS_CUDA(cudaMemcpyAsync(W.norms, sc.data(), o.nev * sizeof(double), cudaMemcpyHostToDevice, s));
+          scale_columns(V, D, D, o.nev, W.norms, s);
+          PBS_CUDA(cudaMemcpyAsync(vout->host + (long)vout->slot[x.pos] * o.nev * D, V, sizeof(double2) * D * o.nev,
+                                   cudaMemcpyDeviceToHost, s));
+          PBS_CUDA(cudaStreamSynchronize(s));
+        }
         out.iters[x.pos] = x.it;
         if (!conv) out.all_converged = false;
         const Chain& ch = chains[x.chain];
@@ -849,7 +877,7 @@ PathResult solve_chain_list(pbs_ctx* ctx, const pbs_opts& o, int nk, const doubl
       const Roles trial = o.span == 1 ? Roles{{Wd, Wd, Wd}, p, D} : Roles{{W.E(), W.P(), W.W()}, p, D};
       const int qt = o.span == 1 ? p : q;
       gram_groups(L0, ctx->K.d_ph, trial, qt, G, W.GM, W.GA, W.gpart, W.gpart_cap, dfa, s);
-      small_rr(W.GM, W.GA, qt, p, W.C, W.theta, W.rr_scr, W.info, G, s);
+      small_rr(W.GM, W.GA, qt, p, W.C, W.theta, W.rr_scr, W.info, G, dfa, s);
       PBS_CUDA(cudaMemcpyAsync(h_info.data(), W.info, sizeof(int) * 8 * G, cudaMemcpyDeviceToHost, s));
       PBS_CUDA(cudaStreamSynchronize(s));
       for (int g = 0; g < G; ++g) {
@@ -864,7 +892,7 @@ PathResult solve_chain_list(pbs_ctx* ctx, const pbs_opts& o, int nk, const doubl
         double2* GMg = W.GM + (long)g * q * q;
         double2* GAg = W.GA + (long)g * q * q;
         gram_groups(L0, Kv.d_ph, tg, q, 1, GMg, GAg, W.gpart, W.gpart_cap, dfa, s);
-        small_rr(GMg, GAg, q, p, W.C + (long)g * q * p, W.theta + (long)g * q, W.rr_scr, W.info + 8 * g, 1, s);
+        small_rr(GMg, GAg, q, p, W.C + (long)g * q * p, W.theta + (long)g * q, W.rr_scr, W.info + 8 * g, 1, dfa, s);
         int inf2[2];
         PBS_CUDA(cudaMemcpyAsync(inf2, W.info + 8 * g, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
         PBS_CUDA(cudaStreamSynchronize(s));
@@ -1091,21 +1119,13 @@ int pbs_num_levels(int n, int m, int coarsest) {
   return num_levels(n, m, coarsest);
 }
 
-// The device this process drives (-1: none yet).  Kernel attributes such as the
-// dynamic shared-memory limits are raised once per process, on this device.
-static std::atomic<int> g_process_device{-1};
-
 int pbs_create(pbs_ctx** ctx, int device, size_t hbm_budget_bytes) {
   if (!ctx) return PBS_EINVAL;
   *ctx = nullptr;
   return run_guarded_impl([&] {
     int count = 0;
     PBS_CUDA(cudaGetDeviceCount(&count));
-    if (device < 0 || device >= count) fail(PBS_EINVAL, "no such CUDA device");
-    int bound = -1;
-    if (!g_process_device.compare_exchange_strong(bound, device) && bound != device)
-      fail(PBS_EINVAL, "this process already drives CUDA device " + std::to_string(bound) +
-                           "; use one process per device");
+    if (device < 0 || device >= count || device >= kMaxDevices) fail(PBS_EINVAL, "no such CUDA device");
     DeviceGuard g(device);
     std::unique_ptr<pbs_ctx> c(new pbs_ctx(hbm_budget_bytes));
     c->device = device;
@@ -1196,6 +1216,36 @@ int pbs_solve_path(pbs_ctx* ctx, const pbs_geom* geom, const pbs_opts* opts, int
   return rc != PBS_OK ? rc : status;
 }
 
+int pbs_solve_path_vectors(pbs_ctx* ctx, const pbs_geom* geom, const pbs_opts* opts, int nk, const double* ks,
+                           double* eigvals, double* resid, int* iters, int nsel, const int* sel, pbs_c64* evecs) {
+  if (!ctx || !geom || !opts || nk < 0 || nsel < 0 || (nk > 0 && (!ks || !eigvals || !resid || !iters)) ||
+      (nsel > 0 && (!sel || !evecs)))
+    return PBS_EINVAL;
+  int status = PBS_OK;
+  const int rc = run_guarded_impl([&] {
+    std::lock_guard<std::mutex> ctx_lock(ctx->gpu_mu);
+    DeviceGuard g(ctx->device);
+    TimerScope ts(ctx);
+    validate_opts(*opts);
+    VecOut vo;
+    vo.slot.assign(nk, -1);
+    vo.host = evecs;
+    for (int t = 0; t < nsel; ++t) {
+      if (sel[t] < 0 || sel[t] >= nk) fail(PBS_EINVAL, "selected Bloch vector out of range");
+      if (vo.slot[sel[t]] >= 0) fail(PBS_EINVAL, "a Bloch vector is selected twice");
+      vo.slot[sel[t]] = t;
+    }
+    if (nk == 0) return;
+    ensure_hierarchy_host(ctx, geom, effective_mu(*opts, geom->a, geom->b), opts->coarsest);
+    const PathResult r = solve_chains(ctx, *opts, nk, ks, opts->kbatch, nullptr, nullptr, nsel > 0 ? &vo : nullptr);
+    std::copy(r.lam.begin(), r.lam.end(), eigvals);
+    std::copy(r.res.begin(), r.res.end(), resid);
+    std::copy(r.iters.begin(), r.iters.end(), iters);
+    if (!r.all_converged) status = PBS_ENOCONV;
+  });
+  return rc != PBS_OK ? rc : status;
+}
+
 int pbs_solve_path_device(pbs_ctx* ctx, double a, double b, int n, int m, const double* d_eps, const pbs_opts* opts,
                           int nk, const double* d_ks, double* d_eigvals, double* d_resid, int* d_iters,
                           void* cuda_stream) {
@@ -1248,7 +1298,7 @@ int pbs_apply(pbs_ctx* ctx, const pbs_geom* geom, const pbs_opts* opts, int op, 
     const bool transfer = op == PBS_OP_PROLONG || op == PBS_OP_RESTRICT || op == PBS_OP_PROLONG_NODAL ||
                           op == PBS_OP_RESTRICT_NODAL;
     if (transfer && level + 1 >= H.nlev) fail(PBS_EINVAL, "no coarser level below `level`");
-    if (op < PBS_OP_A || op > PBS_OP_PROJECT) fail(PBS_EINVAL, "unknown operator");
+    if (op < PBS_OP_A || op > PBS_OP_LH_M) fail(PBS_EINVAL, "unknown operator");
     if (op == PBS_OP_PROJECT && level != 0) fail(PBS_EINVAL, "PROJECT acts on level 0");
     if (ncols == 0) return;
     set_single_k(ctx, k[0], k[1]);
@@ -1274,6 +1324,26 @@ int pbs_apply(pbs_ctx* ctx, const pbs_geom* geom, const pbs_opts* opts, int op, 
       case PBS_OP_L: apply_lift<double>(L, K.d_ph, cpg, X, N, Y, D, ncols, s); break;
       case PBS_OP_LH: apply_lift_adj<double>(L, K.d_ph, cpg, X, D, Y, N, ncols, s); break;
       case PBS_OP_P_NODAL: apply_nodal<double>(L, K.d_ph, cpg, X, Y, nullptr, N, ncols, 1.0, 0.0, s); break;
+      case PBS_OP_LH_M:
+        lift_adj_mass<double>(L, K.d_ph, cpg, X, D, Y, N, ncols, o.precision == PBS_MIXED, s);
+        break;
+      case PBS_OP_RESIDUAL: {
+        // the iteration's residual kernel with Lambda = mu on every column; its
+        // per-column norms go to scratch that lives for this call only
+        const long nblk = ((L.n + 31) / 32) * ((L.m + 7) / 8);
+        double* tmp = (double*)ctx->mem.alloc(sizeof(double) * (ncols + 2L * nblk * ncols + 2L * ncols));
+        try {
+          std::vector<double> lam(ncols, mu);
+          PBS_CUDA(cudaMemcpyAsync(tmp, lam.data(), sizeof(double) * ncols, cudaMemcpyHostToDevice, s));
+          residual(L, K.d_ph, cpg, X, Y, D, ncols, tmp, tmp + ncols, tmp + ncols + 2L * nblk * ncols, s);
+          PBS_CUDA(cudaStreamSynchronize(s));
+        } catch (...) {
+          ctx->mem.free(tmp);
+          throw;
+        }
+        ctx->mem.free(tmp);
+        break;
+      }
       case PBS_OP_PROLONG: {
         const Level& C = H.lev[level + 1];
         prolong_edge<double>(L, C, K.d_ph, cpg, X, C.D(), Y, D, ncols, false, s);
@@ -1523,6 +1593,8 @@ int pbs_profile_read(pbs_ctx* ctx, const char* kernel_class, double* total_ms, l
 }
 
 unsigned long long pbs_launch_count(void) { return g_launches.load(); }
+
+unsigned long long pbs_launch_count_df(void) { return g_df_launches.load(); }
 
 int pbs_solve_grid(pbs_ctx* ctx, const pbs_geom* geom, const pbs_opts* opts, int kappa, double* ks_out,
                    double* eigvals, double* resid, int* iters) {
