@@ -212,3 +212,19 @@ def test_brillouin_zone_grid_schedule(ctx, precision, kappa):
     mirror = (kappa - 1 - j) * kappa + (kappa - 1 - i)
     assert np.allclose(lam, lam[mirror.ravel()], rtol=1e-9)
     assert np.mean(iters[1:]) < iters[0]
+
+
+def test_fp64_policy_has_no_double_float_kernel(ctx):
+    # PBS_FP64 is the all-FP64 path: the full 64 x 64 rod path (31 Bloch vectors, 8 bands,
+    # block 10) matches the oracle while no double-float kernel is launched
+    vals = np.loadtxt(os.path.join(GOLDEN, "rod64_path31.txt"))
+    ks, want = vals[:, :2], vals[:, 2:]
+    geom = pbs.Geometry(gi.rod_eps(64, 64))
+    df0, all0 = pbs.launch_count_df(), pbs.launch_count()
+    lam, res, _ = ctx.solve_path(geom, dict(nev=8, block=10, precision=pbs.PBS_FP64, kbatch=4), ks)
+    assert pbs.launch_count() > all0 and pbs.launch_count_df() == df0
+    assert np.max(np.abs(lam - want) / want) <= 1e-10
+    assert np.all(res <= 1e-8)
+    # the mixed policy does run double-float kernels (the counter is live)
+    ctx.solve_path(geom, dict(nev=8, block=10, precision=pbs.PBS_MIXED, kbatch=4), ks[:4])
+    assert pbs.launch_count_df() > df0
