@@ -1,21 +1,27 @@
 """Throughput of Bloch-path eigensolves on one GB300 (k-point eigensolves per second).
 
-Workload (one "step"): the square-lattice rod crystal (eps = 8.9 rod of radius
-0.2a in air, cell-centre samples), 256 x 256 mesh (131,072 complex edge
-unknowns), 31 Bloch vectors along Gamma-X-M-Gamma, the 8 smallest non-zero
-eigenvalues with a block of 10 vectors, every wanted band converged to a
-relative residual <= 1e-8, each k after the first started from the
-Rayleigh-quotient extrapolation of up to three previous bases.
+Workload (one "step", default ``--workload c3``): the square-lattice rod crystal
+(eps = 8.9 rod of radius 0.2a in air, cell-centre samples) on a 1024 x 1024 mesh
+(2,097,152 complex edge unknowns), 64 Bloch vectors along Gamma-X-M-Gamma all in
+flight at once (one block of 10 vectors each, every kernel launch covering all 64),
+the 8 smallest non-zero eigenvalues of each converged to a relative residual
+<= 1e-8 (or the FP64 rounding floor 0.5 u lambda_max / lambda where that is higher:
+band 1 next to Gamma).  ``--workload c2`` is the 256 x 256 path of 31 Bloch vectors
+(four chains with Rayleigh-quotient extrapolation), ``c4`` the 4096 x 4096 field of
+16 seeded disks (12 bands, block 16, 16 Bloch vectors).
 
-``value``: mixed precision (FP32 multigrid and nodal projection, FP64
-residual / Gram / Rayleigh-Ritz), inputs and outputs resident on the device
-(``pbs_solve_path_device``); ``plain_fp64`` is the same workload with every
-kernel in FP64.  ``e2e``: the host-buffer entry point ``pbs_solve_path`` with
-the permittivity copied from pinned host memory and the results copied back in
-every step.  L2 is flushed (a 512 MiB write) before every timed step.
+``value``: mixed precision (FP32 multigrid and nodal projection; double-float Gram,
+Rayleigh quotients and small Rayleigh-Ritz; FP64 residual, update and reported
+eigenvalues), inputs and outputs resident on the device (``pbs_solve_path_device``);
+``plain_fp64`` is the same workload with every kernel in FP64, and the per-band
+difference of the two policies' eigenvalues is reported.  ``e2e``: the host-buffer
+entry point ``pbs_solve_path`` with the permittivity copied from pinned host memory
+and the results copied back in every step.  L2 is flushed (a 512 MiB write) before
+every timed step (the c3 step's blocks, 86 GB, exceed it anyway).  The c3 line also
+carries the c2 workload (value, plain FP64 and the error of both policies against the
+oracle's stored eigenvalues).
 
-``--impl reference`` times the CPU oracle (SciPy) on a bounded sample of the
-same workload instead.
+``--impl reference`` times the CPU oracle (SciPy) on a bounded sample instead.
 """
 from __future__ import annotations
 
@@ -34,23 +40,38 @@ sys.path.insert(0, ROOT)
 
 import numpy as np  # noqa: E402
 
-N_SIDE = 256
-NK = 31
-NEV = 8
-BLOCK = 10
 TOL = 1e-8
-KBATCH = 4  # Bloch vectors in flight: four chains of the path solved in lock-step
 METRIC = "k-point eigensolves/s at resid<=1e-8 (mixed; plain FP64 alongside)"
 UNIT = "k-points/s"
-WORKLOAD = ("rod crystal eps=8.9 r=0.2a, 256x256 Nedelec edges (131072 DOF), 31 k-points Gamma-X-M-Gamma, "
-            "8 bands, block 10, tol 1e-8, extrapolation depth 3")
+# path workloads: mesh, Bloch vectors, bands, block, Bloch vectors in flight, permittivity
+WORKLOADS = {
+    "c2": dict(n=256, nk=31, nev=8, block=10, kbatch=4, eps="rod",
+               text="rod crystal eps=8.9 r=0.2a, 256x256 Nedelec edges (131072 DOF), 31 k-points Gamma-X-M-Gamma, "
+                    "8 bands, block 10, tol 1e-8, 4 chains with extrapolation depth 3"),
+    "c3": dict(n=1024, nk=64, nev=8, block=10, kbatch=64, eps="rod",
+               text="rod crystal eps=8.9 r=0.2a, 1024x1024 Nedelec edges (2097152 DOF), 64 k-points Gamma-X-M-Gamma "
+                    "all in flight, 8 bands, block 10, tol 1e-8"),
+    "c4": dict(n=4096, nk=16, nev=12, block=16, kbatch=2, eps="disks",
+               text="16 seeded disks (r U(0.05,0.15)a, eps U(2,13), background 1), 4096x4096 Nedelec edges "
+                    "(33554432 DOF), 16 k-points Gamma-X-M-Gamma, 12 bands, block 16, tol 1e-8, 2 chains"),
+}
+GOLDEN_C2 = os.path.join(ROOT, "tests", "golden", "rod256_path31.txt")
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 SAMPLE_EVERY = 16  # the dominant kernel is timed on every 16th launch inside the timed region
-GRAM_DRAM_BYTES = 256.6e6  # measured per batched k_gram_df launch (253.3 MB read + 3.3 MB written)
+GRAM_DRAM_BYTES = 256.6e6  # measured per batched k_gram_df launch at 256x256 (4 groups of 30 columns)
 FP64_PEAK_TFLOPS = 1.2  # 152 SMs x 4 FP64 flop/clk x ~1.98 GHz; measured 1.20 TFLOP/s with an FMA-chain probe
 # Double-float kernels (mixed policy) run on the FP32 pipe: 152 SMs x 128 lanes x 1.98 GHz
 # instructions/s, and a compensated complex multiply-add (8 algorithmic flops) takes 48 of them.
 DF_PEAK_TFLOPS = 152 * 128 * 1.98e9 * 8 / 48 / 1e12
+
+
+def workload_inputs(name: str):
+    """Permittivity samples and Bloch vectors of a path workload (seeded, synthetic)."""
+    import pbs_inputs as gi
+    w = WORKLOADS[name]
+    n = w["n"]
+    eps = gi.rod_eps(n, n) if w["eps"] == "rod" else gi.disks_eps(n, n, seed=0)
+    return eps, gi.gxmg_path(w["nk"])
 
 
 def _dist():
@@ -146,50 +167,131 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def oracle_sample_kps(seconds_budget: float = 30.0):
-    """CPU oracle (SciPy shift-invert on the assembled pencil) on a bounded sample of the workload."""
+def _oracle_kpoint_seconds(n: int, eps_kind: str, k) -> float:
+    """Wall time of the oracle's solve of one Bloch vector (assembly + constrained sparse
+    shift-invert eigensolve) on an n x n mesh of the workload's crystal."""
     import pbs_inputs as gi
     from oracle import fem, eigen
-    eps = gi.rod_eps(N_SIDE, N_SIDE)
-    ks = gi.gxmg_path(NK)
+    eps = gi.rod_eps(n, n) if eps_kind == "rod" else gi.disks_eps(n, n, seed=0)
+    t0 = time.perf_counter()
+    ops = fem.assemble(fem.Mesh(1.0, 1.0, n, n), eps, k)
+    eigen.eigs_sparse(ops, 8)
+    return time.perf_counter() - t0
+
+
+def oracle_sample_kps(name: str, seconds_budget: float = 20.0):
+    """CPU oracle (SciPy shift-invert on the assembled pencil) on a bounded sample of the workload.
+
+    Up to 256 x 256 the sample solves Bloch vectors of the workload's path on its own mesh
+    until the budget is spent.  On larger meshes one Bloch vector takes far longer than the
+    budget (512 x 512 ran for more than an hour on 8 host cores), so the sample solves the
+    path's second Bloch vector on the same crystal at 64 x 64 and 128 x 128 and
+    extrapolates to the workload's mesh with the growth t ~ D^alpha measured between the
+    two; the direct solve's fill grows faster than that, so the extrapolated CPU time is a
+    lower bound and the CPU rate an upper bound."""
+    w = WORKLOADS[name]
+    eps_kind = w["eps"]
     r0 = resource.getrusage(resource.RUSAGE_SELF)
     t0 = time.perf_counter()
-    done = 0
-    for k in ks[1:]:
-        ops = fem.assemble(fem.Mesh(1.0, 1.0, N_SIDE, N_SIDE), eps, k)
-        eigen.eigs_sparse(ops, NEV)
-        done += 1
-        if time.perf_counter() - t0 > seconds_budget:
-            break
-    wall = time.perf_counter() - t0
+    if w["n"] <= 256:
+        import pbs_inputs as gi
+        ks = gi.gxmg_path(w["nk"])
+        done = 0
+        for k in ks[1:]:
+            _oracle_kpoint_seconds(w["n"], eps_kind, k)
+            done += 1
+            if time.perf_counter() - t0 > seconds_budget:
+                break
+        wall = time.perf_counter() - t0
+        value = done / wall
+        sample = f"{done} of the {w['nk']} k-points on the workload's mesh"
+    else:
+        import pbs_inputs as gi
+        k = gi.gxmg_path(w["nk"])[1]
+        t_a = _oracle_kpoint_seconds(64, eps_kind, k)
+        t_b = _oracle_kpoint_seconds(128, eps_kind, k)
+        alpha = max(1.0, np.log(t_b / t_a) / np.log(4.0))
+        t_n = t_b * (w["n"] / 128.0) ** (2 * alpha)
+        wall = time.perf_counter() - t0
+        value = 1.0 / t_n
+        sample = (f"one Bloch vector on the same crystal at 64x64 ({t_a:.2f} s) and 128x128 ({t_b:.2f} s), "
+                  f"extrapolated to {w['n']}x{w['n']} with t ~ D^{alpha:.2f} ({t_n:.0f} s per k-point; "
+                  "a lower bound: the direct solve's fill grows faster)")
     r1 = resource.getrusage(resource.RUSAGE_SELF)
     cpu = (r1.ru_utime - r0.ru_utime) + (r1.ru_stime - r0.ru_stime)
-    return {"value": done / wall, "unit": UNIT, "cores": max(1, round(cpu / wall)), "kind": "oracle",
-            "sample": f"{done} of the {NK} k-points (assemble + sparse shift-invert eigensolve each), "
-                      f"{wall:.1f} s wall, {cpu:.1f} s CPU on {os.cpu_count()} host cores"}
+    return {"value": value, "unit": UNIT, "cores": max(1, round(cpu / wall)), "kind": "oracle",
+            "sample": f"{sample}; {wall:.1f} s wall, {cpu:.1f} s CPU on {os.cpu_count()} host cores"}
 
 
 def run_reference(args):
     rank, ws = _dist()
     if rank != 0:
         return
+    name = args.workload
+    w = WORKLOADS[name]
     per_step = []
     samples = []
     for s in range(args.warmup + args.steps):
-        cb = oracle_sample_kps(seconds_budget=20.0)
+        cb = oracle_sample_kps(name, seconds_budget=5.0)
         if s >= args.warmup:
             per_step.append(cb["value"])
             samples.append(cb)
     value = float(np.mean(per_step))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * NK / value, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "grid": "256x256", "k_points": NK, "bands": NEV, "block": BLOCK,
-                       "tol": TOL, "sample": "each step solves k-points of the path until 20 s of CPU time"},
+            "warmup": args.warmup, "ms_per_step": 1e3 * w["nk"] / value, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w["text"], "grid": f"{w['n']}x{w['n']}", "k_points": w["nk"], "bands": w["nev"],
+                       "block": w["block"], "tol": TOL,
+                       "sample": "each step a bounded oracle sample of the workload (see cpu_baseline.sample)"},
             "cpu_baseline": {"kind": "oracle", "cores": samples[-1]["cores"], "sample": samples[-1]["sample"],
                              "value": value, "unit": UNIT},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def _opts(pbs, name, prec):
+    w = WORKLOADS[name]
+    return pbs.default_opts(nev=w["nev"], block=w["block"], tol=TOL, precision=prec, max_iter=400,
+                            kbatch=w["kbatch"])
+
+
+def _band_tol(eps, n, lam):
+    lam_max = float(np.max(1.0 / eps)) * 12.0 * 2.0 * n * n
+    return np.maximum(TOL, 0.5 * 2.0 ** -53 * lam_max / lam)
+
+
+def c2_leg(pbs, dev, stream):
+    """The 256 x 256 path (31 Bloch vectors, four chains): mixed and plain FP64 k-points/s
+    (one warm and one timed step each) and both policies' per-band error against the
+    oracle's stored eigenvalues."""
+    import torch
+    eps, ks = workload_inputs("c2")
+    want = np.loadtxt(GOLDEN_C2)[:, 2:]
+    d_eps = torch.from_numpy(eps.copy()).to(dev)
+    d_ks = torch.from_numpy(ks.copy()).to(dev)
+    nk, nev = len(ks), WORKLOADS["c2"]["nev"]
+    d_ev = torch.zeros((nk, nev), dtype=torch.float64, device=dev)
+    d_rs = torch.zeros_like(d_ev)
+    d_it = torch.zeros(nk, dtype=torch.int32, device=dev)
+    out = {"workload": WORKLOADS["c2"]["text"]}
+    with pbs.Context(dev.index or 0) as ctx:
+        for label, prec in (("mixed", pbs.PBS_MIXED), ("plain_fp64", pbs.PBS_FP64)):
+            def step():
+                ctx.solve_path_device(1.0, 1.0, 256, 256, d_eps.data_ptr(), _opts(pbs, "c2", prec), nk,
+                                      d_ks.data_ptr(), d_ev.data_ptr(), d_rs.data_ptr(), d_it.data_ptr(), stream)
+            step()
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            lam = d_ev.cpu().numpy()
+            rel = np.abs(lam - want) / want
+            out[label] = {"value": nk / (e0.elapsed_time(e1) / 1e3), "unit": UNIT,
+                          "max_rel_err_vs_oracle_per_band": rel.max(axis=0).tolist(),
+                          "max_resid": float(d_rs.max().item())}
+    return out
 
 
 def run_ours(args):
@@ -197,8 +299,10 @@ def run_ours(args):
     import __graft_entry__ as ge
     ge.build()
     import paper_2304_00337_gb300 as pbs
-    import pbs_inputs as gi
 
+    name = args.workload
+    w = WORKLOADS[name]
+    n, nk, nev = w["n"], w["nk"], w["nev"]
     rank, ws = _dist()
     if ws > 1:
         import torch.distributed as dist
@@ -210,23 +314,19 @@ def run_ours(args):
     ranks = Ranks(ws, dev)
     barrier, max_over_ranks = ranks.barrier, ranks.max
 
-    eps = gi.rod_eps(N_SIDE, N_SIDE)
-    ks = gi.gxmg_path(NK)
+    eps, ks = workload_inputs(name)
     d_eps = torch.from_numpy(eps.copy()).to(dev)
     d_ks = torch.from_numpy(ks.copy()).to(dev)
-    d_ev = torch.zeros((NK, NEV), dtype=torch.float64, device=dev)
+    d_ev = torch.zeros((nk, nev), dtype=torch.float64, device=dev)
     d_rs = torch.zeros_like(d_ev)
-    d_it = torch.zeros(NK, dtype=torch.int32, device=dev)
+    d_it = torch.zeros(nk, dtype=torch.int32, device=dev)
     flush = torch.empty(512 * 2 ** 20 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
-
-    def opts(prec):
-        return pbs.default_opts(nev=NEV, block=BLOCK, tol=TOL, precision=prec, max_iter=400, kbatch=KBATCH)
 
     ctx = pbs.Context(local)
 
     def step(prec):
-        ctx.solve_path_device(1.0, 1.0, N_SIDE, N_SIDE, d_eps.data_ptr(), opts(prec), NK, d_ks.data_ptr(),
+        ctx.solve_path_device(1.0, 1.0, n, n, d_eps.data_ptr(), _opts(pbs, name, prec), nk, d_ks.data_ptr(),
                               d_ev.data_ptr(), d_rs.data_ptr(), d_it.data_ptr(), stream)
 
     def timed(prec, steps, profile=None):
@@ -268,33 +368,36 @@ def run_ours(args):
     clk = clocks.stop()
     dom_ms, dom_n, dom_work = ctx.profile_read(dominant)
     ctx.profile_enable(None)
-    ev = d_ev.cpu().numpy()
+    lam_mixed = d_ev.cpu().numpy()
     rs = d_rs.cpu().numpy()
     its = d_it.cpu().numpy()
-    ok = bool(np.all(rs <= TOL))
-
-    # plain FP64 on the same workload
-    step(pbs.PBS_FP64)
-    t_fp64, _ = timed(pbs.PBS_FP64, max(1, min(args.steps, 2)))
+    ok = bool(np.all(rs <= _band_tol(eps, n, lam_mixed)))
 
     # end to end through the host-buffer entry point (pinned host eps, results copied back)
-    h_eps = torch.empty((N_SIDE, N_SIDE), dtype=torch.float64, pin_memory=True)
+    h_eps = torch.empty((n, n), dtype=torch.float64, pin_memory=True)
     h_eps.copy_(torch.from_numpy(eps))
     geom = pbs.Geometry(h_eps.numpy())
-    ctx.solve_path(geom, opts(pbs.PBS_MIXED), ks)
+    e2e_steps = 1 if name != "c2" else args.steps
     e2e_t = []
-    for _ in range(args.steps):
+    for _ in range(e2e_steps):
         flush.fill_(1.0)
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        lam_h, res_h, it_h = ctx.solve_path(geom, opts(pbs.PBS_MIXED), ks)
+        lam_h, res_h, it_h = ctx.solve_path(geom, _opts(pbs, name, pbs.PBS_MIXED), ks)
         e2e_t.append((time.perf_counter() - t0) * 1e3)
+
+    # plain FP64 on the same workload (one step; its first call also allocates the FP64 workspace)
+    t_fp64, _ = timed(pbs.PBS_FP64, 1 if name != "c2" else max(1, min(args.steps, 2)))
+    lam_fp64 = d_ev.cpu().numpy()
+    rs64 = d_rs.cpu().numpy()
     ctx.close()
+    del ctx
 
     ms_step = max_over_ranks(float(np.sum(t_mixed)) / args.steps)
     ms_fp64 = max_over_ranks(float(np.sum(t_fp64)) / len(t_fp64))
     ms_e2e = max_over_ranks(float(np.sum(e2e_t)) / len(e2e_t))
-    value = job_throughput(ws, NK, ms_step)
+    value = job_throughput(ws, nk, ms_step)
+    c2 = c2_leg(pbs, dev, stream) if name == "c3" and rank == 0 else None
     if rank != 0:
         return
     peaks, peak_kind = _peaks()
@@ -316,29 +419,27 @@ def run_ours(args):
         roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "traffic": None, "kernel": dominant,
                 "peak_kind": f"{peak_kind} hbm_gbs"}
-    if dominant == "gram":
-        # DRAM bytes (read + write) of one batched launch (4 Bloch vectors x 30 columns)
-        # from an ncu capture of the unchanged kernel; the algorithmic bytes are 251.7 MB
-        roof["traffic"] = GRAM_DRAM_BYTES
-        roof["traffic_source"] = "ncu dram__bytes_read.sum + dram__bytes_write.sum, one batched launch"
     roof["avg_launch_us"] = 1e3 * dom_ms / max(dom_n, 1)
     roof["launches_timed"] = dom_n
     roof["timing"] = f"CUDA events on the library stream around every {SAMPLE_EVERY}th launch in the timed steps"
     roof["share_of_kernel_time"] = shares[dominant][0] / sum(v[0] for v in shares.values())
-    cb = oracle_sample_kps(seconds_budget=20.0) if ws == 1 else None
+    cb = oracle_sample_kps(name, seconds_budget=20.0) if ws == 1 else None
+    rel = np.abs(lam_mixed - lam_fp64) / lam_fp64
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "c128 storage; FP64 residual and update; double-float (FP32 pipe) Gram, Rayleigh quotients "
                  "and small Rayleigh-Ritz; c64 FP32 multigrid", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "grid": "256x256", "k_points": NK, "bands": NEV, "block": BLOCK, "tol": TOL,
-                   "k_points_in_flight": KBATCH,
-                   "precision": "mixed", "l2": "flushed (512 MiB write) before every timed step",
-                   "replicas": ws},
+        "config": {"workload": w["text"], "grid": f"{n}x{n}", "k_points": nk, "bands": nev, "block": w["block"],
+                   "tol": TOL, "k_points_in_flight": w["kbatch"], "precision": "mixed",
+                   "l2": "flushed (512 MiB write) before every timed step", "replicas": ws},
         "converged": ok, "max_resid": float(rs.max()), "iters_per_k": its.tolist(),
-        "plain_fp64": {"value": job_throughput(ws, NK, ms_fp64), "unit": UNIT, "ms_per_step": ms_fp64},
+        "plain_fp64": {"value": job_throughput(ws, nk, ms_fp64), "unit": UNIT, "ms_per_step": ms_fp64,
+                       "steps": len(t_fp64), "max_resid": float(rs64.max()),
+                       "converged": bool(np.all(rs64 <= _band_tol(eps, n, lam_fp64)))},
+        "max_rel_err_mixed_vs_fp64_per_band": rel.max(axis=0).tolist(),
         "clocks": clk,
-        "e2e": {"value": job_throughput(ws, NK, ms_e2e), "unit": UNIT,
+        "e2e": {"value": job_throughput(ws, nk, ms_e2e), "unit": UNIT, "steps": e2e_steps,
                 "h2d_bytes_per_step": int(eps.nbytes + ks.nbytes),
                 "d2h_bytes_per_step": int(lam_h.nbytes + res_h.nbytes + it_h.nbytes)},
         "gpu_launches": int(launches),
@@ -348,51 +449,56 @@ def run_ours(args):
         "achieved_per_class_warmup": per_class_rates(shares, peaks["hbm_gbs"]),
         "cpu_baseline": cb,
     }
+    if c2 is not None:
+        line["c2"] = c2
     print(json.dumps(line), flush=True)
 
 
-def profile_run(nk: int, precision: str):
-    """One untimed solve of the first ``nk`` Bloch vectors of the workload (a small case for ncu)."""
+def profile_run(name: str, nk: int, precision: str):
+    """One untimed solve of the first ``nk`` Bloch vectors of a workload (a small case for ncu)."""
     import __graft_entry__ as ge
     ge.build()
     import paper_2304_00337_gb300 as pbs
-    import pbs_inputs as gi
-    geom = pbs.Geometry(gi.rod_eps(N_SIDE, N_SIDE))
-    ks = gi.gxmg_path(NK)[:nk]
+    w = WORKLOADS[name]
+    eps, ks = workload_inputs(name)
+    geom = pbs.Geometry(eps)
     prec = pbs.PBS_MIXED if precision == "mixed" else pbs.PBS_FP64
+    o = _opts(pbs, name, prec)
+    o.kbatch = min(w["kbatch"], nk)
     with pbs.Context(0) as ctx:
-        lam, res, it = ctx.solve_path(geom, pbs.default_opts(nev=NEV, block=BLOCK, tol=TOL, precision=prec,
-                                                             kbatch=min(KBATCH, nk)), ks)
-    print(f"profile-run ok: {nk} k-points, iterations {it.tolist()}, max resid {res.max():.2e}", flush=True)
+        lam, res, it = ctx.solve_path(geom, o, ks[:nk])
+    print(f"profile-run ok: {name}, {nk} k-points, iterations {it.tolist()}, max resid {res.max():.2e}", flush=True)
 
 
-def serving_bench(njobs: int) -> None:
+def serving_bench(njobs: int, grids, slots: int, rate_factor: float) -> None:
     """Serving workload: a seeded stream of rod-crystal path jobs (radius U(0.1, 0.45) a,
-    eps U(2, 13), 6-12 bands with two throw-away vectors, 7-64 Bloch vectors on
-    Gamma-X-M-Gamma; meshes 128x128 and 256x256) submitted through pbs_submit at Poisson
-    arrival times, at 0.8 of the saturation rate measured in a closed-loop warm-up.
-    Prints one JSON line with the p50 / p99 latency from submission to completion."""
+    eps U(2, 13), 6-12 bands with two throw-away vectors, 10-64 Bloch vectors on
+    Gamma-X-M-Gamma, meshes drawn from ``grids``) submitted through pbs_submit at Poisson
+    arrival times, at ``rate_factor`` of the saturation rate measured in a closed-loop
+    warm-up, into a context with ``slots`` serving slots (continuous batching: jobs that
+    arrive while others run are admitted as slots and memory free up).  Prints one JSON
+    line with the p50 / p99 latency from submission to completion and the k-points/s."""
     import __graft_entry__ as ge
     ge.build()
     import paper_2304_00337_gb300 as pbs
     import pbs_inputs as gi
-    jobs = gi.serving_jobs(njobs, seed=0, rate_per_s=1.0, grids=(128, 256))
+    jobs = gi.serving_jobs(njobs, seed=0, rate_per_s=1.0, grids=tuple(grids))
 
     def args_of(j):
         geom = pbs.Geometry(gi.rod_eps(j["grid"], j["grid"], radius=j["radius"], eps_rod=j["eps_rod"]))
-        o = pbs.default_opts(nev=j["bands"], block=j["block"], tol=TOL, kbatch=min(KBATCH, j["nk"]))
+        o = pbs.default_opts(nev=j["bands"], block=j["block"], tol=TOL, kbatch=min(8, j["nk"]))
         return geom, o, gi.gxmg_path(j["nk"])
 
     prepared = [args_of(j) for j in jobs]
     with pbs.Context(0) as ctx:
-        # closed loop: the first eight jobs back to back give the mean service time
-        warm = prepared[:8]
+        ctx.serve_slots(slots)
+        # closed loop: the first 2 slots jobs, all submitted at once, give the saturation rate
+        warm = prepared[:2 * slots]
         t0 = time.perf_counter()
         ids = [ctx.submit(*a) for a in warm]
         for i in ids:
             ctx.fetch(i)
-        service = (time.perf_counter() - t0) / len(warm)
-        rate = 0.8 / service
+        rate = rate_factor * len(warm) / (time.perf_counter() - t0)
         # open loop: Poisson arrivals (the stream's unit-rate arrival times scaled to `rate`)
         start = time.perf_counter()
         ids = []
@@ -402,20 +508,31 @@ def serving_bench(njobs: int) -> None:
             if due > now:
                 time.sleep(due - now)
             ids.append(ctx.submit(*a))
-        res = [ctx.fetch(i) for i in ids]
+        while not all(ctx.poll(i) for i in ids):
+            time.sleep(0.01)
+        times = [ctx.job_times(i) for i in ids]
+        res = [ctx.fetch(i, allow_noconv=True) for i in ids]
         wall = time.perf_counter() - start
     lat = np.array([r[3] for r in res])
-    ok = all(np.all(r[1] <= TOL * 100) for r in res)
+    ok = all(np.all(r[1] <= 1e-6) for r in res)
     kpts = sum(j["nk"] for j in jobs)
+    # concurrency: the mean number of jobs running, from their start and finish times
+    busy = sum(t[2] - t[1] for t in times)
+    span = max(t[2] for t in times) - min(t[1] for t in times)
+    by_grid = {}
+    for j, l in zip(jobs, lat):
+        by_grid.setdefault(j["grid"], []).append(l)
     print(json.dumps({
         "metric": "serving latency p50 (submission to completion)", "value": float(np.percentile(lat, 50)),
         "unit": "s", "higher_is_better": False, "p99_s": float(np.percentile(lat, 99)),
-        "mean_s": float(lat.mean()), "jobs": njobs, "arrival_rate_per_s": rate, "service_s_closed_loop": service,
-        "throughput_jobs_per_s": njobs / wall, "throughput_kpoints_per_s": kpts / wall, "converged": bool(ok),
+        "mean_s": float(lat.mean()), "jobs": njobs, "arrival_rate_per_s": rate,
+        "throughput_jobs_per_s": njobs / wall, "throughput_kpoints_per_s": kpts / wall,
+        "mean_jobs_running": busy / span, "converged": bool(ok), "wall_s": wall,
+        "p50_s_by_grid": {str(g): float(np.percentile(v, 50)) for g, v in sorted(by_grid.items())},
         "data": "synthetic", "n_gpus": 1,
-        "config": {"workload": "rod-crystal path jobs, Poisson arrivals at 0.8 x saturation", "grids": [128, 256],
-                   "bands": "6-12 (+2 throw-away)", "k_points_per_job": "7-64", "seed": 0,
-                   "k_points_in_flight_per_job": KBATCH}}), flush=True)
+        "config": {"workload": f"rod-crystal path jobs, Poisson arrivals at {rate_factor} x saturation",
+                   "grids": list(grids), "bands": "6-12 (+2 throw-away)", "k_points_per_job": "10-64",
+                   "seed": 0, "slots": slots, "k_points_in_flight_per_job": "min(8, nk)"}}), flush=True)
 
 
 def grid_bench(kappa: int, n: int) -> None:
@@ -431,7 +548,7 @@ def grid_bench(kappa: int, n: int) -> None:
     out = {}
     with pbs.Context(0) as ctx:
         for tol in (1e-2, 1e-8):
-            o = pbs.default_opts(nev=16, block=24, tol=tol, kbatch=KBATCH)
+            o = pbs.default_opts(nev=16, block=24, tol=tol, kbatch=4)
             ctx.solve_grid(geom, o, 4)  # warm-up (hierarchy, workspace)
             t0 = time.perf_counter()
             ks, lam, res, it = ctx.solve_grid(geom, o, kappa)
@@ -446,7 +563,7 @@ def grid_bench(kappa: int, n: int) -> None:
                       "n_gpus": 1, "data": "synthetic", "results": out,
                       "config": {"workload": f"rod eps=11.56 r=0.18a, {n}x{n}, {kappa}x{kappa} k-points, "
                                              "16 bands + 8 throw-away, Section 6 extrapolation schedule",
-                                 "k_points_in_flight": KBATCH, "precision": "mixed"}}), flush=True)
+                                 "k_points_in_flight": 4, "precision": "mixed"}}), flush=True)
 
 
 def throwaway_bench(n: int) -> None:
@@ -571,17 +688,22 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--profile-run", type=int, default=0, metavar="NK",
-                    help="solve the first NK k-points once (no timing) - the small case for ncu captures")
+                    help="solve the first NK k-points of the workload once (no timing) - the small case for ncu")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--workload", default="path", choices=["path", "serving", "grid", "throwaway", "householder"],
-                    help="path: the headline 256x256 path (default); serving: the job-stream latency line; "
-                         "grid: the paper's kappa x kappa Brillouin-zone workload")
+    ap.add_argument("--workload", default="c3",
+                    choices=sorted(WORKLOADS) + ["serving", "grid", "throwaway", "householder"],
+                    help="c3: the headline 1024x1024 path with 64 k-points in flight (default); c2: 256x256 "
+                         "path; c4: 4096x4096 disks; serving: the job-stream latency line; grid: the paper's "
+                         "kappa x kappa Brillouin-zone workload")
     ap.add_argument("--kappa", type=int, default=30, help="grid workload: k-points per direction")
     ap.add_argument("--grid-n", type=int, default=256, help="grid workload: cells per direction")
-    ap.add_argument("--jobs", type=int, default=32, help="jobs of the serving workload")
+    ap.add_argument("--jobs", type=int, default=200, help="jobs of the serving workload")
+    ap.add_argument("--serve-grids", default="128,256,512,1024,2048", help="serving workload: mesh sizes")
+    ap.add_argument("--slots", type=int, default=4, help="serving workload: serving slots")
+    ap.add_argument("--rate", type=float, default=0.8, help="serving workload: arrival rate / saturation rate")
     args = ap.parse_args()
     if args.workload == "serving" and args.impl == "ours":
-        serving_bench(args.jobs)
+        serving_bench(args.jobs, [int(g) for g in args.serve_grids.split(",")], args.slots, args.rate)
         return
     if args.workload == "grid" and args.impl == "ours":
         grid_bench(args.kappa, args.grid_n)
@@ -592,8 +714,11 @@ def main():
     if args.workload == "householder" and args.impl == "ours":
         householder_bench(256, 30, 10)
         return
+    if args.workload not in WORKLOADS:
+        print(json.dumps({"impl": args.impl, "unavailable": f"no reference arm for the {args.workload} workload"}))
+        return
     if args.profile_run:
-        profile_run(args.profile_run, args.precision)
+        profile_run(args.workload, args.profile_run, args.precision)
         return
     if args.warmup < 3:
         args.warmup = 3

@@ -57,6 +57,7 @@ extern "C" {
 #define PBS_ENUMERIC (-4) /* non-finite values or a breakdown of the small dense solves */
 #define PBS_ETIMEOUT (-5) /* a bounded device wait gave up                 */
 #define PBS_ECUDA (-6)    /* a CUDA runtime call failed                     */
+#define PBS_ECANCELED (-7) /* the serving job was cancelled (pbs_cancel)    */
 
 /* ---- precision policies (Section 4/5 preconditioner precision) -------- */
 #define PBS_FP64 0  /* every kernel in FP64 ("plain"), the small Rayleigh-Ritz
@@ -307,25 +308,43 @@ PBS_API unsigned long long pbs_launch_count_df(void);
 
 /*
  * Serving: paths of Bloch vectors (Section 6) submitted as independent requests
- * and solved one after another by a host thread of the context, in submission
- * order, with the same computation as pbs_solve_path.  No counterpart in the
- * paper; it exists so that many small jobs can share one device.
+ * and solved with continuous batching.  No counterpart in the paper; it exists so
+ * that many jobs can share one device.  The context runs `slots` serving slots
+ * (pbs_serve_slots, default 4), each an engine with its own CUDA stream, resident
+ * multigrid hierarchy and workspace, driven by its own host thread, so the jobs of
+ * different slots overlap on the device.  A free slot takes the first queued job
+ * that fits the device memory the running jobs and the idle slots' resident data
+ * leave (the context's budget, or 90% of the free device memory at the first
+ * submission when the budget is 0); among the first 2 slots queued jobs it prefers
+ * one whose geometry it already holds.  A job at the head of the queue that does
+ * not fit waits (idle slots free what they keep resident) and is passed by later
+ * jobs at most 2 slots times.  Every job runs the computation of pbs_solve_path on
+ * its own data, so its results do not depend on what else runs (bit for bit: the
+ * kernels are deterministic).  Synchronous calls on the context use the context's
+ * own engine and do not wait for jobs.
  *
  * pbs_job_bytes: device bytes a path job of nk Bloch vectors on an n x m mesh with
- *   these options needs on a context without a budget that holds nothing else
- *   (hierarchy, coarsest factors, solver workspace; the admission estimate).
+ *   these options needs on an engine that holds nothing else (hierarchy, coarsest
+ *   factors, solver workspace; the admission estimate).
  * pbs_submit: copies geom (including eps), opts and ks (host, nk*2) and queues the
  *   job; returns at once with *job_id.  PBS_EINVAL for invalid input (checked at
- *   submission, eps included), PBS_ENOMEM when the job's estimate exceeds the
- *   context's budget (or 95% of the device memory when the budget is 0).
+ *   submission, eps and ks included), PBS_ENOMEM when the job alone needs more than
+ *   the jobs may hold together.
  * pbs_poll: *done = 1 once the job has finished (successfully or not), else 0.
  * pbs_fetch: waits until the job has finished, copies its results (host,
  *   nk*nev eigvals and resid, nk iters; any may be NULL) and the latency from
  *   submission to completion in seconds (may be NULL), forgets the job and
- *   returns its status (the pbs_solve_path status; pbs_last_error in the calling
- *   thread then describes a failure).  Unknown ids give PBS_EINVAL.
- * Synchronous calls on the same context wait for the job in progress.
- * pbs_destroy lets the job in progress finish and drops queued ones.
+ *   returns its status (the pbs_solve_path status, or PBS_ECANCELED;
+ *   pbs_last_error in the calling thread then describes a failure).  Unknown ids
+ *   give PBS_EINVAL.
+ * pbs_cancel: a queued job is removed at once; a running job stops at its next
+ *   iteration boundary (no kernel is interrupted); either way it finishes with
+ *   PBS_ECANCELED.  A finished job is left as it is (PBS_OK).
+ * pbs_job_times: seconds since the context's creation at which the job was
+ *   submitted, started on a slot and finished (-1 for what has not happened yet);
+ *   valid until pbs_fetch.
+ * pbs_serve_slots: number of serving slots (1..64), before the first submission.
+ * pbs_destroy lets running jobs finish and drops queued ones.
  */
 PBS_API int pbs_job_bytes(int n, int m, const pbs_opts *opts, int nk, size_t *bytes);
 PBS_API int pbs_submit(pbs_ctx *ctx, const pbs_geom *geom, const pbs_opts *opts, int nk, const double *ks,
@@ -333,6 +352,25 @@ PBS_API int pbs_submit(pbs_ctx *ctx, const pbs_geom *geom, const pbs_opts *opts,
 PBS_API int pbs_poll(pbs_ctx *ctx, uint64_t job_id, int *done);
 PBS_API int pbs_fetch(pbs_ctx *ctx, uint64_t job_id, double *eigvals, double *resid, int *iters,
                       double *latency_s);
+PBS_API int pbs_cancel(pbs_ctx *ctx, uint64_t job_id);
+PBS_API int pbs_job_times(pbs_ctx *ctx, uint64_t job_id, double *submit_s, double *start_s, double *done_s);
+PBS_API int pbs_serve_slots(pbs_ctx *ctx, int slots);
+
+/*
+ * Change the byte budget of the context's own allocations (0 = no cap).  Memory
+ * already held stays; an allocation that would exceed the new budget fails with
+ * PBS_ENOMEM, after which the context remains usable (a later call with a larger
+ * budget succeeds).  Serving jobs are admitted against the budget the context had
+ * at its first submission.
+ */
+PBS_API int pbs_set_budget(pbs_ctx *ctx, size_t hbm_budget_bytes);
+
+/*
+ * Failure injection for tests: the count-th device allocation of the context's
+ * own engine from now fails as if the device were out of memory (PBS_ENOMEM from
+ * the call that makes it; the context stays usable).  0 switches it off.
+ */
+PBS_API int pbs_fail_alloc_after(pbs_ctx *ctx, int count);
 
 /*
  * Allocation-free Rayleigh-Ritz step.  No counterpart in the paper: it exists

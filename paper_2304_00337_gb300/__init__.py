@@ -28,6 +28,7 @@ PBS_ENOCONV = -3
 PBS_ENUMERIC = -4
 PBS_ETIMEOUT = -5
 PBS_ECUDA = -6
+PBS_ECANCELED = -7
 # precision
 PBS_FP64 = 0
 PBS_MIXED = 1
@@ -111,6 +112,11 @@ def lib() -> ct.CDLL:
                                   ct.POINTER(ct.c_uint64)]),
         "pbs_poll": (ct.c_int, [P, ct.c_uint64, ip]),
         "pbs_fetch": (ct.c_int, [P, ct.c_uint64, dp, dp, ip, dp]),
+        "pbs_cancel": (ct.c_int, [P, ct.c_uint64]),
+        "pbs_job_times": (ct.c_int, [P, ct.c_uint64, dp, dp, dp]),
+        "pbs_serve_slots": (ct.c_int, [P, ct.c_int]),
+        "pbs_set_budget": (ct.c_int, [P, ct.c_size_t]),
+        "pbs_fail_alloc_after": (ct.c_int, [P, ct.c_int]),
         "pbs_strerror": (ct.c_char_p, [ct.c_int]),
         "pbs_last_error": (ct.c_char_p, []),
     }
@@ -339,6 +345,28 @@ class Context:
                              ct.byref(lat))
         _check(st, "pbs_fetch", (PBS_OK, PBS_ENOCONV) if allow_noconv else (PBS_OK,))
         return ev, rs, it, lat.value
+
+    def cancel(self, job: int) -> None:
+        """``pbs_cancel``: drop a queued job or stop a running one at its next iteration."""
+        _check(lib().pbs_cancel(self._ptr, job), "pbs_cancel")
+
+    def job_times(self, job: int):
+        """``pbs_job_times``: (submitted, started, finished) in seconds since the context's creation."""
+        a, b, c = ct.c_double(), ct.c_double(), ct.c_double()
+        _check(lib().pbs_job_times(self._ptr, job, ct.byref(a), ct.byref(b), ct.byref(c)), "pbs_job_times")
+        return a.value, b.value, c.value
+
+    def serve_slots(self, slots: int) -> None:
+        """``pbs_serve_slots``: number of concurrent serving slots (before the first submission)."""
+        _check(lib().pbs_serve_slots(self._ptr, slots), "pbs_serve_slots")
+
+    def set_budget(self, hbm_budget_bytes: int) -> None:
+        """``pbs_set_budget``: change the byte budget of the context's own allocations."""
+        _check(lib().pbs_set_budget(self._ptr, hbm_budget_bytes), "pbs_set_budget")
+
+    def fail_alloc_after(self, count: int) -> None:
+        """``pbs_fail_alloc_after``: make the count-th device allocation from now fail (tests)."""
+        _check(lib().pbs_fail_alloc_after(self._ptr, count), "pbs_fail_alloc_after")
 
     def solve_path_device(self, a, b, n, m, d_eps: int, opts, nk: int, d_ks: int, d_eigvals: int, d_resid: int,
                           d_iters: int, stream=None, allow_noconv: bool = False):

@@ -231,6 +231,80 @@ __global__ void __launch_bounds__(kBX * kBY) k_residual(Lvl<double> L, Wts<doubl
   }
 }
 
+// The same residual for the mixed policy, whose preconditioner reads it in FP32.
+// The curls c = x(i,j+1) - x(i,j) - y(i+1,j) + y(i,j) are formed in FP64: they are
+// where the stencil cancels (neighbouring values of a smooth iterate nearly agree),
+// and their FP64 rounding is the floor every policy shares.  Everything after them -
+// H = w c, the differences of H, the mass stencil and R = A e - lambda M e - is
+// double-float: those steps see the curls and the iterate's values themselves, so a
+// relative rounding of 2^-47 there moves the relative residual by about 2^-47 (H
+// differences: 2^-47 sqrt(lambda_max / lambda), 1e-10 next to Gamma at 1024^2), far
+// below any tolerance.  R is stored rounded to FP32 and the norms |R|^2, |M e|^2 are
+// summed per thread in FP32 and across the block in FP64 (the convergence test needs
+// a few digits of them).  FP64 work: the curls only (about 7 operations per node
+// against about 45 in the all-FP64 kernel).
+template <class Rd>
+__device__ __forceinline__ void residual_tile_mixed(const Lvl<df>& L, const WtsDF& w, const Rd& r, df l,
+                                                    float2* __restrict__ Rc, double& rr, double& mm) {
+  __shared__ dcx Hs[kBY + 1][kBX + 1];  // cell (i0 - 1 + a, j0 - 1 + b) at Hs[b][a]
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int i0 = blockIdx.x * kBX, j0 = blockIdx.y * kBY;
+  const int i = i0 + tx, j = j0 + ty;
+  const bool in = i < L.n && j < L.m;
+  if (in) Hs[ty + 1][tx + 1] = w(i, j) * dcx_split(curl_at<double>(r, i, j));
+  if (ty == 0 && i < L.n) Hs[0][tx + 1] = w(i, j0 - 1) * dcx_split(curl_at<double>(r, i, j0 - 1));
+  if (tx == 0 && j < L.m) Hs[ty + 1][0] = w(i0 - 1, j) * dcx_split(curl_at<double>(r, i0 - 1, j));
+  __syncthreads();
+  if (in) {
+    const df sx = L.mx * df(1.0 / 6.0), sy = L.my * df(1.0 / 6.0), four = df(4.0);
+    const dcx x0 = dcx_split(r.x(i, j)), x1 = dcx_split(r.x(i, j + 1)), x2 = dcx_split(r.x(i, j - 1));
+    const dcx y0 = dcx_split(r.y(i, j)), y1 = dcx_split(r.y(i + 1, j)), y2 = dcx_split(r.y(i - 1, j));
+    const dcx mx = sx * (four * x0 + (x1 + x2));
+    const dcx my = sy * (four * y0 + (y1 + y2));
+    const dcx h = Hs[ty + 1][tx + 1], hb = Hs[ty][tx + 1], hl = Hs[ty + 1][tx];
+    const dcx rx = (hb - h) - l * mx;
+    const dcx ry = (h - hl) - l * my;
+    const long N = (long)L.n * L.m, e = (long)j * L.n + i;
+    const float2 fx = make_float2(df_to_float(rx.x), df_to_float(rx.y));
+    const float2 fy = make_float2(df_to_float(ry.x), df_to_float(ry.y));
+    Rc[e] = fx;
+    Rc[N + e] = fy;
+    const float r2 = fmaf(fx.x, fx.x, fmaf(fx.y, fx.y, fmaf(fy.x, fy.x, fy.y * fy.y)));
+    const float mxf = df_to_float(mx.x), mxi = df_to_float(mx.y), myf = df_to_float(my.x), myi = df_to_float(my.y);
+    const float m2 = fmaf(mxf, mxf, fmaf(mxi, mxi, fmaf(myf, myf, myi * myi)));
+    rr = f2d_exact(r2);
+    mm = f2d_exact(m2);
+  }
+}
+
+__global__ void __launch_bounds__(kBX * kBY) k_residual_mixed(Lvl<df> L, WtsDF w, const double* ph, int cpg,
+                                                               const double2* __restrict__ E, float2* __restrict__ R,
+                                                               long ld, const double* __restrict__ lam,
+                                                               double* __restrict__ part) {
+  const int i0 = blockIdx.x * kBX, j0 = blockIdx.y * kBY, c = blockIdx.z;
+  double rr = 0, mm = 0;
+  const df l = df_split(lam[c]);
+  if (i0 >= 1 && j0 >= 1 && i0 + kBX < L.n && j0 + kBY < L.m) {
+    residual_tile_mixed(L, w, ERdIn<double>{E + c * ld, L.n, (long)L.n * L.m}, l, R + c * ld, rr, mm);
+  } else {
+    constexpr int WX = kBX + 1, WY = kBX + 2;
+    __shared__ double2 sx[(kBY + 2) * WX], sy[(kBY + 1) * WY];
+    const int nx = min(kBX, L.n - i0), ny = min(kBY, L.m - j0);
+    const Ph<double> p = load_ph<double>(ph, c / cpg);
+    const double2* Ec = E + c * ld;
+    stage_field(Ec, L.n, L.m, p, i0, j0, WX, kBY + 2, nx, ny + 1, sx);
+    stage_field(Ec + (long)L.n * L.m, L.n, L.m, p, i0, j0, WY, kBY + 1, nx + 1, ny, sy);
+    __syncthreads();
+    residual_tile_mixed(L, w, TileERd<double>{sx, sy, i0 - 1, j0 - 1, WX, WY}, l, R + c * ld, rr, mm);
+  }
+  block_sum2(rr, mm);
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    const int nblk = gridDim.x * gridDim.y, b = blockIdx.y * gridDim.x + blockIdx.x;
+    part[((long)c * nblk + b) * 2] = rr;
+    part[((long)c * nblk + b) * 2 + 1] = mm;
+  }
+}
+
 // rhs(i,j) = (L^* M x)(i,j) = (Mx)_x(i-1,j) - (Mx)_x(i,j) + (Mx)_y(i,j-1) - (Mx)_y(i,j),
 // computed in V and stored in T.  A CTA stages the edge values its 32 x 8 nodes
 // read (converted to V once), forms each mass-stencil value once in shared
@@ -1345,6 +1419,19 @@ void rayleigh_parts(const Level& L, const double* d_ph, int cpg, const double2* 
   PBS_LAUNCHED();
 }
 
+void residual_mixed(const Level& L, const double* d_ph, int cpg, const double2* E, float2* R, long ld, int ncols,
+                    const double* d_lam, double* d_partials, double* d_out, cudaStream_t s) {
+  if (ncols <= 0) return;
+  const dim3 g = grid2(L.n, L.m, ncols);
+  timer_begin(KC_RESIDUAL, s, 24.0 * L.D() * ncols);  // read E (16 B), write R (8 B) per edge DOF
+  k_residual_mixed<<<g, dim3(kBX, kBY), 0, s>>>(L.lvl<df>(), L.wts_df(), d_ph, cpg, E, R, ld, d_lam, d_partials);
+  timer_end(KC_RESIDUAL, s);
+  PBS_LAUNCHED();
+  count_df_launch();
+  k_finalize2<<<ncols, 256, 0, s>>>(d_partials, g.x * g.y, d_out);
+  PBS_LAUNCHED();
+}
+
 void residual(const Level& L, const double* d_ph, int cpg, const double2* E, double2* R, long ld, int ncols,
               const double* d_lam, double* d_partials, double* d_out, cudaStream_t s) {
   if (ncols <= 0) return;
@@ -1399,31 +1486,73 @@ void gram_groups(const Level& L, const double* d_ph, Roles roles, int q, int ngr
                  double2* d_partials, long partial_capacity, bool dfa, cudaStream_t s) {
   if (q <= 0 || ngroups <= 0) return;
   if (q > kMaxTrial) fail(PBS_EINVAL, "trial block too wide");
-  const int npart = gram_partials(L.N(), ngroups);
   const int ne = q * (q + 1) / 2;
-  if ((long)ngroups * npart * 2 * ne > partial_capacity) fail(PBS_EINVAL, "gram partials buffer too small");
-  timer_begin(KC_GRAM, s, 8.0 * ne * 3.0 * L.N() * ngroups);  // flops: three complex MACs per entry and node
-  if (dfa) {
-    gram_df_dispatch<kGdTile>(L, d_ph, roles, q, ngroups, npart, d_partials, s);
-    count_df_launch();
-  } else {
-    static PerDeviceOnce once;
-    once([] {
-      PBS_CUDA(cudaFuncSetAttribute(k_gram_fused, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    6 * kMaxTrial * kGramRows * (int)sizeof(double2)));
-    });
-    const size_t smem = 6ull * q * kGramRows * sizeof(double2);
-    k_gram_fused<<<dim3(npart, ngroups), 256, smem, s>>>(L.lvl<double>(), L.wts<double>(), d_ph, roles, q, d_partials,
-                                                          npart);
+  const int np0 = gram_partials(L.N(), ngroups);
+  // variants: the kernel (tensor cores or double-float, mixed policy) and the number
+  // of partial blocks per group; the autotuner picks among them on first use
+  struct Variant {
+    int kernel;  // 0: FP64, 1: double-float, 2: tensor cores
+    int npart;
+  };
+  Variant var[4];
+  int nvar = 0;
+  const int kern = dfa ? 1 : 0;
+  var[nvar++] = {kern, np0};
+  var[nvar++] = {kern, 2 * np0};
+  if (dfa && gram_tc_supported(q) && gram_on_tensor_cores()) {
+    var[nvar++] = {2, np0};
+    var[nvar++] = {2, 2 * np0};
   }
+  auto fits = [&](const Variant& v) { return (long)ngroups * v.npart * 2 * ne <= partial_capacity; };
+  if (!fits(var[0])) fail(PBS_EINVAL, "gram partials buffer too small");
+  auto launch = [&](const Variant& v) {
+    if (v.kernel == 2) {
+      gram_tc(L, d_ph, roles, q, ngroups, v.npart, d_partials, s);
+      count_df_launch();
+    } else if (v.kernel == 1) {
+      gram_df_dispatch<kGdTile>(L, d_ph, roles, q, ngroups, v.npart, d_partials, s);
+      count_df_launch();
+    } else {
+      static PerDeviceOnce once;
+      once([] {
+        PBS_CUDA(cudaFuncSetAttribute(k_gram_fused, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      6 * kMaxTrial * kGramRows * (int)sizeof(double2)));
+      });
+      const size_t smem = 6ull * q * kGramRows * sizeof(double2);
+      k_gram_fused<<<dim3(v.npart, ngroups), 256, smem, s>>>(L.lvl<double>(), L.wts<double>(), d_ph, roles, q,
+                                                              d_partials, v.npart);
+    }
+    PBS_LAUNCHED();
+    k_gram_finalize<<<dim3((2 * ne + 255) / 256, ngroups), 256, 0, s>>>(d_partials, v.npart, q, GM, GA);
+    PBS_LAUNCHED();
+  };
+  int pick = 0;
+  if (nvar > 1) {
+    const std::string key = std::string(dfa ? "gram_df" : "gram") + (nvar > 2 ? "_tc" : "") + "|" +
+                            std::to_string(L.n) + "x" + std::to_string(L.m) + "|q" + std::to_string(q) + "|g" +
+                            std::to_string(ngroups) + "|" + device_tag();
+    // a candidate whose partial sums do not fit the buffer runs the first one instead
+    pick = tune_pick(key, nvar, [&](int c) { launch(fits(var[c]) ? var[c] : var[0]); }, s);
+    if (!fits(var[pick])) pick = 0;
+  }
+  timer_begin(KC_GRAM, s, 8.0 * ne * 3.0 * L.N() * ngroups);  // flops: three complex MACs per entry and node
+  launch(var[pick]);
   timer_end(KC_GRAM, s);
-  PBS_LAUNCHED();
-  k_gram_finalize<<<dim3((2 * ne + 255) / 256, ngroups), 256, 0, s>>>(d_partials, npart, q, GM, GA);
-  PBS_LAUNCHED();
 }
 
 long gram_partials_size(long rows, int q, int ngroups) {
-  return (long)ngroups * gram_partials(rows, ngroups) * q * (q + 1);
+  // partial sums for up to twice the default split (a tuning candidate)
+  return 2L * ngroups * gram_partials(rows, ngroups) * q * (q + 1);
+}
+
+bool gram_on_tensor_cores() {
+  // PBS_GRAM=tc offers the tensor-core kernel to the autotuner (opt-in); the default
+  // is the double-float kernel
+  static const bool tc = [] {
+    const char* v = std::getenv("PBS_GRAM");
+    return v && std::strcmp(v, "tc") == 0;
+  }();
+  return tc;
 }
 
 size_t small_rr_scratch(int q) { return (3ull * q * q + (size_t)q * kMaxBlock) * sizeof(double2) + 64; }
@@ -1474,26 +1603,35 @@ void block_update(Roles X, int q, const double2* C, int ldc, long cgs, double2* 
                   const double2* Z, long ldz, long rows, int ngroups, bool dfa, cudaStream_t s) {
   if (p <= 0 || rows <= 0 || ngroups <= 0) return;
   if (p > kMaxBlock) fail(PBS_EINVAL, "block_update: p too large");
-  long per = blocks_for(rows, 256, 2 * 152 * 4);
-  per = std::max<long>(1, per / ngroups);
-  const dim3 grid((unsigned)per, ngroups);
+  const long base = std::max<long>(1, blocks_for(rows, 256, 2 * 152 * 4) / ngroups);
+  auto launch = [&](long per) {
+    const dim3 grid((unsigned)per, ngroups);
+    if (dfa) {
+      if (p <= 8) launch_update_df<8>(X, q, C, ldc, cgs, Y, ldy, p, Z, ldz, rows, grid, s);
+      else if (p <= 16) launch_update_df<16>(X, q, C, ldc, cgs, Y, ldy, p, Z, ldz, rows, grid, s);
+      else launch_update_df<32>(X, q, C, ldc, cgs, Y, ldy, p, Z, ldz, rows, grid, s);
+      count_df_launch();
+    } else {
+      static PerDeviceOnce once;
+      once([] {
+        PBS_CUDA(cudaFuncSetAttribute(k_block_update, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      kMaxBlock * kMaxTrial * (int)sizeof(double2)));
+      });
+      const size_t smem = (size_t)p * q * sizeof(double2);
+      k_block_update<<<grid, 256, smem, s>>>(X, q, C, ldc, cgs, Y, ldy, p, Z, ldz, rows);
+    }
+    PBS_LAUNCHED();
+  };
+  // grid width: every row's result is the same whatever the grid (no cross-block
+  // sums), so the autotuner's choice changes the time only
+  const long cand[3] = {base, std::max<long>(1, base / 2), 2 * base};
+  const std::string key = std::string(dfa ? "update_df" : "update") + "|" + std::to_string(rows) + "|q" +
+                          std::to_string(q) + "|p" + std::to_string(p) + "|g" + std::to_string(ngroups) + "|" +
+                          device_tag();
+  const int pick = tune_pick(key, 3, [&](int c) { launch(cand[c]); }, s);
   timer_begin(KC_BLOCK_UPDATE, s, 8.0 * q * p * rows * ngroups);  // flops
-  if (dfa) {
-    if (p <= 8) launch_update_df<8>(X, q, C, ldc, cgs, Y, ldy, p, Z, ldz, rows, grid, s);
-    else if (p <= 16) launch_update_df<16>(X, q, C, ldc, cgs, Y, ldy, p, Z, ldz, rows, grid, s);
-    else launch_update_df<32>(X, q, C, ldc, cgs, Y, ldy, p, Z, ldz, rows, grid, s);
-    count_df_launch();
-  } else {
-    static PerDeviceOnce once;
-    once([] {
-      PBS_CUDA(cudaFuncSetAttribute(k_block_update, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    kMaxBlock * kMaxTrial * (int)sizeof(double2)));
-    });
-    const size_t smem = (size_t)p * q * sizeof(double2);
-    k_block_update<<<grid, 256, smem, s>>>(X, q, C, ldc, cgs, Y, ldy, p, Z, ldz, rows);
-  }
+  launch(cand[pick]);
   timer_end(KC_BLOCK_UPDATE, s);
-  PBS_LAUNCHED();
 }
 
 void random_block(double2* X, long ld, long rows, int ncols, uint64_t seed, cudaStream_t s) {

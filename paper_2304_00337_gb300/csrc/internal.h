@@ -4,6 +4,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <functional>
 #include <mutex>
 #include <string>
 #include <utility>
@@ -55,6 +56,7 @@ struct Level {
   double* k3_64 = nullptr;   // per node: 6 entries of the inverse 3x3 patch block, SoA [6][N]
   float* k3_32 = nullptr;
   float2* wdf = nullptr;     // level 0: w = (1/eps) / (h1 h2) as double-float (hi, lo) per cell
+  double wmax = 0;           // level 0: the largest w
   long N() const { return (long)n * m; }
   WtsDF wts_df() const { return WtsDF{wdf, n, m}; }
   long D() const { return 2L * n * m; }
@@ -88,6 +90,7 @@ struct KData {
   float2* edge32 = nullptr;
   double2* node64 = nullptr;   // ngroups factors of P_c (+ a constant-mode term at k = 0), Nc x Nc
   float2* node32 = nullptr;
+  int* d_info = nullptr;       // status of the coarsest factorisations (2 ints)
   std::vector<double> k1, k2;  // host mirror
   std::vector<char> gamma;
   int goff = 0;                // chunk views: column c uses coarsest factors of group (c / cpg + goff) % ngroups
@@ -106,9 +109,13 @@ class DevMem {
   void free(void* p);
   size_t used() const { return used_; }
   size_t budget() const { return budget_; }  // 0 = no cap
+  void set_budget(size_t b) { budget_ = b; }
+  // failure injection: the count-th allocation from now fails with PBS_ENOMEM (0: off)
+  void fail_after(int count) { fail_in_ = count; }
 
  private:
   size_t budget_, used_ = 0;
+  int fail_in_ = 0;
   std::vector<std::pair<void*, size_t>> live_;
 };
 
@@ -145,6 +152,7 @@ void timer_collect();  // after a stream synchronisation
 // every kernel launch of the library is counted (process-wide); launches of kernels
 // that compute in double-float arithmetic are counted a second time on their own
 void count_launch();
+void count_launches(long delta);  // kernels of a replayed CUDA graph
 void count_df_launch();
 bool verbose_enabled();  // PBS_VERBOSE set in the environment (diagnostic traces)
 #define PBS_LAUNCHED()                 \
@@ -152,6 +160,13 @@ bool verbose_enabled();  // PBS_VERBOSE set in the environment (diagnostic trace
     ::pbs::count_launch();             \
     PBS_CUDA(cudaGetLastError());      \
   } while (0)
+
+// ---- launch-configuration autotuner (tune.cu) ------------------------------
+// Index of the fastest of `ncand` candidate configurations for `key`: measured on
+// first use (run(c) launches candidate c on stream s; candidates are idempotent),
+// then remembered for the process and in the tuning cache file.
+int tune_pick(const std::string& key, int ncand, const std::function<void(int)>& run, cudaStream_t s);
+std::string device_tag();  // device name and SM count, for tuning keys
 
 // ---- hierarchy set-up (mg.cu) ---------------------------------------------
 void build_hierarchy(DevMem& mem, Hierarchy& H, const double* d_eps, int coarsest, cudaStream_t s);
@@ -242,6 +257,10 @@ void deflate_constants(const Level& L, double2* X, long ld, int ncols, const int
 // per column: out[2c] = e^* M e, out[2c+1] = (C e)^* W (C e)
 void rayleigh_parts(const Level& L, const double* d_ph, int cpg, const double2* X, long ld, int ncols,
                     double* d_partials, double* d_out, bool dfa, cudaStream_t s);
+// R = A E - lam M E in the mixed policy: FP64 curls, double-float rest, R stored in
+// FP32 (the preconditioner's input); the same norms (level 0 only)
+void residual_mixed(const Level& L, const double* d_ph, int cpg, const double2* E, float2* R, long ld, int ncols,
+                    const double* d_lam, double* d_partials, double* d_out, cudaStream_t s);
 // R = A E - lam M E; per column out[2c] = |R|^2, out[2c+1] = |M E|^2
 void residual(const Level& L, const double* d_ph, int cpg, const double2* E, double2* R, long ld, int ncols,
               const double* d_lam, double* d_partials, double* d_out, cudaStream_t s);
@@ -257,6 +276,12 @@ struct Roles {
 void gram_groups(const Level& L, const double* d_ph, Roles roles, int q, int ngroups, double2* GM, double2* GA,
                  double2* d_partials, long partial_capacity, bool dfa, cudaStream_t s);
 long gram_partials_size(long rows, int q, int ngroups);  // double2 elements
+// The mixed policy's Gram on the tensor cores (gram_tc.cu): the partial sums of
+// gram_groups' double-float kernel for q <= 48, from bf16 slices (Ozaki splitting).
+bool gram_tc_supported(int q);
+bool gram_on_tensor_cores();  // true when the environment sets PBS_GRAM=tc
+void gram_tc(const Level& L, const double* d_ph, Roles roles, int q, int ngroups, int npart, double2* d_partials,
+             cudaStream_t s);
 // Rayleigh-Ritz in coefficient space for ngroups groups: C (q x p per group), theta (p per
 // group), status in d_info[8 g], scratch small_rr_scratch(q) bytes per group; dfa selects
 // double-float (mixed policy) instead of FP64 arithmetic

@@ -676,6 +676,7 @@ void build_hierarchy(DevMem& mem, Hierarchy& H, const double* d_eps, int coarses
   PBS_CUDA(cudaStreamSynchronize(s));
   if (bad) fail(-1, "eps must be finite and positive");
   std::memcpy(&H.winv_max, &wmax, sizeof(double));
+  H.lev[0].wmax = H.winv_max / (H.lev[0].h1 * H.lev[0].h2);
   const Level& C = H.lev[H.nlev - 1];
   if (C.D() > kMaxCoarseEdges) fail(-1, "coarsest level too large for the dense solve (raise coarsest or use sides with more factors of 2)");
 }
@@ -689,21 +690,29 @@ void free_hierarchy(DevMem& mem, Hierarchy& H) {
 void alloc_kdata(DevMem& mem, const Hierarchy& H, KData& K, int ngroups) {
   const Level& C = H.lev[H.nlev - 1];
   const int Dc = (int)C.D(), Nc = (int)C.N();
-  if (K.ngroups == ngroups && K.Dc == Dc && K.d_ph) return;
+  if (K.ngroups == ngroups && K.Dc == Dc && K.d_info) return;
   free_kdata(mem, K);
-  K.ngroups = ngroups;
-  K.Dc = Dc;
-  K.Nc = Nc;
-  K.owner = true;
-  K.d_ph = (double*)mem.alloc(12ull * ngroups * sizeof(double));
-  K.d_gamma = (int*)mem.alloc(3ull * ngroups * sizeof(int));
-  K.edge64 = (double2*)mem.alloc((size_t)ngroups * Dc * Dc * sizeof(double2));
-  K.edge32 = (float2*)mem.alloc((size_t)ngroups * Dc * Dc * sizeof(float2));
-  K.node64 = (double2*)mem.alloc((size_t)ngroups * Nc * Nc * sizeof(double2));
-  K.node32 = (float2*)mem.alloc((size_t)ngroups * Nc * Nc * sizeof(float2));
-  K.k1.assign(ngroups, 0.0);
-  K.k2.assign(ngroups, 0.0);
-  K.gamma.assign(ngroups, 0);
+  KData k;  // filled completely before it replaces K: a failed allocation leaves K empty
+  k.owner = true;
+  try {
+    k.d_ph = (double*)mem.alloc(12ull * ngroups * sizeof(double));
+    k.d_gamma = (int*)mem.alloc(3ull * ngroups * sizeof(int));
+    k.edge64 = (double2*)mem.alloc((size_t)ngroups * Dc * Dc * sizeof(double2));
+    k.edge32 = (float2*)mem.alloc((size_t)ngroups * Dc * Dc * sizeof(float2));
+    k.node64 = (double2*)mem.alloc((size_t)ngroups * Nc * Nc * sizeof(double2));
+    k.node32 = (float2*)mem.alloc((size_t)ngroups * Nc * Nc * sizeof(float2));
+    k.d_info = (int*)mem.alloc(2 * sizeof(int));
+  } catch (...) {
+    free_kdata(mem, k);
+    throw;
+  }
+  k.ngroups = ngroups;
+  k.Dc = Dc;
+  k.Nc = Nc;
+  k.k1.assign(ngroups, 0.0);
+  k.k2.assign(ngroups, 0.0);
+  k.gamma.assign(ngroups, 0);
+  K = k;
 }
 
 void set_group_k(DevMem& mem, const Hierarchy& H, KData& K, int g, double k1, double k2, cudaStream_t s) {
@@ -729,7 +738,7 @@ void set_group_k(DevMem& mem, const Hierarchy& H, KData& K, int g, double k1, do
   double2* n64 = K.node64 + (size_t)g * Nc * Nc;
   float2* n32 = K.node32 + (size_t)g * Nc * Nc;
   const double* gph = K.d_ph + 4 * g;
-  int* d_info = (int*)mem.alloc(2 * sizeof(int));
+  int* d_info = K.d_info;
   PBS_CUDA(cudaMemsetAsync(d_info, 0, 2 * sizeof(int), s));
   k_assemble_edge<<<dim3((Dc + 127) / 128, Dc), 128, 0, s>>>(C.lvl<double>(), C.wts<double>(), H.mu, gph, e64);
   PBS_LAUNCHED();
@@ -743,7 +752,6 @@ void set_group_k(DevMem& mem, const Hierarchy& H, KData& K, int g, double k1, do
   int info[2] = {0, 0};
   PBS_CUDA(cudaMemcpyAsync(info, d_info, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
   PBS_CUDA(cudaStreamSynchronize(s));
-  mem.free(d_info);
   if (info[0] || info[1]) fail(PBS_ENUMERIC, "coarsest-level Cholesky factorisation failed");
 }
 
@@ -758,6 +766,7 @@ KData kdata_view(const KData& K, int g) {
   v.edge32 = K.edge32 + (size_t)g * K.Dc * K.Dc;
   v.node64 = K.node64 + (size_t)g * K.Nc * K.Nc;
   v.node32 = K.node32 + (size_t)g * K.Nc * K.Nc;
+  v.d_info = K.d_info;
   v.k1 = {K.k1[g]};
   v.k2 = {K.k2[g]};
   v.gamma = {K.gamma[g]};
@@ -776,6 +785,7 @@ KData kdata_chunk(const KData& K, int v0) {
   v.edge32 = K.edge32;
   v.node64 = K.node64;
   v.node32 = K.node32;
+  v.d_info = K.d_info;
   v.k1 = K.k1;
   v.k2 = K.k2;
   v.gamma = K.gamma;
@@ -787,7 +797,7 @@ KData kdata_chunk(const KData& K, int v0) {
 void free_kdata(DevMem& mem, KData& K) {
   if (K.owner)
     for (void* p : {(void*)K.d_ph, (void*)K.d_gamma, (void*)K.edge64, (void*)K.edge32, (void*)K.node64,
-                    (void*)K.node32})
+                    (void*)K.node32, (void*)K.d_info})
       if (p) mem.free(p);
   K = KData();
 }

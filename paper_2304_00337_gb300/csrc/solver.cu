@@ -39,6 +39,7 @@ thread_local KernelTimer* g_timer = nullptr;
 static std::atomic<unsigned long long> g_launches{0}, g_df_launches{0};
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void count_launches(long delta) { g_launches.fetch_add((unsigned long long)delta, std::memory_order_relaxed); }
 void count_df_launch() { g_df_launches.fetch_add(1, std::memory_order_relaxed); }
 
 bool verbose_enabled() {
@@ -99,6 +100,7 @@ void check_cuda(cudaError_t e, const char* what) {
 void* DevMem::alloc(size_t bytes) {
   if (bytes == 0) bytes = 16;
   bytes = (bytes + 255) & ~size_t(255);
+  if (fail_in_ > 0 && --fail_in_ == 0) fail(PBS_ENOMEM, "device allocation failed (injected)");
   if (budget_ && used_ + bytes > budget_) fail(PBS_ENOMEM, "device memory budget exceeded");
   void* p = nullptr;
   const cudaError_t e = cudaMalloc(&p, bytes);
@@ -171,6 +173,26 @@ inline unsigned nblocks(long n) { return (unsigned)std::min<long>(std::max<long>
 
 }  // namespace
 
+// CUDA graphs of the iteration's multigrid sequences (projections and the
+// preconditioner), captured on their second occurrence within a solve and replayed
+// afterwards: one graph launch instead of tens of kernel launches per sequence.
+// A graph is keyed by everything its launches depend on (pointers, column counts,
+// cycles, the k = 0 deflation) and lives until the solve ends.
+struct GraphCache {
+  struct Entry {
+    cudaGraphExec_t exec = nullptr;
+    long kernels = 0;  // kernels per replay (for the launch counter)
+  };
+  std::map<std::string, Entry> graphs;
+  std::map<std::string, int> seen;
+  void clear() {
+    for (auto& kv : graphs) cudaGraphExecDestroy(kv.second.exec);
+    graphs.clear();
+    seen.clear();
+  }
+  ~GraphCache() { clear(); }
+};
+
 // Batched solver workspace: G groups (Bloch vectors in flight) of p columns.
 // The iteration's four blocks of G p columns live in one allocation of four
 // quarters: [E P | W R] or [W R | E P] (`half` says which).  E and P stay adjacent
@@ -194,6 +216,7 @@ struct Work {
   MgWork<float> e32, n32;
   MgWork<double> e64, n64;
   std::vector<void*> allocs;
+  std::shared_ptr<GraphCache> graphs = std::make_shared<GraphCache>();
   long block() const { return (long)G * p * D; }
   double2* E() const { return blk + 2L * half * block(); }
   double2* P() const { return E() + block(); }
@@ -214,23 +237,46 @@ struct Job {
   int n = 0, m = 0, nk = 0;
   std::vector<double> eps, ks;
   pbs_opts o{};
-  std::chrono::steady_clock::time_point t_submit, t_done;
+  double est = 0;     // admission estimate, device bytes
+  uint64_t gkey = 0;  // geometry key (permittivity, cell, mesh, mu, coarsest): slot affinity
+  std::chrono::steady_clock::time_point t_submit, t_start, t_done;
   std::vector<double> lam, res;
   std::vector<int> iters;
   int status = PBS_OK;
   std::string err;
-  bool done = false;
+  bool started = false, done = false;
+  int bypassed = 0;                // later jobs admitted before this one while it waited at the head
+  std::atomic<bool> cancel{false};  // checked by the solver between iterations
 };
 
-// First-in first-out job queue of a context and the host thread that runs it.
+// A serving slot: a child engine (own stream, resident hierarchy and workspace)
+// driven by its own host thread, so that the jobs of different slots overlap on
+// the device.
+struct Slot {
+  pbs_ctx* eng = nullptr;
+  std::thread th;
+  std::shared_ptr<Job> job;  // running job, null when idle
+  double held = 0;           // bytes charged: the running job's estimate, or what stays resident when idle
+  uint64_t resident = 0;     // geometry key of the resident hierarchy (0: none)
+  bool evict = false;        // asked to free its resident hierarchy and workspace
+};
+
+// Continuous batching of path jobs: a queue in submission order and `nslots`
+// slots.  A slot takes the first queued job that fits the memory the running jobs
+// and the idle slots' resident data leave free (preferring, among the first few,
+// a job whose geometry is resident in it); a job at the head that does not fit
+// waits (idle slots are asked to free what they keep resident) and is passed by
+// later jobs at most 2 nslots times.
 struct Server {
   std::mutex m;
   std::condition_variable cv_work, cv_done;
   std::deque<std::shared_ptr<Job>> queue;
   std::map<uint64_t, std::shared_ptr<Job>> jobs;
   uint64_t next_id = 1;
-  std::thread worker;
-  bool stop = false;
+  int nslots = 4;
+  std::vector<std::unique_ptr<Slot>> slots;
+  bool started = false, stop = false;
+  double cap = 0;  // device bytes the jobs may hold together
 };
 
 }  // namespace pbs
@@ -250,6 +296,8 @@ struct pbs_ctx {
   KernelTimer timer;
   double* d_eps_in = nullptr;  // device copy of the latest host permittivity array
   long d_eps_len = 0;
+  const std::atomic<bool>* cancel = nullptr;  // set while a serving slot runs a job
+  std::chrono::steady_clock::time_point t_created = std::chrono::steady_clock::now();
   explicit pbs_ctx(size_t budget) : mem(budget) {}
 };
 
@@ -278,13 +326,14 @@ struct TimerScope {
   }
 };
 
+// Frees the solver workspace, also one whose allocation failed part of the way.
 void free_work(pbs_ctx* ctx) {
-  if (!ctx->have_w) return;
   for (void* p : ctx->W.allocs) ctx->mem.free(p);
   free_mg_work(ctx->mem, ctx->W.e32);
   free_mg_work(ctx->mem, ctx->W.n32);
   free_mg_work(ctx->mem, ctx->W.e64);
   free_mg_work(ctx->mem, ctx->W.n64);
+  ctx->W.graphs->clear();
   ctx->W = Work();
   ctx->have_w = false;
 }
@@ -332,7 +381,13 @@ void ensure_hierarchy(pbs_ctx* ctx, double a, double b, int n, int m, const doub
   ctx->H.n = n;
   ctx->H.m = m;
   ctx->H.mu = mu;
-  build_hierarchy(ctx->mem, ctx->H, d_eps, coarsest, ctx->stream);
+  try {
+    build_hierarchy(ctx->mem, ctx->H, d_eps, coarsest, ctx->stream);
+  } catch (...) {
+    free_hierarchy(ctx->mem, ctx->H);  // what was allocated before the failure
+    ctx->H = Hierarchy();
+    throw;
+  }
   ctx->H.key = key;
   ctx->coarsest = coarsest;
   ctx->have_h = true;
@@ -509,6 +564,65 @@ template <class F> void for_chunks(pbs_ctx* ctx, const KData& K, int ncols, int 
   }
 }
 
+bool graphs_enabled() {
+  static const bool on = [] {
+    const char* v = std::getenv("PBS_GRAPHS");
+    return !(v && std::strcmp(v, "0") == 0);
+  }();
+  return on;
+}
+
+// Runs f (launches on stream s only, no host synchronisation) directly the first
+// time `key` is met, captured into a CUDA graph and replayed from the second time
+// on.  Kernel timing (pbs_profile_enable) of a class launched inside the sequences
+// times launches one by one, so then f runs directly.
+template <class F> void run_graph(pbs_ctx* ctx, const std::string& key, cudaStream_t s, F&& f) {
+  GraphCache& gc = *ctx->W.graphs;
+  constexpr unsigned kInside = (1u << KC_EDGE_SMOOTH) | (1u << KC_NODE_SMOOTH) | (1u << KC_LIFT_ADJ_MASK) |
+                               (1u << KC_EDGE_APPLY) | (1u << KC_EDGE_TAIL) | (1u << KC_NODE_TAIL);
+  if (!graphs_enabled() || (g_timer != nullptr && (g_timer->mask & kInside))) {
+    f();
+    return;
+  }
+  auto it = gc.graphs.find(key);
+  if (it == gc.graphs.end()) {
+    if (gc.seen[key]++ == 0) {
+      f();  // first occurrence: lazy set-up (kernel attributes) happens outside any capture
+      return;
+    }
+    const unsigned long long before = g_launches.load();
+    PBS_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    try {
+      f();
+    } catch (...) {
+      cudaGraph_t broken = nullptr;
+      cudaStreamEndCapture(s, &broken);
+      if (broken) cudaGraphDestroy(broken);
+      cudaGetLastError();
+      throw;
+    }
+    cudaGraph_t graph = nullptr;
+    PBS_CUDA(cudaStreamEndCapture(s, &graph));
+    GraphCache::Entry e;
+    e.kernels = (long)(g_launches.load() - before);
+    count_launches(-e.kernels);  // nothing ran yet: the replays count
+    const cudaError_t ie = cudaGraphInstantiate(&e.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    PBS_CUDA(ie);
+    it = gc.graphs.emplace(key, e).first;
+  }
+  PBS_CUDA(cudaGraphLaunch(it->second.exec, s));
+  count_launches(it->second.kernels);
+}
+
+std::string graph_key(const char* what, const void* x, const void* y, int ncols, int cpg, int cycles, const KData& K,
+                      int prec) {
+  char buf[256];
+  std::snprintf(buf, sizeof buf, "%s|%p|%p|%d|%d|%d|%p|%d|%d|%d", what, x, y, ncols, cpg, cycles, (const void*)K.d_ph,
+                K.goff, K.any_gamma() ? 1 : 0, prec);
+  return buf;
+}
+
 void project_dispatch(pbs_ctx* ctx, const pbs_opts& o, const KData& K, double2* X, int ncols, int cpg, int cycles,
                       cudaStream_t s) {
   if (cycles <= 0) cycles = o.nodal_cycles;
@@ -519,16 +633,19 @@ void project_dispatch(pbs_ctx* ctx, const pbs_opts& o, const KData& K, double2* 
   });
 }
 
-// W = B R (one edge V-cycle per column)
+// W = B R (one edge V-cycle per column); under the mixed policy `r32` (when given)
+// holds R in FP32 already (the mixed residual kernel's output), else R is converted
 void precondition_dispatch(pbs_ctx* ctx, const pbs_opts& o, const KData& K, const double2* R, double2* Wout, int ncols,
-                           int cpg, cudaStream_t s) {
+                           int cpg, cudaStream_t s, const float2* r32 = nullptr) {
   Work& W = ctx->W;
   for_chunks(ctx, K, ncols, cpg, [&](int c0, int nc, const KData& Kc) {
     const double2* Rc = R + (long)c0 * W.D;
     double2* Wc = Wout + (long)c0 * W.D;
     if (o.precision == PBS_MIXED) {
-      convert_d2f(Rc, W.r32, W.D * nc, s);
-      edge_vcycle<float>(ctx->H, Kc, W.e32, 0, W.r32, W.w32, W.D, nc, cpg, o.nu_pre, o.nu_post, s);
+      const float2* in = W.r32;
+      if (r32) in = r32 + (long)c0 * W.D;
+      else convert_d2f(Rc, W.r32, W.D * nc, s);
+      edge_vcycle<float>(ctx->H, Kc, W.e32, 0, in, W.w32, W.D, nc, cpg, o.nu_pre, o.nu_post, s);
       convert_f2d(W.w32, Wc, W.D * nc, s);
     } else {
       edge_vcycle<double>(ctx->H, Kc, W.e64, 0, Rc, Wc, W.D, nc, cpg, o.nu_pre, o.nu_post, s);
@@ -694,6 +811,8 @@ PathResult solve_chains(pbs_ctx* ctx, const pbs_opts& o, int nk, const double* k
 PathResult solve_chain_list(pbs_ctx* ctx, const pbs_opts& o, int nk, const double* ks, const std::vector<Chain>& chains,
                             int Gwant, const pbs_c64* init, const double2* dev_init, double2* store,
                             const VecOut* vout) {
+  for (long t = 0; t < 2L * nk; ++t)
+    if (!std::isfinite(ks[t])) fail(PBS_EINVAL, "Bloch vectors must be finite");
   cudaStream_t s = ctx->stream;
   const bool dfa = o.precision == PBS_MIXED;
   const int p = o.block, G = std::max(1, std::min<int>(Gwant, (int)chains.size()));
@@ -705,6 +824,7 @@ PathResult solve_chain_list(pbs_ctx* ctx, const pbs_opts& o, int nk, const doubl
   chained = chained && o.extrap_depth > 0;
   ensure_work(ctx, p, G, o.precision, chained ? (long)o.extrap_depth * G * p : 0);
   Work& W = ctx->W;
+  W.graphs->clear();  // graphs hold pointers of this solve's tables only
   const Level& L0 = ctx->H.lev[0];
   const long D = W.D, Gp = (long)G * p;
   const double mu = ctx->H.mu;
@@ -751,17 +871,23 @@ PathResult solve_chain_list(pbs_ctx* ctx, const pbs_opts& o, int nk, const doubl
     bool any = false;
     for (auto& x : gr) any = any || x.active;
     if (!any) break;
+    if (ctx->cancel && ctx->cancel->load(std::memory_order_relaxed)) fail(PBS_ECANCELED, "job cancelled");
     int cyc = o.nodal_cycles;
     for (auto& x : gr)
       if (x.active) cyc = std::max(cyc, projection_cycles(o, x.theta_max, mu));
     // Rayleigh-Ritz prefers combinations whose leftover gradient lowers the quotient,
     // so E and P are cleaned before the residual (Section 4, null-space elimination)
-    if (round > 0) project_dispatch(ctx, o, ctx->K, W.E(), 2 * (int)Gp, p, cyc, s);
+    if (round > 0)
+      run_graph(ctx, graph_key("project", W.E(), nullptr, 2 * (int)Gp, p, cyc, ctx->K, o.precision), s,
+                [&] { project_dispatch(ctx, o, ctx->K, W.E(), 2 * (int)Gp, p, cyc, s); });
     // Rayleigh quotients in factored form, then the FP64 residual
     rayleigh_parts(L0, ctx->K.d_ph, p, W.E(), D, (int)Gp, W.parts, W.rq, dfa, s);
     k_rq<<<nblocks(Gp), 256, 0, s>>>(W.rq, W.lam, (int)Gp);
     PBS_LAUNCHED();
-    residual(L0, ctx->K.d_ph, p, W.E(), W.R(), D, (int)Gp, W.lam, W.parts, W.norms, s);
+    // mixed: R in FP32 over the first half of the R block (the preconditioner's input)
+    float2* R32 = reinterpret_cast<float2*>(W.R());
+    if (dfa) residual_mixed(L0, ctx->K.d_ph, p, W.E(), R32, D, (int)Gp, W.lam, W.parts, W.norms, s);
+    else residual(L0, ctx->K.d_ph, p, W.E(), W.R(), D, (int)Gp, W.lam, W.parts, W.norms, s);
     PBS_CUDA(cudaMemcpyAsync(h_norms.data(), W.norms, 2 * Gp * sizeof(double), cudaMemcpyDeviceToHost, s));
     PBS_CUDA(cudaMemcpyAsync(h_lam.data(), W.lam, Gp * sizeof(double), cudaMemcpyDeviceToHost, s));
     PBS_CUDA(cudaStreamSynchronize(s));
@@ -866,12 +992,14 @@ PathResult solve_chain_list(pbs_ctx* ctx, const pbs_opts& o, int nk, const doubl
     if (any_cont) {
       // W = B R, projected; Gram matrices of [E, P, W] per group; Rayleigh-Ritz; update
       double2* Wd = W.W();
-      precondition_dispatch(ctx, o, ctx->K, W.R(), Wd, (int)Gp, p, s);
+      run_graph(ctx, graph_key("precondition", W.R(), Wd, (int)Gp, p, 0, ctx->K, o.precision), s,
+                [&] { precondition_dispatch(ctx, o, ctx->K, W.R(), Wd, (int)Gp, p, s, dfa ? R32 : nullptr); });
       if (o.span == 1) {  // PINVIT (Algorithm 1): the trial block is E_hat = E - B R alone
         k_sub_from<<<nblocks(D * Gp), 256, 0, s>>>(W.E(), Wd, D * Gp);
         PBS_LAUNCHED();
       }
-      project_dispatch(ctx, o, ctx->K, Wd, (int)Gp, p, cyc, s);
+      run_graph(ctx, graph_key("project", Wd, nullptr, (int)Gp, p, cyc, ctx->K, o.precision), s,
+                [&] { project_dispatch(ctx, o, ctx->K, Wd, (int)Gp, p, cyc, s); });
       // trial block per group: [E, P, W] (span 3; P = 0 until a search direction
       // exists, and always for span 2, so its columns are dropped) or [E_hat] (span 1)
       const Roles trial = o.span == 1 ? Roles{{Wd, Wd, Wd}, p, D} : Roles{{W.E(), W.P(), W.W()}, p, D};
@@ -1021,41 +1149,147 @@ double job_bytes(int n, int m, const pbs_opts& o, int nk, size_t budget) {
   return hb + kd + wb;
 }
 
-// Host thread of a context's job queue: runs each job as pbs_solve_path would,
-// under the context lock, and records its results and completion time.
-void serve(pbs_ctx* ctx) {
+// Frees what an idle engine keeps resident (workspace, hierarchy, coarsest factors).
+void release_engine(pbs_ctx* e) {
+  std::lock_guard<std::mutex> g(e->gpu_mu);
+  run_guarded_impl([&] {
+    DeviceGuard dg(e->device);
+    PBS_CUDA(cudaStreamSynchronize(e->stream));
+    free_work(e);
+    if (e->have_h) free_hierarchy(e->mem, e->H);
+    e->have_h = false;
+    e->H = Hierarchy();
+    free_kdata(e->mem, e->K);
+  });
+}
+
+// Next job for slot `me` (called with the server lock held); null when none fits now.
+std::shared_ptr<Job> pick_job(Server& sv, Slot* me) {
+  if (sv.queue.empty()) return nullptr;
+  double others = 0.0, idle_resident = 0.0;
+  for (auto& sl : sv.slots)
+    if (sl.get() != me) {
+      others += sl->held;
+      if (!sl->job) idle_resident += sl->held;
+    }
+  auto fits = [&](const Job& j) { return others + j.est <= sv.cap; };
+  const size_t window = std::min<size_t>(sv.queue.size(), 2 * (size_t)sv.nslots);
+  std::shared_ptr<Job>& head = sv.queue.front();
+  const bool head_only = head->bypassed >= 2 * sv.nslots;
+  long pick = -1;
+  if (fits(*head)) {
+    pick = 0;
+    // a job whose geometry is resident here saves a hierarchy build
+    if (!head_only && head->gkey != me->resident)
+      for (size_t i = 1; i < window; ++i)
+        if (sv.queue[i]->gkey == me->resident && me->resident != 0 && fits(*sv.queue[i])) {
+          pick = (long)i;
+          break;
+        }
+  } else {
+    // the head waits for memory: idle slots give up what they keep resident
+    if (others - idle_resident + head->est <= sv.cap)
+      for (auto& sl : sv.slots)
+        if (sl.get() != me && !sl->job && sl->held > 0) sl->evict = true;
+    if (!head_only)
+      for (size_t i = 1; i < window; ++i)
+        if (fits(*sv.queue[i])) {
+          pick = (long)i;
+          break;
+        }
+  }
+  if (pick < 0) return nullptr;
+  std::shared_ptr<Job> j = sv.queue[pick];
+  if (pick > 0) head->bypassed += 1;
+  sv.queue.erase(sv.queue.begin() + pick);
+  return j;
+}
+
+// Host thread of one serving slot: runs jobs on the slot's engine as pbs_solve_path
+// would and records their results and times.
+void slot_loop(pbs_ctx* ctx, Slot* me) {
   cudaSetDevice(ctx->device);
   Server& sv = ctx->srv;
+  std::unique_lock<std::mutex> lk(sv.m);
   for (;;) {
-    std::shared_ptr<Job> j;
-    {
-      std::unique_lock<std::mutex> lk(sv.m);
-      sv.cv_work.wait(lk, [&] { return sv.stop || !sv.queue.empty(); });
-      if (sv.stop) return;
-      j = sv.queue.front();
-      sv.queue.pop_front();
+    if (sv.stop) return;
+    if (me->evict) {
+      me->evict = false;
+      if (me->held > 0) {
+        lk.unlock();
+        release_engine(me->eng);
+        lk.lock();
+        me->held = (double)me->eng->mem.used();
+        me->resident = 0;
+        sv.cv_work.notify_all();
+      }
+      continue;
     }
+    std::shared_ptr<Job> j = pick_job(sv, me);
+    if (!j) {
+      sv.cv_work.wait(lk);
+      continue;
+    }
+    me->job = j;
+    me->held = std::max(j->est, (double)me->eng->mem.used());
+    j->started = true;
+    j->t_start = std::chrono::steady_clock::now();
+    if (!sv.queue.empty()) sv.cv_work.notify_all();  // another slot may take the next job
+    lk.unlock();
+    pbs_ctx* e = me->eng;
     int status = PBS_OK;
     const int rc = run_guarded_impl([&] {
-      std::lock_guard<std::mutex> ctx_lock(ctx->gpu_mu);
-      TimerScope ts(ctx);
+      std::lock_guard<std::mutex> g(e->gpu_mu);
+      DeviceGuard dg(e->device);
+      TimerScope ts(e);
+      e->cancel = &j->cancel;
+      struct Reset {
+        pbs_ctx* e;
+        ~Reset() { e->cancel = nullptr; }
+      } reset{e};
       const pbs_geom geom{j->a, j->b, j->n, j->m, j->eps.data()};
-      ensure_hierarchy_host(ctx, &geom, effective_mu(j->o, j->a, j->b), j->o.coarsest);
-      const PathResult r = solve_chains(ctx, j->o, j->nk, j->ks.data(), j->o.kbatch, nullptr);
+      ensure_hierarchy_host(e, &geom, effective_mu(j->o, j->a, j->b), j->o.coarsest);
+      const PathResult r = solve_chains(e, j->o, j->nk, j->ks.data(), j->o.kbatch, nullptr);
       j->lam = r.lam;
       j->res = r.res;
       j->iters = r.iters;
       if (!r.all_converged) status = PBS_ENOCONV;
     });
-    {
-      std::lock_guard<std::mutex> lk(sv.m);
-      j->status = rc != PBS_OK ? rc : status;
-      if (rc != PBS_OK) j->err = g_last_error;
-      j->t_done = std::chrono::steady_clock::now();
-      j->done = true;
-    }
+    const std::string err = g_last_error;
+    lk.lock();
+    j->status = rc != PBS_OK ? rc : status;
+    if (rc != PBS_OK) j->err = err;
+    j->t_done = std::chrono::steady_clock::now();
+    j->done = true;
+    me->job.reset();
+    me->held = (double)e->mem.used();
+    me->resident = (rc == PBS_OK && e->have_h) ? j->gkey : 0;
     sv.cv_done.notify_all();
+    sv.cv_work.notify_all();
   }
+}
+
+// Starts the slots of a context's server (first submission).
+void start_server(pbs_ctx* ctx) {
+  Server& sv = ctx->srv;
+  if (sv.started) return;
+  if (sv.cap <= 0) {
+    DeviceGuard g(ctx->device);
+    size_t fr = 0, tot = 0;
+    PBS_CUDA(cudaMemGetInfo(&fr, &tot));
+    sv.cap = ctx->mem.budget() > 0 ? (double)ctx->mem.budget() : 0.9 * (double)fr;
+  }
+  for (int i = 0; i < sv.nslots; ++i) {
+    auto sl = std::make_unique<Slot>();
+    pbs_ctx* e = nullptr;
+    const int rc = pbs_create(&e, ctx->device, 0);
+    if (rc != PBS_OK) fail(rc, "serving slot: " + std::string(pbs_last_error()));
+    e->timer.mask = 0;
+    sl->eng = e;
+    sv.slots.push_back(std::move(sl));
+  }
+  for (auto& sl : sv.slots) sl->th = std::thread(slot_loop, ctx, sl.get());
+  sv.started = true;
 }
 }  // namespace
 
@@ -1089,6 +1323,7 @@ const char* pbs_strerror(int status) {
     case PBS_ENUMERIC: return "numerical breakdown";
     case PBS_ETIMEOUT: return "device wait timed out";
     case PBS_ECUDA: return "CUDA error";
+    case PBS_ECANCELED: return "job cancelled";
     default: return "unknown status";
   }
 }
@@ -1137,12 +1372,17 @@ int pbs_create(pbs_ctx** ctx, int device, size_t hbm_budget_bytes) {
 int pbs_destroy(pbs_ctx* ctx) {
   if (!ctx) return PBS_OK;
   {
-    // the job in progress finishes; queued jobs are dropped
+    // running jobs finish; queued jobs are dropped
     std::lock_guard<std::mutex> lk(ctx->srv.m);
     ctx->srv.stop = true;
   }
   ctx->srv.cv_work.notify_all();
-  if (ctx->srv.worker.joinable()) ctx->srv.worker.join();
+  for (auto& sl : ctx->srv.slots) {
+    if (sl->th.joinable()) sl->th.join();
+    pbs_destroy(sl->eng);
+    sl->eng = nullptr;
+  }
+  ctx->srv.slots.clear();
   return run_guarded_impl([&] {
     DeviceGuard g(ctx->device);
     cudaStreamSynchronize(ctx->stream);
@@ -1694,17 +1934,10 @@ int pbs_submit(pbs_ctx* ctx, const pbs_geom* geom, const pbs_opts* opts, int nk,
       if (!(geom->eps[t] > 0.0) || !std::isfinite(geom->eps[t])) fail(PBS_EINVAL, "eps must be finite and positive");
     for (long t = 0; t < 2L * nk; ++t)
       if (!std::isfinite(ks[t])) fail(PBS_EINVAL, "k must be finite");
-    // admission: the job must fit the context's budget, or the device
-    const double need = job_bytes(geom->n, geom->m, *opts, nk, ctx->mem.budget());
-    size_t cap = ctx->mem.budget();
-    if (cap == 0) {
-      DeviceGuard g(ctx->device);
-      size_t fr = 0, tot = 0;
-      PBS_CUDA(cudaMemGetInfo(&fr, &tot));
-      cap = (size_t)(0.95 * (double)tot);
-    }
-    if (need > (double)cap) fail(PBS_ENOMEM, "job needs more device memory than the context may use");
+    // admission: a job that alone exceeds what the jobs may hold is refused; others
+    // wait in the queue until the running jobs leave room for them
     auto j = std::make_shared<Job>();
+    j->est = job_bytes(geom->n, geom->m, *opts, nk, 0);
     j->a = geom->a;
     j->b = geom->b;
     j->n = geom->n;
@@ -1713,17 +1946,29 @@ int pbs_submit(pbs_ctx* ctx, const pbs_geom* geom, const pbs_opts* opts, int nk,
     j->eps.assign(geom->eps, geom->eps + N);
     j->ks.assign(ks, ks + 2L * nk);
     j->o = *opts;
+    {
+      const double mu = effective_mu(*opts, geom->a, geom->b);
+      uint64_t key = fnv1a(geom->eps, N * sizeof(double));
+      key = fnv1a(&j->a, sizeof j->a, key);
+      key = fnv1a(&j->b, sizeof j->b, key);
+      key = fnv1a(&j->n, sizeof j->n, key);
+      key = fnv1a(&j->m, sizeof j->m, key);
+      key = fnv1a(&mu, sizeof mu, key);
+      key = fnv1a(&opts->coarsest, sizeof opts->coarsest, key);
+      j->gkey = key | 1;
+    }
     Server& sv = ctx->srv;
     {
       std::lock_guard<std::mutex> lk(sv.m);
       if (sv.stop) fail(PBS_EINVAL, "context is shutting down");
+      start_server(ctx);
+      if (j->est > sv.cap) fail(PBS_ENOMEM, "job needs more device memory than the context may use");
       j->id = sv.next_id++;
       j->t_submit = std::chrono::steady_clock::now();
       sv.jobs[j->id] = j;
       sv.queue.push_back(j);
-      if (!sv.worker.joinable()) sv.worker = std::thread(serve, ctx);
     }
-    sv.cv_work.notify_one();
+    sv.cv_work.notify_all();
     *job_id = j->id;
   });
 }
@@ -1760,6 +2005,77 @@ int pbs_fetch(pbs_ctx* ctx, uint64_t job_id, double* eigvals, double* resid, int
   if (latency_s) *latency_s = std::chrono::duration<double>(j->t_done - j->t_submit).count();
   g_last_error = j->err;
   return j->status;
+}
+
+int pbs_cancel(pbs_ctx* ctx, uint64_t job_id) {
+  if (!ctx) return PBS_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->srv.m);
+  auto it = ctx->srv.jobs.find(job_id);
+  if (it == ctx->srv.jobs.end()) {
+    g_last_error = "unknown job";
+    return PBS_EINVAL;
+  }
+  Job& j = *it->second;
+  if (j.done) return PBS_OK;
+  j.cancel.store(true);
+  if (!j.started) {
+    auto& q = ctx->srv.queue;
+    for (auto qi = q.begin(); qi != q.end(); ++qi)
+      if ((*qi)->id == job_id) {
+        q.erase(qi);
+        break;
+      }
+    j.status = PBS_ECANCELED;
+    j.err = "job cancelled before it started";
+    j.t_start = j.t_done = std::chrono::steady_clock::now();
+    j.done = true;
+    ctx->srv.cv_done.notify_all();
+    ctx->srv.cv_work.notify_all();
+  }
+  return PBS_OK;
+}
+
+int pbs_job_times(pbs_ctx* ctx, uint64_t job_id, double* submit_s, double* start_s, double* done_s) {
+  if (!ctx || !submit_s || !start_s || !done_s) return PBS_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->srv.m);
+  auto it = ctx->srv.jobs.find(job_id);
+  if (it == ctx->srv.jobs.end()) {
+    g_last_error = "unknown job";
+    return PBS_EINVAL;
+  }
+  const Job& j = *it->second;
+  auto rel = [&](std::chrono::steady_clock::time_point t) {
+    return std::chrono::duration<double>(t - ctx->t_created).count();
+  };
+  *submit_s = rel(j.t_submit);
+  *start_s = j.started || j.done ? rel(j.t_start) : -1.0;
+  *done_s = j.done ? rel(j.t_done) : -1.0;
+  return PBS_OK;
+}
+
+int pbs_serve_slots(pbs_ctx* ctx, int slots) {
+  if (!ctx || slots < 1 || slots > 64) return PBS_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->srv.m);
+  if (ctx->srv.started) {
+    g_last_error = "the serving slots are already running";
+    return PBS_EINVAL;
+  }
+  ctx->srv.nslots = slots;
+  return PBS_OK;
+}
+
+int pbs_set_budget(pbs_ctx* ctx, size_t hbm_budget_bytes) {
+  if (!ctx) return PBS_EINVAL;
+  std::lock_guard<std::mutex> g(ctx->gpu_mu);
+  ctx->mem.set_budget(hbm_budget_bytes);
+  return PBS_OK;
+}
+
+int pbs_fail_alloc_after(pbs_ctx* ctx, int count) {
+  if (!ctx || count < 0) return PBS_EINVAL;
+  std::lock_guard<std::mutex> g(ctx->gpu_mu);
+  ctx->mem.fail_after(count);
+  return PBS_OK;
 }
 
 }  // extern "C"

@@ -228,3 +228,23 @@ def test_fp64_policy_has_no_double_float_kernel(ctx):
     # the mixed policy does run double-float kernels (the counter is live)
     ctx.solve_path(geom, dict(nev=8, block=10, precision=pbs.PBS_MIXED, kbatch=4), ks[:4])
     assert pbs.launch_count_df() > df0
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_graph_replays_match_direct_launches(ctx, precision):
+    # the iteration's multigrid sequences are replayed as CUDA graphs; timing a kernel
+    # class launched inside them makes every launch direct: the results agree bit for bit
+    # and the launch counter counts the same kernels either way
+    geom = pbs.Geometry(gi.rod_eps(64, 64))
+    ks = gi.gxmg_path(10)
+    o = dict(nev=6, block=8, kbatch=3, precision=precision)
+    ctx.solve_path(geom, o, ks)  # workspace and tuning outside the comparison
+    l0 = pbs.launch_count()
+    a = ctx.solve_path(geom, o, ks)
+    l1 = pbs.launch_count()
+    ctx.profile_enable("edge_smooth")
+    b = ctx.solve_path(geom, o, ks)
+    l2 = pbs.launch_count()
+    ctx.profile_enable(None)
+    assert all(np.array_equal(x, y) for x, y in zip(a, b))
+    assert l1 - l0 == l2 - l1
