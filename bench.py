@@ -354,7 +354,7 @@ def run_ours(args):
     step(pbs.PBS_MIXED)
     torch.cuda.synchronize(dev)
     classes = ["edge_smooth", "node_smooth", "gram", "small_rr", "residual", "block_update", "lift_adj_mass",
-               "edge_tail", "node_tail"]
+               "edge_tail", "node_tail", "sub_lift", "convert", "node_apply"]
     shares = {c: ctx.profile_read(c) for c in classes}
     ctx.profile_enable(None)
     for _ in range(max(0, args.warmup - 1)):

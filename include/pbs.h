@@ -286,6 +286,8 @@ PBS_API int pbs_rayleigh_ritz(pbs_ctx *ctx, const pbs_geom *geom, const pbs_opts
  * `classes` is "all" or a comma-separated list of "edge_smooth",
  * "node_smooth", "gram", "small_rr", "residual", "block_update",
  * "lift_adj_mass", "edge_apply", "edge_tail", "node_tail", "householder",
+ * "sub_lift" (x - L phi), "convert" (binary64 <-> binary32 copies), "node_apply"
+ * (nodal operator applications and updates of the projection),
  * optionally followed by "/N" to time only every N-th launch
  * of each listed class; NULL or "" switches timing off.  Enabling resets the
  * counters.  pbs_profile_read returns, for one class, the summed device time

@@ -1362,12 +1362,16 @@ inline unsigned blocks_for(long n, int per = 256, unsigned cap = 4096) {
 
 void convert_d2f(const double2* X, float2* Y, long n, cudaStream_t s) {
   if (n <= 0) return;
+  timer_begin(KC_CONVERT, s, 24.0 * n);
   k_d2f<<<blocks_for(n), 256, 0, s>>>(X, Y, n);
+  timer_end(KC_CONVERT, s);
   PBS_LAUNCHED();
 }
 void convert_f2d(const float2* X, double2* Y, long n, cudaStream_t s) {
   if (n <= 0) return;
+  timer_begin(KC_CONVERT, s, 24.0 * n);
   k_f2d<<<blocks_for(n), 256, 0, s>>>(X, Y, n);
+  timer_end(KC_CONVERT, s);
   PBS_LAUNCHED();
 }
 
@@ -1375,7 +1379,10 @@ template <class T>
 void sub_lift(const Level& L, const double* d_ph, int cpg, const cx<T>* Phi, long ldp, double2* X, long ldx, int ncols,
               cudaStream_t s) {
   if (ncols <= 0) return;
+  // read phi, read and write x
+  timer_begin(KC_SUB_LIFT, s, (sizeof(cx<T>) * (double)L.N() + 32.0 * L.D()) * ncols);
   k_sub_lift<T><<<grid2(L.n, L.m, ncols), dim3(kBX, kBY), 0, s>>>(L.n, L.m, d_ph, cpg, Phi, ldp, X, ldx);
+  timer_end(KC_SUB_LIFT, s);
   PBS_LAUNCHED();
 }
 
@@ -1496,13 +1503,14 @@ void gram_groups(const Level& L, const double* d_ph, Roles roles, int q, int ngr
   };
   Variant var[4];
   int nvar = 0;
-  const int kern = dfa ? 1 : 0;
-  var[nvar++] = {kern, np0};
-  var[nvar++] = {kern, 2 * np0};
   if (dfa && gram_tc_supported(q) && gram_on_tensor_cores()) {
+    // offered first: with tuning off (PBS_TUNE=0) the tensor-core kernel runs
     var[nvar++] = {2, np0};
     var[nvar++] = {2, 2 * np0};
   }
+  const int kern = dfa ? 1 : 0;
+  var[nvar++] = {kern, np0};
+  var[nvar++] = {kern, 2 * np0};
   auto fits = [&](const Variant& v) { return (long)ngroups * v.npart * 2 * ne <= partial_capacity; };
   if (!fits(var[0])) fail(PBS_EINVAL, "gram partials buffer too small");
   auto launch = [&](const Variant& v) {

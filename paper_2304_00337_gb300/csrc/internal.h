@@ -127,7 +127,8 @@ int num_levels(int n, int m, int coarsest);
 // flops for arithmetic-bound ones) so the achieved rate can be derived.
 enum KernelClass {
   KC_NONE = 0, KC_EDGE_SMOOTH, KC_NODE_SMOOTH, KC_GRAM, KC_SMALL_RR, KC_RESIDUAL, KC_BLOCK_UPDATE,
-  KC_LIFT_ADJ_MASK, KC_EDGE_APPLY, KC_EDGE_TAIL, KC_NODE_TAIL, KC_HOUSEHOLDER, KC_COUNT
+  KC_LIFT_ADJ_MASK, KC_EDGE_APPLY, KC_EDGE_TAIL, KC_NODE_TAIL, KC_HOUSEHOLDER, KC_SUB_LIFT, KC_CONVERT,
+  KC_NODE_APPLY, KC_COUNT
 };
 struct TimedLaunch {
   int cls;
@@ -279,7 +280,7 @@ long gram_partials_size(long rows, int q, int ngroups);  // double2 elements
 // The mixed policy's Gram on the tensor cores (gram_tc.cu): the partial sums of
 // gram_groups' double-float kernel for q <= 48, from bf16 slices (Ozaki splitting).
 bool gram_tc_supported(int q);
-bool gram_on_tensor_cores();  // true when the environment sets PBS_GRAM=tc
+bool gram_on_tensor_cores();  // true when the environment sets PBS_GRAM=tc (then offered first)
 void gram_tc(const Level& L, const double* d_ph, Roles roles, int q, int ngroups, int npart, double2* d_partials,
              cudaStream_t s);
 // Rayleigh-Ritz in coefficient space for ngroups groups: C (q x p per group), theta (p per

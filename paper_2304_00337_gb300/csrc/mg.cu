@@ -229,6 +229,15 @@ template <class T> struct NRdSm {
   __device__ __forceinline__ cx<T> v(int i, int j) const { return s[(j - ob) * W + (i - oa)]; }
 };
 
+// (u, v) with t = v w + u, 0 <= u < w, for 0 <= t < 2^16 and w >= 1: the float quotient
+// (t + 1/2) / w lies at least 1/(2w) from an integer and is off by at most
+// (t/w) 2^-23 (two roundings), i.e. by at most t 2^-22 <= 1/64 of that distance, so its
+// truncation is exact (an integer division by a run-time w costs ~20 instructions)
+__device__ __forceinline__ void split_index(int t, int w, float inv_w, int& u, int& v) {
+  v = (int)(((float)t + 0.5f) * inv_w);
+  u = t - v * w;
+}
+
 // colour q nodes (global parity (q & 1, q >> 1)) of the region rows/cols [r0, r1) in
 // region coordinates, the region's global origin being (oa, ob)
 template <class T, class F>
@@ -236,7 +245,26 @@ __device__ __forceinline__ void for_colour(int q, int r0, int r1, int oa, int ob
   const int pa = ((q & 1) - oa) & 1, pb = ((q >> 1) - ob) & 1;
   const int a0 = r0 + ((pa - r0) & 1), b0 = r0 + ((pb - r0) & 1);
   const int na = (r1 - a0 + 1) / 2, nb = (r1 - b0 + 1) / 2;
-  for (int t = threadIdx.x; t < na * nb; t += blockDim.x) f(a0 + 2 * (t % na), b0 + 2 * (t / na));
+  const float inv = 1.0f / (float)na;
+  for (int t = threadIdx.x; t < na * nb; t += blockDim.x) {
+    int u, v;
+    split_index(t, na, inv, u, v);
+    f(a0 + 2 * u, b0 + 2 * v);
+  }
+}
+
+// Stage a W x W region of a node field whose element (0,0) is node (oa, ob): direct reads
+// when the region lies inside the level, else through the Bloch extension.
+template <class T>
+__device__ __forceinline__ void stage_region(const cx<T>* __restrict__ f, int oa, int ob, int W, int n, int m,
+                                             const Ph<T>& p, cx<T>* S) {
+  const float inv = 1.0f / (float)W;
+  const bool in = oa >= 0 && ob >= 0 && oa + W <= n && ob + W <= m;
+  for (int t = threadIdx.x; t < W * W; t += blockDim.x) {
+    int u, v;
+    split_index(t, W, inv, u, v);
+    S[t] = in ? f[(long)(ob + v) * n + oa + u] : gread<T>(f, oa + u, ob + v, n, m, p);
+  }
 }
 
 template <class T>
@@ -255,10 +283,8 @@ __global__ void __launch_bounds__(kFineThreads) k_node_down(Lvl<T> L, int nc, in
   const int i0 = blockIdx.x * kFT, j0 = blockIdx.y * kFT, oa = i0 - lo, ob = j0 - lo;
   const Ph<T> p = load_ph<T>(ph, c / cpg);
   const cx<T>* b = B + c * ldb;
-  for (int t = tid; t < W * W; t += nt) {
-    sb[t] = gread<T>(b, oa + t % W, ob + t / W, L.n, L.m, p);
-    sx[t] = czero<T>();
-  }
+  stage_region<T>(b, oa, ob, W, L.n, L.m, p, sb);
+  for (int t = tid; t < W * W; t += nt) sx[t] = czero<T>();
   __syncthreads();
   const NRdSm<T> rs{sx, W, oa, ob};
   for (int it = 0; it < nu; ++it)
@@ -310,13 +336,18 @@ __global__ void __launch_bounds__(kFineThreads) k_node_up(Lvl<T> L, int nc, int 
   const cx<T>* b = B + c * ldb;
   const cx<T>* xs = Xs + c * lds;
   const cx<T>* xc = Xc + c * ldc;
-  for (int t = tid; t < Wc * Wc; t += nt) sc[t] = gread<T>(xc, (oa >> 1) + t % Wc, (ob >> 1) + t / Wc, nc, mc, p);
+  stage_region<T>(xc, oa >> 1, ob >> 1, Wc, nc, mc, p, sc);
+  stage_region<T>(b, oa, ob, W, L.n, L.m, p, sb);
+  stage_region<T>(xs, oa, ob, W, L.n, L.m, p, sx);
   __syncthreads();
   const NRdSm<T> rc{sc, Wc, oa >> 1, ob >> 1};
-  for (int t = tid; t < W * W; t += nt) {
-    const int i = oa + t % W, j = ob + t / W;
-    sb[t] = gread<T>(b, i, j, L.n, L.m, p);
-    sx[t] = gread<T>(xs, i, j, L.n, L.m, p) + prolong_node_at<T>(rc, i, j);
+  {
+    const float inv = 1.0f / (float)W;
+    for (int t = tid; t < W * W; t += nt) {
+      int u, v;
+      split_index(t, W, inv, u, v);
+      sx[t] = sx[t] + prolong_node_at<T>(rc, oa + u, ob + v);
+    }
   }
   __syncthreads();
   const NRdSm<T> rs{sx, W, oa, ob};

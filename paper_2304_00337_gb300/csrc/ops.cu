@@ -204,7 +204,9 @@ template <class T>
 void apply_nodal(const Level& L, const double* d_ph, int cpg, const cx<T>* X, cx<T>* Y, const cx<T>* B, long ld,
                  int ncols, T sP, T sB, cudaStream_t s) {
   if (ncols <= 0) return;
+  timer_begin(KC_NODE_APPLY, s, (B ? 3.0 : 2.0) * sizeof(cx<T>) * L.N() * ncols);  // read x (and b), write y
   k_apply_nodal<T><<<grid2(L.n, L.m, ncols), dim3(kBX, kBY), 0, s>>>(L.lvl<T>(), d_ph, cpg, X, Y, B, ld, sP, sB);
+  timer_end(KC_NODE_APPLY, s);
   PBS_LAUNCHED();
 }
 

@@ -546,7 +546,9 @@ void project(pbs_ctx* ctx, const pbs_opts& o, const KData& K, double2* X, int nc
   for (int c = 1; c < cycles; ++c) {
     apply_nodal<T>(L0, K.d_ph, cpg, phi, res, rhs, N, ncols, T(-1), T(1), s);
     nodal_vcycle<T>(H, K, Bufs<T>::nmg(W), 0, res, dphi, N, ncols, cpg, o.nu_pre, o.nu_post, s);
+    timer_begin(KC_NODE_APPLY, s, 3.0 * sizeof(cx<T>) * N * ncols);
     k_axpy<T><<<nblocks(N * ncols), 256, 0, s>>>(phi, dphi, N * ncols);
+    timer_end(KC_NODE_APPLY, s);
     PBS_LAUNCHED();
   }
   sub_lift<T>(L0, K.d_ph, cpg, phi, N, X, D, ncols, s);
@@ -579,7 +581,8 @@ bool graphs_enabled() {
 template <class F> void run_graph(pbs_ctx* ctx, const std::string& key, cudaStream_t s, F&& f) {
   GraphCache& gc = *ctx->W.graphs;
   constexpr unsigned kInside = (1u << KC_EDGE_SMOOTH) | (1u << KC_NODE_SMOOTH) | (1u << KC_LIFT_ADJ_MASK) |
-                               (1u << KC_EDGE_APPLY) | (1u << KC_EDGE_TAIL) | (1u << KC_NODE_TAIL);
+                               (1u << KC_EDGE_APPLY) | (1u << KC_EDGE_TAIL) | (1u << KC_NODE_TAIL) |
+                               (1u << KC_SUB_LIFT) | (1u << KC_CONVERT) | (1u << KC_NODE_APPLY);
   if (!graphs_enabled() || (g_timer != nullptr && (g_timer->mask & kInside))) {
     f();
     return;
@@ -762,6 +765,62 @@ void init_group(pbs_ctx* ctx, const pbs_opts& o, Group& gr, int g, const pbs_c64
   gr.need_init = false;
 }
 
+// Smoothed random starts of every group at once (the groups' first Bloch vectors at the
+// start of a solve): the steps of init_group's random branch, each one launch over all
+// G groups (columns of group g at g p, cpg = p), with the W, R and P quarters of the
+// block as scratch.  E ends with the groups' start blocks, P zeroed.
+void rr_groups(pbs_ctx* ctx, const double2* S, int p, double2* dst, bool dfa, std::vector<double>& theta_max,
+               cudaStream_t s) {
+  Work& W = ctx->W;
+  const int G = W.G;
+  const Level& L0 = ctx->H.lev[0];
+  const Roles R{{S, S, S}, p, W.D};
+  gram_groups(L0, ctx->K.d_ph, R, p, G, W.GM, W.GA, W.gpart, W.gpart_cap, dfa, s);
+  small_rr(W.GM, W.GA, p, p, W.C, W.theta, W.rr_scr, W.info, G, dfa, s);
+  std::vector<int> info(8 * G);
+  std::vector<double> th((size_t)G * p);
+  PBS_CUDA(cudaMemcpyAsync(info.data(), W.info, sizeof(int) * 8 * G, cudaMemcpyDeviceToHost, s));
+  PBS_CUDA(cudaMemcpyAsync(th.data(), W.theta, sizeof(double) * G * p, cudaMemcpyDeviceToHost, s));
+  PBS_CUDA(cudaStreamSynchronize(s));
+  for (int g = 0; g < G; ++g) {
+    if (info[8 * g] != 0)
+      fail(PBS_ENUMERIC, info[8 * g] == -2 ? "non-finite Gram matrix"
+                                           : info[8 * g] == -3 ? "Rayleigh-Ritz breakdown" : "trial space lost rank");
+    double tm = 0.0;
+    for (int j = 0; j < p; ++j) tm = std::max(tm, std::fabs(th[(size_t)g * p + j]));
+    theta_max[g] = tm;
+  }
+  block_update(R, p, W.C, p, (long)p * p, dst, W.D, p, nullptr, 0, W.D, G, false, s);
+}
+
+void init_random_all(pbs_ctx* ctx, const pbs_opts& o, std::vector<Group>& gr, cudaStream_t s) {
+  Work& W = ctx->W;
+  const int p = o.block, G = W.G;
+  const long D = W.D;
+  const bool dfa = o.precision == PBS_MIXED;
+  double2* X0 = W.W();  // G p columns each
+  double2* X1 = W.R();
+  double2* Y = W.P();
+  for (int g = 0; g < G; ++g) random_block(X0 + (long)g * p * D, D, D, p, o.seed, s);
+  const int cyc = projection_cycles(o, 1e300, ctx->H.mu);
+  std::vector<double> tm(G, 0.0);
+  project_dispatch(ctx, o, ctx->K, X0, G * p, p, cyc, s);
+  rr_groups(ctx, X0, p, X1, dfa, tm, s);
+  for (int step = 0; step < 2; ++step) {
+    apply_edge<double>(ctx->H.lev[0], ctx->K.d_ph, p, X1, Y, nullptr, D, G * p, 0.0, 1.0, 0.0, nullptr, 0.0, s);
+    precondition_dispatch(ctx, o, ctx->K, Y, X0, G * p, p, s);
+    project_dispatch(ctx, o, ctx->K, X0, G * p, p, cyc, s);
+    rr_groups(ctx, X0, p, step == 1 ? W.E() : X1, dfa, tm, s);
+  }
+  PBS_CUDA(cudaMemsetAsync(W.P(), 0, sizeof(double2) * D * G * p, s));
+  for (int g = 0; g < G; ++g) {
+    gr[g].theta_max = tm[g];
+    gr[g].it = 0;
+    gr[g].have_p = false;
+    gr[g].need_init = false;
+  }
+}
+
 struct PathResult {
   std::vector<double> lam, res;  // nk x nev
   std::vector<int> iters;
@@ -861,8 +920,14 @@ PathResult solve_chain_list(pbs_ctx* ctx, const pbs_opts& o, int nk, const doubl
   // smoothed random start
   const double2* first = dev_init;
   if (!first && !init && o.start == PBS_START_NESTED) first = nested_blocks(ctx, o, G, kfirst);
-  for (int g = 0; g < G; ++g)
-    init_group(ctx, o, gr[g], g, g == 0 ? init : nullptr, s, first ? first + (long)g * p * D : nullptr);
+  bool all_random = !first && !init;
+  for (int g = 0; g < G && all_random; ++g) all_random = gr[g].nhist == 0;
+  if (all_random && G > 1) {
+    init_random_all(ctx, o, gr, s);  // every group from a smoothed random start, batched
+  } else {
+    for (int g = 0; g < G; ++g)
+      init_group(ctx, o, gr[g], g, g == 0 ? init : nullptr, s, first ? first + (long)g * p * D : nullptr);
+  }
   std::vector<double> h_norms(2 * Gp), h_lam(Gp);
   const double lam_max = lambda_max_bound(ctx->H);
   std::vector<int> h_info(8 * G);
@@ -1765,7 +1830,7 @@ int pbs_rayleigh_ritz(pbs_ctx* ctx, const pbs_geom* geom, const pbs_opts* opts, 
 
 static const char* kClassNames[KC_COUNT] = {"", "edge_smooth", "node_smooth", "gram", "small_rr", "residual",
                                              "block_update", "lift_adj_mass", "edge_apply", "edge_tail",
-                                             "node_tail", "householder"};
+                                             "node_tail", "householder", "sub_lift", "convert", "node_apply"};
 
 static int class_of(const char* name) {
   for (int c = 1; c < KC_COUNT; ++c)

@@ -263,6 +263,22 @@ def test_gram_matches_oracle(ctx, a, b, n, m, k, q, precision):
     assert np.array_equal(gm, gm.conj().T) and np.array_equal(ga, ga.conj().T)
 
 
+def test_tensor_core_gram_in_a_child_process():
+    # the tensor-core Gram (bf16 slices, opt-in) is selected per process: a child process with
+    # PBS_GRAM=tc and tuning off runs the Gram parity cases above on it, and the mixed 64 x 64
+    # rod path against the oracle's stored values with it inside the iteration
+    import os
+    import subprocess
+    import sys
+    here = os.path.dirname(os.path.abspath(__file__))
+    env = dict(os.environ, PBS_GRAM="tc", PBS_TUNE="0")
+    r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-p", "no:cacheprovider",
+                        os.path.join(here, "test_gpu_ops.py") + "::test_gram_matches_oracle",
+                        os.path.join(here, "test_gpu_eigen.py") + "::test_rod64_path_with_extrapolation"],
+                       env=env, capture_output=True, text=True, timeout=900)
+    assert r.returncode == 0, r.stdout[-3000:] + r.stderr[-2000:]
+
+
 @pytest.mark.parametrize("precision", [pbs.PBS_FP64, pbs.PBS_MIXED])
 @pytest.mark.parametrize("k", [(0.3, 0.1), (0.0, 0.0)])
 def test_rayleigh_ritz_and_extrapolation(ctx, k, precision):
