@@ -561,14 +561,14 @@ __device__ __forceinline__ void mac_conj(acc2& re, acc2& im, const dcx& a, const
 
 template <int P, int TS>
 __global__ void __launch_bounds__(256, 3) k_gram_df(Lvl<df> L, WtsDF w, const double* ph, Roles roles, int q, int qp,
-                                                 int rows, double2* __restrict__ part, int npart) {
+                                                 int lds, int rows, double2* __restrict__ part, int npart) {
   extern __shared__ float4 smf[];
-  dcx* sx = reinterpret_cast<dcx*>(smf);  // [rows][qp] each
-  dcx* sy = sx + rows * qp;
-  dcx* mx = sy + rows * qp;
-  dcx* my = mx + rows * qp;
-  dcx* cc = my + rows * qp;
-  dcx* cw = cc + rows * qp;
+  dcx* sx = reinterpret_cast<dcx*>(smf);  // [rows][lds] each, columns qp .. lds-1 unused
+  dcx* sy = sx + rows * lds;
+  dcx* mx = sy + rows * lds;
+  dcx* my = mx + rows * lds;
+  dcx* cc = my + rows * lds;
+  dcx* cw = cc + rows * lds;
   const int g = blockIdx.y;
   const int tid = threadIdx.x;
   const int T3 = qp / TS, ntile = T3 * (T3 + 1) / 2;
@@ -583,7 +583,7 @@ __global__ void __launch_bounds__(256, 3) k_gram_df(Lvl<df> L, WtsDF w, const do
   }
   const dcx z = dcx_make(df_zero(), df_zero());
   for (int t = tid; t < rows * (qp - q); t += blockDim.x) {
-    const int e = (t / (qp - q)) * qp + q + t % (qp - q);
+    const int e = (t / (qp - q)) * lds + q + t % (qp - q);
     sx[e] = z; sy[e] = z; mx[e] = z; my[e] = z; cc[e] = z; cw[e] = z;
   }
   acc2 mre[TS * TS], mim[TS * TS], are[TS * TS], aim[TS * TS];
@@ -611,7 +611,7 @@ __global__ void __launch_bounds__(256, 3) k_gram_df(Lvl<df> L, WtsDF w, const do
         vc = curl_at<df>(rd, i, j);
         vcw = w(i, j) * vc;
       }
-      const int e = rr * qp + col;
+      const int e = rr * lds + col;
       sx[e] = vx; sy[e] = vy; mx[e] = vmx; my[e] = vmy; cc[e] = vc; cw[e] = vcw;
     }
     __syncthreads();
@@ -619,7 +619,7 @@ __global__ void __launch_bounds__(256, 3) k_gram_df(Lvl<df> L, WtsDF w, const do
       // the M sums take two row streams per node (x and y edges), the A sums one
       // (curls); the streams of a matrix are consecutive rows of one loop
       for (int rr = phase; rr < rows; rr += P) {
-        const int ra = rr * qp + TS * I, rb = rr * qp + TS * J;
+        const int ra = rr * lds + TS * I, rb = rr * lds + TS * J;
 #pragma unroll 1
         for (int st = 0; st < 2; ++st) {
           const dcx* A = st == 0 ? sx : sy;
@@ -1232,10 +1232,13 @@ __global__ void __launch_bounds__(kRRThreads) k_small_rr(const double2* __restri
 
 // Y[:, j] = sum_i X[:, i] C[i, j] (+ Z[:, j]) for group blockIdx.y: trial column i
 // of the group at role_col(X, g, i); output column j at Y + (g p + j) ldy;
-// C of group g at C + g cgs (column-major, leading dimension ldc).
-__global__ void __launch_bounds__(256) k_block_update(Roles X, int q, const double2* __restrict__ C, int ldc, long cgs,
-                                                      double2* __restrict__ Y, long ldy, int p,
-                                                      const double2* __restrict__ Z, long ldz, long rows) {
+// C of group g at C + g cgs (column-major, leading dimension ldc).  PB >= p
+// accumulators per thread: the smallest instance that holds p keeps the register
+// count (and so the number of resident warps) down.
+template <int PB>
+__global__ void __launch_bounds__(256, PB <= 12 ? 3 : 1)
+    k_block_update(Roles X, int q, const double2* __restrict__ C, int ldc, long cgs, double2* __restrict__ Y, long ldy,
+                   int p, const double2* __restrict__ Z, long ldz, long rows) {
   extern __shared__ double2 cs[];  // [p][q]
   const int g = blockIdx.y;
   const double2* Cg = C + g * cgs;
@@ -1244,13 +1247,13 @@ __global__ void __launch_bounds__(256) k_block_update(Roles X, int q, const doub
   double2* Yg = Y + (long)g * p * ldy;
   const double2* Zg = Z ? Z + (long)g * p * ldz : nullptr;
   for (long r = blockIdx.x * (long)blockDim.x + threadIdx.x; r < rows; r += (long)gridDim.x * blockDim.x) {
-    double2 acc[kMaxBlock];
+    double2 acc[PB];
 #pragma unroll
-    for (int j = 0; j < kMaxBlock; ++j) acc[j] = make_double2(0, 0);
+    for (int j = 0; j < PB; ++j) acc[j] = make_double2(0, 0);
     for (int i = 0; i < q; ++i) {
       const double2 x = role_col(X, g, i)[r];
 #pragma unroll
-      for (int j = 0; j < kMaxBlock; ++j) {
+      for (int j = 0; j < PB; ++j) {
         if (j < p) {
           const double2 c = cs[j * q + i];
           acc[j].x = fma(x.x, c.x, fma(-x.y, c.y, acc[j].x));
@@ -1259,7 +1262,7 @@ __global__ void __launch_bounds__(256) k_block_update(Roles X, int q, const doub
       }
     }
 #pragma unroll
-    for (int j = 0; j < kMaxBlock; ++j) {
+    for (int j = 0; j < PB; ++j) {
       if (j < p) {
         double2 v = acc[j];
         if (Zg) v = v + Zg[(long)j * ldz + r];
@@ -1275,9 +1278,9 @@ __global__ void __launch_bounds__(256) k_block_update(Roles X, int q, const doub
 // E C + P, where it is 2^-47 |P| / |E| relative, far below the FP64 rounding of
 // E C once the steps have become small.
 template <int PB>
-__global__ void __launch_bounds__(256) k_block_update_df(Roles X, int q, const double2* __restrict__ C, int ldc,
-                                                         long cgs, double2* __restrict__ Y, long ldy, int p,
-                                                         const double2* __restrict__ Z, long ldz, long rows) {
+__global__ void __launch_bounds__(256, PB <= 12 ? 3 : 1)
+    k_block_update_df(Roles X, int q, const double2* __restrict__ C, int ldc, long cgs, double2* __restrict__ Y,
+                      long ldy, int p, const double2* __restrict__ Z, long ldz, long rows) {
   extern __shared__ float4 csf[];
   dcx* cs = reinterpret_cast<dcx*>(csf);  // [p][q]
   const int g = blockIdx.y;
@@ -1467,26 +1470,32 @@ int gram_partials(long rows, int ngroups) {
   return (int)(chunks < per ? chunks : per);
 }
 
+// Row stride of the staged arrays: qp, or (pad) the next stride that is 1 mod 8 in
+// 16-byte elements, i.e. 4 banks mod 32.  With two row phases per tile (P = 2) the
+// eight threads of a quarter-warp then read eight disjoint groups of four banks.
+inline int gram_lds(int qp, bool pad) { return pad ? qp + ((1 - qp) % 8 + 8) % 8 : qp; }
+
 template <int P, int TS> void launch_gram_df(const Level& L, const double* d_ph, Roles roles, int q, int ngroups,
-                                             int npart, double2* d_partials, cudaStream_t s) {
+                                             int npart, bool pad, double2* d_partials, cudaStream_t s) {
   static PerDeviceOnce once;
   once([] {
     PBS_CUDA(cudaFuncSetAttribute(k_gram_df<P, TS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  6 * (kMaxTrial + TS) * kGdRows * (int)sizeof(dcx)));
+                                  6 * (kMaxTrial + TS + 8) * kGdRows * (int)sizeof(dcx)));
   });
   const int qp = TS * ((q + TS - 1) / TS), T = qp / TS, ntile = T * (T + 1) / 2, per = 256 / P;
-  const size_t smem = 6ull * qp * kGdRows * sizeof(dcx);
+  const int lds = gram_lds(qp, pad);
+  const size_t smem = 6ull * lds * kGdRows * sizeof(dcx);
   k_gram_df<P, TS><<<dim3(npart, ngroups, (ntile + per - 1) / per), 256, smem, s>>>(
-      L.lvl<df>(), L.wts_df(), d_ph, roles, q, qp, kGdRows, d_partials, npart);
+      L.lvl<df>(), L.wts_df(), d_ph, roles, q, qp, lds, kGdRows, d_partials, npart);
 }
 
 template <int TS> void gram_df_dispatch(const Level& L, const double* d_ph, Roles roles, int q, int ngroups, int npart,
-                                        double2* d_partials, cudaStream_t s) {
+                                        bool pad, double2* d_partials, cudaStream_t s) {
   const int T = (q + TS - 1) / TS, ntile = T * (T + 1) / 2;
-  if (ntile <= 16) launch_gram_df<16, TS>(L, d_ph, roles, q, ngroups, npart, d_partials, s);
-  else if (ntile <= 32) launch_gram_df<8, TS>(L, d_ph, roles, q, ngroups, npart, d_partials, s);
-  else if (ntile <= 64) launch_gram_df<4, TS>(L, d_ph, roles, q, ngroups, npart, d_partials, s);
-  else launch_gram_df<2, TS>(L, d_ph, roles, q, ngroups, npart, d_partials, s);
+  if (ntile <= 16) launch_gram_df<16, TS>(L, d_ph, roles, q, ngroups, npart, pad, d_partials, s);
+  else if (ntile <= 32) launch_gram_df<8, TS>(L, d_ph, roles, q, ngroups, npart, pad, d_partials, s);
+  else if (ntile <= 64) launch_gram_df<4, TS>(L, d_ph, roles, q, ngroups, npart, pad, d_partials, s);
+  else launch_gram_df<2, TS>(L, d_ph, roles, q, ngroups, npart, pad, d_partials, s);
 }
 
 void gram_groups(const Level& L, const double* d_ph, Roles roles, int q, int ngroups, double2* GM, double2* GA,
@@ -1500,17 +1509,22 @@ void gram_groups(const Level& L, const double* d_ph, Roles roles, int q, int ngr
   struct Variant {
     int kernel;  // 0: FP64, 1: double-float, 2: tensor cores
     int npart;
+    bool pad;  // double-float kernel: bank-spread row stride of the staged arrays
   };
-  Variant var[4];
+  Variant var[6];
   int nvar = 0;
   if (dfa && gram_tc_supported(q) && gram_on_tensor_cores()) {
     // offered first: with tuning off (PBS_TUNE=0) the tensor-core kernel runs
-    var[nvar++] = {2, np0};
-    var[nvar++] = {2, 2 * np0};
+    var[nvar++] = {2, np0, false};
+    var[nvar++] = {2, 2 * np0, false};
   }
   const int kern = dfa ? 1 : 0;
-  var[nvar++] = {kern, np0};
-  var[nvar++] = {kern, 2 * np0};
+  var[nvar++] = {kern, np0, false};
+  var[nvar++] = {kern, 2 * np0, false};
+  if (dfa) {
+    var[nvar++] = {kern, np0, true};
+    var[nvar++] = {kern, 2 * np0, true};
+  }
   auto fits = [&](const Variant& v) { return (long)ngroups * v.npart * 2 * ne <= partial_capacity; };
   if (!fits(var[0])) fail(PBS_EINVAL, "gram partials buffer too small");
   auto launch = [&](const Variant& v) {
@@ -1518,7 +1532,7 @@ void gram_groups(const Level& L, const double* d_ph, Roles roles, int q, int ngr
       gram_tc(L, d_ph, roles, q, ngroups, v.npart, d_partials, s);
       count_df_launch();
     } else if (v.kernel == 1) {
-      gram_df_dispatch<kGdTile>(L, d_ph, roles, q, ngroups, v.npart, d_partials, s);
+      gram_df_dispatch<kGdTile>(L, d_ph, roles, q, ngroups, v.npart, v.pad, d_partials, s);
       count_df_launch();
     } else {
       static PerDeviceOnce once;
@@ -1536,7 +1550,7 @@ void gram_groups(const Level& L, const double* d_ph, Roles roles, int q, int ngr
   };
   int pick = 0;
   if (nvar > 1) {
-    const std::string key = std::string(dfa ? "gram_df" : "gram") + (nvar > 2 ? "_tc" : "") + "|" +
+    const std::string key = std::string(dfa ? "gram_df" : "gram") + std::to_string(nvar) + "|" +
                             std::to_string(L.n) + "x" + std::to_string(L.m) + "|q" + std::to_string(q) + "|g" +
                             std::to_string(ngroups) + "|" + device_tag();
     // a candidate whose partial sums do not fit the buffer runs the first one instead
@@ -1607,6 +1621,16 @@ template <int PB> void launch_update_df(Roles X, int q, const double2* C, int ld
   k_block_update_df<PB><<<grid, 256, (size_t)p * q * sizeof(dcx), s>>>(X, q, C, ldc, cgs, Y, ldy, p, Z, ldz, rows);
 }
 
+template <int PB> void launch_update(Roles X, int q, const double2* C, int ldc, long cgs, double2* Y, long ldy, int p,
+                                     const double2* Z, long ldz, long rows, dim3 grid, cudaStream_t s) {
+  static PerDeviceOnce once;
+  once([] {
+    PBS_CUDA(cudaFuncSetAttribute(k_block_update<PB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  kMaxBlock * kMaxTrial * (int)sizeof(double2)));
+  });
+  k_block_update<PB><<<grid, 256, (size_t)p * q * sizeof(double2), s>>>(X, q, C, ldc, cgs, Y, ldy, p, Z, ldz, rows);
+}
+
 void block_update(Roles X, int q, const double2* C, int ldc, long cgs, double2* Y, long ldy, int p,
                   const double2* Z, long ldz, long rows, int ngroups, bool dfa, cudaStream_t s) {
   if (p <= 0 || rows <= 0 || ngroups <= 0) return;
@@ -1616,17 +1640,15 @@ void block_update(Roles X, int q, const double2* C, int ldc, long cgs, double2* 
     const dim3 grid((unsigned)per, ngroups);
     if (dfa) {
       if (p <= 8) launch_update_df<8>(X, q, C, ldc, cgs, Y, ldy, p, Z, ldz, rows, grid, s);
+      else if (p <= 12) launch_update_df<12>(X, q, C, ldc, cgs, Y, ldy, p, Z, ldz, rows, grid, s);
       else if (p <= 16) launch_update_df<16>(X, q, C, ldc, cgs, Y, ldy, p, Z, ldz, rows, grid, s);
       else launch_update_df<32>(X, q, C, ldc, cgs, Y, ldy, p, Z, ldz, rows, grid, s);
       count_df_launch();
     } else {
-      static PerDeviceOnce once;
-      once([] {
-        PBS_CUDA(cudaFuncSetAttribute(k_block_update, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      kMaxBlock * kMaxTrial * (int)sizeof(double2)));
-      });
-      const size_t smem = (size_t)p * q * sizeof(double2);
-      k_block_update<<<grid, 256, smem, s>>>(X, q, C, ldc, cgs, Y, ldy, p, Z, ldz, rows);
+      if (p <= 8) launch_update<8>(X, q, C, ldc, cgs, Y, ldy, p, Z, ldz, rows, grid, s);
+      else if (p <= 12) launch_update<12>(X, q, C, ldc, cgs, Y, ldy, p, Z, ldz, rows, grid, s);
+      else if (p <= 16) launch_update<16>(X, q, C, ldc, cgs, Y, ldy, p, Z, ldz, rows, grid, s);
+      else launch_update<32>(X, q, C, ldc, cgs, Y, ldy, p, Z, ldz, rows, grid, s);
     }
     PBS_LAUNCHED();
   };

@@ -233,6 +233,12 @@ void edge_vcycle(const Hierarchy& H, const KData& K, MgWork<T>& w, int l0, const
 template <class T>
 void nodal_vcycle(const Hierarchy& H, const KData& K, MgWork<T>& w, int l0, const cx<T>* X, cx<T>* Y, long ld,
                   int ncols, int cpg, int nu_pre, int nu_post, cudaStream_t s);
+// Y = X0 + B (X - P X0): one nodal V-cycle continuing from the iterate X0 (Y may be X0),
+// for levels where nodal_takes_guess holds; the residual is formed inside the cycle
+template <class T> bool nodal_takes_guess(const Hierarchy& H, int l0, int nu_pre, int nu_post);
+template <class T>
+void nodal_vcycle_from(const Hierarchy& H, const KData& K, MgWork<T>& w, int l0, const cx<T>* X, const cx<T>* X0,
+                       cx<T>* Y, long ld, int ncols, int cpg, int nu_pre, int nu_post, cudaStream_t s);
 
 // ---- dense block kernels (dense.cu) ---------------------------------------
 // Every kernel below reads and writes FP64 blocks.  Where a `dfa` flag is given it

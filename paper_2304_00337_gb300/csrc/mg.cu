@@ -27,9 +27,11 @@
 // Same-colour patches share no edge and are not coupled by A or M, so each
 // colour is one parallel launch and equals the sequential block Gauss-Seidel
 // sweep; the resulting V-cycle is Hermitian.
+#include <algorithm>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <string>
 
 #include "internal.h"
 #include "mgpoint.cuh"
@@ -212,15 +214,17 @@ __global__ void k_node_smooth(Lvl<T> L, const double* ph, int cpg, cx<T>* X, con
 // ---- tiled fine-level nodal steps ------------------------------------------------
 // On levels too large for the fused tail, the pre-smoothing, residual and
 // restriction of the nodal cycle run as one kernel ("down") and the prolongation
-// and post-smoothing as another ("up").  A CTA owns a 32 x 32 tile of fine nodes of
+// and post-smoothing as another ("up").  A CTA owns an FT x FT tile of fine nodes of
 // one column and keeps a halo in shared memory wide enough that every colour step
 // can be carried out there: colour step s of S = 4 nu needs the previous state one
 // node further out, so the region shrinks by one ring per step.  Nodes outside the
 // level are read through the Bloch extension and keep their colour (the sides are
 // even), so the redundant halo work reproduces the neighbours' values exactly.
 // The node updates use the per-node formulas of the step-by-step kernels.
-constexpr int kFT = 32;          // fine tile side
-constexpr int kFineThreads = 256;
+// The tile side FT (32 or 64) and the block size are launch choices (the
+// autotuner picks per level, column count and precision): a larger tile
+// recomputes a smaller share of halo nodes but holds more shared memory.
+constexpr int kFineMaxThreads = 512;
 
 // reader of a shared-memory region whose element (0,0) is global node (oa, ob)
 template <class T> struct NRdSm {
@@ -267,30 +271,35 @@ __device__ __forceinline__ void stage_region(const cx<T>* __restrict__ f, int oa
   }
 }
 
-template <class T>
-__global__ void __launch_bounds__(kFineThreads) k_node_down(Lvl<T> L, int nc, int mc, const double* ph, int cpg,
+template <class T, int FT>
+__global__ void __launch_bounds__(kFineMaxThreads) k_node_down(Lvl<T> L, int nc, int mc, const double* ph, int cpg,
                                                             const cx<T>* __restrict__ B, long ldb,
+                                                            const cx<T>* __restrict__ X0, long ld0,
                                                             cx<T>* __restrict__ Xs, long lds, cx<T>* __restrict__ Bc,
                                                             long ldc, int nu) {
   extern __shared__ float4 fine_sm[];
   // rows/cols [lo-2, lo+T+1) hold x after the last colour step (the residual reads
   // them); step s works on that range widened by 4 nu - 1 - s rings and reads one
   // ring further, so the region adds 4 nu + 2 rings below and 4 nu + 1 above
-  const int lo = 4 * nu + 2, W = kFT + 8 * nu + 3;
+  const int lo = 4 * nu + 2, W = FT + 8 * nu + 3;
   cx<T>* sx = reinterpret_cast<cx<T>*>(fine_sm);
   cx<T>* sb = sx + W * W;
   const int c = blockIdx.z, tid = threadIdx.x, nt = blockDim.x;
-  const int i0 = blockIdx.x * kFT, j0 = blockIdx.y * kFT, oa = i0 - lo, ob = j0 - lo;
+  const int i0 = blockIdx.x * FT, j0 = blockIdx.y * FT, oa = i0 - lo, ob = j0 - lo;
   const Ph<T> p = load_ph<T>(ph, c / cpg);
   const cx<T>* b = B + c * ldb;
   stage_region<T>(b, oa, ob, W, L.n, L.m, p, sb);
-  for (int t = tid; t < W * W; t += nt) sx[t] = czero<T>();
+  // the smoothing starts from X0 where one is given (a cycle that continues from an
+  // iterate: the same steps as a zero start on the residual b - P X0, plus X0)
+  if (X0) stage_region<T>(X0 + c * ld0, oa, ob, W, L.n, L.m, p, sx);
+  else
+    for (int t = tid; t < W * W; t += nt) sx[t] = czero<T>();
   __syncthreads();
   const NRdSm<T> rs{sx, W, oa, ob};
   for (int it = 0; it < nu; ++it)
     for (int q = 0; q < 4; ++q) {
       const int e = 4 * nu - 1 - (4 * it + q);  // rings beyond what the residual needs
-      for_colour<T>(q, lo - 2 - e, lo + kFT + 1 + e, oa, ob, [&](int a, int bb) {
+      for_colour<T>(q, lo - 2 - e, lo + FT + 1 + e, oa, ob, [&](int a, int bb) {
         const int k = bb * W + a;
         const cx<T> res = sb[k] - P_at<T>(rs, L, oa + a, ob + bb);
         sx[k] = sx[k] + (T(1) / P_diag<T>(L)) * res;
@@ -298,26 +307,26 @@ __global__ void __launch_bounds__(kFineThreads) k_node_down(Lvl<T> L, int nc, in
       __syncthreads();
     }
   // residual b - P x in place on the fine nodes the restriction reads
-  for (int t = tid; t < (kFT + 1) * (kFT + 1); t += nt) {
-    const int a = lo - 1 + t % (kFT + 1), bb = lo - 1 + t / (kFT + 1), k = bb * W + a;
+  for (int t = tid; t < (FT + 1) * (FT + 1); t += nt) {
+    const int a = lo - 1 + t % (FT + 1), bb = lo - 1 + t / (FT + 1), k = bb * W + a;
     cx<T> y = T(-1) * P_at<T>(rs, L, oa + a, ob + bb);
     y = y + T(1) * sb[k];
     sb[k] = y;
   }
   __syncthreads();
   const NRdSm<T> rr{sb, W, oa, ob};
-  for (int t = tid; t < (kFT / 2) * (kFT / 2); t += nt) {
-    const int I = i0 / 2 + t % (kFT / 2), J = j0 / 2 + t / (kFT / 2);
+  for (int t = tid; t < (FT / 2) * (FT / 2); t += nt) {
+    const int I = i0 / 2 + t % (FT / 2), J = j0 / 2 + t / (FT / 2);
     if (I < nc && J < mc) Bc[c * ldc + (long)J * nc + I] = restrict_node_at<T>(rr, I, J);
   }
-  for (int t = tid; t < kFT * kFT; t += nt) {
-    const int i = i0 + t % kFT, j = j0 + t / kFT;
-    if (i < L.n && j < L.m) Xs[c * lds + (long)j * L.n + i] = sx[(lo + t / kFT) * W + lo + t % kFT];
+  for (int t = tid; t < FT * FT; t += nt) {
+    const int i = i0 + t % FT, j = j0 + t / FT;
+    if (i < L.n && j < L.m) Xs[c * lds + (long)j * L.n + i] = sx[(lo + t / FT) * W + lo + t % FT];
   }
 }
 
-template <class T>
-__global__ void __launch_bounds__(kFineThreads) k_node_up(Lvl<T> L, int nc, int mc, const double* ph, int cpg,
+template <class T, int FT>
+__global__ void __launch_bounds__(kFineMaxThreads) k_node_up(Lvl<T> L, int nc, int mc, const double* ph, int cpg,
                                                           const cx<T>* __restrict__ B, long ldb,
                                                           const cx<T>* __restrict__ Xs, long lds,
                                                           const cx<T>* __restrict__ Xc, long ldc,
@@ -326,12 +335,12 @@ __global__ void __launch_bounds__(kFineThreads) k_node_up(Lvl<T> L, int nc, int 
   // step s works on the tile widened by 4 nu - 1 - s rings and reads one ring further;
   // the coarse nodes the region's prolongation reads (origin (oa/2, ob/2), W/2 + 1
   // per side, oa and ob even) are staged first
-  const int lo = 4 * nu, W = kFT + 8 * nu, Wc = W / 2 + 1;
+  const int lo = 4 * nu, W = FT + 8 * nu, Wc = W / 2 + 1;
   cx<T>* sx = reinterpret_cast<cx<T>*>(fine_sm);
   cx<T>* sb = sx + W * W;
   cx<T>* sc = sb + W * W;
   const int c = blockIdx.z, tid = threadIdx.x, nt = blockDim.x;
-  const int i0 = blockIdx.x * kFT, j0 = blockIdx.y * kFT, oa = i0 - lo, ob = j0 - lo;
+  const int i0 = blockIdx.x * FT, j0 = blockIdx.y * FT, oa = i0 - lo, ob = j0 - lo;
   const Ph<T> p = load_ph<T>(ph, c / cpg);
   const cx<T>* b = B + c * ldb;
   const cx<T>* xs = Xs + c * lds;
@@ -354,16 +363,16 @@ __global__ void __launch_bounds__(kFineThreads) k_node_up(Lvl<T> L, int nc, int 
   for (int it = 0; it < nu; ++it)
     for (int q = 3; q >= 0; --q) {
       const int e = 4 * nu - 1 - (4 * it + 3 - q);
-      for_colour<T>(q, lo - e, lo + kFT + e, oa, ob, [&](int a, int bb) {
+      for_colour<T>(q, lo - e, lo + FT + e, oa, ob, [&](int a, int bb) {
         const int k = bb * W + a;
         const cx<T> res = sb[k] - P_at<T>(rs, L, oa + a, ob + bb);
         sx[k] = sx[k] + (T(1) / P_diag<T>(L)) * res;
       });
       __syncthreads();
     }
-  for (int t = tid; t < kFT * kFT; t += nt) {
-    const int i = i0 + t % kFT, j = j0 + t / kFT;
-    if (i < L.n && j < L.m) X[c * ldx + (long)j * L.n + i] = sx[(lo + t / kFT) * W + lo + t % kFT];
+  for (int t = tid; t < FT * FT; t += nt) {
+    const int i = i0 + t % FT, j = j0 + t / FT;
+    if (i < L.n && j < L.m) X[c * ldx + (long)j * L.n + i] = sx[(lo + t / FT) * W + lo + t % FT];
   }
 }
 
@@ -907,27 +916,54 @@ template <class T> double tail_bytes(const Hierarchy& H, int l, int ncols, int c
 // The tiled fine-level nodal kernels need the halo to wrap at most once (sides of at
 // least one tile plus both halos) and at most three sweeps per side.
 constexpr int kFineMaxNu = 3;
-inline bool fine_tiled(const Level& L, int nu_pre, int nu_post) {
-  const int need = kFT + 8 * kFineMaxNu + 3;
-  return nu_pre >= 1 && nu_post >= 1 && nu_pre <= kFineMaxNu && nu_post <= kFineMaxNu && L.n >= need && L.m >= need;
+constexpr size_t kSmemOptIn = 232448;  // largest dynamic shared memory a CTA may opt into (227 KB)
+inline bool fine_fits(const Level& L, int ft) {
+  const int need = ft + 8 * kFineMaxNu + 3;
+  return L.n >= need && L.m >= need;
 }
-// shared memory of the tiled kernels for nu sweeps
-template <class T> size_t fine_down_smem(int nu) {
-  const size_t W = kFT + 8 * nu + 3;
+inline bool fine_tiled(const Level& L, int nu_pre, int nu_post) {
+  return nu_pre >= 1 && nu_post >= 1 && nu_pre <= kFineMaxNu && nu_post <= kFineMaxNu && fine_fits(L, 32);
+}
+// shared memory of the tiled kernels for tile side ft and nu sweeps
+template <class T> size_t fine_down_smem(int ft, int nu) {
+  const size_t W = ft + 8 * nu + 3;
   return 2 * W * W * sizeof(cx<T>);
 }
-template <class T> size_t fine_up_smem(int nu) {
-  const size_t W = kFT + 8 * nu, Wc = W / 2 + 1;
+template <class T> size_t fine_up_smem(int ft, int nu) {
+  const size_t W = ft + 8 * nu, Wc = W / 2 + 1;
   return (2 * W * W + Wc * Wc) * sizeof(cx<T>);
 }
-template <class T> void set_fine_smem() {
+// the largest of fn(nu) over the sweep counts whose shared memory fits a CTA
+template <class F> size_t fine_smem_cap(F&& fn) {
+  size_t m = 0;
+  for (int nu = 1; nu <= kFineMaxNu; ++nu)
+    if (fn(nu) <= kSmemOptIn) m = std::max(m, fn(nu));
+  return m;
+}
+template <class T, int FT> void set_fine_smem() {
   static PerDeviceOnce once;
   once([] {
-    PBS_CUDA(cudaFuncSetAttribute(k_node_down<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)fine_down_smem<T>(kFineMaxNu)));
-    PBS_CUDA(cudaFuncSetAttribute(k_node_up<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)fine_up_smem<T>(kFineMaxNu)));
+    PBS_CUDA(cudaFuncSetAttribute(k_node_down<T, FT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)fine_smem_cap([](int nu) { return fine_down_smem<T>(FT, nu); })));
+    PBS_CUDA(cudaFuncSetAttribute(k_node_up<T, FT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)fine_smem_cap([](int nu) { return fine_up_smem<T>(FT, nu); })));
   });
+}
+// launch shapes of the tiled steps offered to the autotuner: (tile side, threads);
+// the first one fits every level the tiled path takes
+struct FineShape {
+  int ft, nt;
+};
+constexpr FineShape kFineShapes[] = {{32, 256}, {64, 512}, {64, 256}};
+constexpr int kNumFineShapes = 3;
+template <class T>
+int fine_shapes(const Level& L, int nu, bool down, FineShape* out) {
+  int n = 0;
+  for (const FineShape& f : kFineShapes) {
+    const size_t sm = down ? fine_down_smem<T>(f.ft, nu) : fine_up_smem<T>(f.ft, nu);
+    if (fine_fits(L, f.ft) && sm <= kSmemOptIn) out[n++] = f;
+  }
+  return n;
 }
 // algorithmic bytes of a tiled step: each level vector read or written once
 // (down: b in, x and the coarse right-hand side out; up: b, x, the coarse
@@ -935,6 +971,31 @@ template <class T> void set_fine_smem() {
 template <class T> double fine_bytes(const Level& L, int ncols, int, bool down) {
   const double v = (double)L.N() * ncols * sizeof(cx<T>);
   return down ? 2.25 * v : 3.25 * v;
+}
+
+template <class T> std::string fine_key(const Level& L, int ncols, int cpg) {
+  return std::to_string(L.n) + "x" + std::to_string(L.m) + "|c" + std::to_string(ncols) + "|g" +
+         std::to_string(cpg) + "|" + (sizeof(T) == 4 ? "f32" : "f64") + "|" + device_tag();
+}
+
+template <class T, int FT>
+void launch_node_down(const Level& L, const Level& C, const KData& K, MgWork<T>& w, int l, const cx<T>* b,
+                      const cx<T>* x0, long ld, int ncols, int cpg, int nu, int nt, cudaStream_t s) {
+  set_fine_smem<T, FT>();
+  const dim3 grid((L.n + FT - 1) / FT, (L.m + FT - 1) / FT, ncols);
+  k_node_down<T, FT><<<grid, nt, fine_down_smem<T>(FT, nu), s>>>(L.lvl<T>(), C.n, C.m, K.d_ph, cpg, b, ld, x0, ld,
+                                                                  w.r[l], L.N(), w.b[l + 1], C.N(), nu);
+  PBS_LAUNCHED();
+}
+
+template <class T, int FT>
+void launch_node_up(const Level& L, const Level& C, const KData& K, MgWork<T>& w, int l, const cx<T>* b, cx<T>* x,
+                    long ld, int ncols, int cpg, int nu, int nt, cudaStream_t s) {
+  set_fine_smem<T, FT>();
+  const dim3 grid((L.n + FT - 1) / FT, (L.m + FT - 1) / FT, ncols);
+  k_node_up<T, FT><<<grid, nt, fine_up_smem<T>(FT, nu), s>>>(L.lvl<T>(), C.n, C.m, K.d_ph, cpg, b, ld, w.r[l], L.N(),
+                                                              w.x[l + 1], C.N(), x, ld, nu);
+  PBS_LAUNCHED();
 }
 
 template <class T>
@@ -1032,10 +1093,17 @@ void edge_cycle(const Hierarchy& H, const KData& K, MgWork<T>& w, int l, const c
     }
 }
 
+// A nodal cycle can continue from a given iterate when its top level runs the tiled steps
+// (whose first kernel stages the iterate as it stages the right-hand side).
+template <class T> bool takes_guess(const Hierarchy& H, int l, int nu_pre, int nu_post) {
+  return l < H.nlev - 1 && !tail_from<T>(H, l, true) && fine_tiled(H.lev[l], nu_pre, nu_post);
+}
+
 template <class T>
 void node_cycle(const Hierarchy& H, const KData& K, MgWork<T>& w, int l, const cx<T>* b, cx<T>* x, long ld, int ncols,
-                int cpg, int nu_pre, int nu_post, cudaStream_t s) {
+                int cpg, int nu_pre, int nu_post, cudaStream_t s, const cx<T>* x0 = nullptr) {
   const Level& L = H.lev[l];
+  if (x0 && !takes_guess<T>(H, l, nu_pre, nu_post)) fail(-1, "nodal cycle: initial iterate on an untiled level");
   if (l == H.nlev - 1) {
     k_chol_solve<T><<<(ncols * 32 + 127) / 128, 128, 0, s>>>(node_factor<T>(K), (int)L.N(), b, ld, x, ld, ncols, cpg,
                                                              K.ngroups, K.goff);
@@ -1054,20 +1122,28 @@ void node_cycle(const Hierarchy& H, const KData& K, MgWork<T>& w, int l, const c
   }
   if (fine_tiled(L, nu_pre, nu_post)) {
     const Level& C = H.lev[l + 1];
-    const dim3 grid((L.n + kFT - 1) / kFT, (L.m + kFT - 1) / kFT, ncols);
-    const size_t smd = fine_down_smem<T>(nu_pre), smu = fine_up_smem<T>(nu_post);
-    set_fine_smem<T>();
+    const auto down = [&](const FineShape& f) {
+      if (f.ft == 64) launch_node_down<T, 64>(L, C, K, w, l, b, x0, ld, ncols, cpg, nu_pre, f.nt, s);
+      else launch_node_down<T, 32>(L, C, K, w, l, b, x0, ld, ncols, cpg, nu_pre, f.nt, s);
+    };
+    const auto up = [&](const FineShape& f) {
+      if (f.ft == 64) launch_node_up<T, 64>(L, C, K, w, l, b, x, ld, ncols, cpg, nu_post, f.nt, s);
+      else launch_node_up<T, 32>(L, C, K, w, l, b, x, ld, ncols, cpg, nu_post, f.nt, s);
+    };
+    FineShape fd[kNumFineShapes], fu[kNumFineShapes];
+    const int nd = fine_shapes<T>(L, nu_pre, true, fd), nup = fine_shapes<T>(L, nu_post, false, fu);
+    // both steps are idempotent (the down step reads b, the up step b, its saved
+    // pre-smoothed x and the coarse correction, and neither writes what it reads)
+    const std::string key = fine_key<T>(L, ncols, cpg);
+    const int pd = tune_pick("node_down|" + key + "|nu" + std::to_string(nu_pre), nd, [&](int c) { down(fd[c]); }, s);
     timer_begin(KC_NODE_SMOOTH, s, fine_bytes<T>(L, ncols, nu_pre, true));
-    k_node_down<T><<<grid, kFineThreads, smd, s>>>(L.lvl<T>(), C.n, C.m, K.d_ph, cpg, b, ld, w.r[l], L.N(), w.b[l + 1],
-                                                    C.N(), nu_pre);
+    down(fd[pd]);
     timer_end(KC_NODE_SMOOTH, s);
-    PBS_LAUNCHED();
     node_cycle<T>(H, K, w, l + 1, w.b[l + 1], w.x[l + 1], C.N(), ncols, cpg, nu_pre, nu_post, s);
+    const int pu = tune_pick("node_up|" + key + "|nu" + std::to_string(nu_post), nup, [&](int c) { up(fu[c]); }, s);
     timer_begin(KC_NODE_SMOOTH, s, fine_bytes<T>(L, ncols, nu_post, false));
-    k_node_up<T><<<grid, kFineThreads, smu, s>>>(L.lvl<T>(), C.n, C.m, K.d_ph, cpg, b, ld, w.r[l], L.N(), w.x[l + 1],
-                                                  C.N(), x, ld, nu_post);
+    up(fu[pu]);
     timer_end(KC_NODE_SMOOTH, s);
-    PBS_LAUNCHED();
     return;
   }
   zero_columns<T>(x, ld, L.N(), ncols, s);
@@ -1114,7 +1190,22 @@ void nodal_vcycle(const Hierarchy& H, const KData& K, MgWork<T>& w, int l0, cons
   node_cycle<T>(H, K, w, l0, X, Y, ld, ncols, cpg, nu_pre, nu_post, s);
 }
 
+template <class T> bool nodal_takes_guess(const Hierarchy& H, int l0, int nu_pre, int nu_post) {
+  return takes_guess<T>(H, l0, nu_pre, nu_post);
+}
+
+template <class T>
+void nodal_vcycle_from(const Hierarchy& H, const KData& K, MgWork<T>& w, int l0, const cx<T>* X, const cx<T>* X0,
+                       cx<T>* Y, long ld, int ncols, int cpg, int nu_pre, int nu_post, cudaStream_t s) {
+  if (ncols <= 0) return;
+  if (ncols > w.ncols) fail(-1, "multigrid workspace too small");
+  node_cycle<T>(H, K, w, l0, X, Y, ld, ncols, cpg, nu_pre, nu_post, s, X0);
+}
+
 #define PBS_INST_MG(T)                                                                                            \
+  template bool nodal_takes_guess<T>(const Hierarchy&, int, int, int);                                            \
+  template void nodal_vcycle_from<T>(const Hierarchy&, const KData&, MgWork<T>&, int, const cx<T>*, const cx<T>*, \
+                                     cx<T>*, long, int, int, int, int, cudaStream_t);                             \
   template void alloc_mg_work<T>(DevMem&, const Hierarchy&, int, bool, MgWork<T>&);                               \
   template void free_mg_work<T>(DevMem&, MgWork<T>&);                                                             \
   template void edge_vcycle<T>(const Hierarchy&, const KData&, MgWork<T>&, int, const cx<T>*, cx<T>*, long, int, \

@@ -543,7 +543,13 @@ void project(pbs_ctx* ctx, const pbs_opts& o, const KData& K, double2* X, int nc
   const bool dfa = o.precision == PBS_MIXED;
   lift_adj_mass<T>(L0, K.d_ph, cpg, X, D, rhs, N, ncols, dfa, s);
   nodal_vcycle<T>(H, K, Bufs<T>::nmg(W), 0, rhs, phi, N, ncols, cpg, o.nu_pre, o.nu_post, s);
+  const bool guess = nodal_takes_guess<T>(H, 0, o.nu_pre, o.nu_post);
   for (int c = 1; c < cycles; ++c) {
+    if (guess) {
+      // the next cycle continues from phi: phi + B (rhs - P phi) in one sweep of kernels
+      nodal_vcycle_from<T>(H, K, Bufs<T>::nmg(W), 0, rhs, phi, phi, N, ncols, cpg, o.nu_pre, o.nu_post, s);
+      continue;
+    }
     apply_nodal<T>(L0, K.d_ph, cpg, phi, res, rhs, N, ncols, T(-1), T(1), s);
     nodal_vcycle<T>(H, K, Bufs<T>::nmg(W), 0, res, dphi, N, ncols, cpg, o.nu_pre, o.nu_post, s);
     timer_begin(KC_NODE_APPLY, s, 3.0 * sizeof(cx<T>) * N * ncols);

@@ -10,6 +10,9 @@
 // $HOME/.cache/pbs_tune.json; PBS_TUNE=0 switches tuning off and takes the first
 // candidate), so later processes on the same device start from it.  Candidates
 // must be idempotent: each run overwrites its outputs from unchanged inputs.
+// PBS_TUNE_FORCE="prefix=i,prefix=j,..." makes every key that begins with a listed
+// prefix take candidate i (where it exists) without timing, so that tests can run
+// each candidate.
 #include <functional>
 #include <cstdio>
 #include <cstdlib>
@@ -19,6 +22,8 @@
 #include <mutex>
 #include <sstream>
 #include <string>
+#include <utility>
+#include <vector>
 
 #include <sys/stat.h>
 
@@ -45,6 +50,24 @@ bool tuning_on() {
     return !(v && std::strcmp(v, "0") == 0);
   }();
   return on;
+}
+
+// PBS_TUNE_FORCE entries (prefix, candidate), read once
+const std::vector<std::pair<std::string, int>>& forced() {
+  static const std::vector<std::pair<std::string, int>> f = [] {
+    std::vector<std::pair<std::string, int>> v;
+    const char* e = std::getenv("PBS_TUNE_FORCE");
+    if (!e) return v;
+    std::stringstream ss(e);
+    std::string item;
+    while (std::getline(ss, item, ',')) {
+      const size_t eq = item.rfind('=');
+      if (eq == std::string::npos || eq == 0) continue;
+      v.emplace_back(item.substr(0, eq), std::atoi(item.c_str() + eq + 1));
+    }
+    return v;
+  }();
+  return f;
 }
 
 std::string cache_path() {
@@ -116,7 +139,10 @@ std::string device_tag() {
 }
 
 int tune_pick(const std::string& key, int ncand, const std::function<void(int)>& run, cudaStream_t s) {
-  if (ncand <= 1 || !tuning_on()) return 0;
+  if (ncand <= 1) return 0;
+  for (const auto& f : forced())
+    if (key.compare(0, f.first.size(), f.first) == 0 && f.second >= 0 && f.second < ncand) return f.second;
+  if (!tuning_on()) return 0;
   TuneCache& c = cache();
   {
     std::lock_guard<std::mutex> lk(c.mu);

@@ -233,6 +233,53 @@ def test_projection_matches_reference(ctx, a, b, n, m, k, cycles):
     assert _rel(got32, want) <= 1e-5
 
 
+# The tiled nodal steps on meshes where every launch shape the autotuner may pick fits
+# (32 x 32 tiles of 256 threads, 64 x 64 tiles of 512 or 256 threads): 192 x 96 has a
+# partial last row of 64 x 64 tiles, 128 x 128 at Gamma whole ones and the constant
+# remainder.  Run as they are here (the tuned shape) and with each shape forced below.
+@pytest.mark.parametrize("a,b,n,m,k", [(1.0, 0.5, 192, 96, (0.4, -1.3)), (1.0, 1.0, 128, 128, (0.0, 0.0))])
+def test_nodal_cycle_and_projection_on_large_tiles(ctx, a, b, n, m, k):
+    eps = _eps(n, m)
+    geom = pbs.Geometry(eps, a, b)
+    mesh = fem.Mesh(a, b, n, m)
+    nlev = mg.nodal_hierarchy(mesh, eps, k, 4)
+    xn = _block(2, mesh.N, 12)
+    # at Gamma the nodal operator annihilates the constants on every level, and the
+    # cycle's output is compared modulo them (the projection's L phi does not see them)
+    gamma = fem.is_gamma(*fem.bloch_phases(k, a, b))
+    if gamma:
+        xn -= xn.mean(axis=1, keepdims=True)
+
+    def mod(y):
+        return y - y.mean(axis=1, keepdims=True) if gamma else y
+    want = mod(np.stack([mg.nodal_vcycle(nlev, xn[c]) for c in range(2)]))
+    assert _rel(mod(_apply(ctx, geom, "VCYCLE_NODAL", xn, mesh.N, k, precision=pbs.PBS_FP64)), want) <= 1e-11
+    assert _rel(mod(_apply(ctx, geom, "VCYCLE_NODAL", xn, mesh.N, k, precision=pbs.PBS_MIXED)), want) <= 1e-5
+    ops = fem.assemble(mesh, eps, k)
+    x = _block(2, mesh.D, 13)
+    want = mg.project_approx(ops, nlev, x.T, 2).T
+    assert _rel(_apply(ctx, geom, "PROJECT", x, mesh.D, k, precision=pbs.PBS_FP64, nodal_cycles=2), want) <= 1e-12
+    assert _rel(_apply(ctx, geom, "PROJECT", x, mesh.D, k, precision=pbs.PBS_MIXED, nodal_cycles=2), want) <= 1e-5
+
+
+@pytest.mark.parametrize("shape", [0, 1, 2])
+def test_nodal_tile_shapes_in_child_processes(shape):
+    # each launch shape of the tiled nodal steps forced (PBS_TUNE_FORCE) in a child process:
+    # the cycle and projection cases above, and with the 64 x 64 tiles of 512 threads the
+    # 256 x 256 rod path (levels 256 and 128 tiled) against the oracle's stored eigenvalues
+    import os
+    import subprocess
+    import sys
+    here = os.path.dirname(os.path.abspath(__file__))
+    tests = [os.path.join(here, "test_gpu_ops.py") + "::test_nodal_cycle_and_projection_on_large_tiles"]
+    if shape == 1:
+        tests.append(os.path.join(here, "test_gpu_eigen.py") + "::test_rod256_path_full_size")
+    env = dict(os.environ, PBS_TUNE_FORCE=f"node_down={shape},node_up={shape}")
+    r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-p", "no:cacheprovider", *tests],
+                       env=env, capture_output=True, text=True, timeout=900)
+    assert r.returncode == 0, r.stdout[-3000:] + r.stderr[-2000:]
+
+
 # mixed policy: the double-float kernel (q = 12 .. 60); 128 x 96 has interior tiles and
 # chunks that end inside a row
 @pytest.mark.parametrize("precision", [pbs.PBS_FP64, pbs.PBS_MIXED])
