@@ -184,6 +184,16 @@ template <class T> struct ERdD {
   __device__ __forceinline__ cx<T> y(int i, int j) const { return gread_d<T>(X + (long)n * m, i, j, n, m, p); }
 };
 
+// The same away from the boundary (no wrap, no phase): the caller checks that every
+// read stays inside the level.
+template <class T> struct ERdDIn {
+  const double2* __restrict__ X;
+  int n;
+  long N;
+  __device__ __forceinline__ cx<T> x(int i, int j) const { return ld_as<T>(X + (long)j * n + i); }
+  __device__ __forceinline__ cx<T> y(int i, int j) const { return ld_as<T>(X + N + (long)j * n + i); }
+};
+
 // Reader of one edge vector from memory (x-edges at X, y-edges at X + n*m).
 template <class T> struct ERd {
   const cx<T>* __restrict__ X;

@@ -559,6 +559,22 @@ __device__ __forceinline__ void mac_conj(acc2& re, acc2& im, const dcx& a, const
   dot2_neg(im, a.y, b.x);
 }
 
+// The six staged values (x, y, M x on both edge sets, curl, w curl) of a node whose
+// stencil reaches across the level's boundary (Bloch extension), written at out,
+// out + stride, ..., out + 5 stride.  Out of line: few nodes take it, and the
+// common interior path keeps its registers.
+__device__ __noinline__ void gram_stage_boundary(const double2* X, Lvl<df> L, WtsDF w, const double* ph, int g, int i,
+                                                 int j, dcx* out, int stride) {
+  const ERdD<df> rd{X, L.n, L.m, load_ph<df>(ph, g)};
+  out[0] = rd.x(i, j);
+  out[stride] = rd.y(i, j);
+  out[2 * stride] = M_x<df>(rd, L, i, j);
+  out[3 * stride] = M_y<df>(rd, L, i, j);
+  const dcx vc = curl_at<df>(rd, i, j);
+  out[4 * stride] = vc;
+  out[5 * stride] = w(i, j) * vc;
+}
+
 template <int P, int TS>
 __global__ void __launch_bounds__(256, 3) k_gram_df(Lvl<df> L, WtsDF w, const double* ph, Roles roles, int q, int qp,
                                                  int lds, int rows, double2* __restrict__ part, int npart) {
@@ -591,7 +607,6 @@ __global__ void __launch_bounds__(256, 3) k_gram_df(Lvl<df> L, WtsDF w, const do
   for (int k = 0; k < TS * TS; ++k) {
     mre[k] = acc2_zero(); mim[k] = acc2_zero(); are[k] = acc2_zero(); aim[k] = acc2_zero();
   }
-  const Ph<df> p = load_ph<df>(ph, g);
   const long N = (long)L.n * L.m;
   const long nchunks = (N + rows - 1) / rows;
   for (long ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
@@ -600,19 +615,23 @@ __global__ void __launch_bounds__(256, 3) k_gram_df(Lvl<df> L, WtsDF w, const do
     for (int t = tid; t < q * rows; t += blockDim.x) {
       const int col = t / rows, rr = t % rows;
       const long node = r0 + rr;
-      dcx vx = z, vy = z, vmx = z, vmy = z, vc = z, vcw = z;
-      if (node < N) {
-        const int i = int(node % L.n), j = int(node / L.n);
-        const ERdD<df> rd{role_col(roles, g, col), L.n, L.m, p};
-        vx = rd.x(i, j);
-        vy = rd.y(i, j);
-        vmx = M_x<df>(rd, L, i, j);
-        vmy = M_y<df>(rd, L, i, j);
-        vc = curl_at<df>(rd, i, j);
-        vcw = w(i, j) * vc;
-      }
       const int e = rr * lds + col;
-      sx[e] = vx; sy[e] = vy; mx[e] = vmx; my[e] = vmy; cc[e] = vc; cw[e] = vcw;
+      const int i = int(node % L.n), j = int(node / L.n);
+      if (node < N && inside(i, j, L.n, L.m, 1, 1)) {
+        // the stencil's reads stay inside the level: no Bloch extension
+        const ERdDIn<df> rd{role_col(roles, g, col), L.n, N};
+        sx[e] = rd.x(i, j);
+        sy[e] = rd.y(i, j);
+        mx[e] = M_x<df>(rd, L, i, j);
+        my[e] = M_y<df>(rd, L, i, j);
+        const dcx vc = curl_at<df>(rd, i, j);
+        cc[e] = vc;
+        cw[e] = w(i, j) * vc;
+      } else if (node < N) {
+        gram_stage_boundary(role_col(roles, g, col), L, w, ph, g, i, j, sx + e, rows * lds);
+      } else {
+        sx[e] = z; sy[e] = z; mx[e] = z; my[e] = z; cc[e] = z; cw[e] = z;
+      }
     }
     __syncthreads();
     if (active) {
@@ -1498,6 +1517,14 @@ template <int TS> void gram_df_dispatch(const Level& L, const double* d_ph, Role
   else launch_gram_df<2, TS>(L, d_ph, roles, q, ngroups, npart, pad, d_partials, s);
 }
 
+// Tuning keys count the groups of a launch in powers of two: the engine's launches
+// shrink group by group as Bloch vectors converge, and one choice serves each range.
+int group_bucket(int ngroups) {
+  int b = 1;
+  while (b < ngroups) b *= 2;
+  return b;
+}
+
 void gram_groups(const Level& L, const double* d_ph, Roles roles, int q, int ngroups, double2* GM, double2* GA,
                  double2* d_partials, long partial_capacity, bool dfa, cudaStream_t s) {
   if (q <= 0 || ngroups <= 0) return;
@@ -1552,7 +1579,7 @@ void gram_groups(const Level& L, const double* d_ph, Roles roles, int q, int ngr
   if (nvar > 1) {
     const std::string key = std::string(dfa ? "gram_df" : "gram") + std::to_string(nvar) + "|" +
                             std::to_string(L.n) + "x" + std::to_string(L.m) + "|q" + std::to_string(q) + "|g" +
-                            std::to_string(ngroups) + "|" + device_tag();
+                            std::to_string(group_bucket(ngroups)) + "|" + device_tag();
     // a candidate whose partial sums do not fit the buffer runs the first one instead
     pick = tune_pick(key, nvar, [&](int c) { launch(fits(var[c]) ? var[c] : var[0]); }, s);
     if (!fits(var[pick])) pick = 0;
@@ -1656,7 +1683,7 @@ void block_update(Roles X, int q, const double2* C, int ldc, long cgs, double2* 
   // sums), so the autotuner's choice changes the time only
   const long cand[3] = {base, std::max<long>(1, base / 2), 2 * base};
   const std::string key = std::string(dfa ? "update_df" : "update") + "|" + std::to_string(rows) + "|q" +
-                          std::to_string(q) + "|p" + std::to_string(p) + "|g" + std::to_string(ngroups) + "|" +
+                          std::to_string(q) + "|p" + std::to_string(p) + "|g" + std::to_string(group_bucket(ngroups)) + "|" +
                           device_tag();
   const int pick = tune_pick(key, 3, [&](int c) { launch(cand[c]); }, s);
   timer_begin(KC_BLOCK_UPDATE, s, 8.0 * q * p * rows * ngroups);  // flops

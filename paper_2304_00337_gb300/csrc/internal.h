@@ -174,6 +174,8 @@ void build_hierarchy(DevMem& mem, Hierarchy& H, const double* d_eps, int coarses
 void free_hierarchy(DevMem& mem, Hierarchy& H);
 void alloc_kdata(DevMem& mem, const Hierarchy& H, KData& K, int ngroups);
 void set_group_k(DevMem& mem, const Hierarchy& H, KData& K, int g, double k1, double k2, cudaStream_t s);
+// group src's tables (phases, k = 0 flags, coarsest factors, host mirror) copied into slot dst
+void copy_group_k(KData& K, int src, int dst, cudaStream_t s);
 KData kdata_view(const KData& K, int g);  // non-owning single-group view of group g
 // non-owning view for a chunk of a role-major block starting at column group v0
 // (phase and flag tables shifted by v0, factors selected with the matching offset)

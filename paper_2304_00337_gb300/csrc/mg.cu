@@ -795,6 +795,24 @@ void set_group_k(DevMem& mem, const Hierarchy& H, KData& K, int g, double k1, do
   if (info[0] || info[1]) fail(PBS_ENUMERIC, "coarsest-level Cholesky factorisation failed");
 }
 
+void copy_group_k(KData& K, int src, int dst, cudaStream_t s) {
+  if (src < 0 || dst < 0 || src >= K.ngroups || dst >= K.ngroups) fail(PBS_EINVAL, "group out of range");
+  if (src == dst) return;
+  K.k1[dst] = K.k1[src];
+  K.k2[dst] = K.k2[src];
+  K.gamma[dst] = K.gamma[src];
+  for (int rep = 0; rep < 3; ++rep) {
+    const long es = (long)rep * K.ngroups + src, ed = (long)rep * K.ngroups + dst;
+    PBS_CUDA(cudaMemcpyAsync(K.d_ph + 4 * ed, K.d_ph + 4 * es, 4 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    PBS_CUDA(cudaMemcpyAsync(K.d_gamma + ed, K.d_gamma + es, sizeof(int), cudaMemcpyDeviceToDevice, s));
+  }
+  const size_t de = (size_t)K.Dc * K.Dc, dn = (size_t)K.Nc * K.Nc;
+  PBS_CUDA(cudaMemcpyAsync(K.edge64 + dst * de, K.edge64 + src * de, de * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+  PBS_CUDA(cudaMemcpyAsync(K.edge32 + dst * de, K.edge32 + src * de, de * sizeof(float2), cudaMemcpyDeviceToDevice, s));
+  PBS_CUDA(cudaMemcpyAsync(K.node64 + dst * dn, K.node64 + src * dn, dn * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+  PBS_CUDA(cudaMemcpyAsync(K.node32 + dst * dn, K.node32 + src * dn, dn * sizeof(float2), cudaMemcpyDeviceToDevice, s));
+}
+
 KData kdata_view(const KData& K, int g) {
   KData v;
   v.ngroups = 1;

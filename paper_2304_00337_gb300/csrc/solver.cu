@@ -938,6 +938,24 @@ PathResult solve_chain_list(pbs_ctx* ctx, const pbs_opts& o, int nk, const doubl
   const double lam_max = lambda_max_bound(ctx->H);
   std::vector<int> h_info(8 * G);
   const int q = 3 * p;
+  int Ga = G;       // groups in the launches: the active ones, moved to the front
+  long Gpa = Gp;
+  // group src's state into slot dst (whose own group is finished): E, P, the residual
+  // of this round (FP32 R32 under the mixed policy), the history ring and the tables
+  auto move_group = [&](int src, int dst, float2* R32) {
+    const size_t cb = sizeof(double2) * D * p;
+    const long so = (long)src * p * D, d0 = (long)dst * p * D;
+    PBS_CUDA(cudaMemcpyAsync(W.E() + d0, W.E() + so, cb, cudaMemcpyDeviceToDevice, s));
+    PBS_CUDA(cudaMemcpyAsync(W.P() + d0, W.P() + so, cb, cudaMemcpyDeviceToDevice, s));
+    if (R32) PBS_CUDA(cudaMemcpyAsync(R32 + d0, R32 + so, sizeof(float2) * D * p, cudaMemcpyDeviceToDevice, s));
+    else PBS_CUDA(cudaMemcpyAsync(W.R() + d0, W.R() + so, cb, cudaMemcpyDeviceToDevice, s));
+    if (W.hist) {
+      const long hs = (long)o.extrap_depth * p * D;
+      PBS_CUDA(cudaMemcpyAsync(W.hist + dst * hs, W.hist + src * hs, sizeof(double2) * hs, cudaMemcpyDeviceToDevice, s));
+    }
+    copy_group_k(ctx->K, src, dst, s);
+    gr[dst] = gr[src];
+  };
   for (int round = 0;; ++round) {
     bool any = false;
     for (auto& x : gr) any = any || x.active;
@@ -948,23 +966,31 @@ PathResult solve_chain_list(pbs_ctx* ctx, const pbs_opts& o, int nk, const doubl
       if (x.active) cyc = std::max(cyc, projection_cycles(o, x.theta_max, mu));
     // Rayleigh-Ritz prefers combinations whose leftover gradient lowers the quotient,
     // so E and P are cleaned before the residual (Section 4, null-space elimination)
-    if (round > 0)
-      run_graph(ctx, graph_key("project", W.E(), nullptr, 2 * (int)Gp, p, cyc, ctx->K, o.precision), s,
-                [&] { project_dispatch(ctx, o, ctx->K, W.E(), 2 * (int)Gp, p, cyc, s); });
+    if (round > 0) {
+      // E and P are adjacent quarters: one pass while every group is launched, else two
+      if (Ga == G) {
+        run_graph(ctx, graph_key("project", W.E(), nullptr, 2 * (int)Gpa, p, cyc, ctx->K, o.precision), s,
+                  [&] { project_dispatch(ctx, o, ctx->K, W.E(), 2 * (int)Gpa, p, cyc, s); });
+      } else {
+        for (double2* X : {W.E(), W.P()})
+          run_graph(ctx, graph_key("project", X, nullptr, (int)Gpa, p, cyc, ctx->K, o.precision), s,
+                    [&] { project_dispatch(ctx, o, ctx->K, X, (int)Gpa, p, cyc, s); });
+      }
+    }
     // Rayleigh quotients in factored form, then the FP64 residual
-    rayleigh_parts(L0, ctx->K.d_ph, p, W.E(), D, (int)Gp, W.parts, W.rq, dfa, s);
-    k_rq<<<nblocks(Gp), 256, 0, s>>>(W.rq, W.lam, (int)Gp);
+    rayleigh_parts(L0, ctx->K.d_ph, p, W.E(), D, (int)Gpa, W.parts, W.rq, dfa, s);
+    k_rq<<<nblocks(Gpa), 256, 0, s>>>(W.rq, W.lam, (int)Gpa);
     PBS_LAUNCHED();
     // mixed: R in FP32 over the first half of the R block (the preconditioner's input)
     float2* R32 = reinterpret_cast<float2*>(W.R());
-    if (dfa) residual_mixed(L0, ctx->K.d_ph, p, W.E(), R32, D, (int)Gp, W.lam, W.parts, W.norms, s);
-    else residual(L0, ctx->K.d_ph, p, W.E(), W.R(), D, (int)Gp, W.lam, W.parts, W.norms, s);
-    PBS_CUDA(cudaMemcpyAsync(h_norms.data(), W.norms, 2 * Gp * sizeof(double), cudaMemcpyDeviceToHost, s));
-    PBS_CUDA(cudaMemcpyAsync(h_lam.data(), W.lam, Gp * sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (dfa) residual_mixed(L0, ctx->K.d_ph, p, W.E(), R32, D, (int)Gpa, W.lam, W.parts, W.norms, s);
+    else residual(L0, ctx->K.d_ph, p, W.E(), W.R(), D, (int)Gpa, W.lam, W.parts, W.norms, s);
+    PBS_CUDA(cudaMemcpyAsync(h_norms.data(), W.norms, 2 * Gpa * sizeof(double), cudaMemcpyDeviceToHost, s));
+    PBS_CUDA(cudaMemcpyAsync(h_lam.data(), W.lam, Gpa * sizeof(double), cudaMemcpyDeviceToHost, s));
     PBS_CUDA(cudaStreamSynchronize(s));
     timer_collect();
-    std::vector<char> cont(G, 0);
-    for (int g = 0; g < G; ++g) {
+    std::vector<char> cont(Ga, 0);
+    for (int g = 0; g < Ga; ++g) {
       Group& x = gr[g];
       if (!x.active) continue;
       bool conv = true;
@@ -1058,28 +1084,46 @@ PathResult solve_chain_list(pbs_ctx* ctx, const pbs_opts& o, int nk, const doubl
         cont[g] = 1;
       }
     }
+    // groups with nothing left to solve leave the launches: the last active group moves
+    // into each hole below the new count (E, P, this round's residual, history, tables),
+    // so the rest of this round and the later rounds cover the active groups only
+    {
+      int na = 0;
+      for (int g = 0; g < Ga; ++g) na += gr[g].active ? 1 : 0;
+      int src = Ga - 1;
+      for (int dst = 0; dst < na; ++dst) {
+        if (gr[dst].active) continue;
+        while (!gr[src].active) --src;  // an active group above na exists for every hole below it
+        move_group(src, dst, dfa ? reinterpret_cast<float2*>(W.R()) : nullptr);
+        cont[dst] = cont[src];
+        gr[src].active = false;
+        --src;
+      }
+      Ga = na;
+      Gpa = (long)Ga * p;
+    }
     bool any_cont = false;
     for (char c : cont) any_cont = any_cont || c;
     if (any_cont) {
       // W = B R, projected; Gram matrices of [E, P, W] per group; Rayleigh-Ritz; update
       double2* Wd = W.W();
-      run_graph(ctx, graph_key("precondition", W.R(), Wd, (int)Gp, p, 0, ctx->K, o.precision), s,
-                [&] { precondition_dispatch(ctx, o, ctx->K, W.R(), Wd, (int)Gp, p, s, dfa ? R32 : nullptr); });
+      run_graph(ctx, graph_key("precondition", W.R(), Wd, (int)Gpa, p, 0, ctx->K, o.precision), s,
+                [&] { precondition_dispatch(ctx, o, ctx->K, W.R(), Wd, (int)Gpa, p, s, dfa ? R32 : nullptr); });
       if (o.span == 1) {  // PINVIT (Algorithm 1): the trial block is E_hat = E - B R alone
-        k_sub_from<<<nblocks(D * Gp), 256, 0, s>>>(W.E(), Wd, D * Gp);
+        k_sub_from<<<nblocks(D * Gpa), 256, 0, s>>>(W.E(), Wd, D * Gpa);
         PBS_LAUNCHED();
       }
-      run_graph(ctx, graph_key("project", Wd, nullptr, (int)Gp, p, cyc, ctx->K, o.precision), s,
-                [&] { project_dispatch(ctx, o, ctx->K, Wd, (int)Gp, p, cyc, s); });
+      run_graph(ctx, graph_key("project", Wd, nullptr, (int)Gpa, p, cyc, ctx->K, o.precision), s,
+                [&] { project_dispatch(ctx, o, ctx->K, Wd, (int)Gpa, p, cyc, s); });
       // trial block per group: [E, P, W] (span 3; P = 0 until a search direction
       // exists, and always for span 2, so its columns are dropped) or [E_hat] (span 1)
       const Roles trial = o.span == 1 ? Roles{{Wd, Wd, Wd}, p, D} : Roles{{W.E(), W.P(), W.W()}, p, D};
       const int qt = o.span == 1 ? p : q;
-      gram_groups(L0, ctx->K.d_ph, trial, qt, G, W.GM, W.GA, W.gpart, W.gpart_cap, dfa, s);
-      small_rr(W.GM, W.GA, qt, p, W.C, W.theta, W.rr_scr, W.info, G, dfa, s);
-      PBS_CUDA(cudaMemcpyAsync(h_info.data(), W.info, sizeof(int) * 8 * G, cudaMemcpyDeviceToHost, s));
+      gram_groups(L0, ctx->K.d_ph, trial, qt, Ga, W.GM, W.GA, W.gpart, W.gpart_cap, dfa, s);
+      small_rr(W.GM, W.GA, qt, p, W.C, W.theta, W.rr_scr, W.info, Ga, dfa, s);
+      PBS_CUDA(cudaMemcpyAsync(h_info.data(), W.info, sizeof(int) * 8 * Ga, cudaMemcpyDeviceToHost, s));
       PBS_CUDA(cudaStreamSynchronize(s));
-      for (int g = 0; g < G; ++g) {
+      for (int g = 0; g < Ga; ++g) {
         if (!cont[g] || h_info[8 * g] == 0) continue;
         if (h_info[8 * g] == -2) fail(PBS_ENUMERIC, "non-finite Gram matrix");
         if (h_info[8 * g] == -3) fail(PBS_ENUMERIC, "Rayleigh-Ritz breakdown");
@@ -1099,28 +1143,28 @@ PathResult solve_chain_list(pbs_ctx* ctx, const pbs_opts& o, int nk, const doubl
       }
       if (o.span == 1) {
         // E_new = E_hat C over the old E (E_hat lives in W); P stays zero
-        block_update(trial, p, W.C, p, (long)p * p, W.E(), D, p, nullptr, 0, D, G, false, s);
-        PBS_CUDA(cudaMemsetAsync(W.P(), 0, sizeof(double2) * D * Gp, s));
+        block_update(trial, p, W.C, p, (long)p * p, W.E(), D, p, nullptr, 0, D, Ga, false, s);
+        PBS_CUDA(cudaMemsetAsync(W.P(), 0, sizeof(double2) * D * Gpa, s));
       } else {
         // P_new = [P, W] C[p:q] over R, E_new = E C[0:p] + P_new over W, then the
         // halves swap roles (new E, P = old W, R blocks)
         double2* P2 = W.R();
         double2* E2 = W.W();
         const Roles pw{{W.P(), W.W(), W.W()}, p, D};
-        block_update(pw, 2 * p, W.C + p, q, (long)q * p, P2, D, p, nullptr, 0, D, G, dfa, s);
+        block_update(pw, 2 * p, W.C + p, q, (long)q * p, P2, D, p, nullptr, 0, D, Ga, dfa, s);
         const Roles ee{{W.E(), W.E(), W.E()}, p, D};
-        block_update(ee, p, W.C, q, (long)q * p, E2, D, p, P2, D, D, G, false, s);
+        block_update(ee, p, W.C, q, (long)q * p, E2, D, p, P2, D, D, Ga, false, s);
         W.half = 1 - W.half;
-        if (o.span == 2) PBS_CUDA(cudaMemsetAsync(W.P(), 0, sizeof(double2) * D * Gp, s));  // gradient method: no P
+        if (o.span == 2) PBS_CUDA(cudaMemsetAsync(W.P(), 0, sizeof(double2) * D * Gpa, s));  // gradient method: no P
       }
-      for (int g = 0; g < G; ++g)
+      for (int g = 0; g < Ga; ++g)
         if (cont[g]) {
           gr[g].have_p = true;
           gr[g].it += 1;
         }
     }
     // groups that moved to their next Bloch vector
-    for (int g = 0; g < G; ++g) {
+    for (int g = 0; g < Ga; ++g) {
       if (!gr[g].need_init) continue;
       set_group_k(ctx->mem, ctx->H, ctx->K, g, ks[2 * gr[g].pos], ks[2 * gr[g].pos + 1], s);
       init_group(ctx, o, gr[g], g, nullptr, s);
