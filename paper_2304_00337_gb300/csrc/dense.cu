@@ -559,31 +559,46 @@ __device__ __forceinline__ void mac_conj(acc2& re, acc2& im, const dcx& a, const
   dot2_neg(im, a.y, b.x);
 }
 
-// The six staged values (x, y, M x on both edge sets, curl, w curl) of a node whose
-// stencil reaches across the level's boundary (Bloch extension), written at out,
-// out + stride, ..., out + 5 stride.  Out of line: few nodes take it, and the
-// common interior path keeps its registers.
-__device__ __noinline__ void gram_stage_boundary(const double2* X, Lvl<df> L, WtsDF w, const double* ph, int g, int i,
-                                                 int j, dcx* out, int stride) {
+// The mass part of the Gram matrix in factored form.  Along an edge set the mass
+// matrix is mx tridiag(1/6, 2/3, 1/6) with Bloch wrap (x-edges couple in j, y-edges
+// in i), and tridiag(1/6, 2/3, 1/6) = B^* B for the bidiagonal B with diagonal alpha
+// and upper diagonal beta, alpha = (1 + 1/sqrt(3))/2, beta = (1 - 1/sqrt(3))/2
+// (alpha^2 + beta^2 = 2/3, alpha beta = 1/6; the wrap entry carries the phase).  So
+// S^* M S = (B S)^* (B S) with z_x(i,j) = sqrt(mx) (alpha x(i,j) + beta x(i,j+1))
+// and z_y(i,j) = sqrt(my) (alpha y(i,j) + beta y(i+1,j)): two staged arrays read
+// on both sides of the product instead of x, y and M x, M y.
+struct MassFactor {
+  df ax, bx, ay, by;  // sqrt(mx) alpha, sqrt(mx) beta, sqrt(my) alpha, sqrt(my) beta
+};
+MassFactor mass_factor(const Level& L) {
+  const double r3 = 1.0 / std::sqrt(3.0), al = 0.5 * (1.0 + r3), be = 0.5 * (1.0 - r3);
+  const double sx = std::sqrt(L.h2 / L.h1), sy = std::sqrt(L.h1 / L.h2);
+  return MassFactor{df(sx * al), df(sx * be), df(sy * al), df(sy * be)};
+}
+
+// The four staged values (z_x, z_y, curl, w curl) of a node whose stencil reaches
+// across the level's boundary (Bloch extension), written at out, out + stride,
+// out + 2 stride, out + 3 stride.  Out of line: few nodes take it, and the common
+// interior path keeps its registers.
+__device__ __noinline__ void gram_stage_boundary(const double2* X, Lvl<df> L, WtsDF w, MassFactor mf,
+                                                 const double* ph, int g, int i, int j, dcx* out, int stride) {
   const ERdD<df> rd{X, L.n, L.m, load_ph<df>(ph, g)};
-  out[0] = rd.x(i, j);
-  out[stride] = rd.y(i, j);
-  out[2 * stride] = M_x<df>(rd, L, i, j);
-  out[3 * stride] = M_y<df>(rd, L, i, j);
-  const dcx vc = curl_at<df>(rd, i, j);
-  out[4 * stride] = vc;
-  out[5 * stride] = w(i, j) * vc;
+  const dcx x0 = rd.x(i, j), x1 = rd.x(i, j + 1), y0 = rd.y(i, j), y1 = rd.y(i + 1, j);
+  out[0] = mf.ax * x0 + mf.bx * x1;
+  out[stride] = mf.ay * y0 + mf.by * y1;
+  const dcx vc = x1 - x0 - y1 + y0;  // curl_at's order
+  out[2 * stride] = vc;
+  out[3 * stride] = w(i, j) * vc;
 }
 
 template <int P, int TS>
-__global__ void __launch_bounds__(256, 3) k_gram_df(Lvl<df> L, WtsDF w, const double* ph, Roles roles, int q, int qp,
-                                                 int lds, int rows, double2* __restrict__ part, int npart) {
+__global__ void __launch_bounds__(256, 3) k_gram_df(Lvl<df> L, WtsDF w, MassFactor mf, const double* ph, Roles roles,
+                                                 int q, int qp, int lds, int rows, double2* __restrict__ part,
+                                                 int npart) {
   extern __shared__ float4 smf[];
-  dcx* sx = reinterpret_cast<dcx*>(smf);  // [rows][lds] each, columns qp .. lds-1 unused
-  dcx* sy = sx + rows * lds;
-  dcx* mx = sy + rows * lds;
-  dcx* my = mx + rows * lds;
-  dcx* cc = my + rows * lds;
+  dcx* zx = reinterpret_cast<dcx*>(smf);  // [rows][lds] each, columns qp .. lds-1 unused
+  dcx* zy = zx + rows * lds;
+  dcx* cc = zy + rows * lds;
   dcx* cw = cc + rows * lds;
   const int g = blockIdx.y;
   const int tid = threadIdx.x;
@@ -600,7 +615,7 @@ __global__ void __launch_bounds__(256, 3) k_gram_df(Lvl<df> L, WtsDF w, const do
   const dcx z = dcx_make(df_zero(), df_zero());
   for (int t = tid; t < rows * (qp - q); t += blockDim.x) {
     const int e = (t / (qp - q)) * lds + q + t % (qp - q);
-    sx[e] = z; sy[e] = z; mx[e] = z; my[e] = z; cc[e] = z; cw[e] = z;
+    zx[e] = z; zy[e] = z; cc[e] = z; cw[e] = z;
   }
   acc2 mre[TS * TS], mim[TS * TS], are[TS * TS], aim[TS * TS];
 #pragma unroll
@@ -620,17 +635,16 @@ __global__ void __launch_bounds__(256, 3) k_gram_df(Lvl<df> L, WtsDF w, const do
       if (node < N && inside(i, j, L.n, L.m, 1, 1)) {
         // the stencil's reads stay inside the level: no Bloch extension
         const ERdDIn<df> rd{role_col(roles, g, col), L.n, N};
-        sx[e] = rd.x(i, j);
-        sy[e] = rd.y(i, j);
-        mx[e] = M_x<df>(rd, L, i, j);
-        my[e] = M_y<df>(rd, L, i, j);
-        const dcx vc = curl_at<df>(rd, i, j);
+        const dcx x0 = rd.x(i, j), x1 = rd.x(i, j + 1), y0 = rd.y(i, j), y1 = rd.y(i + 1, j);
+        zx[e] = mf.ax * x0 + mf.bx * x1;
+        zy[e] = mf.ay * y0 + mf.by * y1;
+        const dcx vc = x1 - x0 - y1 + y0;  // curl_at's order
         cc[e] = vc;
         cw[e] = w(i, j) * vc;
       } else if (node < N) {
-        gram_stage_boundary(role_col(roles, g, col), L, w, ph, g, i, j, sx + e, rows * lds);
+        gram_stage_boundary(role_col(roles, g, col), L, w, mf, ph, g, i, j, zx + e, rows * lds);
       } else {
-        sx[e] = z; sy[e] = z; mx[e] = z; my[e] = z; cc[e] = z; cw[e] = z;
+        zx[e] = z; zy[e] = z; cc[e] = z; cw[e] = z;
       }
     }
     __syncthreads();
@@ -641,8 +655,8 @@ __global__ void __launch_bounds__(256, 3) k_gram_df(Lvl<df> L, WtsDF w, const do
         const int ra = rr * lds + TS * I, rb = rr * lds + TS * J;
 #pragma unroll 1
         for (int st = 0; st < 2; ++st) {
-          const dcx* A = st == 0 ? sx : sy;
-          const dcx* B = st == 0 ? mx : my;
+          const dcx* A = st == 0 ? zx : zy;  // (B S)^* (B S): both sides from one array
+          const dcx* B = A;
           dcx a[TS], b[TS];
 #pragma unroll
           for (int k = 0; k < TS; ++k) { a[k] = A[ra + k]; b[k] = B[rb + k]; }
@@ -1499,13 +1513,13 @@ template <int P, int TS> void launch_gram_df(const Level& L, const double* d_ph,
   static PerDeviceOnce once;
   once([] {
     PBS_CUDA(cudaFuncSetAttribute(k_gram_df<P, TS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  6 * (kMaxTrial + TS + 8) * kGdRows * (int)sizeof(dcx)));
+                                  4 * (kMaxTrial + TS + 8) * kGdRows * (int)sizeof(dcx)));
   });
   const int qp = TS * ((q + TS - 1) / TS), T = qp / TS, ntile = T * (T + 1) / 2, per = 256 / P;
   const int lds = gram_lds(qp, pad);
-  const size_t smem = 6ull * lds * kGdRows * sizeof(dcx);
+  const size_t smem = 4ull * lds * kGdRows * sizeof(dcx);
   k_gram_df<P, TS><<<dim3(npart, ngroups, (ntile + per - 1) / per), 256, smem, s>>>(
-      L.lvl<df>(), L.wts_df(), d_ph, roles, q, qp, lds, kGdRows, d_partials, npart);
+      L.lvl<df>(), L.wts_df(), mass_factor(L), d_ph, roles, q, qp, lds, kGdRows, d_partials, npart);
 }
 
 template <int TS> void gram_df_dispatch(const Level& L, const double* d_ph, Roles roles, int q, int ngroups, int npart,
