@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <type_traits>
 
 #include "df32.cuh"
 #include "internal.h"
@@ -86,15 +87,44 @@ __global__ void k_finalize2(const double* __restrict__ part, int nblk, double* _
   }
 }
 
+// The mass matrix in factored form (Gram matrices, Rayleigh quotients).  Along an edge set the mass
+// matrix is mx tridiag(1/6, 2/3, 1/6) with Bloch wrap (x-edges couple in j, y-edges
+// in i), and tridiag(1/6, 2/3, 1/6) = B^* B for the bidiagonal B with diagonal alpha
+// and upper diagonal beta, alpha = (1 + 1/sqrt(3))/2, beta = (1 - 1/sqrt(3))/2
+// (alpha^2 + beta^2 = 2/3, alpha beta = 1/6; the wrap entry carries the phase).  So
+// S^* M S = (B S)^* (B S) with z_x(i,j) = sqrt(mx) (alpha x(i,j) + beta x(i,j+1))
+// and z_y(i,j) = sqrt(my) (alpha y(i,j) + beta y(i+1,j)): two staged arrays read
+// on both sides of the product instead of x, y and M x, M y.
+struct MassFactor {
+  df ax, bx, ay, by;  // sqrt(mx) alpha, sqrt(mx) beta, sqrt(my) alpha, sqrt(my) beta
+};
+MassFactor mass_factor(const Level& L) {
+  const double r3 = 1.0 / std::sqrt(3.0), al = 0.5 * (1.0 + r3), be = 0.5 * (1.0 - r3);
+  const double sx = std::sqrt(L.h2 / L.h1), sy = std::sqrt(L.h1 / L.h2);
+  return MassFactor{df(sx * al), df(sx * be), df(sy * al), df(sy * be)};
+}
+
 // The kernels below read and write FP64 blocks; V is the arithmetic: double
 // (plain FP64) or df (double-float on the FP32 pipe, about 2^-47 relative).
 
 template <class V, class W>
-__global__ void k_rayleigh_parts(Lvl<V> L, W w, const double* ph, int cpg, const double2* __restrict__ X, long ld,
-                                 double* __restrict__ part) {
+__global__ void k_rayleigh_parts(Lvl<V> L, W w, MassFactor mf, const double* ph, int cpg,
+                                 const double2* __restrict__ X, long ld, double* __restrict__ part) {
   const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y, c = blockIdx.z;
   V den = V(0.0), num = V(0.0);
-  if (i < L.n && j < L.m) {
+  if constexpr (std::is_same<V, df>::value) {
+    // double-float: e^* M e = |z_x|^2 + |z_y|^2 (factored mass), and plain reads where
+    // the stencil stays inside the level
+    const auto parts = [&](const auto& r) {
+      const dcx x0 = r.x(i, j), x1 = r.x(i, j + 1), y0 = r.y(i, j), y1 = r.y(i + 1, j);
+      den = nrm2(mf.ax * x0 + mf.bx * x1) + nrm2(mf.ay * y0 + mf.by * y1);
+      num = w(i, j) * nrm2(x1 - x0 - y1 + y0);  // curl_at's order
+    };
+    if (i < L.n && j < L.m) {
+      if (inside(i, j, L.n, L.m, 1, 1)) parts(ERdDIn<df>{X + c * ld, L.n, (long)L.n * L.m});
+      else parts(ERdD<df>{X + c * ld, L.n, L.m, load_ph<df>(ph, c / cpg)});
+    }
+  } else if (i < L.n && j < L.m) {
     const ERdD<V> r{X + c * ld, L.n, L.m, load_ph<V>(ph, c / cpg)};
     const cx<V> mx = M_x<V>(r, L, i, j), my = M_y<V>(r, L, i, j);
     const cx<V> ex = r.x(i, j), ey = r.y(i, j);
@@ -557,23 +587,6 @@ __device__ __forceinline__ void mac_conj(acc2& re, acc2& im, const dcx& a, const
   dot2(re, a.y, b.y);
   dot2(im, a.x, b.y);
   dot2_neg(im, a.y, b.x);
-}
-
-// The mass part of the Gram matrix in factored form.  Along an edge set the mass
-// matrix is mx tridiag(1/6, 2/3, 1/6) with Bloch wrap (x-edges couple in j, y-edges
-// in i), and tridiag(1/6, 2/3, 1/6) = B^* B for the bidiagonal B with diagonal alpha
-// and upper diagonal beta, alpha = (1 + 1/sqrt(3))/2, beta = (1 - 1/sqrt(3))/2
-// (alpha^2 + beta^2 = 2/3, alpha beta = 1/6; the wrap entry carries the phase).  So
-// S^* M S = (B S)^* (B S) with z_x(i,j) = sqrt(mx) (alpha x(i,j) + beta x(i,j+1))
-// and z_y(i,j) = sqrt(my) (alpha y(i,j) + beta y(i+1,j)): two staged arrays read
-// on both sides of the product instead of x, y and M x, M y.
-struct MassFactor {
-  df ax, bx, ay, by;  // sqrt(mx) alpha, sqrt(mx) beta, sqrt(my) alpha, sqrt(my) beta
-};
-MassFactor mass_factor(const Level& L) {
-  const double r3 = 1.0 / std::sqrt(3.0), al = 0.5 * (1.0 + r3), be = 0.5 * (1.0 - r3);
-  const double sx = std::sqrt(L.h2 / L.h1), sy = std::sqrt(L.h1 / L.h2);
-  return MassFactor{df(sx * al), df(sx * be), df(sy * al), df(sy * be)};
 }
 
 // The four staged values (z_x, z_y, curl, w curl) of a node whose stencil reaches
@@ -1452,11 +1465,12 @@ void rayleigh_parts(const Level& L, const double* d_ph, int cpg, const double2* 
   if (ncols <= 0) return;
   const dim3 g = grid2(L.n, L.m, ncols);
   if (dfa) {
-    k_rayleigh_parts<df><<<g, dim3(kBX, kBY), 0, s>>>(L.lvl<df>(), L.wts_df(), d_ph, cpg, X, ld, d_partials);
+    k_rayleigh_parts<df><<<g, dim3(kBX, kBY), 0, s>>>(L.lvl<df>(), L.wts_df(), mass_factor(L), d_ph, cpg, X, ld,
+                                                     d_partials);
     count_df_launch();
   } else
-    k_rayleigh_parts<double><<<g, dim3(kBX, kBY), 0, s>>>(L.lvl<double>(), L.wts<double>(), d_ph, cpg, X, ld,
-                                                         d_partials);
+    k_rayleigh_parts<double><<<g, dim3(kBX, kBY), 0, s>>>(L.lvl<double>(), L.wts<double>(), mass_factor(L), d_ph,
+                                                         cpg, X, ld, d_partials);
   PBS_LAUNCHED();
   k_finalize2<<<ncols, 256, 0, s>>>(d_partials, g.x * g.y, d_out);
   PBS_LAUNCHED();
