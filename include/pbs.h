@@ -32,6 +32,15 @@
  *  - permittivity: one sample per finest-level cell, eps[j*n + i] > 0, taken
  *    at the cell centre (the reading of the paper's "standard quadrature" for
  *    a cellwise-constant 1/eps, Section 5).
+ *
+ * Environment (read once per process; none changes a result beyond rounding):
+ *  - PBS_TUNE=0: no launch tuning, the first candidate of every choice;
+ *  - PBS_TUNE_CACHE=<file>: where tuned choices are kept (default
+ *    $HOME/.cache/pbs_tune.json); PBS_TUNE_FORCE=<prefix>=<i>,...: choice i for
+ *    every tuning key with that prefix (tests);
+ *  - PBS_GRAM=tc: offer the tensor-core Gram kernel to the tuner;
+ *  - PBS_GRAPHS=0: no CUDA-graph replays of the multigrid sequences;
+ *  - PBS_VERBOSE: per-iteration traces on stderr (synchronises the stream).
  */
 #ifndef PBS_H
 #define PBS_H
