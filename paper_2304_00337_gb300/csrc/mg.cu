@@ -32,9 +32,11 @@
 #include <cstdlib>
 #include <cstring>
 #include <string>
+#include <type_traits>
 
 #include "internal.h"
 #include "mgpoint.cuh"
+#include "nodal_tiles.cuh"
 
 namespace pbs {
 
@@ -209,171 +211,6 @@ __global__ void k_node_smooth(Lvl<T> L, const double* ph, int cpg, cx<T>* X, con
     node_smooth_at<T>(L, inner_n<T>(X + c * ld, L.n), X + c * ld, B + c * ld, i, j);
   else
     node_smooth_at<T>(L, r, X + c * ld, B + c * ld, i, j);
-}
-
-// ---- tiled fine-level nodal steps ------------------------------------------------
-// On levels too large for the fused tail, the pre-smoothing, residual and
-// restriction of the nodal cycle run as one kernel ("down") and the prolongation
-// and post-smoothing as another ("up").  A CTA owns an FT x FT tile of fine nodes of
-// one column and keeps a halo in shared memory wide enough that every colour step
-// can be carried out there: colour step s of S = 4 nu needs the previous state one
-// node further out, so the region shrinks by one ring per step.  Nodes outside the
-// level are read through the Bloch extension and keep their colour (the sides are
-// even), so the redundant halo work reproduces the neighbours' values exactly.
-// The node updates use the per-node formulas of the step-by-step kernels.
-// The tile side FT (32 or 64) and the block size are launch choices (the
-// autotuner picks per level, column count and precision): a larger tile
-// recomputes a smaller share of halo nodes but holds more shared memory.
-constexpr int kFineMaxThreads = 512;
-
-// reader of a shared-memory region whose element (0,0) is global node (oa, ob)
-template <class T> struct NRdSm {
-  const cx<T>* s;
-  int W, oa, ob;
-  __device__ __forceinline__ cx<T> v(int i, int j) const { return s[(j - ob) * W + (i - oa)]; }
-};
-
-// (u, v) with t = v w + u, 0 <= u < w, for 0 <= t < 2^16 and w >= 1: the float quotient
-// (t + 1/2) / w lies at least 1/(2w) from an integer and is off by at most
-// (t/w) 2^-23 (two roundings), i.e. by at most t 2^-22 <= 1/64 of that distance, so its
-// truncation is exact (an integer division by a run-time w costs ~20 instructions)
-__device__ __forceinline__ void split_index(int t, int w, float inv_w, int& u, int& v) {
-  v = (int)(((float)t + 0.5f) * inv_w);
-  u = t - v * w;
-}
-
-// colour q nodes (global parity (q & 1, q >> 1)) of the region rows/cols [r0, r1) in
-// region coordinates, the region's global origin being (oa, ob)
-template <class T, class F>
-__device__ __forceinline__ void for_colour(int q, int r0, int r1, int oa, int ob, F&& f) {
-  const int pa = ((q & 1) - oa) & 1, pb = ((q >> 1) - ob) & 1;
-  const int a0 = r0 + ((pa - r0) & 1), b0 = r0 + ((pb - r0) & 1);
-  const int na = (r1 - a0 + 1) / 2, nb = (r1 - b0 + 1) / 2;
-  const float inv = 1.0f / (float)na;
-  for (int t = threadIdx.x; t < na * nb; t += blockDim.x) {
-    int u, v;
-    split_index(t, na, inv, u, v);
-    f(a0 + 2 * u, b0 + 2 * v);
-  }
-}
-
-// Stage a W x W region of a node field whose element (0,0) is node (oa, ob): direct reads
-// when the region lies inside the level, else through the Bloch extension.
-template <class T>
-__device__ __forceinline__ void stage_region(const cx<T>* __restrict__ f, int oa, int ob, int W, int n, int m,
-                                             const Ph<T>& p, cx<T>* S) {
-  const float inv = 1.0f / (float)W;
-  const bool in = oa >= 0 && ob >= 0 && oa + W <= n && ob + W <= m;
-  for (int t = threadIdx.x; t < W * W; t += blockDim.x) {
-    int u, v;
-    split_index(t, W, inv, u, v);
-    S[t] = in ? f[(long)(ob + v) * n + oa + u] : gread<T>(f, oa + u, ob + v, n, m, p);
-  }
-}
-
-template <class T, int FT>
-__global__ void __launch_bounds__(kFineMaxThreads) k_node_down(Lvl<T> L, int nc, int mc, const double* ph, int cpg,
-                                                            const cx<T>* __restrict__ B, long ldb,
-                                                            const cx<T>* __restrict__ X0, long ld0,
-                                                            cx<T>* __restrict__ Xs, long lds, cx<T>* __restrict__ Bc,
-                                                            long ldc, int nu) {
-  extern __shared__ float4 fine_sm[];
-  // rows/cols [lo-2, lo+T+1) hold x after the last colour step (the residual reads
-  // them); step s works on that range widened by 4 nu - 1 - s rings and reads one
-  // ring further, so the region adds 4 nu + 2 rings below and 4 nu + 1 above
-  const int lo = 4 * nu + 2, W = FT + 8 * nu + 3;
-  cx<T>* sx = reinterpret_cast<cx<T>*>(fine_sm);
-  cx<T>* sb = sx + W * W;
-  const int c = blockIdx.z, tid = threadIdx.x, nt = blockDim.x;
-  const int i0 = blockIdx.x * FT, j0 = blockIdx.y * FT, oa = i0 - lo, ob = j0 - lo;
-  const Ph<T> p = load_ph<T>(ph, c / cpg);
-  const cx<T>* b = B + c * ldb;
-  stage_region<T>(b, oa, ob, W, L.n, L.m, p, sb);
-  // the smoothing starts from X0 where one is given (a cycle that continues from an
-  // iterate: the same steps as a zero start on the residual b - P X0, plus X0)
-  if (X0) stage_region<T>(X0 + c * ld0, oa, ob, W, L.n, L.m, p, sx);
-  else
-    for (int t = tid; t < W * W; t += nt) sx[t] = czero<T>();
-  __syncthreads();
-  const NRdSm<T> rs{sx, W, oa, ob};
-  for (int it = 0; it < nu; ++it)
-    for (int q = 0; q < 4; ++q) {
-      const int e = 4 * nu - 1 - (4 * it + q);  // rings beyond what the residual needs
-      for_colour<T>(q, lo - 2 - e, lo + FT + 1 + e, oa, ob, [&](int a, int bb) {
-        const int k = bb * W + a;
-        const cx<T> res = sb[k] - P_at<T>(rs, L, oa + a, ob + bb);
-        sx[k] = sx[k] + (T(1) / P_diag<T>(L)) * res;
-      });
-      __syncthreads();
-    }
-  // residual b - P x in place on the fine nodes the restriction reads
-  for (int t = tid; t < (FT + 1) * (FT + 1); t += nt) {
-    const int a = lo - 1 + t % (FT + 1), bb = lo - 1 + t / (FT + 1), k = bb * W + a;
-    cx<T> y = T(-1) * P_at<T>(rs, L, oa + a, ob + bb);
-    y = y + T(1) * sb[k];
-    sb[k] = y;
-  }
-  __syncthreads();
-  const NRdSm<T> rr{sb, W, oa, ob};
-  for (int t = tid; t < (FT / 2) * (FT / 2); t += nt) {
-    const int I = i0 / 2 + t % (FT / 2), J = j0 / 2 + t / (FT / 2);
-    if (I < nc && J < mc) Bc[c * ldc + (long)J * nc + I] = restrict_node_at<T>(rr, I, J);
-  }
-  for (int t = tid; t < FT * FT; t += nt) {
-    const int i = i0 + t % FT, j = j0 + t / FT;
-    if (i < L.n && j < L.m) Xs[c * lds + (long)j * L.n + i] = sx[(lo + t / FT) * W + lo + t % FT];
-  }
-}
-
-template <class T, int FT>
-__global__ void __launch_bounds__(kFineMaxThreads) k_node_up(Lvl<T> L, int nc, int mc, const double* ph, int cpg,
-                                                          const cx<T>* __restrict__ B, long ldb,
-                                                          const cx<T>* __restrict__ Xs, long lds,
-                                                          const cx<T>* __restrict__ Xc, long ldc,
-                                                          cx<T>* __restrict__ X, long ldx, int nu) {
-  extern __shared__ float4 fine_sm[];
-  // step s works on the tile widened by 4 nu - 1 - s rings and reads one ring further;
-  // the coarse nodes the region's prolongation reads (origin (oa/2, ob/2), W/2 + 1
-  // per side, oa and ob even) are staged first
-  const int lo = 4 * nu, W = FT + 8 * nu, Wc = W / 2 + 1;
-  cx<T>* sx = reinterpret_cast<cx<T>*>(fine_sm);
-  cx<T>* sb = sx + W * W;
-  cx<T>* sc = sb + W * W;
-  const int c = blockIdx.z, tid = threadIdx.x, nt = blockDim.x;
-  const int i0 = blockIdx.x * FT, j0 = blockIdx.y * FT, oa = i0 - lo, ob = j0 - lo;
-  const Ph<T> p = load_ph<T>(ph, c / cpg);
-  const cx<T>* b = B + c * ldb;
-  const cx<T>* xs = Xs + c * lds;
-  const cx<T>* xc = Xc + c * ldc;
-  stage_region<T>(xc, oa >> 1, ob >> 1, Wc, nc, mc, p, sc);
-  stage_region<T>(b, oa, ob, W, L.n, L.m, p, sb);
-  stage_region<T>(xs, oa, ob, W, L.n, L.m, p, sx);
-  __syncthreads();
-  const NRdSm<T> rc{sc, Wc, oa >> 1, ob >> 1};
-  {
-    const float inv = 1.0f / (float)W;
-    for (int t = tid; t < W * W; t += nt) {
-      int u, v;
-      split_index(t, W, inv, u, v);
-      sx[t] = sx[t] + prolong_node_at<T>(rc, oa + u, ob + v);
-    }
-  }
-  __syncthreads();
-  const NRdSm<T> rs{sx, W, oa, ob};
-  for (int it = 0; it < nu; ++it)
-    for (int q = 3; q >= 0; --q) {
-      const int e = 4 * nu - 1 - (4 * it + 3 - q);
-      for_colour<T>(q, lo - e, lo + FT + e, oa, ob, [&](int a, int bb) {
-        const int k = bb * W + a;
-        const cx<T> res = sb[k] - P_at<T>(rs, L, oa + a, ob + bb);
-        sx[k] = sx[k] + (T(1) / P_diag<T>(L)) * res;
-      });
-      __syncthreads();
-    }
-  for (int t = tid; t < FT * FT; t += nt) {
-    const int i = i0 + t % FT, j = j0 + t / FT;
-    if (i < L.n && j < L.m) X[c * ldx + (long)j * L.n + i] = sx[(lo + t / FT) * W + lo + t % FT];
-  }
 }
 
 // ---- fused coarse-level V-cycles ---------------------------------------------
@@ -967,18 +804,32 @@ template <class T, int FT> void set_fine_smem() {
                                   (int)fine_smem_cap([](int nu) { return fine_up_smem<T>(FT, nu); })));
   });
 }
-// launch shapes of the tiled steps offered to the autotuner: (tile side, threads);
-// the first one fits every level the tiled path takes
+// shared memory of the register-blocked steps (FP32, one sweep per side)
+template <int FT, int NT> void set_fine_rb_smem() {
+  static PerDeviceOnce once;
+  once([] {
+    PBS_CUDA(cudaFuncSetAttribute(k_node_down_rb<FT, NT, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)RbDown<FT, NT, 1>::smem));
+    PBS_CUDA(cudaFuncSetAttribute(k_node_up_rb<FT, NT, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)RbUp<FT, NT, 1>::smem));
+  });
+}
+// launch shapes of the tiled steps offered to the autotuner: (tile side, threads,
+// register-blocked); the first one fits every level the tiled path takes, the
+// register-blocked ones run FP32 cycles with one sweep per side
 struct FineShape {
   int ft, nt;
+  bool rb;
 };
-constexpr FineShape kFineShapes[] = {{32, 256}, {64, 512}, {64, 256}};
-constexpr int kNumFineShapes = 3;
+constexpr FineShape kFineShapes[] = {{32, 256, false}, {64, 512, false}, {64, 256, false},
+                                     {32, 256, true},  {64, 512, true},  {32, 128, true}};
+constexpr int kNumFineShapes = 6;
 template <class T>
 int fine_shapes(const Level& L, int nu, bool down, FineShape* out) {
   int n = 0;
   for (const FineShape& f : kFineShapes) {
-    const size_t sm = down ? fine_down_smem<T>(f.ft, nu) : fine_up_smem<T>(f.ft, nu);
+    if (f.rb && (!std::is_same<T, float>::value || nu != 1)) continue;
+    const size_t sm = f.rb ? 0 : down ? fine_down_smem<T>(f.ft, nu) : fine_up_smem<T>(f.ft, nu);
     if (fine_fits(L, f.ft) && sm <= kSmemOptIn) out[n++] = f;
   }
   return n;
@@ -1014,6 +865,47 @@ void launch_node_up(const Level& L, const Level& C, const KData& K, MgWork<T>& w
   k_node_up<T, FT><<<grid, nt, fine_up_smem<T>(FT, nu), s>>>(L.lvl<T>(), C.n, C.m, K.d_ph, cpg, b, ld, w.r[l], L.N(),
                                                               w.x[l + 1], C.N(), x, ld, nu);
   PBS_LAUNCHED();
+}
+
+template <int FT, int NT>
+void launch_node_down_rb(const Level& L, const Level& C, const KData& K, MgWork<float>& w, int l, const float2* b,
+                         const float2* x0, long ld, int ncols, int cpg, cudaStream_t s) {
+  set_fine_rb_smem<FT, NT>();
+  const dim3 grid((L.n + FT - 1) / FT, (L.m + FT - 1) / FT, ncols);
+  k_node_down_rb<FT, NT, 1><<<grid, NT, RbDown<FT, NT, 1>::smem, s>>>(L.lvl<float>(), C.n, C.m, K.d_ph, cpg, b, ld,
+                                                                      x0, ld, w.r[l], L.N(), w.b[l + 1], C.N());
+  PBS_LAUNCHED();
+}
+
+template <int FT, int NT>
+void launch_node_up_rb(const Level& L, const Level& C, const KData& K, MgWork<float>& w, int l, const float2* b,
+                       float2* x, long ld, int ncols, int cpg, cudaStream_t s) {
+  set_fine_rb_smem<FT, NT>();
+  const dim3 grid((L.n + FT - 1) / FT, (L.m + FT - 1) / FT, ncols);
+  k_node_up_rb<FT, NT, 1><<<grid, NT, RbUp<FT, NT, 1>::smem, s>>>(L.lvl<float>(), C.n, C.m, K.d_ph, cpg, b, ld,
+                                                                  w.r[l], L.N(), w.x[l + 1], C.N(), x, ld);
+  PBS_LAUNCHED();
+}
+
+// the register-blocked steps exist in FP32 only (fine_shapes offers them nowhere else)
+template <class T>
+void launch_rb(bool down, const FineShape& f, const Level& L, const Level& C, const KData& K, MgWork<T>& w, int l,
+               const cx<T>* b, const cx<T>* x0, cx<T>* x, long ld, int ncols, int cpg, cudaStream_t s) {
+  if constexpr (std::is_same<T, float>::value) {
+    const bool s32 = f.ft == 32 && f.nt == 256, s64 = f.ft == 64 && f.nt == 512, t32 = f.ft == 32 && f.nt == 128;
+    if (!s32 && !s64 && !t32) fail(-1, "nodal step: no register-blocked kernel for this shape");
+    if (down) {
+      if (s64) launch_node_down_rb<64, 512>(L, C, K, w, l, b, x0, ld, ncols, cpg, s);
+      else if (s32) launch_node_down_rb<32, 256>(L, C, K, w, l, b, x0, ld, ncols, cpg, s);
+      else launch_node_down_rb<32, 128>(L, C, K, w, l, b, x0, ld, ncols, cpg, s);
+    } else {
+      if (s64) launch_node_up_rb<64, 512>(L, C, K, w, l, b, x, ld, ncols, cpg, s);
+      else if (s32) launch_node_up_rb<32, 256>(L, C, K, w, l, b, x, ld, ncols, cpg, s);
+      else launch_node_up_rb<32, 128>(L, C, K, w, l, b, x, ld, ncols, cpg, s);
+    }
+  } else {
+    fail(-1, "nodal step: register-blocked kernels run FP32 only");
+  }
 }
 
 template <class T>
@@ -1141,11 +1033,13 @@ void node_cycle(const Hierarchy& H, const KData& K, MgWork<T>& w, int l, const c
   if (fine_tiled(L, nu_pre, nu_post)) {
     const Level& C = H.lev[l + 1];
     const auto down = [&](const FineShape& f) {
-      if (f.ft == 64) launch_node_down<T, 64>(L, C, K, w, l, b, x0, ld, ncols, cpg, nu_pre, f.nt, s);
+      if (f.rb) launch_rb<T>(true, f, L, C, K, w, l, b, x0, nullptr, ld, ncols, cpg, s);
+      else if (f.ft == 64) launch_node_down<T, 64>(L, C, K, w, l, b, x0, ld, ncols, cpg, nu_pre, f.nt, s);
       else launch_node_down<T, 32>(L, C, K, w, l, b, x0, ld, ncols, cpg, nu_pre, f.nt, s);
     };
     const auto up = [&](const FineShape& f) {
-      if (f.ft == 64) launch_node_up<T, 64>(L, C, K, w, l, b, x, ld, ncols, cpg, nu_post, f.nt, s);
+      if (f.rb) launch_rb<T>(false, f, L, C, K, w, l, b, nullptr, x, ld, ncols, cpg, s);
+      else if (f.ft == 64) launch_node_up<T, 64>(L, C, K, w, l, b, x, ld, ncols, cpg, nu_post, f.nt, s);
       else launch_node_up<T, 32>(L, C, K, w, l, b, x, ld, ncols, cpg, nu_post, f.nt, s);
     };
     FineShape fd[kNumFineShapes], fu[kNumFineShapes];

@@ -166,6 +166,7 @@ int tune_pick(const std::string& key, int ncand, const std::function<void(int)>&
       PBS_CUDA(cudaEventSynchronize(e1));
       float ms = 0.0f;
       PBS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      if (verbose_enabled()) std::fprintf(stderr, "[pbs] tune %s candidate %d: %.3f ms per run\n", key.c_str(), cand, ms / 2);
       if (cand == 0 || ms < best_ms) {
         best = cand;
         best_ms = ms;

@@ -234,9 +234,11 @@ def test_projection_matches_reference(ctx, a, b, n, m, k, cycles):
 
 
 # The tiled nodal steps on meshes where every launch shape the autotuner may pick fits
-# (32 x 32 tiles of 256 threads, 64 x 64 tiles of 512 or 256 threads): 192 x 96 has a
-# partial last row of 64 x 64 tiles, 128 x 128 at Gamma whole ones and the constant
-# remainder.  Run as they are here (the tuned shape) and with each shape forced below.
+# (32 x 32 tiles of 256 threads, 64 x 64 tiles of 512 or 256 threads, and for FP32 cycles
+# the register-blocked steps on 32 x 32 tiles of 256 or 128 threads and 64 x 64 tiles of
+# 512): 192 x 96 has a partial last row of 64 x 64 tiles, 128 x 128 at Gamma whole ones
+# and the constant remainder.  Run as they are here (the tuned shape) and with each shape
+# forced below (FP64 cycles, which have the first three shapes only, tune the others).
 @pytest.mark.parametrize("a,b,n,m,k", [(1.0, 0.5, 192, 96, (0.4, -1.3)), (1.0, 1.0, 128, 128, (0.0, 0.0))])
 def test_nodal_cycle_and_projection_on_large_tiles(ctx, a, b, n, m, k):
     eps = _eps(n, m)
@@ -262,17 +264,18 @@ def test_nodal_cycle_and_projection_on_large_tiles(ctx, a, b, n, m, k):
     assert _rel(_apply(ctx, geom, "PROJECT", x, mesh.D, k, precision=pbs.PBS_MIXED, nodal_cycles=2), want) <= 1e-5
 
 
-@pytest.mark.parametrize("shape", [0, 1, 2])
+@pytest.mark.parametrize("shape", [0, 1, 2, 3, 4, 5])
 def test_nodal_tile_shapes_in_child_processes(shape):
     # each launch shape of the tiled nodal steps forced (PBS_TUNE_FORCE) in a child process:
-    # the cycle and projection cases above, and with the 64 x 64 tiles of 512 threads the
-    # 256 x 256 rod path (levels 256 and 128 tiled) against the oracle's stored eigenvalues
+    # the cycle and projection cases above, and with the 64 x 64 tiles of 512 threads (plain
+    # and register-blocked) the 256 x 256 rod path (levels 256 and 128 tiled) against the
+    # oracle's stored eigenvalues
     import os
     import subprocess
     import sys
     here = os.path.dirname(os.path.abspath(__file__))
     tests = [os.path.join(here, "test_gpu_ops.py") + "::test_nodal_cycle_and_projection_on_large_tiles"]
-    if shape == 1:
+    if shape in (1, 4):
         tests.append(os.path.join(here, "test_gpu_eigen.py") + "::test_rod256_path_full_size")
     env = dict(os.environ, PBS_TUNE_FORCE=f"node_down={shape},node_up={shape}")
     r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-p", "no:cacheprovider", *tests],
