@@ -15,11 +15,15 @@
 //
 // Checked, bit for bit: k_node_down_rb against k_node_down and k_node_up_rb
 // against k_node_up (one sweep per side, FP32) on several levels, Bloch vectors
-// and tile shapes.  Prints "ok" on success.
+// and tile shapes.  Checked against whole-level colour sweeps: k_node_down and
+// k_node_up with one to three sweeps per side in FP32 and FP64 (bit for bit on
+// tiles whose region lies inside the level, to rounding elsewhere).  Prints "ok"
+// on success.
 #include <cuda_runtime.h>
 #include <sched.h>
 #include <sanitizer/asan_interface.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
@@ -223,6 +227,139 @@ bool check_shape(const Case& cs) {
   return ok;
 }
 
+// ---- the plain tiled steps against whole-level sweeps, 1 to 3 sweeps per side ----
+// The whole-level steps below run the same per-node expressions (P_at, the update,
+// the residual, restrict_node_at, prolong_node_at) over the level in colour order,
+// reading across the boundary through the Bloch extension.  A tile whose region
+// lies inside the level reads no Bloch phase, so its outputs must agree bit for
+// bit; elsewhere the tile's halo carries phase products of staged values instead
+// of phase products of updated values, and the two agree to rounding.
+
+template <class T> using CVec = std::vector<cx<T>>;
+
+template <class T> CVec<T> random_cvec(size_t len, std::mt19937_64& g) {
+  std::normal_distribution<double> d(0.0, 1.0);
+  CVec<T> v(len);
+  for (auto& z : v) z = mk<T>(T(d(g)), T(d(g)));
+  return v;
+}
+
+template <class T> void level_sweep(const Lvl<T>& L, const Ph<T>& p, const cx<T>* b, cx<T>* x, int q) {
+  const NRdPlain<T> r{x, L.n, L.m, p};
+  for (int j = q >> 1; j < L.m; j += 2)
+    for (int i = q & 1; i < L.n; i += 2) {
+      const long e = (long)j * L.n + i;
+      const cx<T> res = b[e] - P_at<T>(r, L, i, j);
+      x[e] = x[e] + (T(1) / P_diag<T>(L)) * res;
+    }
+}
+
+template <class T>
+void level_down(const Lvl<T>& L, int nc, int mc, const Ph<T>& p, const cx<T>* b, const cx<T>* x0, int nu, cx<T>* x,
+                cx<T>* bc) {
+  const long N = (long)L.n * L.m;
+  for (long e = 0; e < N; ++e) x[e] = x0 ? x0[e] : czero<T>();
+  for (int it = 0; it < nu; ++it)
+    for (int q = 0; q < 4; ++q) level_sweep<T>(L, p, b, x, q);
+  CVec<T> r(N);
+  const NRdPlain<T> rx{x, L.n, L.m, p};
+  for (int j = 0; j < L.m; ++j)
+    for (int i = 0; i < L.n; ++i) {
+      const long e = (long)j * L.n + i;
+      cx<T> y = T(-1) * P_at<T>(rx, L, i, j);
+      y = y + T(1) * b[e];
+      r[e] = y;
+    }
+  const NRdPlain<T> rr{r.data(), L.n, L.m, p};
+  for (int J = 0; J < mc; ++J)
+    for (int I = 0; I < nc; ++I) bc[(long)J * nc + I] = restrict_node_at<T>(rr, I, J);
+}
+
+template <class T>
+void level_up(const Lvl<T>& L, int nc, int mc, const Ph<T>& p, const cx<T>* b, const cx<T>* xs, const cx<T>* xc,
+              int nu, cx<T>* x) {
+  const NRdPlain<T> rc{xc, nc, mc, p};
+  for (int j = 0; j < L.m; ++j)
+    for (int i = 0; i < L.n; ++i) {
+      const long e = (long)j * L.n + i;
+      x[e] = xs[e] + prolong_node_at<T>(rc, i, j);
+    }
+  for (int it = 0; it < nu; ++it)
+    for (int q = 3; q >= 0; --q) level_sweep<T>(L, p, b, x, q);
+}
+
+// got against want on one column: bit for bit where inner(i, j), else within tol of
+// the column's largest value
+template <class T, class F>
+bool agree(const cx<T>* got, const cx<T>* want, int n, int m, F&& inner, double tol, const char* what, int nu, int ft) {
+  double mx = 0;
+  long ninner = 0;
+  for (long e = 0; e < (long)n * m; ++e) mx = std::max(mx, (double)std::hypot(want[e].x, want[e].y));
+  for (int j = 0; j < m; ++j)
+    for (int i = 0; i < n; ++i) ninner += inner(i, j) ? 1 : 0;
+  if (ninner == 0 || ninner == (long)n * m) {
+    std::printf("CASE %s nu=%d ft=%d n=%d m=%d has %ld of %ld values on inner tiles (needs both kinds)\n", what,
+                nu, ft, n, m, ninner, (long)n * m);
+    return false;
+  }
+  for (int j = 0; j < m; ++j)
+    for (int i = 0; i < n; ++i) {
+      const long e = (long)j * n + i;
+      const double d = std::hypot((double)got[e].x - want[e].x, (double)got[e].y - want[e].y);
+      const bool bits = std::memcmp(&got[e], &want[e], sizeof(cx<T>)) == 0;
+      if (!std::isfinite(d) || (inner(i, j) ? !bits : d > tol * mx)) {
+        std::printf("MISMATCH %s (%s) nu=%d ft=%d n=%d m=%d at (%d, %d): diff %.3g of %.3g (inner %d)\n", what,
+                    sizeof(T) == 4 ? "f32" : "f64", nu, ft, n, m, i, j, d, mx, (int)inner(i, j));
+        return false;
+      }
+    }
+  return true;
+}
+
+template <class T, int FT>
+bool check_sweeps(int n, int m, double a, double b, double k1, double k2, bool with_x0, int nu) {
+  constexpr int NT = 64;  // the plain kernels stride their loops by the block size
+  const int nc = n / 2, mc = m / 2;
+  const long N = (long)n * m, Nc = (long)nc * mc;
+  const int Wd = FT + 8 * nu + 3, Wu = FT + 8 * nu, Wc = Wu / 2 + 1;
+  const size_t smem_d = 2 * (size_t)Wd * Wd * sizeof(cx<T>);
+  const size_t smem_u = (2 * (size_t)Wu * Wu + (size_t)Wc * Wc) * sizeof(cx<T>);
+  if (n < FT + 27 || m < FT + 27 || smem_d > kEmuSmem || smem_u > kEmuSmem) return true;  // not offered
+  const double h1 = a / n, h2 = b / m;
+  const Lvl<T> L{n, m, T(h2 / h1), T(h1 / h2)};
+  const double ph[4] = {std::cos(k1 * a), std::sin(k1 * a), std::cos(k2 * b), std::sin(k2 * b)};
+  const Ph<T> p = load_ph<T>(ph, 0);
+  std::mt19937_64 g(99u + 3u * n + 5u * m + FT + 17u * nu);
+  const CVec<T> B = random_cvec<T>(N, g), X0 = random_cvec<T>(N, g), Xc = random_cvec<T>(Nc, g);
+  const cx<T>* x0 = with_x0 ? X0.data() : nullptr;
+  const int gx = (n + FT - 1) / FT, gy = (m + FT - 1) / FT;
+  CVec<T> xs(N), bc(Nc), x(N), xs_w(N), bc_w(Nc), x_w(N);
+  launch(gx, gy, 1, NT, smem_d, false, [&] {
+    k_node_down<T, FT>(L, nc, mc, ph, 1, B.data(), N, x0, N, xs.data(), N, bc.data(), Nc, nu);
+  });
+  launch(gx, gy, 1, NT, smem_u, false, [&] {
+    k_node_up<T, FT>(L, nc, mc, ph, 1, B.data(), N, X0.data(), N, Xc.data(), Nc, x.data(), N, nu);
+  });
+  level_down<T>(L, nc, mc, p, B.data(), x0, nu, xs_w.data(), bc_w.data());
+  level_up<T>(L, nc, mc, p, B.data(), X0.data(), Xc.data(), nu, x_w.data());
+  // a tile is inner when its region (down: margin 4 nu + 2 below, width Wd; up: margin
+  // 4 nu, width Wu, and its coarse region) lies inside the level
+  const auto down_in = [&](int i, int j) {
+    const int oa = (i / FT) * FT - (4 * nu + 2), ob = (j / FT) * FT - (4 * nu + 2);
+    return oa >= 0 && ob >= 0 && oa + Wd <= n && ob + Wd <= m;
+  };
+  const auto coarse_in = [&](int I, int J) { return down_in(2 * I, 2 * J); };
+  const auto up_in = [&](int i, int j) {
+    const int oa = (i / FT) * FT - 4 * nu, ob = (j / FT) * FT - 4 * nu;
+    return oa >= 0 && ob >= 0 && oa + Wu <= n && ob + Wu <= m && oa / 2 + Wc <= nc && ob / 2 + Wc <= mc;
+  };
+  const double tol = sizeof(T) == 4 ? 2e-5 : 1e-13;
+  bool ok = agree<T>(xs.data(), xs_w.data(), n, m, down_in, tol, "down x", nu, FT);
+  ok = agree<T>(bc.data(), bc_w.data(), nc, mc, coarse_in, tol, "down coarse rhs", nu, FT) && ok;
+  ok = agree<T>(x.data(), x_w.data(), n, m, up_in, tol, "up x", nu, FT) && ok;
+  return ok;
+}
+
 int main() {
   // one core: the threads of a CTA run one at a time anyway, and a hand-over
   // between threads on one core is a plain context switch
@@ -251,6 +388,14 @@ int main() {
     ok = check_shape<32, 256>(cs) && ok;
     ok = check_shape<32, 128>(cs) && ok;
     ok = check_shape<64, 512>(cs) && ok;
+  }
+  for (int nu = 1; nu <= 3; ++nu) {
+    // levels with tiles on both sides of the boundary: 32 x 32 tiles on 128 x 96, 64 x 64
+    // tiles on 192 x 160 (a partial last row), Gamma and generic Bloch vectors
+    ok = check_sweeps<float, 32>(128, 96, 1.0, 0.5, 0.4, -1.3, true, nu) && ok;
+    ok = check_sweeps<double, 32>(128, 96, 1.0, 0.5, 0.4, -1.3, false, nu) && ok;
+    ok = check_sweeps<float, 64>(192, 160, 1.0, 1.0, 0.0, 0.0, false, nu) && ok;
+    ok = check_sweeps<double, 64>(192, 160, 1.0, 1.0, 2.2, -0.9, true, nu) && ok;
   }
   std::printf(ok ? "ok\n" : "FAILED\n");
   return ok ? 0 : 1;

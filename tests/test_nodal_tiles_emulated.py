@@ -9,7 +9,12 @@ poisoned and the rest filled with NaN.  It checks that the register-blocked FP32
 results of ``k_node_down`` / ``k_node_up`` bit for bit, in ascending and descending
 thread order (a read of a word another thread writes in the same barrier interval would
 make the two orders differ), on ragged levels, at Gamma, at the zone corner and with two
-Bloch vectors per launch.  The GPU tests compare both against the oracle.
+Bloch vectors per launch.  It also runs the plain tiled steps with one, two and three
+sweeps per side, in FP32 and FP64, against the same steps written over the whole level in
+colour order: tiles whose halo lies inside the level agree bit for bit, the others to
+rounding (their halos carry phase products of staged values).  The GPU tests compare the
+kernels with one sweep per side against the oracle; two and three sweeps are checked here
+only.
 """
 import os
 import shutil
