@@ -220,11 +220,15 @@ template <int FT, int NT, int NU> struct RbDown {
   static constexpr int W = FT + 8 * NU + 4;  // its region plus one unread ring (even)
   static constexpr int H = W / 2, P = H * H, KB = (P + NT - 1) / NT;
   static constexpr size_t smem = 2 * (size_t)W * W * sizeof(float2);  // x and the residual
+  // even tile sides, margin and width: region coordinates keep the parity (colour) of
+  // the level's, and the region splits into whole 2 x 2 blocks
+  static_assert(FT % 2 == 0 && lo % 2 == 0 && W % 2 == 0, "register-blocked down step: odd tile geometry");
 };
 template <int FT, int NT, int NU> struct RbUp {
   static constexpr int lo = 4 * NU, W = FT + 8 * NU;
   static constexpr int H = W / 2, P = H * H, KB = (P + NT - 1) / NT;
   static constexpr size_t smem = (size_t)W * W * sizeof(float2);  // x
+  static_assert(FT % 2 == 0 && lo % 2 == 0 && W % 2 == 0, "register-blocked up step: odd tile geometry");
 };
 
 template <int FT, int NT, int NU>
